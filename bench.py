@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the sorted-table search on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0).  A step is one pass of the hot path over one
+batch of synthetic input that is already resident in HBM; `value` is the
+whole-job throughput in Gtargets/s (a 2D (rho, T) pair counts as one
+target).  Inputs are larger than L2, so no flush is needed between steps.
+`e2e` is the same metric with the inputs copied in from pinned host memory
+and the outputs copied back inside the timed region.  `--impl reference`
+times the plain CPU oracle on host cores on a bounded sample of the same
+workload (the oracle is test infrastructure; this arm is its only use here
+besides `cpu_baseline`).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gtargets/s and HBM fraction of peak, learned vs plain search, same GB300"
+UNIT = "Gtargets/s"
+
+
+# ---------------------------------------------------------------------------
+# Peaks
+# ---------------------------------------------------------------------------
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            v = float(json.load(f)["hbm_gbs"])
+            return v, "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_sources_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2112_03229_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            rec = json.load(f)[f"{kernel}@{workload}"]
+        if rec.get("sources") != kernel_sources_hash():
+            return None
+        return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Workloads
+# ---------------------------------------------------------------------------
+class Workload:
+    name = ""
+    kernel = ""               # dominant kernel (ncu name)
+    bytes_per_target = 0      # algorithmic HBM bytes per target
+
+    def setup(self, dev, seed):
+        raise NotImplementedError
+
+    def step(self):
+        raise NotImplementedError
+
+    def targets(self):
+        raise NotImplementedError
+
+
+class Interp2D(Workload):
+    """Fused 2D search + bilinear: 200 x 100 axes, 64M (rho, T) pairs (one table)."""
+    name = "interp2d-200x100-64M"
+    kernel = "k_search_interp_2d"
+    bytes_per_target = 16 + 8 + 8      # pair in, index pair out, value out
+
+    def __init__(self, m=64 << 20):
+        self.m = m
+
+    def setup(self, dev, seed):
+        from paper_2112_03229_gb300 import workloads as wl
+        import paper_2112_03229_gb300 as ss
+        self.ss = ss
+        self.R, self.T, self.F, self.Y2 = wl.interp_2d(m=self.m, seed=2 + 1000 * seed, device=dev)
+        self.idx = torch.empty((self.m, 2), dtype=torch.int32, device=dev)
+        self.val = torch.empty((self.m,), dtype=torch.float64, device=dev)
+
+    def step(self):
+        self.ss.search_interp_2d(self.R, self.T, self.F, self.Y2, idx=self.idx, val=self.val)
+        return 1
+
+    def targets(self):
+        return self.m
+
+    def e2e_setup(self):
+        self.hY = torch.empty(self.Y2.shape, dtype=torch.float64, pin_memory=True)
+        self.hY.copy_(self.Y2)
+        self.hI = torch.empty(self.idx.shape, dtype=torch.int32, pin_memory=True)
+        self.hV = torch.empty(self.val.shape, dtype=torch.float64, pin_memory=True)
+        return self.hY.numel() * 8, self.hI.numel() * 4 + self.hV.numel() * 8
+
+    def e2e_step(self):
+        self.Y2.copy_(self.hY, non_blocking=True)
+        self.step()
+        self.hI.copy_(self.idx, non_blocking=True)
+        self.hV.copy_(self.val, non_blocking=True)
+
+    def cpu_sample(self, budget_s):
+        import oracle
+        R, T, F = self.R.cpu().numpy(), self.T.cpu().numpy(), self.F.cpu().numpy()
+        probe = self.Y2[: 1 << 18].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.search_interp_2d(R, T, F, probe)
+        rate = probe.shape[0] / (time.perf_counter() - t0)
+        ns = int(min(self.m, max(1 << 18, rate * budget_s)))
+        Y = self.Y2[:ns].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.search_interp_2d(R, T, F, Y)
+        dt = time.perf_counter() - t0
+        return ns / dt, "first %d of the %d pairs (same tables), single thread" % (ns, self.m)
+
+
+class Plain1D(Workload):
+    """One 64-entry table, 1B float64 targets (bucket search)."""
+    name = "plain1d-n64-1B"
+    kernel = "k_search_1d_bucket"
+    bytes_per_target = 8 + 4
+
+    def __init__(self, m=1 << 30, algo="auto"):
+        self.m, self.algo = m, algo
+
+    def setup(self, dev, seed):
+        from paper_2112_03229_gb300 import workloads as wl
+        import paper_2112_03229_gb300 as ss
+        self.ss = ss
+        self.X, self.Y = wl.plain_1d(m=self.m, seed=1 + 1000 * seed, device=dev)
+        self.out = torch.empty((self.m,), dtype=torch.int32, device=dev)
+
+    def step(self):
+        self.ss.search_1d(self.X, self.Y, out=self.out, algo=self.algo)
+        return 1
+
+    def targets(self):
+        return self.m
+
+    def e2e_setup(self):
+        self.hY = torch.empty(self.Y.shape, dtype=torch.float64, pin_memory=True)
+        self.hY.copy_(self.Y)
+        self.hO = torch.empty(self.out.shape, dtype=torch.int32, pin_memory=True)
+        return self.hY.numel() * 8, self.hO.numel() * 4
+
+    def e2e_step(self):
+        self.Y.copy_(self.hY, non_blocking=True)
+        self.step()
+        self.hO.copy_(self.out, non_blocking=True)
+
+    def cpu_sample(self, budget_s):
+        import oracle
+        X = self.X.cpu().numpy()
+        probe = self.Y[: 1 << 20].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.search_1d(X, probe)
+        rate = probe.shape[0] / (time.perf_counter() - t0)
+        ns = int(min(self.m, max(1 << 20, rate * budget_s)))
+        Y = self.Y[:ns].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.search_1d(X, Y)
+        dt = time.perf_counter() - t0
+        return ns / dt, "first %d of the %d targets (same table), single thread" % (ns, self.m)
+
+
+WORKLOADS = {
+    "interp2d": Interp2D,
+    "plain1d": Plain1D,
+}
+DEFAULT_WORKLOAD = "interp2d"
+
+
+# ---------------------------------------------------------------------------
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def run_reference(args, wl_obj):
+    """Oracle arm: the plain CPU oracle on host cores, a bounded sample per step."""
+    rank, world, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    dev = "cpu"
+    # build the workload's inputs on the CPU at a bounded size
+    wl_obj.m = min(wl_obj.m, 1 << 23)
+    wl_obj.setup(dev, 0)
+    times = []
+    for s in range(args.warmup + args.steps):
+        rate, sample = wl_obj.cpu_sample(budget_s=2.0)
+        times.append(rate)
+    rates = times[args.warmup:]
+    value = statistics.median(rates) / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl_obj.name},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    wl_obj = WORKLOADS[args.workload]()
+    if args.impl == "reference":
+        return run_reference(args, wl_obj)
+
+    rank, world, local = dist_setup(args.gpus)
+    import __graft_entry__
+    __graft_entry__.build()
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    wl_obj.setup(dev, rank)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        wl_obj.step()
+    torch.cuda.synchronize()
+
+    # timed region: per-launch events on the launching stream, K steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches = 0
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        t_all0 = torch.cuda.Event(enable_timing=True)
+        t_all1 = torch.cuda.Event(enable_timing=True)
+        t_all0.record(stream)
+        for i in range(args.steps):
+            starts[i].record(stream)
+            launches += wl_obj.step()
+            ends[i].record(stream)
+        t_all1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    elapsed_ms = t_all0.elapsed_time(t_all1)
+    elapsed_ms = max_over_ranks(elapsed_ms, world)
+    per_launch_ms = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
+    units = wl_obj.targets() * args.steps * world
+    value = units / (elapsed_ms / 1e3) / 1e9
+
+    # end to end through the public API with host buffers
+    h2d, d2h = wl_obj.e2e_setup()
+    for _ in range(2):
+        wl_obj.e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        wl_obj.e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    e2e_value = wl_obj.targets() * args.steps * world / (e2e_ms / 1e3) / 1e9
+
+    peak, peak_kind = hbm_peak()
+    achieved = wl_obj.targets() * wl_obj.bytes_per_target / (per_launch_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                "traffic": recorded_traffic(wl_obj.kernel, wl_obj.name), "kernel": wl_obj.kernel,
+                "algorithmic_bytes_per_target": wl_obj.bytes_per_target}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, sample = wl_obj.cpu_sample(args.cpu_budget)
+        cpu = {"value": rate / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl_obj.name, "targets_per_gpu": wl_obj.targets(),
+                           "l2": "inputs larger than L2 (no flush needed)", "parallelism": "dp%d" % world},
+                "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

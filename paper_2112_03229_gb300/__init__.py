@@ -1,0 +1,135 @@
+"""GB300 (sm_103a) sorted-table search: Python binding of libsimdsearch.so.
+
+Argument marshalling only: every step of the search and of the 2D lookup
+runs in the CUDA kernels of the shared library; PyTorch supplies device
+memory and the current stream.  There is no CPU fallback -- if the library
+has not been built, every call raises.
+
+The operation (arXiv 2112.03229, Sec. 3): for each target, the index of the
+largest table entry below it, with both end clamps; the 2D form (Sec. 1,
+2.2) searches a density and a temperature axis and interpolates bilinearly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import _build
+
+LIB_PATH = _build.LIB
+
+SIDE_LT, SIDE_LE = 0, 1
+ALGO_AUTO, ALGO_BINARY, ALGO_BUCKET, ALGO_BALLOT, ALGO_BRANCHY = 0, 1, 2, 3, 4
+ALGOS = {"auto": ALGO_AUTO, "binary": ALGO_BINARY, "bucket": ALGO_BUCKET, "ballot": ALGO_BALLOT,
+         "branchy": ALGO_BRANCHY}
+FLAG_NOT_SORTED = 0x1
+
+STATUS = {0: "SS_OK", 1: "SS_EINVAL", 2: "SS_ENOTSORTED", 3: "SS_ENOMEM", 4: "SS_ECUDA", 5: "SS_ETIMEOUT",
+          6: "SS_EUNSUPPORTED"}
+
+
+class SSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+class DevStat(C.Structure):
+    _fields_ = [("nan_targets", C.c_ulonglong), ("fallbacks", C.c_ulonglong), ("flags", C.c_uint),
+                ("max_window", C.c_uint)]
+
+
+_lib = None
+_vp, _i32, _i64 = C.c_void_p, C.c_int32, C.c_int64
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsimdsearch.so is not built (run __graft_entry__.build()); "
+                               "this package has no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        L.ss_last_error.restype = C.c_char_p
+        L.ss_version.restype = _i32
+        L.ss_search_1d.argtypes = [_vp, _i32, _vp, _i64, _vp, _i32, _i32, _vp, _vp]
+        L.ss_search_1d_tuned.argtypes = [_vp, _i32, _vp, _i64, _vp, _i32, _i32, _i32, _i32, _vp, _vp]
+        L.ss_search_interp_2d.argtypes = [_vp, _i32, _vp, _i32, _vp, _vp, _i64, _vp, _vp, _i32, _vp, _vp]
+        L.ss_sync_status.argtypes = [_vp, _vp, _vp, _i32]
+        for name in ("ss_search_1d", "ss_search_1d_tuned", "ss_search_interp_2d", "ss_sync_status"):
+            getattr(L, name).restype = _i32
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code != 0:
+        raise SSError(code, lib().ss_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s" % (name, dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return C.c_void_p(t.data_ptr())
+
+
+def _algo(a):
+    return ALGOS[a] if isinstance(a, str) else int(a)
+
+
+def new_stat(device=None) -> torch.Tensor:
+    """A zeroed device status record (24 bytes) to pass as `stat`."""
+    return torch.zeros(C.sizeof(DevStat), dtype=torch.uint8, device=device or "cuda")
+
+
+def read_stat(stat: torch.Tensor, stream=None, timeout_ms: int = 60_000) -> DevStat:
+    out = DevStat()
+    _check(lib().ss_sync_status(_stream(stream), C.c_void_p(stat.data_ptr()), C.byref(out), timeout_ms))
+    return out
+
+
+def _statp(stat):
+    return C.c_void_p(stat.data_ptr()) if stat is not None else None
+
+
+def search_1d(X: torch.Tensor, Y: torch.Tensor, out: torch.Tensor | None = None, side: int = SIDE_LT,
+              algo="auto", stat=None, stream=None, dir_cap: int = 0, ballot_g: int = 0) -> torch.Tensor:
+    """ss_search_1d: int32 index of the largest entry of X below each target of Y."""
+    if out is None:
+        out = torch.empty(Y.shape, dtype=torch.int32, device=Y.device)
+    args = (_dev(X, torch.float64, "X"), X.numel(), _dev(Y, torch.float64, "Y"), Y.numel(),
+            _dev(out, torch.int32, "out"), side, _algo(algo))
+    if dir_cap or ballot_g:
+        _check(lib().ss_search_1d_tuned(*args, dir_cap, ballot_g, _statp(stat), _stream(stream)))
+    else:
+        _check(lib().ss_search_1d(*args, _statp(stat), _stream(stream)))
+    return out
+
+
+def search_interp_2d(R, T, F, Y2, idx=None, val=None, algo="auto", stat=None, stream=None):
+    """ss_search_interp_2d: per (rho, T) pair the index pair and the bilinear value."""
+    m = Y2.numel() // 2
+    if F.numel() != R.numel() * T.numel():
+        raise ValueError("F must hold len(R) * len(T) values")
+    if idx is None:
+        idx = torch.empty((m, 2), dtype=torch.int32, device=Y2.device)
+    if val is None:
+        val = torch.empty((m,), dtype=torch.float64, device=Y2.device)
+    _check(lib().ss_search_interp_2d(_dev(R, torch.float64, "R"), R.numel(), _dev(T, torch.float64, "T"), T.numel(),
+                                     _dev(F, torch.float64, "F"), _dev(Y2, torch.float64, "Y2"), m,
+                                     _dev(idx, torch.int32, "idx"), _dev(val, torch.float64, "val"), _algo(algo),
+                                     _statp(stat), _stream(stream)))
+    return idx, val

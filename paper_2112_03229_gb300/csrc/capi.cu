@@ -1,0 +1,61 @@
+// capi.cu -- host-side plumbing of the C ABI: per-thread error messages,
+// device properties, the polling status read-back.
+#include <chrono>
+#include <string>
+#include <thread>
+
+#include "ss_common.cuh"
+
+namespace ss {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+ss_status fail(ss_status code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+ss_status cuda_fail(cudaError_t err, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorName(err) + " (" + cudaGetErrorString(err) + ")";
+  return SS_ECUDA;
+}
+
+int num_sms() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  return v > 0 ? v : 1;
+}
+
+int max_smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v > 0 ? v : 48 * 1024;
+}
+
+}  // namespace ss
+
+extern "C" {
+
+const char* ss_last_error(void) { return ss::g_last_error.c_str(); }
+
+int32_t ss_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+ss_status ss_sync_status(cudaStream_t stream, const ss_devstat* stat, ss_devstat* out, int32_t timeout_ms) {
+  if (stat == nullptr || out == nullptr || timeout_ms < 0) return ss::fail(SS_EINVAL, "ss_sync_status: null pointer or negative timeout");
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+  for (;;) {
+    cudaError_t q = cudaStreamQuery(stream);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) return ss::cuda_fail(q, "cudaStreamQuery");
+    if (std::chrono::steady_clock::now() >= deadline) return ss::fail(SS_ETIMEOUT, "ss_sync_status: stream still busy at the deadline");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  SS_CHECK_CUDA(cudaMemcpy(out, stat, sizeof(ss_devstat), cudaMemcpyDeviceToHost));
+  return SS_OK;
+}
+
+}  // extern "C"

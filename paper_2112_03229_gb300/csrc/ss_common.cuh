@@ -1,0 +1,70 @@
+// ss_common.cuh -- device helpers shared by every kernel of the library:
+// the order-preserving integer image of a float64, 128-bit streaming
+// loads/stores, status reporting and host-side error plumbing.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/simdsearch.h"
+
+namespace ss {
+
+constexpr uint64_t kKeyMax = ~0ull;                    // sentinel above every real key
+constexpr uint64_t kKeyPosInf = 0xFFF0000000000000ull;  // image of +inf
+constexpr int kNumThreads = 256;                       // threads per block of the streaming kernels
+
+// ---------------------------------------------------------------------------
+// Order-preserving image of a double (Sec. 3.5 reads the exponent bits of the
+// IEEE-754 pattern; this extends that to a total order over all non-NaN
+// doubles).  Non-negative values: set the sign bit.  Negative values: two's
+// complement of the pattern, which also sends -0 onto +0.  For non-NaN a, b:
+// a < b  <=>  key(a) < key(b), and key(-0) == key(+0).
+// A NaN target is mapped to 0, below every table key, so that its count of
+// smaller entries is 0 (index 0).  Negative NaNs already land below key(-inf);
+// positive NaNs land above key(+inf) and are moved down explicitly.
+// All integer work: no fp64 instruction is issued.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t order_key(double x) {
+  const uint64_t u = static_cast<uint64_t>(__double_as_longlong(x));
+  const uint64_t neg = static_cast<uint64_t>(static_cast<int64_t>(u) >> 63);  // all ones if negative
+  uint64_t k = (u ^ (neg | 0x8000000000000000ull)) - neg;                      // ~u + 1 or u | 2^63
+  return k > kKeyPosInf ? 0ull : k;
+}
+
+__device__ __forceinline__ bool is_nan_key_input(double x) {
+  const uint64_t u = static_cast<uint64_t>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
+  return u > 0x7FF0000000000000ull;
+}
+
+// Streaming (evict-first) 128-bit global accesses for data touched once.
+__device__ __forceinline__ double2 ld_stream(const double2* p) { return __ldcs(p); }
+__device__ __forceinline__ void st_stream(int4* p, int4 v) { __stcs(p, v); }
+__device__ __forceinline__ void st_stream(double2* p, double2 v) { __stcs(p, v); }
+
+// Warp-aggregated increment of a device counter (one atomic per warp).
+__device__ __forceinline__ void warp_count(unsigned long long* ctr, bool pred) {
+  const unsigned mask = __ballot_sync(0xFFFFFFFFu, pred);
+  if (ctr != nullptr && mask != 0u && (threadIdx.x & 31) == 0) atomicAdd(ctr, (unsigned long long)__popc(mask));
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+ss_status fail(ss_status code, const std::string& msg);
+ss_status cuda_fail(cudaError_t err, const char* what);
+int num_sms();
+int max_smem_optin();
+
+#define SS_CHECK_CUDA(call)                                   \
+  do {                                                        \
+    cudaError_t err_ = (call);                                \
+    if (err_ != cudaSuccess) return ::ss::cuda_fail(err_, #call); \
+  } while (0)
+
+inline bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+}  // namespace ss

@@ -1,0 +1,204 @@
+"""GPU parity of the one-shot 1D search and 2D lookup against the CPU oracle.
+
+Indices must match bit for bit; interpolated values within 1e-12 relative.
+All calls go through the C ABI (ctypes binding).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2112_03229_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-12     # interpolated values, relative to the fp64 oracle
+
+
+@pytest.fixture(scope="module")
+def ss():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2112_03229_gb300 as m
+    return m
+
+
+DEV = "cuda"
+VARIANTS = [("bucket", 0), ("binary", 0), ("branchy", 0), ("ballot", 8), ("ballot", 16), ("ballot", 32)]
+
+
+def special_targets(X):
+    X = np.asarray(X, dtype=np.float64)
+    t = [X, np.nextafter(X, -np.inf), np.nextafter(X, np.inf), (X[1:] + X[:-1]) / 2]
+    t.append(np.array([0.0, -0.0, np.inf, -np.inf, np.nan, -np.nan, 5e-324, -5e-324, 2.2250738585072014e-308,
+                       X[0] / 2, X[-1] * 2, -X[-1], 1e300, -1e300, 1.0, -1.0]))
+    return np.concatenate(t)
+
+
+def run1d(ss, X, Y, side=0, algo="bucket", g=0, **kw):
+    Xd = torch.as_tensor(X, dtype=torch.float64).to(DEV)
+    Yd = torch.as_tensor(Y, dtype=torch.float64).to(DEV)
+    return ss.search_1d(Xd, Yd, side=side, algo=algo, ballot_g=g, **kw).cpu().numpy()
+
+
+@pytest.mark.parametrize("algo,g", VARIANTS)
+@pytest.mark.parametrize("side", [0, 1])
+def test_1d_sizes_and_specials(ss, algo, g, side):
+    rng = np.random.default_rng(3)
+    for n in (2, 3, 4, 31, 32, 33, 63, 64, 65, 110, 257, 1000):
+        X = wl.log_spaced_table(n, 1e-6, 1e4, 0.1, seed=n).numpy()
+        Y = np.concatenate([special_targets(X), 10 ** rng.uniform(-7, 5, 5000)])
+        np.testing.assert_array_equal(run1d(ss, X, Y, side, algo, g), oracle.search_1d(X, Y, side),
+                                      err_msg=f"{algo}/{g} n={n} side={side}")
+    # tables with negatives, zero and subnormals
+    for X in (np.array([-1e300, -1.0, -5e-324, 0.0, 5e-324, 1.0, 1e300]), np.array([-np.inf, 0.0, np.inf]),
+              np.sort(rng.standard_normal(500) * 10.0 ** rng.integers(-200, 200, 500))):
+        X = np.unique(X)
+        Y = special_targets(X[np.isfinite(X)])
+        np.testing.assert_array_equal(run1d(ss, X, Y, side, algo, g), oracle.search_1d(X, Y, side))
+
+
+@pytest.mark.parametrize("algo,g", VARIANTS)
+def test_1d_config0_full(ss, algo, g):
+    # one table of 64 entries, 1M targets with 1% exact key hits (ragged m)
+    X, Y = wl.plain_1d(m=(1 << 20) + 3, seed=1)
+    np.testing.assert_array_equal(run1d(ss, X.numpy(), Y.numpy(), 0, algo, g), oracle.search_1d(X.numpy(), Y.numpy()))
+
+
+@pytest.mark.parametrize("algo,g", [("bucket", 0), ("binary", 0), ("ballot", 32)])
+def test_1d_ragged_and_misaligned(ss, algo, g):
+    X, Y = wl.plain_1d(m=4099, seed=5)
+    Xd, Yd = X.to(DEV), Y.to(DEV)
+    want = oracle.search_1d(X.numpy(), Y.numpy())
+    for m in (0, 1, 2, 3, 4, 5, 7, 8, 9, 4098):
+        for yoff in (0, 1):
+            for ooff in (0, 1, 2, 3):
+                out = torch.full((m + 8,), -7, dtype=torch.int32, device=DEV)
+                ys = Yd[yoff:yoff + m]
+                ss.search_1d(Xd, ys, out=out[ooff:ooff + m], algo=algo, ballot_g=g)
+                o = out.cpu().numpy()
+                np.testing.assert_array_equal(o[ooff:ooff + m], want[yoff:yoff + m])
+                assert np.all(o[:ooff] == -7) and np.all(o[ooff + m:] == -7)   # nothing written outside
+
+
+@pytest.mark.parametrize("algo", ["binary", "bucket", "branchy"])
+def test_1d_two_level_large_tables(ss, algo):
+    # n-1 above the staged limit: sampled top level in shared memory, leaves in global memory
+    for n in (8129, 8193, 20000, 65536):
+        X = wl.sweep_table(n).numpy() if n == 65536 else wl.log_spaced_table(n, 1e-6, 1e4, 0.1, seed=n).numpy()
+        Y = np.concatenate([special_targets(X[:2000]), special_targets(X[-2000:]),
+                            10 ** np.random.default_rng(n).uniform(-7, 5, 200_000)])
+        np.testing.assert_array_equal(run1d(ss, X, Y, 0, algo), oracle.search_1d(X, Y), err_msg=f"n={n}")
+
+
+def test_1d_status_nan_and_unsorted(ss):
+    X = wl.log_spaced_table(64, 1e-6, 1e4, 0.1, seed=1)
+    Y = wl.log_uniform(10_000, 1e-7, 1e5, seed=2)
+    Y[::100] = float("nan")
+    Y[1::100] = -float("nan")
+    stat = ss.new_stat()
+    out = ss.search_1d(X.to(DEV), Y.to(DEV), stat=stat)
+    st = ss.read_stat(stat)
+    assert st.nan_targets == 200 and st.flags == 0
+    np.testing.assert_array_equal(out.cpu().numpy(), oracle.search_1d(X.numpy(), Y.numpy()))
+    Xbad = X.clone()
+    Xbad[10] = Xbad[9]
+    stat = ss.new_stat()
+    out = ss.search_1d(Xbad.to(DEV), Y.to(DEV), stat=stat)
+    st = ss.read_stat(stat)
+    assert st.flags & ss.FLAG_NOT_SORTED
+    o = out.cpu().numpy()
+    assert o.min() >= 0 and o.max() <= 63     # unspecified but in range
+
+
+def test_1d_argument_errors(ss):
+    X = torch.linspace(1, 2, 8, dtype=torch.float64, device=DEV)
+    Y = torch.ones(4, dtype=torch.float64, device=DEV)
+    with pytest.raises(ss.SSError):
+        ss.search_1d(X[:1], Y)
+    with pytest.raises(ss.SSError):
+        ss.search_1d(X, Y, algo=9)
+
+
+# ---------------------------------------------------------------- 2D lookup
+
+def check_2d(idx, val, wi, wv):
+    np.testing.assert_array_equal(idx, wi)
+    nan = np.isnan(wv)
+    assert np.array_equal(np.isnan(val), nan)
+    rel = np.abs(val[~nan] - wv[~nan]) / np.abs(wv[~nan])
+    assert rel.max(initial=0.0) <= REL_TOL, rel.max()
+
+
+@pytest.mark.parametrize("algo", ["bucket", "binary"])
+def test_2d_config1_small(ss, algo):
+    R, T, F, Y2 = wl.interp_2d(m=(1 << 20) + 1, seed=2)
+    # add out-of-range, exact-node and NaN pairs
+    extra = np.array([[R[0].item(), T[0].item()], [R[-1].item(), T[-1].item()], [1e-9, 1e9], [1e9, 1e-9],
+                      [np.nan, 1.0], [1.0, np.nan], [-0.0, 0.0], [np.inf, -np.inf], [R[5].item(), T[7].item()]])
+    Y2 = torch.cat([Y2, torch.as_tensor(extra)])
+    idx, val = ss.search_interp_2d(R.to(DEV), T.to(DEV), F.to(DEV), Y2.to(DEV), algo=algo)
+    wi, wv = oracle.search_interp_2d(R.numpy(), T.numpy(), F.numpy(), Y2.numpy())
+    check_2d(idx.cpu().numpy(), val.cpu().numpy(), wi, wv)
+
+
+def test_2d_ragged_misaligned_and_sizes(ss):
+    for nr, nt in ((2, 2), (2, 3), (3, 2), (33, 65), (500, 300), (4096, 17)):
+        R = wl.log_spaced_table(nr, 1e-6, 1e4, 0.1, seed=nr)
+        T = wl.log_spaced_table(nt, 1e-4, 1e4, 0.1, seed=nt + 1)
+        F = wl.field_grid(R, T, wl.smooth_field(1e-6, 1e4, 1e-4, 1e4, seed=3))
+        Y2 = wl.pairs_log_uniform(2003, 0.5e-6, 2e4, 0.5e-4, 2e4, seed=4)
+        wi, wv = oracle.search_interp_2d(R.numpy(), T.numpy(), F.numpy(), Y2.numpy())
+        Rd, Td, Fd, Yd = R.to(DEV), T.to(DEV), F.to(DEV), Y2.reshape(-1).to(DEV)
+        for m in (0, 1, 2, 3, 2002):
+            for off in (0, 1):          # off=1 shifts pairs by one double: 8-byte aligned only
+                ybuf = torch.empty(2 * m + 2, dtype=torch.float64, device=DEV)
+                ybuf[off:off + 2 * m] = Yd[:2 * m]
+                ib = torch.full((2 * m + 4,), -7, dtype=torch.int32, device=DEV)
+                vb = torch.full((m + 2,), -7.0, dtype=torch.float64, device=DEV)
+                ss.search_interp_2d(Rd, Td, Fd, ybuf[off:off + 2 * m], idx=ib[2 * off:2 * off + 2 * m],
+                                    val=vb[off:off + m])
+                check_2d(ib[2 * off:2 * off + 2 * m].cpu().numpy().reshape(-1, 2), vb[off:off + m].cpu().numpy(),
+                         wi[:m], wv[:m])
+                assert torch.all(vb[:off] == -7.0) and torch.all(vb[off + m:] == -7.0)
+
+
+def test_2d_affine_field_exact(ss):
+    R = wl.log_spaced_table(200, 1e-6, 1e4, 0.1, seed=1)
+    T = wl.log_spaced_table(100, 1e-4, 1e4, 0.1, seed=2)
+    F = 3.0 + 0.5 * R[:, None] + 2.0 * T[None, :] + 0.25 * R[:, None] * T[None, :]
+    Y2 = wl.pairs_log_uniform(100_000, 1e-6, 1e4, 1e-4, 1e4, seed=3)
+    _, val = ss.search_interp_2d(R.to(DEV), T.to(DEV), F.contiguous().to(DEV), Y2.to(DEV))
+    want = 3.0 + 0.5 * Y2[:, 0] + 2.0 * Y2[:, 1] + 0.25 * Y2[:, 0] * Y2[:, 1]
+    rel = ((val.cpu() - want).abs() / want).max().item()
+    assert rel <= 1e-12
+
+
+# ---------------------------------------------------------------- full sizes, sampled
+
+@pytest.mark.slow
+def test_1d_one_billion_sampled(ss):
+    """The bench-size 1D run (1B targets, bucket search) checked at 2M sampled positions."""
+    m = 1 << 30
+    X, Y = wl.plain_1d(m=m, seed=1, device=DEV)
+    out = ss.search_1d(X, Y)
+    sample = torch.randint(0, m, (2_000_000,), device=DEV)
+    sample[:1000] = torch.arange(m - 1000, m, device=DEV)
+    got = out[sample].cpu().numpy()
+    want = oracle.search_1d_sampled(X.cpu().numpy(), Y[sample].cpu().numpy(), np.arange(len(sample)))
+    np.testing.assert_array_equal(got, want)
+    # properties at full size: range and the interval invariant on a second sample
+    assert int(out.min()) >= 0 and int(out.max()) <= 63
+    del out, Y
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.slow
+def test_2d_full_size_sampled(ss):
+    """The bench-size 2D run (64M pairs) checked at 1M sampled positions."""
+    m = 64 << 20
+    R, T, F, Y2 = wl.interp_2d(m=m, seed=2, device=DEV)
+    idx, val = ss.search_interp_2d(R, T, F, Y2)
+    sample = torch.randint(0, m, (1_000_000,), device=DEV)
+    wi, wv = oracle.search_interp_2d(R.cpu().numpy(), T.cpu().numpy(), F.cpu().numpy(), Y2[sample].cpu().numpy())
+    check_2d(idx[sample].cpu().numpy(), val[sample].cpu().numpy(), wi, wv)
