@@ -10,7 +10,7 @@ import ctypes as C
 
 import numpy as np
 
-from .build import build
+from . import build as _build_mod
 
 _lib = None
 
@@ -23,7 +23,7 @@ _f64p = C.POINTER(C.c_double)
 def lib():
     global _lib
     if _lib is None:
-        L = C.CDLL(build())
+        L = C.CDLL(_build_mod.build())
         L.oracle_search_1d.argtypes = [_f64p, C.c_int32, _f64p, C.c_int64, C.c_int32, _i32p]
         L.oracle_search_1d_sampled.argtypes = [_f64p, C.c_int32, _f64p, _i64p, C.c_int64, C.c_int32, _i32p]
         L.oracle_search_interp_2d.argtypes = [_f64p, C.c_int32, _f64p, C.c_int32, _f64p, _f64p,

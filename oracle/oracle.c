@@ -185,9 +185,9 @@ int64_t oracle_bucket_directory(const double* X, int32_t n, int32_t shift,
                                 uint64_t* base, int32_t* L, int64_t cap) {
   uint64_t b0 = oracle_order_key(X[0]) >> shift;
   uint64_t b1 = oracle_order_key(X[n - 1]) >> shift;
-  int64_t B = (int64_t)(b1 - b0) + 1;
   *base = b0;
-  if (B + 1 > cap) return -1;
+  if (b1 - b0 + 1 >= (uint64_t)cap) return -1;   /* B + 1 entries must fit in cap */
+  int64_t B = (int64_t)(b1 - b0) + 1;
   for (int64_t b = 0; b <= B; ++b) {
     int32_t c = 0;
     for (int32_t j = 0; j < n; ++j)  /* linear count, one bucket at a time */
@@ -200,8 +200,8 @@ int64_t oracle_bucket_directory(const double* X, int32_t n, int32_t shift,
 /* The finest shift whose directory has at most cap_buckets buckets. */
 int32_t oracle_bucket_shift(const double* X, int32_t n, int64_t cap_buckets) {
   uint64_t k0 = oracle_order_key(X[0]), k1 = oracle_order_key(X[n - 1]);
-  for (int32_t s = 0; s < 64; ++s)
-    if ((int64_t)((k1 >> s) - (k0 >> s)) + 1 <= cap_buckets) return s;
+  for (int32_t s = 0; s < 64; ++s)   /* spans are unsigned: a table may cover most of the key range */
+    if ((k1 >> s) - (k0 >> s) < (uint64_t)cap_buckets) return s;
   return 63;
 }
 

@@ -139,10 +139,11 @@ __device__ __forceinline__ void stage_table_1d(const double* __restrict__ X, int
     if (tid == 0) {
       const uint64_t k0 = keys[0], k1 = keys[ns - 1];
       int s = 0;
-      while (s < 63 && (int64_t)((k1 >> s) - (k0 >> s)) + 1 > (int64_t)lay.dir_cap) ++s;
+      // the span is unsigned: a table may cover more than half of the key range
+      while (s < 63 && ((k1 >> s) - (k0 >> s)) >= (uint64_t)lay.dir_cap) ++s;
       h.shift = s;
       h.base = k0 >> s;
-      h.nb = (int)((k1 >> s) - (k0 >> s)) + 1;
+      h.nb = (int)min((k1 >> s) - (k0 >> s) + 1, (uint64_t)lay.dir_cap);
     }
     __syncthreads();
     const int s = h.shift, nb = h.nb;

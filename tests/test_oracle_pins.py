@@ -187,6 +187,20 @@ def test_bucket_shift_and_directory_invariants():
                 assert L[b] <= j < L[b + 1]
 
 
+def test_bucket_directory_wide_key_span():
+    # a table from -1e300 to 1e300 covers most of the 64-bit key range
+    X = np.array([-1e300, -1.0, -5e-324, 0.0, 5e-324, 1.0, 1e300])
+    for cap in (2, 3, 64, 112, 4096):
+        s = oracle.bucket_shift(X, cap)
+        base, L = oracle.bucket_directory(X, s, cap=cap + 1)
+        assert 1 <= len(L) - 1 <= cap
+        k0, k1 = _bits_key(X[0]), _bits_key(X[-1])
+        assert (k1 >> s) - (k0 >> s) + 1 == len(L) - 1
+        for j, x in enumerate(X):
+            b = (_bits_key(x) >> s) - base
+            assert L[b] <= j < L[b + 1]
+
+
 def test_spline_knots_closed_form():
     # entries exact powers of two: with K = n-1 segments, knot j (j >= 1) sits
     # one step above 2^j in the image, so j+1 entries lie below it
