@@ -313,10 +313,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--targets", type=int, default=0, help="override the workload's target count (profiling cases)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     wl_obj = WORKLOADS[args.workload]()
+    if args.targets:
+        wl_obj.m = args.targets
     if args.impl == "reference":
         return run_reference(args, wl_obj)
 

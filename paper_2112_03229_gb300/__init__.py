@@ -59,7 +59,11 @@ def lib():
         L.ss_search_1d_tuned.argtypes = [_vp, _i32, _vp, _i64, _vp, _i32, _i32, _i32, _i32, _vp, _vp]
         L.ss_search_interp_2d.argtypes = [_vp, _i32, _vp, _i32, _vp, _vp, _i64, _vp, _vp, _i32, _vp, _vp]
         L.ss_sync_status.argtypes = [_vp, _vp, _vp, _i32]
-        for name in ("ss_search_1d", "ss_search_1d_tuned", "ss_search_interp_2d", "ss_sync_status"):
+        L.ss_mlp_loss_grad.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp, _vp]
+        L.ss_mlp_forward.argtypes = [_vp, _vp, _i64, _vp, _vp]
+        L.ss_mlp_adam_step.argtypes = [_vp, _vp, _vp, _vp, _i32, C.c_float, C.c_float, C.c_float, C.c_float, _vp]
+        for name in ("ss_search_1d", "ss_search_1d_tuned", "ss_search_interp_2d", "ss_sync_status",
+                     "ss_mlp_loss_grad", "ss_mlp_forward", "ss_mlp_adam_step"):
             getattr(L, name).restype = _i32
         _lib = L
     return _lib
@@ -133,3 +137,29 @@ def search_interp_2d(R, T, F, Y2, idx=None, val=None, algo="auto", stat=None, st
                                      _dev(idx, torch.int32, "idx"), _dev(val, torch.float64, "val"), _algo(algo),
                                      _statp(stat), _stream(stream)))
     return idx, val
+
+
+# ---------------------------------------------------------------------------
+# Position model (2 -> 16 -> 1 MLP) training kernels, exposed for checks
+# ---------------------------------------------------------------------------
+def mlp_loss_grad(params, x, y, stream=None):
+    """Mean squared error of the MLP over (x, y) and its gradient (65 floats), on the GPU."""
+    grad = torch.empty(65, dtype=torch.float32, device=params.device)
+    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    _check(lib().ss_mlp_loss_grad(_dev(params, torch.float32, "params"), _dev(x, torch.float32, "x"),
+                                  _dev(y, torch.float32, "y"), y.numel(), _dev(grad, torch.float32, "grad"),
+                                  _dev(loss, torch.float32, "loss"), _stream(stream)))
+    return loss, grad
+
+
+def mlp_forward(params, x, stream=None):
+    y = torch.empty(x.numel() // 2, dtype=torch.float32, device=x.device)
+    _check(lib().ss_mlp_forward(_dev(params, torch.float32, "params"), _dev(x, torch.float32, "x"), y.numel(),
+                                _dev(y, torch.float32, "y"), _stream(stream)))
+    return y
+
+
+def mlp_adam_step(params, grad, m1, m2, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().ss_mlp_adam_step(_dev(params, torch.float32, "params"), _dev(grad, torch.float32, "grad"),
+                                  _dev(m1, torch.float32, "m1"), _dev(m2, torch.float32, "m2"), step, lr, beta1,
+                                  beta2, eps, _stream(stream)))

@@ -1,0 +1,106 @@
+// ss_model.cuh -- position models that propose where a target falls in a
+// table (the learned counterpart of the analytic hashes of Sec. 3.4-3.5).
+//
+// MLP: 2 -> 16 -> 1, ReLU hidden layer, fp32.  Inputs are read from the
+// IEEE-754 bits of the target: x0 = (e - e_lo) * e_scale with e the unbiased
+// base-2 exponent, x1 = f the mantissa fraction in [0, 1).  The output
+// approximates idx / (n - 1).  Parameter layout (65 floats): W1[16][2],
+// b1[16], w2[16], b2 -- the same order as the CPU oracle.
+//
+// Spline: piecewise linear in the order-preserving key between knots spaced
+// 2^shift apart; the knot values are the counts of table keys below each
+// knot, i.e. exactly the bucket directory.  The proposal interpolates
+// between the two knots around the query key.
+#pragma once
+
+#include "ss_common.cuh"
+
+namespace ss {
+
+constexpr int kHidden = 16;
+constexpr int kMlpParams = 4 * kHidden + 1;   // 65
+
+struct MlpFeatScale {
+  float e_lo, e_scale;
+};
+
+// Features from the bits of t.  f keeps the top 23 mantissa bits (exact in fp32).
+__device__ __forceinline__ void mlp_features(double t, const MlpFeatScale& s, float& x0, float& x1) {
+  const uint64_t u = static_cast<uint64_t>(__double_as_longlong(t));
+  const int e = (int)((u >> 52) & 0x7FF) - 1023;
+  x1 = __int_as_float(0x3F800000 | (int)((u >> 29) & 0x7FFFFF)) - 1.0f;
+  x0 = ((float)e - s.e_lo) * s.e_scale;
+}
+
+__device__ __forceinline__ float mlp_forward(const float* __restrict__ p, float x0, float x1) {
+  float y = p[4 * kHidden];
+#pragma unroll
+  for (int k = 0; k < kHidden; ++k) {
+    const float h = fmaxf(fmaf(p[2 * k], x0, fmaf(p[2 * k + 1], x1, p[2 * kHidden + k])), 0.0f);
+    y = fmaf(p[3 * kHidden + k], h, y);
+  }
+  return y;
+}
+
+// Adds the gradient of scale * (y - target)^2 with respect to the 65
+// parameters into g (chain rule through the ReLU); returns the squared error.
+__device__ __forceinline__ float mlp_backward_accum(const float* __restrict__ p, float x0, float x1, float target,
+                                                    float scale, float* g) {
+  float h[kHidden];
+  float y = p[4 * kHidden];
+#pragma unroll
+  for (int k = 0; k < kHidden; ++k) {
+    h[k] = fmaf(p[2 * k], x0, fmaf(p[2 * k + 1], x1, p[2 * kHidden + k]));
+    y = fmaf(p[3 * kHidden + k], fmaxf(h[k], 0.0f), y);
+  }
+  const float r = y - target;
+  const float dy = 2.0f * r * scale;
+  g[4 * kHidden] += dy;
+#pragma unroll
+  for (int k = 0; k < kHidden; ++k) {
+    const float hk = fmaxf(h[k], 0.0f);
+    g[3 * kHidden + k] = fmaf(dy, hk, g[3 * kHidden + k]);
+    const float dz = h[k] > 0.0f ? dy * p[3 * kHidden + k] : 0.0f;
+    g[2 * k] = fmaf(dz, x0, g[2 * k]);
+    g[2 * k + 1] = fmaf(dz, x1, g[2 * k + 1]);
+    g[2 * kHidden + k] += dz;
+  }
+  return r * r;
+}
+
+// Adam (Kingma & Ba, 2015), one parameter.
+__device__ __forceinline__ void adam_update(float& p, float g, float& m1, float& m2, float lr, float b1, float b2,
+                                            float eps, float c1, float c2) {
+  m1 = b1 * m1 + (1.0f - b1) * g;
+  m2 = b2 * m2 + (1.0f - b2) * g * g;
+  p -= lr * (m1 / c1) / (sqrtf(m2 / c2) + eps);
+}
+
+// Proposal of the MLP for target t: rint(y * (n-1)) clamped to [0, n-1].
+__device__ __forceinline__ int mlp_propose(const float* __restrict__ p, const MlpFeatScale& s, int n, double t) {
+  float x0, x1;
+  mlp_features(t, s, x0, x1);
+  const float y = mlp_forward(p, x0, x1);
+  const float pos = rintf(y * (float)(n - 1));
+  return (int)fminf(fmaxf(pos, 0.0f), (float)(n - 1));     // NaN -> 0 through fmaxf
+}
+
+// Proposal of the spline for query key q over directory dir[0..nb] (counts
+// of keys below each knot (base + b) << shift).
+__device__ __forceinline__ int spline_propose(const int* __restrict__ dir, int shift, uint64_t base, int nb,
+                                              uint64_t q) {
+  const uint64_t hb = q >> shift;
+  if (hb < base) return 0;
+  const uint64_t d = hb - base;
+  if (d >= (uint64_t)nb) return dir[nb];
+  const int b = (int)d;
+  const int lo = dir[b], hi = dir[b + 1];
+  // fraction of the way through the bucket, from the key bits below the shift
+  const uint64_t below = shift > 0 ? (q & ((1ull << shift) - 1)) : 0ull;
+  const float frac = shift > 0 ? (float)(below >> (shift > 24 ? shift - 24 : 0)) *
+                                     __int_as_float((127 - min(shift, 24)) << 23)
+                               : 0.0f;
+  return lo + (int)rintf(frac * (float)(hi - lo));
+}
+
+}  // namespace ss

@@ -246,9 +246,10 @@ __device__ __forceinline__ int search_ballot(const uint64_t* __restrict__ keys, 
 // X[1 + c*stride .. ] of block c that lie below q, reading X from global.
 __device__ __forceinline__ int search_leaf_global(const double* __restrict__ X, int nk, int stride, int c,
                                                   uint64_t q) {
-  int lo = c * stride;                     // count so far (0-based among X[1..])
+  // all keys of blocks 0..c-1 lie below q; when every sample does (c = ns)
+  // the count is nk even if the last block is short
+  int lo = min(c * stride, nk);
   int len = min(stride, nk - lo);
-  if (len < 0) len = 0;
   while (len > 0) {
     const int half = len >> 1;
     const uint64_t k = order_key(__ldg(X + 1 + lo + half));
