@@ -48,22 +48,23 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
-def kernel_sources_hash():
+def sources_hash(files):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2112_03229_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in files:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel, workload):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current sources."""
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel's source files changed since the counters were taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             rec = json.load(f)[f"{kernel}@{workload}"]
-        if rec.get("sources") != kernel_sources_hash():
+        if rec.get("sources") != sources_hash(rec["files"]):
             return None
         return float(rec["dram_bytes_per_launch"])
     except Exception:

@@ -86,6 +86,7 @@ typedef struct ss_devstat {
 
 #define SS_FLAG_NOT_SORTED 0x1u     /* a table was not strictly increasing (or held NaN) */
 #define SS_FLAG_BAD_VALUE 0x2u      /* a 2D value-path precondition failed; fp64 path used */
+#define SS_FLAG_STAGING_TIMEOUT 0x4u /* a shared-memory staging copy did not complete in time; outputs incomplete */
 
 /* ---------------------------------------------------------------------- */
 /* One-shot calls: no set-up kept between calls ("zero set-up cost",       */
@@ -109,6 +110,99 @@ ss_status ss_search_interp_2d(const double* R, int32_t nr, const double* T, int3
                               const double* F, const double* Y2, int64_t m,
                               int32_t* lowbounds2, double* values, int32_t algo,
                               ss_devstat* stat, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Plans: set-up once per set of loaded tables, then many searches.        */
+/* EOSPAC loads its tables once at program start, so search set-up is paid  */
+/* once (Sec. 5.3).  A plan prepares every table on the GPU (order-         */
+/* preserving keys, bucket directory, breadth-first layout, optional        */
+/* learned position model trained by the library's own kernels), chooses    */
+/* per table-size bucket the in-block algorithm and tile size (autotuner),  */
+/* and runs a whole batch of tables -- each with its own targets -- in one  */
+/* persistent kernel launch that walks a tile queue, captured in a CUDA     */
+/* graph.  The plan owns all device memory it allocates.                    */
+/* ---------------------------------------------------------------------- */
+typedef struct ss_plan ss_plan;
+
+/* Learned position model used as the proposal of every table of a plan.
+ * The model only proposes: each index is checked exactly against the table
+ * (the answer must lie in a window [p-E, p+E] whose ends are compared with
+ * the target) and a failed check falls back to the plain search, so results
+ * are identical with or without a model. */
+typedef enum ss_model {
+  SS_MODEL_NONE = 0,    /* plain search only */
+  SS_MODEL_SPLINE = 1,  /* piecewise-linear map of the target's key, knots = bucket directory */
+  SS_MODEL_MLP = 2      /* 2-16-1 fp32 MLP on the target's exponent and mantissa, trained on the GPU */
+} ss_model;
+
+typedef struct ss_plan_opts {
+  int32_t side;             /* ss_side */
+  int32_t algo;             /* plain algorithm without a model: AUTO (tuner or bucket), BINARY, BUCKET, BALLOT */
+  int32_t model;            /* ss_model */
+  int32_t autotune;         /* 1: time the candidates of each table-size bucket and keep the fastest */
+  int32_t tile;             /* targets per tile; 0: library default or tuned */
+  int32_t mlp_epochs;       /* full-batch Adam steps of the MLP (default 400; 0 keeps the untrained initialisation) */
+  float mlp_lr;             /* Adam learning rate (default 1e-2) */
+  int32_t dir_cap;          /* bucket-directory budget per table (0: 16 n clamped to [64, 8192]) */
+  uint64_t seed;            /* seed of the counter-based sampler of training and probe targets */
+  const char* tune_cache;   /* JSON file the autotuner reads and writes (NULL: none) */
+} ss_plan_opts;
+
+typedef struct ss_plan_info {
+  int32_t kind;             /* 1: 1D tables, 2: 2D tables */
+  int32_t ntables;
+  int64_t device_bytes;     /* device memory held by the plan */
+  int32_t max_window;       /* largest learned half-window E over tables (0 without a model) */
+  float mean_window;
+  float train_loss;         /* mean final training loss of the MLP (MLP model only) */
+  int32_t nbuckets;         /* table-size buckets [2,16) [16,64) [64,256) ... */
+  int32_t bucket_algo[8];   /* chosen algorithm per bucket: 0 bucket, 1 binary, 2-4 ballot 8/16/32, 5 spline, 6 mlp */
+  int32_t bucket_tile[8];   /* chosen targets per tile per bucket */
+  int32_t bucket_tables[8]; /* tables per bucket */
+  int64_t ntiles;           /* tiles of the bound batch */
+  int32_t tuned;            /* 1 if the autotuner (or its cache) set the choices */
+} ss_plan_info;
+
+/* Fill *opts with the defaults. */
+void ss_plan_opts_default(ss_plan_opts* opts);
+
+/* Prepare ntables 1D tables.  X_off (host) [ntables+1] offsets into X
+ * (device), table k = X[X_off[k] .. X_off[k+1]), each strictly increasing with
+ * at least 2 entries.  Synchronises `stream`; SS_ENOTSORTED if a table is not
+ * strictly increasing.  X is no longer needed once this returns. */
+ss_status ss_plan_create_1d(ss_plan** plan, int32_t ntables, const int64_t* X_off, const double* X,
+                            const ss_plan_opts* opts, cudaStream_t stream);
+
+/* Prepare ntables 2D tables (Sec. 1 / 2.2 lookup): axes R, T and row-major
+ * value grids F, each given by host offsets into device arrays (R_off, T_off,
+ * F_off have ntables+1 entries; F_off[k+1]-F_off[k] = nr_k * nt_k). */
+ss_status ss_plan_create_2d(ss_plan** plan, int32_t ntables, const int64_t* R_off, const double* R,
+                            const int64_t* T_off, const double* T, const int64_t* F_off, const double* F,
+                            const ss_plan_opts* opts, cudaStream_t stream);
+
+/* Bind a batch: table k's targets are Y[Y_off[k] .. Y_off[k+1]) (Y_off host,
+ * non-decreasing; empty tables allowed) and its results go to the same
+ * positions of lowbounds.  Builds the tile queue and captures the launch in a
+ * CUDA graph; buffers must stay valid while the plan executes. */
+ss_status ss_plan_bind_1d(ss_plan* plan, const int64_t* Y_off, const double* Y, int32_t* lowbounds,
+                          ss_devstat* stat, cudaStream_t stream);
+
+/* 2D batch: pairs of table k are Y2[2 Y_off[k] .. 2 Y_off[k+1]) (interleaved
+ * rho, T); lowbounds2 interleaved index pairs; values one double per pair. */
+ss_status ss_plan_bind_2d(ss_plan* plan, const int64_t* Y_off, const double* Y2, int32_t* lowbounds2,
+                          double* values, ss_devstat* stat, cudaStream_t stream);
+
+/* Run the bound batch: one graph launch (a counter reset and the persistent kernel). */
+ss_status ss_plan_execute(ss_plan* plan, cudaStream_t stream);
+
+ss_status ss_plan_info_get(const ss_plan* plan, ss_plan_info* info);
+
+/* Write the prepared tables, models and tuning choices to a file, and read
+ * them back (the loaded plan gives identical results; bind it again). */
+ss_status ss_plan_save(const ss_plan* plan, const char* path);
+ss_status ss_plan_load(ss_plan** plan, const char* path, cudaStream_t stream);
+
+void ss_plan_destroy(ss_plan* plan);
 
 /* ---------------------------------------------------------------------- */
 /* Status and diagnostics                                                  */

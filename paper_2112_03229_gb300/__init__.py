@@ -25,6 +25,7 @@ ALGO_AUTO, ALGO_BINARY, ALGO_BUCKET, ALGO_BALLOT, ALGO_BRANCHY = 0, 1, 2, 3, 4
 ALGOS = {"auto": ALGO_AUTO, "binary": ALGO_BINARY, "bucket": ALGO_BUCKET, "ballot": ALGO_BALLOT,
          "branchy": ALGO_BRANCHY}
 FLAG_NOT_SORTED = 0x1
+FLAG_BAD_VALUE = 0x2
 
 STATUS = {0: "SS_OK", 1: "SS_EINVAL", 2: "SS_ENOTSORTED", 3: "SS_ENOMEM", 4: "SS_ECUDA", 5: "SS_ETIMEOUT",
           6: "SS_EUNSUPPORTED"}
@@ -58,11 +59,13 @@ def lib():
         L.ss_search_1d.argtypes = [_vp, _i32, _vp, _i64, _vp, _i32, _i32, _vp, _vp]
         L.ss_search_1d_tuned.argtypes = [_vp, _i32, _vp, _i64, _vp, _i32, _i32, _i32, _i32, _vp, _vp]
         L.ss_search_interp_2d.argtypes = [_vp, _i32, _vp, _i32, _vp, _vp, _i64, _vp, _vp, _i32, _vp, _vp]
+        L.ss_search_interp_2d_fp64.argtypes = [_vp, _i32, _vp, _i32, _vp, _vp, _i64, _vp, _vp, _i32, _vp, _vp]
         L.ss_sync_status.argtypes = [_vp, _vp, _vp, _i32]
         L.ss_mlp_loss_grad.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp, _vp]
         L.ss_mlp_forward.argtypes = [_vp, _vp, _i64, _vp, _vp]
         L.ss_mlp_adam_step.argtypes = [_vp, _vp, _vp, _vp, _i32, C.c_float, C.c_float, C.c_float, C.c_float, _vp]
-        for name in ("ss_search_1d", "ss_search_1d_tuned", "ss_search_interp_2d", "ss_sync_status",
+        for name in ("ss_search_1d", "ss_search_1d_tuned", "ss_search_interp_2d", "ss_search_interp_2d_fp64",
+                     "ss_sync_status",
                      "ss_mlp_loss_grad", "ss_mlp_forward", "ss_mlp_adam_step"):
             getattr(L, name).restype = _i32
         _lib = L
@@ -123,8 +126,9 @@ def search_1d(X: torch.Tensor, Y: torch.Tensor, out: torch.Tensor | None = None,
     return out
 
 
-def search_interp_2d(R, T, F, Y2, idx=None, val=None, algo="auto", stat=None, stream=None):
-    """ss_search_interp_2d: per (rho, T) pair the index pair and the bilinear value."""
+def search_interp_2d(R, T, F, Y2, idx=None, val=None, algo="auto", stat=None, stream=None, fp64=False):
+    """ss_search_interp_2d: per (rho, T) pair the index pair and the bilinear value.
+    fp64=True calls ss_search_interp_2d_fp64 (fp64 weights and blend)."""
     m = Y2.numel() // 2
     if F.numel() != R.numel() * T.numel():
         raise ValueError("F must hold len(R) * len(T) values")
@@ -132,7 +136,8 @@ def search_interp_2d(R, T, F, Y2, idx=None, val=None, algo="auto", stat=None, st
         idx = torch.empty((m, 2), dtype=torch.int32, device=Y2.device)
     if val is None:
         val = torch.empty((m,), dtype=torch.float64, device=Y2.device)
-    _check(lib().ss_search_interp_2d(_dev(R, torch.float64, "R"), R.numel(), _dev(T, torch.float64, "T"), T.numel(),
+    fn = lib().ss_search_interp_2d_fp64 if fp64 else lib().ss_search_interp_2d
+    _check(fn(_dev(R, torch.float64, "R"), R.numel(), _dev(T, torch.float64, "T"), T.numel(),
                                      _dev(F, torch.float64, "F"), _dev(Y2, torch.float64, "Y2"), m,
                                      _dev(idx, torch.int32, "idx"), _dev(val, torch.float64, "val"), _algo(algo),
                                      _statp(stat), _stream(stream)))
@@ -163,3 +168,153 @@ def mlp_adam_step(params, grad, m1, m2, step, lr, beta1=0.9, beta2=0.999, eps=1e
     _check(lib().ss_mlp_adam_step(_dev(params, torch.float32, "params"), _dev(grad, torch.float32, "grad"),
                                   _dev(m1, torch.float32, "m1"), _dev(m2, torch.float32, "m2"), step, lr, beta1,
                                   beta2, eps, _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# Plans: set-up once per set of tables, many batched searches
+# ---------------------------------------------------------------------------
+MODEL_NONE, MODEL_SPLINE, MODEL_MLP = 0, 1, 2
+MODELS = {"none": MODEL_NONE, "spline": MODEL_SPLINE, "mlp": MODEL_MLP}
+BLOB_ALGOS = ["bucket", "binary", "ballot8", "ballot16", "ballot32", "spline", "mlp"]
+
+
+class PlanOpts(C.Structure):
+    _fields_ = [("side", C.c_int32), ("algo", C.c_int32), ("model", C.c_int32), ("autotune", C.c_int32),
+                ("tile", C.c_int32), ("mlp_epochs", C.c_int32), ("mlp_lr", C.c_float), ("dir_cap", C.c_int32),
+                ("seed", C.c_uint64), ("tune_cache", C.c_char_p)]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("ntables", C.c_int32), ("device_bytes", C.c_int64),
+                ("max_window", C.c_int32), ("mean_window", C.c_float), ("train_loss", C.c_float),
+                ("nbuckets", C.c_int32), ("bucket_algo", C.c_int32 * 8), ("bucket_tile", C.c_int32 * 8),
+                ("bucket_tables", C.c_int32 * 8), ("ntiles", C.c_int64), ("tuned", C.c_int32)]
+
+
+def _plan_sigs(L):
+    P = C.POINTER(C.c_void_p)
+    i64p = C.POINTER(C.c_int64)
+    L.ss_plan_opts_default.argtypes = [C.POINTER(PlanOpts)]
+    L.ss_plan_opts_default.restype = None
+    L.ss_plan_create_1d.argtypes = [P, _i32, i64p, _vp, C.POINTER(PlanOpts), _vp]
+    L.ss_plan_create_2d.argtypes = [P, _i32, i64p, _vp, i64p, _vp, i64p, _vp, C.POINTER(PlanOpts), _vp]
+    L.ss_plan_bind_1d.argtypes = [_vp, i64p, _vp, _vp, _vp, _vp]
+    L.ss_plan_bind_2d.argtypes = [_vp, i64p, _vp, _vp, _vp, _vp, _vp]
+    L.ss_plan_execute.argtypes = [_vp, _vp]
+    L.ss_plan_info_get.argtypes = [_vp, C.POINTER(PlanInfo)]
+    L.ss_plan_save.argtypes = [_vp, C.c_char_p]
+    L.ss_plan_load.argtypes = [P, C.c_char_p, _vp]
+    L.ss_plan_destroy.argtypes = [_vp]
+    L.ss_plan_destroy.restype = None
+    for n in ("ss_plan_create_1d", "ss_plan_create_2d", "ss_plan_bind_1d", "ss_plan_bind_2d", "ss_plan_execute",
+              "ss_plan_info_get", "ss_plan_save", "ss_plan_load"):
+        getattr(L, n).restype = _i32
+
+
+def _offsets(off):
+    import numpy as np
+    a = np.ascontiguousarray(off.cpu().numpy() if isinstance(off, torch.Tensor) else off, dtype=np.int64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_int64))
+
+
+def plan_opts(side=SIDE_LT, algo="auto", model="none", autotune=False, tile=0, mlp_epochs=None, mlp_lr=0.0,
+              dir_cap=0, seed=0x5EED, tune_cache=None) -> PlanOpts:
+    o = PlanOpts()
+    L = lib()
+    if not hasattr(L, "_plan_sigs"):
+        _plan_sigs(L)
+        L._plan_sigs = True
+    L.ss_plan_opts_default(C.byref(o))
+    o.side = side
+    o.algo = _algo(algo)
+    o.model = MODELS[model] if isinstance(model, str) else int(model)
+    o.autotune = int(bool(autotune))
+    o.tile = tile
+    if mlp_epochs is not None:
+        o.mlp_epochs = mlp_epochs
+    if mlp_lr:
+        o.mlp_lr = mlp_lr
+    o.dir_cap = dir_cap
+    o.seed = seed
+    o.tune_cache = tune_cache.encode() if tune_cache else None
+    return o
+
+
+class Plan:
+    """ss_plan: prepared tables (and learned models) for repeated batched searches."""
+
+    def __init__(self, handle, kind, ntables):
+        self._h = handle
+        self.kind = kind
+        self.ntables = ntables
+        self._keep = None
+
+    @classmethod
+    def create_1d(cls, X_off, X, stream=None, **opts):
+        o = plan_opts(**opts)
+        off, offp = _offsets(X_off)
+        h = C.c_void_p()
+        _check(lib().ss_plan_create_1d(C.byref(h), len(off) - 1, offp, _dev(X, torch.float64, "X"), C.byref(o),
+                                       _stream(stream)))
+        return cls(h, 1, len(off) - 1)
+
+    @classmethod
+    def create_2d(cls, R_off, R, T_off, T, F_off, F, stream=None, **opts):
+        o = plan_opts(**opts)
+        ro, rp = _offsets(R_off)
+        to, tp = _offsets(T_off)
+        fo, fp = _offsets(F_off)
+        h = C.c_void_p()
+        _check(lib().ss_plan_create_2d(C.byref(h), len(ro) - 1, rp, _dev(R, torch.float64, "R"), tp,
+                                       _dev(T, torch.float64, "T"), fp, _dev(F, torch.float64, "F"), C.byref(o),
+                                       _stream(stream)))
+        return cls(h, 2, len(ro) - 1)
+
+    @classmethod
+    def load(cls, path, stream=None):
+        plan_opts()   # registers signatures
+        h = C.c_void_p()
+        _check(lib().ss_plan_load(C.byref(h), str(path).encode(), _stream(stream)))
+        p = cls(h, 0, 0)
+        inf = p.info()
+        p.kind, p.ntables = inf.kind, inf.ntables
+        return p
+
+    def bind_1d(self, Y_off, Y, out, stat=None, stream=None):
+        off, offp = _offsets(Y_off)
+        self._keep = (Y, out, stat)
+        _check(lib().ss_plan_bind_1d(self._h, offp, _dev(Y, torch.float64, "Y"), _dev(out, torch.int32, "out"),
+                                     _statp(stat), _stream(stream)))
+
+    def bind_2d(self, Y_off, Y2, idx, val, stat=None, stream=None):
+        off, offp = _offsets(Y_off)
+        self._keep = (Y2, idx, val, stat)
+        _check(lib().ss_plan_bind_2d(self._h, offp, _dev(Y2, torch.float64, "Y2"), _dev(idx, torch.int32, "idx"),
+                                     _dev(val, torch.float64, "val"), _statp(stat), _stream(stream)))
+
+    def execute(self, stream=None):
+        _check(lib().ss_plan_execute(self._h, _stream(stream)))
+
+    def info(self) -> PlanInfo:
+        inf = PlanInfo()
+        _check(lib().ss_plan_info_get(self._h, C.byref(inf)))
+        return inf
+
+    def choices(self):
+        inf = self.info()
+        return {b: (BLOB_ALGOS[inf.bucket_algo[b]], inf.bucket_tile[b], inf.bucket_tables[b])
+                for b in range(inf.nbuckets) if inf.bucket_tables[b]}
+
+    def save(self, path):
+        _check(lib().ss_plan_save(self._h, str(path).encode()))
+
+    def close(self):
+        if self._h:
+            lib().ss_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

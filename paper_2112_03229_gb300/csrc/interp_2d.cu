@@ -2,14 +2,24 @@
 // each (density, temperature) target in both grids of a SESAME table and
 // interpolates).  Per pair: two exact searches (the 1D routines of
 // ss_table.cuh on two staged axes), cell selection c = min(i, n-2), clamped
-// weights from per-cell reciprocal gaps staged once per block, four gathers
-// from the row-major value grid and the convex bilinear blend.
+// weights, four gathers from the row-major value grid and the convex
+// bilinear blend.
 //
-// The value grid stays in global memory (L2-resident for the sizes of interest);
-// axes, bucket directories and per-cell origins / reciprocal gaps live in
-// shared memory.
+// Two arithmetic paths, chosen once per launch from the staged axes:
+//  * float-float (default): exact integer weight numerators and a
+//    float-float blend on the fp32 pipe (ss_ff.cuh); needs positive axes
+//    with entries in [2^-70, 2^101) and cells spanning at most 2^10.
+//    A pair whose four grid values are not splittable (zero excepted) is
+//    finished in fp64.
+//  * fp64: weights (x - X[c]) * (1 / gap) and the blend in double.
+// Both agree with an fp64 evaluation of the formula to well within 1e-12
+// relative for positive grids.
+//
+// The value grid stays in global memory (L2-resident for the sizes of
+// interest); axes, bucket directories and per-cell data live in shared memory.
 #include <algorithm>
 
+#include "ss_ff.cuh"
 #include "ss_table.cuh"
 
 namespace ss {
@@ -18,8 +28,14 @@ constexpr int kMaxAxis2D = 4096;   // largest axis staged whole with its per-cel
 
 struct Axis2D {                    // shared-memory offsets of one axis
   Layout1D lay;
-  int cx;                          // double[n-1]: left end X[c] of cell c
-  int cg;                          // double[n-1]: 1 / (X[c+1] - X[c])
+  int cells;                       // CellFF[n-1]: X[c] bits and the float-float weight scale
+  int rg;                          // double[n-1]: 1 / (X[c+1] - X[c]) for the fp64 path
+  int aux;                         // AxisAux
+};
+
+struct AxisAux {
+  uint64_t k0;                     // key of X[0]
+  int ffok;                        // 1 if the float-float path applies to this axis
 };
 
 struct Args2D {
@@ -35,17 +51,40 @@ struct Args2D {
   int64_t head;     // pairs [0, head) scalar
   int64_t np2;      // pairs in the vector body, in units of 2 pairs
   int algo;         // SS_ALGO_BUCKET or SS_ALGO_BINARY
+  int force_fp64;   // 1: skip the float-float path
   Axis2D ar, at;
   ss_devstat* stat;
 };
 
+// Per-cell data and the float-float eligibility of one axis.
 static __device__ void stage_cells(const double* __restrict__ X, int n, const Axis2D& ax, unsigned char* smem) {
-  double* cx = reinterpret_cast<double*>(smem + ax.cx);
-  double* cg = reinterpret_cast<double*>(smem + ax.cg);
+  CellFF* cells = reinterpret_cast<CellFF*>(smem + ax.cells);
+  double* rg = reinterpret_cast<double*>(smem + ax.rg);
+  AxisAux& aux = *reinterpret_cast<AxisAux*>(smem + ax.aux);
+  bool ok = true;
   for (int c = threadIdx.x; c < n - 1; c += blockDim.x) {
     const double a = __ldg(X + c), b = __ldg(X + c + 1);
-    cx[c] = a;
-    cg[c] = 1.0 / (b - a);
+    const double gap = b - a;
+    rg[c] = 1.0 / gap;
+    const uint64_t ua = static_cast<uint64_t>(__double_as_longlong(a));
+    const uint64_t ub = static_cast<uint64_t>(__double_as_longlong(b));
+    const int ea = (int)((ua >> 52) & 0x7FF), eb = (int)((ub >> 52) & 0x7FF);
+    const bool cell_ok = (ua >> 63) == 0 && ea >= kFFMinExp && eb <= kFFMaxExp && eb - ea <= kMaxCellOctaves &&
+                         gap > 0.0;
+    double g = 0.0;
+    float ghi = 0.0f, glo = 0.0f;
+    if (cell_ok) {
+      g = ldexp(1.0, ea - 1075) / gap;
+      ghi = __double2float_rn(g);
+      glo = __double2float_rn(g - (double)ghi);
+    }
+    ok &= cell_ok && ghi != 0.0f && isfinite(ghi) && fabsf(ghi) >= 1.0e-36f;
+    cells[c] = CellFF{ua, ghi, glo};
+  }
+  ok = __syncthreads_and(ok);
+  if (threadIdx.x == 0) {
+    aux.k0 = order_key(__ldg(X));
+    aux.ffok = ok ? 1 : 0;
   }
 }
 
@@ -56,57 +95,90 @@ struct AxisView {
   const uint64_t* keys;
   const uint64_t* eyt;
   const int* dir;
-  const double* cx;
-  const double* cg;
+  const CellFF* cells;
+  const double* rg;
   int shift, nb, T, D, n;
-  uint64_t base;
+  uint64_t base, k0;
 };
 
 __device__ __forceinline__ AxisView view_of(const Axis2D& ax, const unsigned char* smem) {
   const TableHdr& h = *reinterpret_cast<const TableHdr*>(smem + ax.lay.hdr);
+  const AxisAux& aux = *reinterpret_cast<const AxisAux*>(smem + ax.aux);
   AxisView v;
   v.keys = ax.lay.keys >= 0 ? reinterpret_cast<const uint64_t*>(smem + ax.lay.keys) : nullptr;
   v.eyt = ax.lay.eyt >= 0 ? reinterpret_cast<const uint64_t*>(smem + ax.lay.eyt) : nullptr;
   v.dir = ax.lay.dir >= 0 ? reinterpret_cast<const int*>(smem + ax.lay.dir) : nullptr;
-  v.cx = reinterpret_cast<const double*>(smem + ax.cx);
-  v.cg = reinterpret_cast<const double*>(smem + ax.cg);
+  v.cells = reinterpret_cast<const CellFF*>(smem + ax.cells);
+  v.rg = reinterpret_cast<const double*>(smem + ax.rg);
   v.shift = h.shift;
   v.nb = h.nb;
   v.T = h.occ > 0 ? 32 - __clz(h.occ) : 0;
   v.D = h.D;
   v.n = h.n;
   v.base = h.base;
+  v.k0 = aux.k0;
   return v;
 }
 
-// One pair: indices and value.  MODE 0: both axes bucket with occupancy <= 1;
-// 1: bucket with bounded bisection; 2: breadth-first binary.
 template <int MODE>
-__device__ __forceinline__ void lookup_pair(const AxisView& vr, const AxisView& vt, const double* __restrict__ F,
-                                            int nt, double rho, double tem, int& ir, int& it, double& v, int& nans) {
-  const uint64_t kr = order_key(rho), kt = order_key(tem);
-  nans += (kr < 0x0010000000000000ull) + (kt < 0x0010000000000000ull);
-  if (MODE == 0) {
-    ir = search_bucket<1>(vr.keys, vr.dir, vr.shift, vr.base, vr.nb, kr);
-    it = search_bucket<1>(vt.keys, vt.dir, vt.shift, vt.base, vt.nb, kt);
-  } else if (MODE == 1) {
-    ir = search_bucket_bisect(vr.keys, vr.dir, vr.shift, vr.base, vr.nb, vr.T, kr);
-    it = search_bucket_bisect(vt.keys, vt.dir, vt.shift, vt.base, vt.nb, vt.T, kt);
-  } else {
-    ir = search_eyt_rt(vr.eyt, vr.D, kr);
-    it = search_eyt_rt(vt.eyt, vt.D, kt);
-  }
-  const int cr = min(ir, vr.n - 2), ct = min(it, nt - 2);
-  const double wr = clamp01((rho - vr.cx[cr]) * vr.cg[cr]);
-  const double wt = clamp01((tem - vt.cx[ct]) * vt.cg[ct]);
-  const double* f = F + (int64_t)cr * nt + ct;
-  const double f00 = __ldg(f), f01 = __ldg(f + 1), f10 = __ldg(f + nt), f11 = __ldg(f + nt + 1);
-  const double lo = (1.0 - wt) * f00 + wt * f01;
-  const double hi = (1.0 - wt) * f10 + wt * f11;
-  v = (1.0 - wr) * lo + wr * hi;
+__device__ __forceinline__ int axis_search(const AxisView& a, uint64_t k) {
+  if (MODE == 0) return search_bucket<1>(a.keys, a.dir, a.shift, a.base, a.nb, k);
+  if (MODE == 1) return search_bucket_bisect(a.keys, a.dir, a.shift, a.base, a.nb, a.T, k);
+  return search_eyt_rt(a.eyt, a.D, k);
 }
 
-template <int MODE>
+// Float-float weight of a target with key k and bits u whose lower-bound index is i.
+__device__ __forceinline__ ff axis_weight_ff(const AxisView& a, int i, int c, uint64_t k, uint64_t u) {
+  if (i >= a.n - 1) return {1.0f, 0.0f};                 // above the last entry
+  if (i == 0 && k <= a.k0) return {0.0f, 0.0f};          // at or below the first entry
+  return ff_clamp01(cell_weight(u, a.cells[c]));
+}
+
+// Convex blend in fp64 (fallback path of a pair).
+__device__ __forceinline__ double blend64(double wr, double wt, double f00, double f01, double f10, double f11) {
+  const double lo = (1.0 - wt) * f00 + wt * f01;
+  const double hi = (1.0 - wt) * f10 + wt * f11;
+  return (1.0 - wr) * lo + wr * hi;
+}
+
+// One pair: indices and value.  MODE 0: both axes bucket with occupancy <= 1;
+// 1: bucket with bounded bisection; 2: breadth-first binary.  FF: arithmetic path.
+template <int MODE, bool FF>
+__device__ __forceinline__ void lookup_pair(const AxisView& vr, const AxisView& vt, const double* __restrict__ F,
+                                            int nt, double rho, double tem, int& ir, int& it, double& v, int& nans) {
+  const uint64_t ur = static_cast<uint64_t>(__double_as_longlong(rho));
+  const uint64_t ut = static_cast<uint64_t>(__double_as_longlong(tem));
+  const uint64_t kr = order_key(rho), kt = order_key(tem);
+  const bool nan = (kr < 0x0010000000000000ull) | (kt < 0x0010000000000000ull);
+  nans += (kr < 0x0010000000000000ull) + (kt < 0x0010000000000000ull);
+  ir = axis_search<MODE>(vr, kr);
+  it = axis_search<MODE>(vt, kt);
+  const int cr = min(ir, vr.n - 2), ct = min(it, nt - 2);
+  const double* f = F + (int64_t)cr * nt + ct;
+  const double f00 = __ldg(f), f01 = __ldg(f + 1), f10 = __ldg(f + nt), f11 = __ldg(f + nt + 1);
+  if (!FF) {
+    const double wr = clamp01((rho - __longlong_as_double((long long)vr.cells[cr].xbits)) * vr.rg[cr]);
+    const double wt = clamp01((tem - __longlong_as_double((long long)vt.cells[ct].xbits)) * vt.rg[ct]);
+    v = blend64(wr, wt, f00, f01, f10, f11);
+    return;
+  }
+  const ff wr = axis_weight_ff(vr, ir, cr, kr, ur);
+  const ff wt = axis_weight_ff(vt, it, ct, kt, ut);
+  ff a00, a01, a10, a11;
+  const bool ok = d2ff(f00, a00) & d2ff(f01, a01) & d2ff(f10, a10) & d2ff(f11, a11);
+  if (nan) {
+    v = __longlong_as_double(0x7FF8000000000000ll);
+  } else if (ok) {
+    const ff omt = ff_one_minus(wt), omr = ff_one_minus(wr);
+    const ff lo = ff_add(ff_mul(omt, a00), ff_mul(wt, a01));
+    const ff hi = ff_add(ff_mul(omt, a10), ff_mul(wt, a11));
+    v = ff2d(ff_add(ff_mul(omr, lo), ff_mul(wr, hi)));
+  } else {
+    v = blend64(ff2d(wr), ff2d(wt), f00, f01, f10, f11);
+  }
+}
+
+template <int MODE, bool FF>
 __device__ __forceinline__ int stream_pairs(const Args2D& a, const AxisView& vr, const AxisView& vt) {
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gs = (int64_t)gridDim.x * blockDim.x;
@@ -114,7 +186,7 @@ __device__ __forceinline__ int stream_pairs(const Args2D& a, const AxisView& vr,
   auto scalar = [&](int64_t i) {
     int ir, it;
     double v;
-    lookup_pair<MODE>(vr, vt, a.F, a.nt, a.Y2[2 * i], a.Y2[2 * i + 1], ir, it, v, nans);
+    lookup_pair<MODE, FF>(vr, vt, a.F, a.nt, a.Y2[2 * i], a.Y2[2 * i + 1], ir, it, v, nans);
     a.idx[2 * i] = ir;
     a.idx[2 * i + 1] = it;
     a.val[i] = v;
@@ -127,8 +199,8 @@ __device__ __forceinline__ int stream_pairs(const Args2D& a, const AxisView& vr,
     const double2 p0 = ld_stream(Y + 2 * g), p1 = ld_stream(Y + 2 * g + 1);
     int i0, j0, i1, j1;
     double v0, v1;
-    lookup_pair<MODE>(vr, vt, a.F, a.nt, p0.x, p0.y, i0, j0, v0, nans);
-    lookup_pair<MODE>(vr, vt, a.F, a.nt, p1.x, p1.y, i1, j1, v1, nans);
+    lookup_pair<MODE, FF>(vr, vt, a.F, a.nt, p0.x, p0.y, i0, j0, v0, nans);
+    lookup_pair<MODE, FF>(vr, vt, a.F, a.nt, p1.x, p1.y, i1, j1, v1, nans);
     st_stream(I4 + g, make_int4(i0, j0, i1, j1));
     st_stream(V2 + g, make_double2(v0, v1));
   }
@@ -146,14 +218,24 @@ __global__ void __launch_bounds__(kNumThreads) k_search_interp_2d(Args2D a) {
   const AxisView vr = view_of(a.ar, smem), vt = view_of(a.at, smem);
   const TableHdr& hr = *reinterpret_cast<const TableHdr*>(smem + a.ar.lay.hdr);
   const TableHdr& ht = *reinterpret_cast<const TableHdr*>(smem + a.at.lay.hdr);
+  const bool ff = !a.force_fp64 && reinterpret_cast<const AxisAux*>(smem + a.ar.aux)->ffok &&
+                  reinterpret_cast<const AxisAux*>(smem + a.at.aux)->ffok;
+  const int mode = a.algo == SS_ALGO_BINARY ? 2 : (hr.occ <= 1 && ht.occ <= 1) ? 0 : 1;
   int nans;
-  if (a.algo == SS_ALGO_BINARY) nans = stream_pairs<2>(a, vr, vt);
-  else if (hr.occ <= 1 && ht.occ <= 1) nans = stream_pairs<0>(a, vr, vt);
-  else nans = stream_pairs<1>(a, vr, vt);
+  if (ff) {
+    nans = mode == 0 ? stream_pairs<0, true>(a, vr, vt)
+         : mode == 1 ? stream_pairs<1, true>(a, vr, vt) : stream_pairs<2, true>(a, vr, vt);
+  } else {
+    nans = mode == 0 ? stream_pairs<0, false>(a, vr, vt)
+         : mode == 1 ? stream_pairs<1, false>(a, vr, vt) : stream_pairs<2, false>(a, vr, vt);
+  }
   nans = __reduce_add_sync(0xFFFFFFFFu, nans);
   if (a.stat != nullptr) {
     if ((threadIdx.x & 31) == 0 && nans) atomicAdd(&a.stat->nan_targets, (unsigned long long)nans);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && (hr.bad | ht.bad)) atomicOr(&a.stat->flags, SS_FLAG_NOT_SORTED);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (hr.bad | ht.bad) atomicOr(&a.stat->flags, SS_FLAG_NOT_SORTED);
+      if (!ff && !a.force_fp64) atomicOr(&a.stat->flags, SS_FLAG_BAD_VALUE);
+    }
   }
 }
 
@@ -164,17 +246,17 @@ static Axis2D make_axis(int n, int algo, int offset) {
   const bool bucket = algo == SS_ALGO_BUCKET;
   ax.lay = make_layout_1d(n, bucket, !bucket, bucket ? default_dir_cap(n) : 0, offset);
   int off = ax.lay.bytes;
-  ax.cx = off;
-  off += ((n - 1) * 8 + 15) & ~15;
-  ax.cg = off;
-  off += ((n - 1) * 8 + 15) & ~15;
+  auto take = [&](int bytes) { int o = off; off += (bytes + 15) & ~15; return o; };
+  ax.cells = take((n - 1) * (int)sizeof(CellFF));
+  ax.rg = take((n - 1) * 8);
+  ax.aux = take((int)sizeof(AxisAux));
   ax.lay.bytes = off;   // end of this axis' region
   return ax;
 }
 
 ss_status search_interp_2d(const double* R, int32_t nr, const double* T, int32_t nt, const double* F,
-                           const double* Y2, int64_t m, int32_t* idx, double* val, int32_t algo, ss_devstat* stat,
-                           cudaStream_t stream) {
+                           const double* Y2, int64_t m, int32_t* idx, double* val, int32_t algo, int force_fp64,
+                           ss_devstat* stat, cudaStream_t stream) {
   if (R == nullptr || T == nullptr || F == nullptr || (m > 0 && (Y2 == nullptr || idx == nullptr || val == nullptr)))
     return fail(SS_EINVAL, "ss_search_interp_2d: null pointer");
   if (nr < 2 || nt < 2) return fail(SS_EINVAL, "ss_search_interp_2d: each axis needs >= 2 entries");
@@ -188,7 +270,7 @@ ss_status search_interp_2d(const double* R, int32_t nr, const double* T, int32_t
   if (m == 0) return SS_OK;
   Args2D a{};
   a.R = R; a.nr = nr; a.T = T; a.nt = nt; a.F = F; a.Y2 = Y2; a.m = m; a.idx = idx; a.val = val;
-  a.algo = algo; a.stat = stat;
+  a.algo = algo; a.force_fp64 = force_fp64; a.stat = stat;
   a.ar = make_axis(nr, algo, 0);
   a.at = make_axis(nt, algo, a.ar.lay.bytes);
   const int smem = a.at.lay.bytes;
@@ -216,8 +298,20 @@ ss_status search_interp_2d(const double* R, int32_t nr, const double* T, int32_t
 
 }  // namespace ss
 
-extern "C" ss_status ss_search_interp_2d(const double* R, int32_t nr, const double* T, int32_t nt, const double* F,
-                                         const double* Y2, int64_t m, int32_t* lowbounds2, double* values,
-                                         int32_t algo, ss_devstat* stat, cudaStream_t stream) {
-  return ss::search_interp_2d(R, nr, T, nt, F, Y2, m, lowbounds2, values, algo, stat, stream);
+extern "C" {
+
+ss_status ss_search_interp_2d(const double* R, int32_t nr, const double* T, int32_t nt, const double* F,
+                              const double* Y2, int64_t m, int32_t* lowbounds2, double* values, int32_t algo,
+                              ss_devstat* stat, cudaStream_t stream) {
+  return ss::search_interp_2d(R, nr, T, nt, F, Y2, m, lowbounds2, values, algo, 0, stat, stream);
 }
+
+// Same lookup with the float-float path disabled (fp64 weights and blend);
+// for comparisons and tables outside the float-float preconditions.
+ss_status ss_search_interp_2d_fp64(const double* R, int32_t nr, const double* T, int32_t nt, const double* F,
+                                   const double* Y2, int64_t m, int32_t* lowbounds2, double* values, int32_t algo,
+                                   ss_devstat* stat, cudaStream_t stream) {
+  return ss::search_interp_2d(R, nr, T, nt, F, Y2, m, lowbounds2, values, algo, 1, stat, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// plan.h -- structures shared by the plan's host code and its kernels.
+#pragma once
+
+#include "ss_plan.cuh"
+
+namespace ss {
+
+__host__ __device__ inline BlobGeom blob_geom_dev(int n, int dir_cap, bool cells) {
+  BlobGeom g{};
+  const int nk = n - 1;
+  g.stride = 1;
+  while ((nk + g.stride - 1) / g.stride > kMaxSmemKeys) g.stride <<= 1;
+  g.ns = (nk + g.stride - 1) / g.stride;
+  g.P = ceil_pow2(g.ns + 1);
+  g.D = ilog2(g.P);
+  int off = (int)sizeof(BlobHdr);
+  g.off_mlp = off;  off += kMlpBytes;
+  g.off_dir = off;  off += (((dir_cap + 1) * 4) + 15) & ~15;
+  g.off_keys = off; off += (g.ns + kPad) * 8;
+  g.off_eyt = off;  off += g.P * 8;
+  g.off_cells = -1;
+  if (cells) { g.off_cells = off; off += ((n * (int)sizeof(CellFF)) + 15) & ~15; }
+  g.staged_end = off;
+  g.off_full = g.stride > 1 ? off : -1;
+  g.bytes = g.stride > 1 ? (int64_t)off + (int64_t)(nk + kPad) * 8 : off;
+  g.bytes = (g.bytes + 15) & ~(int64_t)15;
+  return g;
+}
+
+struct Tile {            // a contiguous run of targets of one table
+  int table;
+  int count;
+  int64_t begin;         // index of the first target (pair for 2D) in Y / out
+};
+
+struct PrepArgs {
+  int ntables;
+  const int64_t* X_off;  // device
+  const double* X;
+  unsigned char* blobs;
+  const int64_t* blob_off;
+  const int* dir_cap;
+  const int* algo;
+  int cells;
+  unsigned* bad_flag;
+};
+
+struct TrainArgs {
+  int ntables;
+  unsigned char* blobs;
+  const int64_t* blob_off;
+  int epochs;
+  float lr;
+  uint64_t seed;
+};
+
+struct WindowArgs {
+  int ntables;
+  unsigned char* blobs;
+  const int64_t* blob_off;
+  uint64_t seed;
+};
+
+struct BatchArgs1D {
+  const unsigned char* blobs;
+  const int64_t* blob_off;
+  const Tile* tiles;
+  int ntiles;
+  int* counter;
+  const double* Y;
+  int32_t* out;
+  int vec;               // Y and out 16-byte aligned: 128-bit path inside tiles
+  ss_devstat* stat;
+};
+
+struct BatchArgs2D {
+  const unsigned char* blobs;
+  const int64_t* blob_off;      // [2*ntables]: rho axis, T axis
+  const float2* grid;           // float-float values of all tables
+  const double* grid64;         // the caller's fp64 values (fallback)
+  const int64_t* grid_off;      // [ntables]
+  const Tile* tiles;
+  int ntiles;
+  int* counter;
+  const double* Y2;
+  int32_t* idx;
+  double* val;
+  int vec;
+  ss_devstat* stat;
+};
+
+__global__ void k_prep_1d(PrepArgs a);
+__global__ void k_train_mlp(TrainArgs a);
+__global__ void k_window(WindowArgs a);
+const void* batched_1d_kernel(bool le);
+__global__ void k_batched_2d(BatchArgs2D a);
+__global__ void k_grid_to_ff(const double* F, float2* G, int64_t count, unsigned* bad);
+__global__ void k_prep_cells(PrepArgs a);
+
+}  // namespace ss

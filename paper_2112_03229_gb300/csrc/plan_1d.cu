@@ -1,0 +1,363 @@
+// plan_1d.cu -- device side of 1D plans: table preparation (keys, bucket
+// directory / spline knots, breadth-first layout, MLP initialisation),
+// on-GPU training of the MLP position model, the learned half-window, and the
+// persistent batched search kernel that walks a tile queue.
+#include "learned.cuh"
+#include "plan.h"
+
+namespace ss {
+
+// ---------------------------------------------------------------------------
+// Counter-based generator (SplitMix64, Steele, Lea & Flood 2014) for the
+// training targets of the position model.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// Inverse of order_key for keys of non-NaN doubles.
+__device__ __forceinline__ double key_to_double(uint64_t k) {
+  const uint64_t u = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : (0ull - k);
+  return __longlong_as_double((long long)u);
+}
+
+// ---------------------------------------------------------------------------
+// Preparation: one block per table.  Writes the blob of table k.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_prep_1d(PrepArgs a) {
+  const int k = blockIdx.x;
+  if (k >= a.ntables) return;
+  const double* X = a.X + a.X_off[k];
+  const int n = (int)(a.X_off[k + 1] - a.X_off[k]);
+  unsigned char* blob = a.blobs + a.blob_off[k];
+  const BlobGeom g = blob_geom_dev(n, a.dir_cap[k], a.cells);
+  BlobHdr* h = reinterpret_cast<BlobHdr*>(blob);
+  uint64_t* keys = reinterpret_cast<uint64_t*>(blob + g.off_keys);
+  uint64_t* eyt = reinterpret_cast<uint64_t*>(blob + g.off_eyt);
+  int* dir = reinterpret_cast<int*>(blob + g.off_dir);
+  float* mlp = reinterpret_cast<float*>(blob + g.off_mlp);
+  uint64_t* full = g.off_full >= 0 ? reinterpret_cast<uint64_t*>(blob + g.off_full) : nullptr;
+  const int nk = n - 1, tid = threadIdx.x, nt = blockDim.x;
+  __shared__ int s_bad, s_occ, s_shift, s_nb;
+  __shared__ uint64_t s_base;
+  if (tid == 0) { s_bad = 0; s_occ = 0; }
+  __syncthreads();
+  bool bad = false;
+  for (int j = tid; j < nk; j += nt) bad |= !(X[j + 1] > X[j]);
+  if (bad) atomicOr(&s_bad, 1);
+  // keys: staged sample (last key of each stride block) and, for big tables, all keys
+  for (int s = tid; s < g.ns + kPad; s += nt)
+    keys[s] = s < g.ns ? order_key(X[min((s + 1) * g.stride, nk)]) : kKeyMax;
+  if (full != nullptr)
+    for (int j = tid; j < nk + kPad; j += nt) full[j] = j < nk ? order_key(X[j + 1]) : kKeyMax;
+  for (int i = tid; i < g.P; i += nt) {
+    if (i == 0) { eyt[0] = kKeyMax; continue; }
+    const int r = eyt_rank(i, g.D);
+    eyt[i] = r < g.ns ? order_key(X[min((r + 1) * g.stride, nk)]) : kKeyMax;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const uint64_t k0 = keys[0], k1 = keys[g.ns - 1];
+    int s = 0;
+    while (s < 63 && ((k1 >> s) - (k0 >> s)) >= (uint64_t)a.dir_cap[k]) ++s;
+    s_shift = s;
+    s_base = k0 >> s;
+    s_nb = (int)min((k1 >> s) - (k0 >> s) + 1, (uint64_t)a.dir_cap[k]);
+  }
+  __syncthreads();
+  const int shift = s_shift, nb = s_nb;
+  const uint64_t base = s_base;
+  for (int b = tid; b <= nb; b += nt) dir[b] = b == nb ? g.ns : lower_count(keys, g.ns, (base + (uint64_t)b) << shift);
+  __syncthreads();
+  int occ = 0;
+  for (int b = tid; b < nb; b += nt) occ = max(occ, dir[b + 1] - dir[b]);
+  occ = __reduce_max_sync(0xFFFFFFFFu, occ);
+  if ((tid & 31) == 0) atomicMax(&s_occ, occ);
+  // MLP feature scaling and initial parameters: hinge units spread evenly over
+  // the normalised log2 coordinate z = x0 + e_scale * x1 of the table's range
+  const uint64_t u0 = static_cast<uint64_t>(__double_as_longlong(X[0]));
+  const uint64_t u1 = static_cast<uint64_t>(__double_as_longlong(X[nk]));
+  const float e_lo = (float)((int)((u0 >> 52) & 0x7FF) - 1023);
+  const float e_hi = (float)((int)((u1 >> 52) & 0x7FF) - 1023);
+  const float e_scale = 1.0f / fmaxf(e_hi - e_lo + 1.0f, 1.0f);
+  if (tid < kHidden) {
+    mlp[2 * tid] = 1.0f;
+    mlp[2 * tid + 1] = e_scale;
+    mlp[2 * kHidden + tid] = -((float)tid + 0.5f) / (float)kHidden;
+    mlp[3 * kHidden + tid] = 0.0f;
+  }
+  if (tid == kHidden) {
+    mlp[4 * kHidden] = 0.5f;
+    for (int i = kMlpParams; i < kMlpBytes / 4; ++i) mlp[i] = 0.0f;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    BlobHdr hh{};
+    hh.n = n; hh.nk = nk; hh.ns = g.ns; hh.stride = g.stride;
+    hh.algo = a.algo[k];
+    hh.D = g.D;
+    hh.shift = shift; hh.nb = nb; hh.occ = s_occ;
+    hh.E = s_occ;                              // spline window: the bucket occupancy bounds its error
+    int S0 = 1;
+    const int G = hh.algo == BL_BALLOT8 ? 8 : hh.algo == BL_BALLOT16 ? 16 : 32;
+    while ((int64_t)S0 * (G + 1) < (int64_t)g.ns + 1) S0 *= (G + 1);
+    hh.S0 = S0;
+    hh.dir_cap = a.dir_cap[k];
+    hh.off_mlp = g.off_mlp; hh.off_dir = g.off_dir; hh.off_keys = g.off_keys; hh.off_eyt = g.off_eyt;
+    hh.staged_end = g.staged_end;
+    hh.off_full = g.off_full;
+    hh.base = base;
+    hh.k0 = order_key(X[0]);
+    hh.e_lo = e_lo; hh.e_scale = e_scale;
+    hh.loss = 0.0f;
+    hh.off_cells = g.off_cells;
+    hh.ffok = 0;
+    *h = hh;
+    if (s_bad) atomicOr(a.bad_flag, 1u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// MLP training: one block per table, full-batch Adam over a training set of
+// table keys (every entry, or an evenly strided subset) and targets drawn
+// uniformly in key space over the table range with SplitMix64.  Labels are
+// exact counts of keys below each sample, normalised by n-1.
+// ---------------------------------------------------------------------------
+constexpr int kTrainThreads = 256;
+constexpr int kTrainSamples = 2048;
+
+__device__ __forceinline__ int count_keys_below(const StagedView& v, uint64_t q) { return plain_bucket(v, q); }
+
+__global__ void __launch_bounds__(kTrainThreads) k_train_mlp(TrainArgs a) {
+  const int k = blockIdx.x;
+  if (k >= a.ntables) return;
+  unsigned char* blob = a.blobs + a.blob_off[k];
+  BlobHdr* gh = reinterpret_cast<BlobHdr*>(blob);
+  const BlobHdr h = *gh;
+  __shared__ float xs[kTrainSamples][2];
+  __shared__ float ys[kTrainSamples];
+  __shared__ float p[kMlpParams];
+  __shared__ float red[kTrainThreads / 32][kMlpParams + 1];
+  float* gp = reinterpret_cast<float*>(blob + h.off_mlp);
+  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) p[i] = gp[i];
+  // global view of the blob for labelling (no staging needed: reads hit L2)
+  StagedView v;
+  v.h = gh;
+  v.dir = reinterpret_cast<const int*>(blob + h.off_dir);
+  v.keys = reinterpret_cast<const uint64_t*>(blob + h.off_keys);
+  v.full = h.off_full >= 0 ? reinterpret_cast<const uint64_t*>(blob + h.off_full) : nullptr;
+  const MlpFeatScale sc{h.e_lo, h.e_scale};
+  const uint64_t k0 = h.k0, k1 = h.stride == 1 ? v.keys[h.nk - 1] : v.full[h.nk - 1];
+  const int nkeys = min(h.n, kTrainSamples / 2);
+  const float inv = 1.0f / (float)max(h.nk, 1);
+  for (int i = threadIdx.x; i < kTrainSamples; i += blockDim.x) {
+    uint64_t q;
+    if (i < nkeys) {
+      // table entry j (evenly strided), nudged to just above the entry so its count includes it
+      const int j = (int)(((int64_t)i * (h.n - 1)) / max(nkeys - 1, 1));
+      q = (j == 0 ? k0 : (h.stride == 1 ? v.keys[j - 1] : v.full[j - 1])) + 1;
+    } else {
+      const uint64_t r = splitmix64(a.seed ^ ((uint64_t)k << 32) ^ (uint64_t)i);
+      q = k0 + (uint64_t)((double)(r >> 11) * 0x1.0p-53 * (double)(k1 - k0));
+    }
+    const double t = key_to_double(q);
+    float x0, x1;
+    mlp_features(t, sc, x0, x1);
+    xs[i][0] = x0;
+    xs[i][1] = x1;
+    ys[i] = (float)count_keys_below(v, q) * inv;
+  }
+  __syncthreads();
+  float m1 = 0.0f, m2 = 0.0f;     // Adam moments of parameter threadIdx.x
+  const float lr = a.lr, b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float scale = 1.0f / (float)kTrainSamples;
+  float loss = 0.0f;
+  for (int step = 1; step <= a.epochs; ++step) {
+    float g[kMlpParams];
+#pragma unroll
+    for (int i = 0; i < kMlpParams; ++i) g[i] = 0.0f;
+    float l = 0.0f;
+    for (int i = threadIdx.x; i < kTrainSamples; i += blockDim.x) l += mlp_backward_accum(p, xs[i][0], xs[i][1], ys[i], scale, g);
+    block_reduce_params(g, l, red);
+    loss = red[0][kMlpParams] * scale;
+    if (threadIdx.x < kMlpParams) {
+      const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+      float pv = p[threadIdx.x];
+      adam_update(pv, red[0][threadIdx.x], m1, m2, lr, b1, b2, eps, c1, c2);
+      p[threadIdx.x] = pv;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) gp[i] = p[i];
+  if (threadIdx.x == 0) gh->loss = loss;
+}
+
+// ---------------------------------------------------------------------------
+// Learned half-window: the largest |proposal - exact count| over probes
+// (every key, one unit above it, and key-space samples), plus one.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_window(WindowArgs a) {
+  const int k = blockIdx.x;
+  if (k >= a.ntables) return;
+  unsigned char* blob = a.blobs + a.blob_off[k];
+  BlobHdr* gh = reinterpret_cast<BlobHdr*>(blob);
+  const BlobHdr h = *gh;
+  if (h.algo != BL_SPLINE && h.algo != BL_MLP) return;
+  StagedView v;
+  v.h = gh;
+  v.mlp = reinterpret_cast<const float*>(blob + h.off_mlp);
+  v.dir = reinterpret_cast<const int*>(blob + h.off_dir);
+  v.keys = reinterpret_cast<const uint64_t*>(blob + h.off_keys);
+  v.full = h.off_full >= 0 ? reinterpret_cast<const uint64_t*>(blob + h.off_full) : nullptr;
+  const MlpFeatScale sc{h.e_lo, h.e_scale};
+  __shared__ int s_err;
+  if (threadIdx.x == 0) s_err = 0;
+  __syncthreads();
+  const uint64_t k0 = h.k0, k1 = key_at(v, h.nk - 1);
+  int err = 0;
+  const int nprobe = 2 * h.nk + 4096;
+  for (int i = threadIdx.x; i < nprobe; i += blockDim.x) {
+    uint64_t q;
+    if (i < 2 * h.nk) q = key_at(v, i >> 1) + (uint64_t)(i & 1);
+    else q = k0 + (uint64_t)((double)(splitmix64(a.seed ^ ((uint64_t)k << 40) ^ (uint64_t)i) >> 11) * 0x1.0p-53 *
+                             (double)(k1 - k0));
+    const int c = plain_bucket(v, q);
+    const int prop = h.algo == BL_SPLINE ? spline_propose(v.dir, h.shift, h.base, h.nb, q)
+                                         : mlp_propose(v.mlp, sc, h.n, key_to_double(q));
+    err = max(err, abs(prop - c));
+  }
+  err = __reduce_max_sync(0xFFFFFFFFu, err);
+  if ((threadIdx.x & 31) == 0) atomicMax(&s_err, err);
+  __syncthreads();
+  if (threadIdx.x == 0) gh->E = s_err + 1;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent batched search.  Each block takes tiles from a global counter
+// (one atomicAdd per tile), stages the tile's table with a TMA bulk copy when
+// it differs from the one already in shared memory, and streams the tile's
+// targets.  Targets of a tile are contiguous in Y / out.
+// ---------------------------------------------------------------------------
+template <bool LE>
+__device__ __forceinline__ int count_for(const StagedView& v, int algo, double t, uint64_t q, int& fallbacks) {
+  switch (algo) {
+    case BL_BINARY: return plain_binary(v, q);
+    case BL_SPLINE: return spline_count(v, q, fallbacks);
+    case BL_MLP: return mlp_count(v, t, q, fallbacks);
+    default: return plain_bucket(v, q);
+  }
+}
+
+template <int G>
+__device__ __forceinline__ void ballot_tile(const StagedView& v, const double* __restrict__ Y, int32_t* __restrict__ out,
+                                            int64_t b, int cnt, uint64_t le, int& nans) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int gbase = lane & ~(G - 1);
+  const BlobHdr& h = *v.h;
+  for (int base = w * 32; base < cnt; base += nw * 32) {
+    const int i = base + lane;
+    const bool ok = i < cnt;
+    uint64_t q = 0;
+    if (ok) {
+      const uint64_t k = order_key(Y[b + i]);
+      nans += k < 0x0010000000000000ull;
+      q = k + le;
+    }
+    int r = 0;
+    for (int src = 0; src < G; ++src) {
+      const uint64_t qq = __shfl_sync(0xFFFFFFFFu, q, gbase + src);
+      const int c = finish_full(v, search_ballot<G>(v.keys, h.ns, h.S0, qq), qq);
+      if ((lane & (G - 1)) == src) r = c;
+    }
+    if (ok) out[b + i] = r;
+  }
+}
+
+template <bool LE>
+__global__ void __launch_bounds__(kNumThreads) k_batched_1d(BatchArgs1D a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bar;
+  __shared__ int s_tile;
+  __shared__ int s_err;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    s_err = 0;
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  int cur_table = -1;
+  StagedView v{};
+  bool ok = true;
+  int nans = 0, fallbacks = 0;
+  const uint64_t le = LE ? 1 : 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int t = s_tile;
+    __syncthreads();                      // everyone has read s_tile before it is rewritten
+    if (t >= a.ntiles) break;
+    const Tile tile = a.tiles[t];
+    if (tile.table != cur_table) {
+      v = stage_blob(a.blobs + a.blob_off[tile.table], smem, &bar, phase, ok);
+      cur_table = tile.table;
+      if (!ok) break;
+    }
+    const int algo = v.h->algo;
+    const int64_t b = tile.begin;
+    const int cnt = tile.count;
+    if (algo >= BL_BALLOT8 && algo <= BL_BALLOT32) {
+      if (algo == BL_BALLOT8) ballot_tile<8>(v, a.Y, a.out, b, cnt, le, nans);
+      else if (algo == BL_BALLOT16) ballot_tile<16>(v, a.Y, a.out, b, cnt, le, nans);
+      else ballot_tile<32>(v, a.Y, a.out, b, cnt, le, nans);
+      continue;
+    }
+    // scalar head up to a 4-target boundary, quads with 128-bit I/O, scalar tail
+    const int head = a.vec ? min(cnt, (int)((-b) & 3)) : cnt;
+    const int nq = (cnt - head) >> 2;
+    for (int i = threadIdx.x; i < head; i += blockDim.x) {
+      const double y = a.Y[b + i];
+      const uint64_t k = order_key(y);
+      nans += k < 0x0010000000000000ull;
+      a.out[b + i] = count_for<LE>(v, algo, y, k + le, fallbacks);
+    }
+    const double2* Y2 = reinterpret_cast<const double2*>(a.Y + b + head);
+    int4* O4 = reinterpret_cast<int4*>(a.out + b + head);
+    for (int g = threadIdx.x; g < nq; g += blockDim.x) {
+      const double2 p0 = ld_stream(Y2 + 2 * g), p1 = ld_stream(Y2 + 2 * g + 1);
+      const double y[4] = {p0.x, p0.y, p1.x, p1.y};
+      int r[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint64_t k = order_key(y[j]);
+        nans += k < 0x0010000000000000ull;
+        r[j] = count_for<LE>(v, algo, y[j], k + le, fallbacks);
+      }
+      st_stream(O4 + g, make_int4(r[0], r[1], r[2], r[3]));
+    }
+    for (int i = head + 4 * nq + threadIdx.x; i < cnt; i += blockDim.x) {
+      const double y = a.Y[b + i];
+      const uint64_t k = order_key(y);
+      nans += k < 0x0010000000000000ull;
+      a.out[b + i] = count_for<LE>(v, algo, y, k + le, fallbacks);
+    }
+  }
+  if (!ok && threadIdx.x == 0) s_err = 1;
+  __syncthreads();
+  nans = __reduce_add_sync(0xFFFFFFFFu, nans);
+  fallbacks = __reduce_add_sync(0xFFFFFFFFu, fallbacks);
+  if (a.stat != nullptr && (threadIdx.x & 31) == 0) {
+    if (nans) atomicAdd(&a.stat->nan_targets, (unsigned long long)nans);
+    if (fallbacks) atomicAdd(&a.stat->fallbacks, (unsigned long long)fallbacks);
+  }
+  if (a.stat != nullptr && threadIdx.x == 0 && s_err) atomicOr(&a.stat->flags, SS_FLAG_STAGING_TIMEOUT);
+}
+
+// Kernel entry of the batched search (template stubs stay local to this unit).
+const void* batched_1d_kernel(bool le) {
+  return le ? reinterpret_cast<const void*>(&k_batched_1d<true>) : reinterpret_cast<const void*>(&k_batched_1d<false>);
+}
+
+}  // namespace ss

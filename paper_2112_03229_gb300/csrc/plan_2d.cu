@@ -1,0 +1,363 @@
+// plan_2d.cu -- 2D plans: many density x temperature tables (Sec. 1, 2.2),
+// each axis prepared like a 1D table (with its own learned proposal when a
+// model is requested) plus per-cell float-float weight data, the value grids
+// converted once to float-float, and a persistent kernel over a tile queue
+// of (table, pair range) work items.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "plan.h"
+#include "plan_host.h"
+
+namespace ss {
+
+int default_dir_cap(int n);
+
+// Per-cell data of one axis blob (n cells: the last one only holds X[n-1]).
+__global__ void __launch_bounds__(256) k_prep_cells(PrepArgs a) {
+  const int k = blockIdx.x;
+  if (k >= a.ntables) return;
+  const double* X = a.X + a.X_off[k];
+  const int n = (int)(a.X_off[k + 1] - a.X_off[k]);
+  unsigned char* blob = a.blobs + a.blob_off[k];
+  BlobHdr* h = reinterpret_cast<BlobHdr*>(blob);
+  CellFF* cells = reinterpret_cast<CellFF*>(blob + h->off_cells);
+  bool ok = true;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    const double lo = X[c];
+    const uint64_t ua = static_cast<uint64_t>(__double_as_longlong(lo));
+    float ghi = 0.0f, glo = 0.0f;
+    if (c < n - 1) {
+      const double hi = X[c + 1];
+      const double gap = hi - lo;
+      const uint64_t ub = static_cast<uint64_t>(__double_as_longlong(hi));
+      const int ea = (int)((ua >> 52) & 0x7FF), eb = (int)((ub >> 52) & 0x7FF);
+      const bool cell_ok = (ua >> 63) == 0 && ea >= kFFMinExp && eb <= kFFMaxExp && eb - ea <= kMaxCellOctaves &&
+                           gap > 0.0;
+      if (cell_ok) {
+        const double g = ldexp(1.0, ea - 1075) / gap;
+        ghi = __double2float_rn(g);
+        glo = __double2float_rn(g - (double)ghi);
+      }
+      ok &= cell_ok && isfinite(ghi) && fabsf(ghi) >= 1.0e-36f;
+    }
+    cells[c] = CellFF{ua, ghi, glo};
+  }
+  ok = __syncthreads_and(ok);
+  if (threadIdx.x == 0) h->ffok = ok ? 1 : 0;
+}
+
+// Value grid to float-float; values that cannot be split (outside
+// [2^-70, 2^101) in magnitude, not zero) are marked with a NaN high part and
+// set *bad so the plan keeps an fp64 copy for them.
+__global__ void k_grid_to_ff(const double* __restrict__ F, float2* __restrict__ G, int64_t count, unsigned* bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    ff r;
+    if (d2ff(F[i], r)) {
+      G[i] = make_float2(r.hi, r.lo);
+    } else {
+      G[i] = make_float2(__int_as_float(0x7FC00000), 0.0f);
+      atomicOr(bad, 1u);
+    }
+  }
+}
+
+// Exact count for one axis with the axis' algorithm.
+__device__ __forceinline__ int axis_count(const StagedView& v, double t, uint64_t q, int& fallbacks) {
+  switch (v.h->algo) {
+    case BL_BINARY: return plain_binary(v, q);
+    case BL_SPLINE: return spline_count(v, q, fallbacks);
+    case BL_MLP: return mlp_count(v, t, q, fallbacks);
+    default: return plain_bucket(v, q);
+  }
+}
+
+// Weight of a coordinate on an axis (float-float; fp64 division when the axis
+// is outside the float-float preconditions).
+__device__ __forceinline__ ff axis_weight(const StagedView& v, int i, int c, uint64_t k, double x) {
+  const BlobHdr& h = *v.h;
+  if (i >= h.n - 1) return {1.0f, 0.0f};
+  if (i == 0 && k <= h.k0) return {0.0f, 0.0f};
+  if (h.ffok) return ff_clamp01(cell_weight(static_cast<uint64_t>(__double_as_longlong(x)), v.cells[c]));
+  const double a = __longlong_as_double((long long)v.cells[c].xbits);
+  const double b = __longlong_as_double((long long)v.cells[c + 1].xbits);
+  double w = (x - a) / (b - a);
+  w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
+  ff r;
+  r.hi = __double2float_rn(w);
+  r.lo = __double2float_rn(w - (double)r.hi);
+  return r;
+}
+
+__device__ __forceinline__ void pair_2d(const StagedView& vr, const StagedView& vt, const float2* __restrict__ G,
+                                        const double* __restrict__ G64, double rho, double tem, int& ir, int& it,
+                                        double& v, int& nans, int& fallbacks) {
+  const uint64_t kr = order_key(rho), kt = order_key(tem);
+  const bool nan = (kr < 0x0010000000000000ull) | (kt < 0x0010000000000000ull);
+  nans += (kr < 0x0010000000000000ull) + (kt < 0x0010000000000000ull);
+  ir = axis_count(vr, rho, kr, fallbacks);
+  it = axis_count(vt, tem, kt, fallbacks);
+  const int nt = vt.h->n;
+  const int cr = min(ir, vr.h->n - 2), ct = min(it, nt - 2);
+  const int64_t o = (int64_t)cr * nt + ct;
+  const float2 g00 = __ldg(G + o), g01 = __ldg(G + o + 1), g10 = __ldg(G + o + nt), g11 = __ldg(G + o + nt + 1);
+  const ff wr = axis_weight(vr, ir, cr, kr, rho);
+  const ff wt = axis_weight(vt, it, ct, kt, tem);
+  if (nan) {
+    v = __longlong_as_double(0x7FF8000000000000ll);
+  } else if (!(isnan(g00.x) | isnan(g01.x) | isnan(g10.x) | isnan(g11.x))) {
+    const ff omt = ff_one_minus(wt), omr = ff_one_minus(wr);
+    const ff lo = ff_add(ff_mul(omt, ff{g00.x, g00.y}), ff_mul(wt, ff{g01.x, g01.y}));
+    const ff hi = ff_add(ff_mul(omt, ff{g10.x, g10.y}), ff_mul(wt, ff{g11.x, g11.y}));
+    v = ff2d(ff_add(ff_mul(omr, lo), ff_mul(wr, hi)));
+  } else {
+    const double w1 = ff2d(wr), w2 = ff2d(wt);
+    const double lo = (1.0 - w2) * G64[o] + w2 * G64[o + 1];
+    const double hi = (1.0 - w2) * G64[o + nt] + w2 * G64[o + nt + 1];
+    v = (1.0 - w1) * lo + w1 * hi;
+  }
+}
+
+__global__ void __launch_bounds__(kNumThreads) k_batched_2d(BatchArgs2D a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bar;
+  __shared__ int s_tile;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  int cur = -1;
+  StagedView vr{}, vt{};
+  int t_off = 0;
+  bool ok = true;
+  int nans = 0, fallbacks = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int t = s_tile;
+    __syncthreads();
+    if (t >= a.ntiles) break;
+    const Tile tile = a.tiles[t];
+    if (tile.table != cur) {
+      const unsigned char* br = a.blobs + a.blob_off[2 * tile.table];
+      const unsigned char* bt = a.blobs + a.blob_off[2 * tile.table + 1];
+      // the rho axis goes first, the T axis at the next 128-byte boundary
+      const BlobHdr* hr = reinterpret_cast<const BlobHdr*>(br);
+      int lo, hi;
+      BlobHdr hcopy;
+      const int4* g4 = reinterpret_cast<const int4*>(hr);
+      int4* c4 = reinterpret_cast<int4*>(&hcopy);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) c4[i] = __ldg(g4 + i);
+      staged_range(hcopy, lo, hi);
+      t_off = (((int)sizeof(BlobHdr) + hi - lo) + 127) & ~127;
+      vr = stage_blob(br, smem, &bar, phase, ok);
+      if (ok) vt = stage_blob(bt, smem + t_off, &bar, phase, ok);
+      cur = tile.table;
+      if (!ok) break;
+    }
+    const float2* G = a.grid + a.grid_off[tile.table];
+    const double* G64 = a.grid64 != nullptr ? a.grid64 + a.grid_off[tile.table] : nullptr;
+    const int64_t b = tile.begin;
+    const int cnt = tile.count;
+    auto scalar = [&](int i) {
+      int ir, it;
+      double v;
+      pair_2d(vr, vt, G, G64, a.Y2[2 * (b + i)], a.Y2[2 * (b + i) + 1], ir, it, v, nans, fallbacks);
+      a.idx[2 * (b + i)] = ir;
+      a.idx[2 * (b + i) + 1] = it;
+      a.val[b + i] = v;
+    };
+    const int head = a.vec ? min(cnt, (int)(b & 1)) : cnt;
+    const int np2 = (cnt - head) >> 1;
+    for (int i = threadIdx.x; i < head; i += blockDim.x) scalar(i);
+    const double2* Y = reinterpret_cast<const double2*>(a.Y2) + b + head;
+    int4* I4 = reinterpret_cast<int4*>(a.idx + 2 * (b + head));
+    double2* V2 = reinterpret_cast<double2*>(a.val + b + head);
+    for (int g = threadIdx.x; g < np2; g += blockDim.x) {
+      const double2 p0 = ld_stream(Y + 2 * g), p1 = ld_stream(Y + 2 * g + 1);
+      int i0, j0, i1, j1;
+      double v0, v1;
+      pair_2d(vr, vt, G, G64, p0.x, p0.y, i0, j0, v0, nans, fallbacks);
+      pair_2d(vr, vt, G, G64, p1.x, p1.y, i1, j1, v1, nans, fallbacks);
+      st_stream(I4 + g, make_int4(i0, j0, i1, j1));
+      st_stream(V2 + g, make_double2(v0, v1));
+    }
+    for (int i = head + 2 * np2 + threadIdx.x; i < cnt; i += blockDim.x) scalar(i);
+  }
+  nans = __reduce_add_sync(0xFFFFFFFFu, nans);
+  fallbacks = __reduce_add_sync(0xFFFFFFFFu, fallbacks);
+  if (a.stat != nullptr && (threadIdx.x & 31) == 0) {
+    if (nans) atomicAdd(&a.stat->nan_targets, (unsigned long long)nans);
+    if (fallbacks) atomicAdd(&a.stat->fallbacks, (unsigned long long)fallbacks);
+  }
+  if (a.stat != nullptr && threadIdx.x == 0 && !ok) atomicOr(&a.stat->flags, SS_FLAG_STAGING_TIMEOUT);
+}
+
+ss_status plan_build_2d(ss_plan* p, const double* R, const double* T, const double* F, cudaStream_t stream) {
+  const int nt = p->ntables;
+  const ss_plan_opts& o = p->opts;
+  p->dir_cap.resize(2 * nt);
+  p->algo.assign(2 * nt, initial_algo(o));
+  p->blob_off.resize(2 * nt);
+  int64_t off = 0;
+  for (int k = 0; k < nt; ++k) {
+    for (int ax = 0; ax < 2; ++ax) {
+      const int n = ax == 0 ? p->sizes[k] : p->sizes_t[k];
+      const int j = 2 * k + ax;
+      p->dir_cap[j] = o.dir_cap > 0 ? o.dir_cap : default_dir_cap(n);
+      p->blob_off[j] = off;
+      off += (blob_geom_dev(n, p->dir_cap[j], true).bytes + 255) & ~(int64_t)255;
+    }
+  }
+  p->blob_bytes = off;
+  for (int b = 0; b < kNumBuckets; ++b) {
+    p->bucket_algo[b] = initial_algo(o);
+    p->bucket_tile[b] = o.tile > 0 ? o.tile : kDefaultTile / 2;
+    p->bucket_tables[b] = 0;
+  }
+  for (int k = 0; k < nt; ++k) p->bucket_tables[size_bucket(std::max(p->sizes[k], p->sizes_t[k]))]++;
+  const int64_t gcount = p->grid_off[nt];
+  std::vector<int64_t> offR(nt), offT(nt), axR(nt + 1), axT(nt + 1);
+  for (int k = 0; k < nt; ++k) { offR[k] = p->blob_off[2 * k]; offT[k] = p->blob_off[2 * k + 1]; }
+  for (int k = 0; k <= nt; ++k) { axR[k] = p->X_off[k]; axT[k] = p->X_off[nt + 1 + k]; }
+  std::vector<int> capR(nt), capT(nt), algR(nt), algT(nt);
+  for (int k = 0; k < nt; ++k) {
+    capR[k] = p->dir_cap[2 * k]; capT[k] = p->dir_cap[2 * k + 1];
+    algR[k] = p->algo[2 * k]; algT[k] = p->algo[2 * k + 1];
+  }
+  std::vector<void*> temps;
+  auto dev_copy = [&](const void* src, size_t bytes) -> void* {
+    void* d = nullptr;
+    if (cudaMalloc(&d, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+    temps.push_back(d);
+    if (cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+    return d;
+  };
+  auto cleanup = [&]() { for (void* d : temps) cudaFree(d); };
+  if (cudaMalloc(&p->d_blobs, p->blob_bytes) != cudaSuccess ||
+      cudaMalloc(&p->d_grid, std::max<int64_t>(gcount, 1) * sizeof(float2)) != cudaSuccess) {
+    return fail(SS_ENOMEM, "plan: device allocation failed");
+  }
+  p->device_bytes = p->blob_bytes + gcount * (int64_t)sizeof(float2);
+  ss_status st = [&]() -> ss_status {
+    SS_CHECK_CUDA(cudaMalloc(&p->d_blob_off, 2 * nt * sizeof(int64_t)));
+    SS_CHECK_CUDA(cudaMemcpy(p->d_blob_off, p->blob_off.data(), 2 * nt * sizeof(int64_t), cudaMemcpyHostToDevice));
+    SS_CHECK_CUDA(cudaMalloc(&p->d_grid_off, (nt + 1) * sizeof(int64_t)));
+    SS_CHECK_CUDA(cudaMemcpy(p->d_grid_off, p->grid_off.data(), (nt + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    auto* dR = (int64_t*)dev_copy(offR.data(), nt * 8);
+    auto* dT = (int64_t*)dev_copy(offT.data(), nt * 8);
+    auto* dAR = (int64_t*)dev_copy(axR.data(), (nt + 1) * 8);
+    auto* dAT = (int64_t*)dev_copy(axT.data(), (nt + 1) * 8);
+    auto* dCR = (int*)dev_copy(capR.data(), nt * 4);
+    auto* dCT = (int*)dev_copy(capT.data(), nt * 4);
+    auto* dGR = (int*)dev_copy(algR.data(), nt * 4);
+    auto* dGT = (int*)dev_copy(algT.data(), nt * 4);
+    unsigned zero[2] = {0, 0};
+    auto* dBad = (unsigned*)dev_copy(zero, 8);
+    if (!dR || !dT || !dAR || !dAT || !dCR || !dCT || !dGR || !dGT || !dBad) return fail(SS_ENOMEM, "plan: device allocation failed");
+    PrepArgs pr{nt, dAR, R, p->d_blobs, dR, dCR, dGR, 1, dBad};
+    PrepArgs pt{nt, dAT, T, p->d_blobs, dT, dCT, dGT, 1, dBad};
+    k_prep_1d<<<nt, 256, 0, stream>>>(pr);
+    k_prep_1d<<<nt, 256, 0, stream>>>(pt);
+    k_prep_cells<<<nt, 256, 0, stream>>>(pr);
+    k_prep_cells<<<nt, 256, 0, stream>>>(pt);
+    SS_CHECK_CUDA(cudaGetLastError());
+    if (gcount > 0) {
+      const int grid = (int)std::min<int64_t>((gcount + 255) / 256, (int64_t)num_sms() * 16);
+      k_grid_to_ff<<<grid, 256, 0, stream>>>(F, p->d_grid, gcount, dBad + 1);
+      SS_CHECK_CUDA(cudaGetLastError());
+    }
+    if (o.model == SS_MODEL_MLP && o.mlp_epochs > 0) {
+      TrainArgs ta{2 * nt, p->d_blobs, p->d_blob_off, o.mlp_epochs,
+                   o.mlp_lr > 0 ? o.mlp_lr : 1e-2f, o.seed};
+      k_train_mlp<<<2 * nt, 256, 0, stream>>>(ta);
+      SS_CHECK_CUDA(cudaGetLastError());
+    }
+    if (o.model != SS_MODEL_NONE) {
+      WindowArgs wa{2 * nt, p->d_blobs, p->d_blob_off, o.seed ^ 0xA5A5A5A5ull};
+      k_window<<<2 * nt, 256, 0, stream>>>(wa);
+      SS_CHECK_CUDA(cudaGetLastError());
+    }
+    SS_CHECK_CUDA(cudaStreamSynchronize(stream));
+    unsigned bad[2];
+    SS_CHECK_CUDA(cudaMemcpy(bad, dBad, 8, cudaMemcpyDeviceToHost));
+    if (bad[0]) return fail(SS_ENOTSORTED, "ss_plan_create_2d: an axis is not strictly increasing (or holds NaN)");
+    if (bad[1]) {
+      // some values need the fp64 blend: keep a copy of the caller's grids
+      SS_CHECK_CUDA(cudaMalloc(&p->d_grid64, gcount * sizeof(double)));
+      SS_CHECK_CUDA(cudaMemcpy(p->d_grid64, F, gcount * sizeof(double), cudaMemcpyDeviceToDevice));
+      p->device_bytes += gcount * (int64_t)sizeof(double);
+    }
+    return SS_OK;
+  }();
+  cleanup();
+  if (st != SS_OK) return st;
+  if (o.autotune) {
+    if ((st = plan_tune(p, stream)) != SS_OK) return st;
+  }
+  return plan_window_stats(p);
+}
+
+}  // namespace ss
+
+using namespace ss;
+
+extern "C" ss_status ss_plan_create_2d(ss_plan** out, int32_t ntables, const int64_t* R_off, const double* R,
+                                       const int64_t* T_off, const double* T, const int64_t* F_off, const double* F,
+                                       const ss_plan_opts* opts_in, cudaStream_t stream) {
+  if (out == nullptr || R_off == nullptr || T_off == nullptr || F_off == nullptr || R == nullptr || T == nullptr ||
+      F == nullptr)
+    return fail(SS_EINVAL, "ss_plan_create_2d: null pointer");
+  *out = nullptr;
+  if (ntables < 1) return fail(SS_EINVAL, "ss_plan_create_2d: ntables must be >= 1");
+  if (!aligned(R, 8) || !aligned(T, 8) || !aligned(F, 8)) return fail(SS_EINVAL, "ss_plan_create_2d: misaligned pointer");
+  ss_plan_opts o;
+  ss_plan_opts_default(&o);
+  if (opts_in) o = *opts_in;
+  if (o.side != SS_SIDE_LT) return fail(SS_EINVAL, "ss_plan_create_2d: the 2D lookup uses side SS_SIDE_LT");
+  if (o.model < SS_MODEL_NONE || o.model > SS_MODEL_MLP || o.algo == SS_ALGO_BALLOT || o.algo == SS_ALGO_BRANCHY ||
+      o.algo < 0 || o.algo > SS_ALGO_BALLOT)
+    return fail(SS_EINVAL, "ss_plan_create_2d: algo must be auto, binary or bucket");
+  auto* p = new ss_plan();
+  p->kind = 2;
+  p->ntables = ntables;
+  p->opts = o;
+  p->sizes.resize(ntables);
+  p->sizes_t.resize(ntables);
+  p->X_off.resize(2 * (ntables + 1));
+  p->grid_off.assign(F_off, F_off + ntables + 1);
+  for (int k = 0; k <= ntables; ++k) {
+    p->X_off[k] = R_off[k];
+    p->X_off[ntables + 1 + k] = T_off[k];
+  }
+  for (int k = 0; k < ntables; ++k) {
+    const int64_t nr = R_off[k + 1] - R_off[k], ntt = T_off[k + 1] - T_off[k];
+    if (nr < 2 || ntt < 2 || nr > (1 << 20) || ntt > (1 << 20) || F_off[k + 1] - F_off[k] != nr * ntt || F_off[k] < 0) {
+      delete p;
+      return fail(SS_EINVAL, "ss_plan_create_2d: each table needs axes of >= 2 entries and nr*nt values");
+    }
+    p->sizes[k] = (int)nr;
+    p->sizes_t[k] = (int)ntt;
+  }
+  ss_status st = plan_build_2d(p, R, T, F, stream);
+  if (st != SS_OK) {
+    delete p;
+    return st;
+  }
+  *out = p;
+  return SS_OK;
+}
+
+extern "C" ss_status ss_plan_bind_2d(ss_plan* p, const int64_t* Y_off, const double* Y2, int32_t* lowbounds2,
+                                     double* values, ss_devstat* stat, cudaStream_t stream) {
+  if (p == nullptr || Y_off == nullptr) return fail(SS_EINVAL, "ss_plan_bind_2d: null pointer");
+  if (p->kind != 2) return fail(SS_EINVAL, "ss_plan_bind_2d: not a 2D plan");
+  if (Y_off[p->ntables] > 0 && (Y2 == nullptr || lowbounds2 == nullptr || values == nullptr))
+    return fail(SS_EINVAL, "ss_plan_bind_2d: null pointer");
+  if (!aligned(Y2, 8) || !aligned(lowbounds2, 4) || !aligned(values, 8))
+    return fail(SS_EINVAL, "ss_plan_bind_2d: misaligned pointer");
+  for (int k = 0; k < p->ntables; ++k)
+    if (Y_off[k + 1] < Y_off[k] || Y_off[k] < 0) return fail(SS_EINVAL, "ss_plan_bind_2d: offsets must be non-decreasing");
+  return plan_bind(p, std::vector<int64_t>(Y_off, Y_off + p->ntables + 1), Y2, lowbounds2, values, stat, stream);
+}

@@ -1,0 +1,457 @@
+// plan_build.cu -- plan preparation, binding (tile queue + CUDA graph) and
+// the autotuner that picks, per table-size bucket, the in-block algorithm
+// (threads per target: 1 for bucket/binary/learned, G lanes for the
+// warp-ballot search with G keys per ballot) and the tile size.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "plan.h"
+#include "plan_host.h"
+
+namespace ss {
+
+int default_dir_cap(int n);
+
+// Algorithm field (and the ballot top-level stride) of every blob.
+__global__ void k_set_algo(unsigned char* blobs, const int64_t* blob_off, const int* algo, int nblobs) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nblobs) return;
+  BlobHdr* h = reinterpret_cast<BlobHdr*>(blobs + blob_off[k]);
+  const int a = algo[k];
+  h->algo = a;
+  const int G = a == BL_BALLOT8 ? 8 : a == BL_BALLOT16 ? 16 : 32;
+  int S0 = 1;
+  while ((int64_t)S0 * (G + 1) < (int64_t)h->ns + 1) S0 *= (G + 1);
+  h->S0 = S0;
+}
+
+// Synthetic tuning targets for table tab[r]: uniform in key space over the
+// table range widened by 1/8 on each side (about log-uniform).
+__global__ void k_synth_1d(const unsigned char* blobs, const int64_t* blob_off, const int* tab, const int64_t* Y_off,
+                           double* Y, uint64_t seed) {
+  const int r = blockIdx.x;
+  const BlobHdr* h = reinterpret_cast<const BlobHdr*>(blobs + blob_off[tab[r]]);
+  const uint64_t* keys = reinterpret_cast<const uint64_t*>(blobs + blob_off[tab[r]] + h->off_keys);
+  const uint64_t k0 = h->k0, k1 = keys[h->ns - 1];
+  const uint64_t span = k1 - k0, pad = span / 8;
+  const uint64_t lo = k0 - ::min(pad, (uint64_t)(k0 - 0x0010000000000000ull));
+  const uint64_t hi = k1 + ::min(pad, (uint64_t)(0xFFF0000000000000ull - k1));
+  for (int64_t i = Y_off[r] + threadIdx.x; i < Y_off[r + 1]; i += blockDim.x) {
+    uint64_t x = seed ^ ((uint64_t)r << 40) ^ (uint64_t)i;
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    const uint64_t q = lo + (uint64_t)((double)(x >> 11) * 0x1.0p-53 * (double)(hi - lo));
+    const uint64_t u = (q >> 63) ? (q & 0x7FFFFFFFFFFFFFFFull) : (0ull - q);
+    Y[i] = __longlong_as_double((long long)u);
+  }
+}
+
+ss_status plan_set_algos(ss_plan* p, cudaStream_t stream) {
+  int* d_algo = nullptr;
+  const int nb = (int)p->algo.size();
+  if (cudaMalloc(&d_algo, nb * sizeof(int)) != cudaSuccess) return fail(SS_ENOMEM, "plan: device allocation failed");
+  cudaError_t e = cudaMemcpyAsync(d_algo, p->algo.data(), nb * sizeof(int), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) {
+    k_set_algo<<<(nb + 255) / 256, 256, 0, stream>>>(p->d_blobs, p->d_blob_off, d_algo, nb);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  cudaFree(d_algo);
+  return e == cudaSuccess ? SS_OK : cuda_fail(e, "plan_set_algos");
+}
+
+// Largest window and mean window / loss over the blobs (read back the headers).
+ss_status plan_window_stats(ss_plan* p) {
+  const int nb = (int)p->blob_off.size();
+  std::vector<BlobHdr> hs(nb);
+  for (int k = 0; k < nb; ++k)
+    SS_CHECK_CUDA(cudaMemcpy(&hs[k], p->d_blobs + p->blob_off[k], sizeof(BlobHdr), cudaMemcpyDeviceToHost));
+  double sw = 0, sl = 0;
+  int mw = 0, cnt = 0;
+  for (const auto& h : hs) {
+    if (h.algo == BL_SPLINE || h.algo == BL_MLP) {
+      mw = std::max(mw, h.E);
+      sw += h.E;
+      sl += h.loss;
+      ++cnt;
+    }
+  }
+  p->max_window = mw;
+  p->mean_window = cnt ? (float)(sw / cnt) : 0.0f;
+  p->train_loss = cnt ? (float)(sl / cnt) : 0.0f;
+  return SS_OK;
+}
+
+ss_status plan_build_1d(ss_plan* p, const double* X, cudaStream_t stream) {
+  const int nt = p->ntables;
+  const ss_plan_opts& o = p->opts;
+  p->dir_cap.resize(nt);
+  p->algo.assign(nt, initial_algo(o));
+  p->blob_off.resize(nt);
+  int64_t off = 0;
+  for (int k = 0; k < nt; ++k) {
+    const int n = p->sizes[k];
+    p->dir_cap[k] = o.dir_cap > 0 ? o.dir_cap : default_dir_cap(n);
+    p->blob_off[k] = off;
+    off += (blob_geom_dev(n, p->dir_cap[k], false).bytes + 255) & ~(int64_t)255;
+  }
+  p->blob_bytes = off;
+  for (int b = 0; b < kNumBuckets; ++b) {
+    p->bucket_algo[b] = initial_algo(o);
+    p->bucket_tile[b] = o.tile > 0 ? o.tile : kDefaultTile;
+    p->bucket_tables[b] = 0;
+  }
+  for (int k = 0; k < nt; ++k) p->bucket_tables[size_bucket(p->sizes[k])]++;
+  if (cudaMalloc(&p->d_blobs, p->blob_bytes) != cudaSuccess) return fail(SS_ENOMEM, "plan: device allocation failed");
+  p->device_bytes = p->blob_bytes;
+  int64_t* d_X_off = nullptr;
+  int* d_cap = nullptr;
+  int* d_algo = nullptr;
+  unsigned* d_bad = nullptr;
+  ss_status st = SS_OK;
+  auto cleanup = [&]() {
+    free_dev(d_X_off);
+    free_dev(d_cap);
+    free_dev(d_algo);
+    free_dev(d_bad);
+  };
+  std::vector<int64_t> blob_off = p->blob_off;
+  if ((st = [&]() -> ss_status {
+         SS_CHECK_CUDA(cudaMalloc(&p->d_blob_off, nt * sizeof(int64_t)));
+         SS_CHECK_CUDA(cudaMemcpy(p->d_blob_off, blob_off.data(), nt * sizeof(int64_t), cudaMemcpyHostToDevice));
+         SS_CHECK_CUDA(cudaMalloc(&d_X_off, (nt + 1) * sizeof(int64_t)));
+         SS_CHECK_CUDA(cudaMemcpy(d_X_off, p->X_off.data(), (nt + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+         SS_CHECK_CUDA(cudaMalloc(&d_cap, nt * sizeof(int)));
+         SS_CHECK_CUDA(cudaMemcpy(d_cap, p->dir_cap.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
+         SS_CHECK_CUDA(cudaMalloc(&d_algo, nt * sizeof(int)));
+         SS_CHECK_CUDA(cudaMemcpy(d_algo, p->algo.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
+         SS_CHECK_CUDA(cudaMalloc(&d_bad, sizeof(unsigned)));
+         SS_CHECK_CUDA(cudaMemset(d_bad, 0, sizeof(unsigned)));
+         PrepArgs pa{nt, d_X_off, X, p->d_blobs, p->d_blob_off, d_cap, d_algo, 0, d_bad};
+         k_prep_1d<<<nt, 256, 0, stream>>>(pa);
+         SS_CHECK_CUDA(cudaGetLastError());
+         if (o.model == SS_MODEL_MLP && o.mlp_epochs > 0) {
+           TrainArgs ta{nt, p->d_blobs, p->d_blob_off, o.mlp_epochs,
+                        o.mlp_lr > 0 ? o.mlp_lr : 1e-2f, o.seed};
+           k_train_mlp<<<nt, 256, 0, stream>>>(ta);
+           SS_CHECK_CUDA(cudaGetLastError());
+         }
+         if (o.model != SS_MODEL_NONE) {
+           WindowArgs wa{nt, p->d_blobs, p->d_blob_off, o.seed ^ 0xA5A5A5A5ull};
+           k_window<<<nt, 256, 0, stream>>>(wa);
+           SS_CHECK_CUDA(cudaGetLastError());
+         }
+         SS_CHECK_CUDA(cudaStreamSynchronize(stream));
+         unsigned bad = 0;
+         SS_CHECK_CUDA(cudaMemcpy(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost));
+         if (bad) return fail(SS_ENOTSORTED, "ss_plan_create: a table is not strictly increasing (or holds NaN)");
+         return SS_OK;
+       }()) != SS_OK) {
+    cleanup();
+    return st;
+  }
+  cleanup();
+  if (o.autotune) {
+    if ((st = plan_tune(p, stream)) != SS_OK) return st;
+  }
+  return plan_window_stats(p);
+}
+
+// ---------------------------------------------------------------------------
+// Binding: tile queue, persistent grid, graph capture.
+// ---------------------------------------------------------------------------
+static void unbind(ss_plan* p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->exec = nullptr;
+  p->graph = nullptr;
+  free_dev(p->d_tiles);
+  p->d_tiles = nullptr;
+  p->ntiles = 0;
+  p->bound = false;
+}
+
+ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double* Y, int32_t* out, double* val,
+                    ss_devstat* stat, cudaStream_t stream) {
+  unbind(p);
+  std::vector<int> bucket_of(p->ntables);
+  for (int k = 0; k < p->ntables; ++k) bucket_of[k] = size_bucket(std::max(p->sizes[k], p->kind == 2 ? p->sizes_t[k] : 0));
+  int64_t total = 0;
+  std::vector<Tile> tiles = make_tiles(Y_off, bucket_of, p->bucket_tile, total);
+  if (tiles.size() > (size_t)0x7FFFFFFF) return fail(SS_EUNSUPPORTED, "plan: too many tiles");
+  p->ntiles = (int64_t)tiles.size();
+  if (p->d_counter == nullptr) SS_CHECK_CUDA(cudaMalloc(&p->d_counter, sizeof(int)));
+  if (!tiles.empty()) {
+    SS_CHECK_CUDA(cudaMalloc(&p->d_tiles, tiles.size() * sizeof(Tile)));
+    SS_CHECK_CUDA(cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+  }
+  // dynamic shared memory: the largest staged table (both axes for 2D)
+  int smem = 0;
+  for (int k = 0; k < p->ntables; ++k) {
+    if (p->kind == 1) {
+      smem = std::max(smem, staged_bytes(p->sizes[k], p->dir_cap[k], false, p->algo[k]));
+    } else {
+      const int a = (staged_bytes(p->sizes[k], p->dir_cap[2 * k], true, p->algo[2 * k]) + 127) & ~127;
+      const int b = staged_bytes(p->sizes_t[k], p->dir_cap[2 * k + 1], true, p->algo[2 * k + 1]);
+      smem = std::max(smem, a + b);
+    }
+  }
+  smem = (smem + 127) & ~127;
+  if (smem > max_smem_optin()) return fail(SS_EUNSUPPORTED, "plan: staged tables exceed shared memory");
+  const void* kern;
+  if (p->kind == 1) kern = batched_1d_kernel(p->opts.side == SS_SIDE_LE);
+  else kern = reinterpret_cast<const void*>(&k_batched_2d);
+  SS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int per_sm = 0;
+  SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNumThreads, smem));
+  if (per_sm < 1) return fail(SS_EUNSUPPORTED, "plan: kernel does not fit on an SM");
+  p->smem_bytes = smem;
+  p->grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms() * per_sm, p->ntiles));
+  if (p->ntiles == 0) {
+    p->bound = true;
+    return SS_OK;
+  }
+  if (p->cap_stream == nullptr) SS_CHECK_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+  SS_CHECK_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaMemsetAsync(p->d_counter, 0, sizeof(int), p->cap_stream);
+  if (e == cudaSuccess) {
+    if (p->kind == 1) {
+      BatchArgs1D a{p->d_blobs, p->d_blob_off, p->d_tiles, (int)p->ntiles, p->d_counter, Y, out,
+                    (aligned(Y, 16) && aligned(out, 16)) ? 1 : 0, stat};
+      void* args[1] = {&a};
+      e = cudaLaunchKernel(kern, dim3(p->grid_blocks), dim3(kNumThreads), args, (size_t)smem, p->cap_stream);
+    } else {
+      BatchArgs2D a{p->d_blobs, p->d_blob_off, p->d_grid, p->d_grid64, p->d_grid_off, p->d_tiles, (int)p->ntiles,
+                    p->d_counter, Y, out, val,
+                    (aligned(Y, 16) && aligned(out, 16) && aligned(val, 16)) ? 1 : 0, stat};
+      void* args[1] = {&a};
+      e = cudaLaunchKernel(kern, dim3(p->grid_blocks), dim3(kNumThreads), args, (size_t)smem, p->cap_stream);
+    }
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &g);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(e, "plan: capture of the batched launch");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+  p->graph = g;
+  SS_CHECK_CUDA(cudaGraphInstantiate(&p->exec, p->graph, 0));
+  p->bound = true;
+  (void)stream;
+  return SS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner
+// ---------------------------------------------------------------------------
+static std::string device_name() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+  return prop.name;
+}
+
+static bool read_cache(ss_plan* p, const std::string& dev) {
+  if (p->opts.tune_cache == nullptr) return false;
+  std::ifstream f(p->opts.tune_cache);
+  if (!f) return false;
+  std::stringstream ss_;
+  ss_ << f.rdbuf();
+  const std::string s = ss_.str();
+  char want[512];
+  std::snprintf(want, sizeof(want), "\"device\": \"%s\", \"kind\": %d, \"model\": %d, \"side\": %d", dev.c_str(),
+                p->kind, p->opts.model, p->opts.side);
+  if (s.find(want) == std::string::npos) return false;
+  int found = 0;
+  size_t pos = 0;
+  while ((pos = s.find("{\"bucket\": ", pos)) != std::string::npos) {
+    int b = -1, tile = 0;
+    char name[32] = {0};
+    if (std::sscanf(s.c_str() + pos, "{\"bucket\": %d, \"algo\": \"%31[^\"]\", \"tile\": %d}", &b, name, &tile) == 3 &&
+        b >= 0 && b < kNumBuckets && algo_from_name(name) >= 0 && tile > 0) {
+      p->bucket_algo[b] = algo_from_name(name);
+      p->bucket_tile[b] = tile;
+      ++found;
+    }
+    pos += 10;
+  }
+  return found > 0;
+}
+
+static void write_cache(const ss_plan* p, const std::string& dev) {
+  if (p->opts.tune_cache == nullptr) return;
+  std::ofstream f(p->opts.tune_cache);
+  if (!f) return;
+  f << "{\"device\": \"" << dev << "\", \"kind\": " << p->kind << ", \"model\": " << p->opts.model
+    << ", \"side\": " << p->opts.side << ", \"buckets\": [\n";
+  bool first = true;
+  for (int b = 0; b < kNumBuckets; ++b) {
+    if (p->bucket_tables[b] == 0) continue;
+    if (!first) f << ",\n";
+    first = false;
+    f << " {\"bucket\": " << b << ", \"algo\": \"" << algo_name(p->bucket_algo[b]) << "\", \"tile\": "
+      << p->bucket_tile[b] << "}";
+  }
+  f << "\n]}\n";
+}
+
+// Apply the bucket choices to every table's algorithm (both axes for 2D).
+static ss_status apply_buckets(ss_plan* p, cudaStream_t stream) {
+  for (int k = 0; k < p->ntables; ++k) {
+    const int b = size_bucket(std::max(p->sizes[k], p->kind == 2 ? p->sizes_t[k] : 0));
+    if (p->kind == 1) p->algo[k] = p->bucket_algo[b];
+    else p->algo[2 * k] = p->algo[2 * k + 1] = p->bucket_algo[b];
+  }
+  return plan_set_algos(p, stream);
+}
+
+ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
+  const std::string dev = device_name();
+  if (read_cache(p, dev)) {
+    p->tuned = 1;
+    return apply_buckets(p, stream);
+  }
+  std::vector<int> cands;
+  if (p->opts.model == SS_MODEL_SPLINE) cands = {BL_SPLINE};
+  else if (p->opts.model == SS_MODEL_MLP) cands = {BL_MLP};
+  else if (p->kind == 1) cands = {BL_BUCKET, BL_BINARY, BL_BALLOT8, BL_BALLOT16, BL_BALLOT32};
+  else cands = {BL_BUCKET, BL_BINARY};
+  const std::vector<int> tile_cands = {4096, 16384, 65536};
+  const int kReps = 8;
+  const int64_t kPerRep = 1 << 19;
+  cudaEvent_t e0, e1;
+  SS_CHECK_CUDA(cudaEventCreate(&e0));
+  SS_CHECK_CUDA(cudaEventCreate(&e1));
+  double* d_Y = nullptr;
+  int32_t* d_out = nullptr;
+  double* d_val = nullptr;
+  int* d_tab = nullptr;
+  int64_t* d_yoff = nullptr;
+  const int64_t per_pair = p->kind == 2 ? 2 : 1;
+  ss_status st = SS_OK;
+  if (cudaMalloc(&d_Y, kReps * kPerRep * 8 * per_pair) != cudaSuccess ||
+      cudaMalloc(&d_out, kReps * kPerRep * 4 * per_pair) != cudaSuccess ||
+      cudaMalloc(&d_val, kReps * kPerRep * 8) != cudaSuccess || cudaMalloc(&d_tab, kReps * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&d_yoff, (kReps + 1) * sizeof(int64_t)) != cudaSuccess) {
+    st = fail(SS_ENOMEM, "autotune: device allocation failed");
+  }
+  std::vector<int> saved_algo = p->algo;
+  for (int b = 0; b < kNumBuckets && st == SS_OK; ++b) {
+    if (p->bucket_tables[b] == 0) continue;
+    // representative tables of this bucket
+    std::vector<int> reps;
+    for (int k = 0; k < p->ntables && (int)reps.size() < kReps; ++k)
+      if (size_bucket(std::max(p->sizes[k], p->kind == 2 ? p->sizes_t[k] : 0)) == b) reps.push_back(k);
+    const int nr = (int)reps.size();
+    std::vector<int64_t> yoff_r(nr + 1);
+    for (int r = 0; r <= nr; ++r) yoff_r[r] = r * kPerRep;
+    std::vector<int> blob_of_rep(nr);
+    for (int r = 0; r < nr; ++r) blob_of_rep[r] = p->kind == 1 ? reps[r] : 2 * reps[r];
+    cudaMemcpy(d_tab, blob_of_rep.data(), nr * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(d_yoff, yoff_r.data(), (nr + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (p->kind == 1) {
+      k_synth_1d<<<nr, 256, 0, stream>>>(p->d_blobs, p->d_blob_off, d_tab, d_yoff, d_Y, p->opts.seed ^ 0x7E57ull);
+    } else {
+      // pairs: synthesise each coordinate from its own axis into a strided layout
+      std::vector<int> tab_t(nr);
+      for (int r = 0; r < nr; ++r) tab_t[r] = 2 * reps[r] + 1;
+      int* d_tab_t = nullptr;
+      double* d_tmp = nullptr;
+      cudaMalloc(&d_tab_t, nr * sizeof(int));
+      cudaMalloc(&d_tmp, kReps * kPerRep * 8);
+      cudaMemcpy(d_tab_t, tab_t.data(), nr * sizeof(int), cudaMemcpyHostToDevice);
+      k_synth_1d<<<nr, 256, 0, stream>>>(p->d_blobs, p->d_blob_off, d_tab, d_yoff, d_tmp, p->opts.seed ^ 0x7E57ull);
+      cudaMemcpy2DAsync(d_Y, 16, d_tmp, 8, 8, nr * kPerRep, cudaMemcpyDeviceToDevice, stream);
+      k_synth_1d<<<nr, 256, 0, stream>>>(p->d_blobs, p->d_blob_off, d_tab_t, d_yoff, d_tmp, p->opts.seed ^ 0x7E58ull);
+      cudaMemcpy2DAsync(d_Y + 1, 16, d_tmp, 8, 8, nr * kPerRep, cudaMemcpyDeviceToDevice, stream);
+      cudaStreamSynchronize(stream);
+      cudaFree(d_tab_t);
+      cudaFree(d_tmp);
+    }
+    if (cudaGetLastError() != cudaSuccess) { st = fail(SS_ECUDA, "autotune: synthetic targets"); break; }
+    // batch offsets over all tables: only the representatives have targets
+    std::vector<int64_t> Y_off(p->ntables + 1, 0);
+    {
+      int r = 0;
+      int64_t acc = 0;
+      for (int k = 0; k < p->ntables; ++k) {
+        Y_off[k] = acc;
+        if (r < nr && reps[r] == k) { acc += kPerRep; ++r; }
+      }
+      Y_off[p->ntables] = acc;
+    }
+    auto time_config = [&](int algo, int tile, float& ms) -> ss_status {
+      for (int r : reps) {
+        if (p->kind == 1) p->algo[r] = algo;
+        else p->algo[2 * r] = p->algo[2 * r + 1] = algo;
+      }
+      if (ss_status s2 = plan_set_algos(p, stream)) return s2;
+      const int saved_tile = p->bucket_tile[b];
+      p->bucket_tile[b] = tile;
+      ss_status s2 = plan_bind(p, Y_off, d_Y, d_out, d_val, nullptr, stream);
+      p->bucket_tile[b] = saved_tile;
+      if (s2 != SS_OK) return s2;
+      float best = 1e30f;
+      for (int rep = 0; rep < 4; ++rep) {
+        SS_CHECK_CUDA(cudaEventRecord(e0, stream));
+        SS_CHECK_CUDA(cudaGraphLaunch(p->exec, stream));
+        SS_CHECK_CUDA(cudaEventRecord(e1, stream));
+        SS_CHECK_CUDA(cudaEventSynchronize(e1));
+        float t = 0;
+        SS_CHECK_CUDA(cudaEventElapsedTime(&t, e0, e1));
+        if (rep > 0) best = std::min(best, t);
+      }
+      ms = best;
+      return SS_OK;
+    };
+    int best_algo = cands[0];
+    float best_ms = 1e30f;
+    for (int a : cands) {
+      float ms = 0;
+      ss_status s2 = time_config(a, p->bucket_tile[b], ms);
+      if (s2 == SS_EUNSUPPORTED) continue;     // e.g. staged tables too large for this variant
+      if (s2 != SS_OK) { st = s2; break; }
+      if (ms < best_ms) { best_ms = ms; best_algo = a; }
+    }
+    if (st != SS_OK) break;
+    int best_tile = p->bucket_tile[b];
+    if (p->opts.tile <= 0) {
+      best_ms = 1e30f;
+      for (int t : tile_cands) {
+        float ms = 0;
+        if ((st = time_config(best_algo, t, ms)) != SS_OK) break;
+        if (ms < best_ms) { best_ms = ms; best_tile = t; }
+      }
+      if (st != SS_OK) break;
+    }
+    p->bucket_algo[b] = best_algo;
+    p->bucket_tile[b] = best_tile;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  free_dev(d_Y);
+  free_dev(d_out);
+  free_dev(d_val);
+  free_dev(d_tab);
+  free_dev(d_yoff);
+  unbind(p);
+  if (st != SS_OK) {
+    p->algo = saved_algo;
+    plan_set_algos(p, stream);
+    return st;
+  }
+  p->tuned = 1;
+  write_cache(p, dev);
+  return apply_buckets(p, stream);
+}
+
+}  // namespace ss

@@ -1,0 +1,75 @@
+// plan_host.h -- the host-side plan object and the helpers shared by the
+// plan translation units.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "plan.h"
+
+namespace ss {
+
+constexpr int kNumBuckets = 8;       // table-size buckets: [2,16) [16,64) [64,256) ... [65536, inf)
+constexpr int kDefaultTile = 16384;  // targets per tile before tuning
+
+int size_bucket(int n);
+const char* algo_name(int a);
+int algo_from_name(const std::string& s);
+int staged_bytes(int n, int dir_cap, bool cells, int algo);
+int initial_algo(const ss_plan_opts& o);
+std::vector<Tile> make_tiles(const std::vector<int64_t>& Y_off, const std::vector<int>& bucket_of,
+                             const int* bucket_tile, int64_t& total);
+void free_dev(void* p);
+
+struct PlanBase {
+  virtual ~PlanBase();
+  int kind = 0;                       // 1: 1D tables, 2: 2D tables
+  int ntables = 0;
+  ss_plan_opts opts{};
+  std::vector<int> sizes;             // 1D: n per table; 2D: nr per table
+  std::vector<int> sizes_t;           // 2D: nt per table
+  std::vector<int64_t> X_off;
+  std::vector<int> dir_cap;           // per blob
+  std::vector<int> algo;              // per blob (BlobAlgo)
+  std::vector<int64_t> blob_off;      // per blob
+  int64_t blob_bytes = 0;
+  unsigned char* d_blobs = nullptr;
+  int64_t* d_blob_off = nullptr;
+  // 2D value grids (float-float) and their fp64 copies for tables that need them
+  float2* d_grid = nullptr;
+  double* d_grid64 = nullptr;
+  int64_t* d_grid_off = nullptr;
+  std::vector<int64_t> grid_off;
+  // autotuner choices per table-size bucket
+  int bucket_algo[kNumBuckets] = {0};
+  int bucket_tile[kNumBuckets] = {0};
+  int bucket_tables[kNumBuckets] = {0};
+  int tuned = 0;
+  // bound batch
+  bool bound = false;
+  Tile* d_tiles = nullptr;
+  int64_t ntiles = 0;
+  int* d_counter = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int grid_blocks = 0;
+  int smem_bytes = 0;
+  // diagnostics
+  int64_t device_bytes = 0;
+  int max_window = 0;
+  float mean_window = 0.0f;
+  float train_loss = 0.0f;
+};
+
+ss_status plan_build_1d(ss_plan* p, const double* X, cudaStream_t stream);
+ss_status plan_build_2d(ss_plan* p, const double* R, const double* T, const double* F, cudaStream_t stream);
+ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double* Y, int32_t* out, double* val,
+                    ss_devstat* stat, cudaStream_t stream);
+ss_status plan_set_algos(ss_plan* p, cudaStream_t stream);
+ss_status plan_tune(ss_plan* p, cudaStream_t stream);
+ss_status plan_window_stats(ss_plan* p);
+
+}  // namespace ss
+
+struct ss_plan : public ss::PlanBase {};

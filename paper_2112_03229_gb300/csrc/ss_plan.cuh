@@ -1,0 +1,220 @@
+// ss_plan.cuh -- prepared tables ("blobs") kept in device memory by a plan,
+// staged into shared memory with one TMA bulk copy per table, and the
+// searches that run on a staged blob (plain, bucket, ballot, and the two
+// learned proposals with their exact fix-up).
+//
+// Set-up happens once per loaded table, as Sec. 5.3 prescribes for EOSPAC
+// (tables are loaded once at program start), so the per-call work is only
+// the stream of targets.
+//
+// Blob layout (all offsets from the blob start, 16-byte aligned):
+//   [BlobHdr 128 B][mlp 65 floats, padded to 272 B][dir (cap+1) int32]
+//   [keys (ns + kPad) uint64][eyt P uint64]           <- staged part
+//   [full keys nk + kPad uint64]                      <- global only (stride > 1)
+// keys hold the images of X[1..n-1] (sampled every `stride` entries for big
+// tables, see ss_table.cuh); full keys hold all of them.
+#pragma once
+
+#include "ss_ff.cuh"
+#include "ss_model.cuh"
+#include "ss_table.cuh"
+
+namespace ss {
+
+enum BlobAlgo : int { BL_BUCKET = 0, BL_BINARY = 1, BL_BALLOT8 = 2, BL_BALLOT16 = 3, BL_BALLOT32 = 4,
+                      BL_SPLINE = 5, BL_MLP = 6, BL_NUM = 7 };
+
+struct __align__(16) BlobHdr {
+  int n, nk, ns, stride;     // table length, searched keys, staged keys, sample stride
+  int algo;                  // BlobAlgo in use (written by plan creation / the autotuner)
+  int D;                     // Eytzinger depth of the staged keys
+  int shift, nb, occ;        // bucket directory (also the spline knots)
+  int E;                     // learned half-window (count units); proposals are checked exactly
+  int S0;                    // top-level stride of the ballot search
+  int dir_cap;
+  int off_mlp, off_dir, off_keys, off_eyt;   // staged sections
+  int staged_end;            // end of the staged part
+  int pad0;
+  int64_t off_full;          // full keys (global)
+  uint64_t base;             // bucket of keys[0]
+  uint64_t k0;               // key of X[0]
+  float e_lo, e_scale;       // MLP feature scaling
+  float loss;                // final training loss of the MLP (diagnostic)
+  int pad1;
+  // 2D axes only: per-cell float-float data follows the staged part
+  int off_cells;             // CellFF[n-1] (staged with the axis), -1 for 1D
+  int ffok;                  // cells usable by the float-float path
+  int pad2[2];
+};
+static_assert(sizeof(BlobHdr) == 128, "blob header must stay 128 bytes");
+
+constexpr int kMlpBytes = 272;
+
+struct BlobGeom {
+  int ns, stride, P, D;
+  int off_mlp, off_dir, off_keys, off_eyt, off_cells, staged_end;
+  int64_t off_full, bytes;
+};
+
+// Byte range of the staged part that an algorithm needs: [lo, hi) besides the header.
+__host__ __device__ inline void staged_range(const BlobHdr& h, int& lo, int& hi) {
+  switch (h.algo) {
+    case BL_BINARY: lo = h.off_eyt; hi = h.off_eyt + (1 << h.D) * 8; break;
+    case BL_BALLOT8: case BL_BALLOT16: case BL_BALLOT32: lo = h.off_keys; hi = h.off_keys + (h.ns + kPad) * 8; break;
+    default: lo = h.off_mlp; hi = h.off_keys + (h.ns + kPad) * 8; break;   // bucket, spline, mlp
+  }
+  if (h.off_cells >= 0) hi = h.staged_end;   // 2D axes keep their cells right after
+  lo &= ~15;
+  hi = (hi + 15) & ~15;
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copy global -> shared, completed on an mbarrier.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Wait for phase `parity` of the barrier; gives up after a bounded number of
+// polls and returns false (the caller records an error instead of hanging).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 24); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (it > 64) __nanosleep(64);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// View of a staged blob in shared memory.
+struct StagedView {
+  const BlobHdr* h;
+  const float* mlp;
+  const int* dir;
+  const uint64_t* keys;
+  const uint64_t* eyt;
+  const CellFF* cells;
+  const uint64_t* full;      // global full keys (stride > 1)
+};
+
+// Stage blob `src` (global) into smem at `dst`: header, then the range the
+// algorithm needs placed right after it.  Must be called by all threads;
+// thread 0 issues the copies.  Returns the view (pointers into dst) and
+// sets ok=false if the wait timed out.
+__device__ __forceinline__ StagedView stage_blob(const unsigned char* __restrict__ src, unsigned char* dst,
+                                                 uint64_t* bar, uint32_t& phase, bool& ok) {
+  const BlobHdr* gh = reinterpret_cast<const BlobHdr*>(src);
+  BlobHdr hdr;
+  // every thread reads the header through the read-only path (it is tiny and cached)
+  const int4* gh4 = reinterpret_cast<const int4*>(gh);
+  int4* hp = reinterpret_cast<int4*>(&hdr);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) hp[i] = __ldg(gh4 + i);
+  int lo, hi;
+  staged_range(hdr, lo, hi);
+  __syncthreads();          // previous users of dst are done
+  if (threadIdx.x == 0) {
+    fence_proxy_async();
+    const uint32_t bytes = (uint32_t)(sizeof(BlobHdr) + (hi - lo));
+    mbar_expect_tx(bar, bytes);
+    tma_load_1d(dst, src, (uint32_t)sizeof(BlobHdr), bar);
+    if (hi > lo) tma_load_1d(dst + sizeof(BlobHdr), src + lo, (uint32_t)(hi - lo), bar);
+  }
+  ok &= mbar_wait(bar, phase);
+  ok = __syncthreads_and(ok);          // uniform outcome for the whole block
+  phase ^= 1u;
+  const int shift_off = (int)sizeof(BlobHdr) - lo;     // smem position of blob offset o is o + shift_off
+  StagedView v;
+  v.h = reinterpret_cast<const BlobHdr*>(dst);
+  v.mlp = reinterpret_cast<const float*>(dst + hdr.off_mlp + shift_off);
+  v.dir = reinterpret_cast<const int*>(dst + hdr.off_dir + shift_off);
+  v.keys = reinterpret_cast<const uint64_t*>(dst + hdr.off_keys + shift_off);
+  v.eyt = reinterpret_cast<const uint64_t*>(dst + hdr.off_eyt + shift_off);
+  v.cells = hdr.off_cells >= 0 ? reinterpret_cast<const CellFF*>(dst + hdr.off_cells + shift_off) : nullptr;
+  v.full = hdr.off_full >= 0 ? reinterpret_cast<const uint64_t*>(src + hdr.off_full) : nullptr;
+  return v;
+}
+
+// Count over the full searched set after the staged count c (two-level tables).
+__device__ __forceinline__ int finish_full(const StagedView& v, int c, uint64_t q) {
+  const BlobHdr& h = *v.h;
+  if (h.stride == 1) return c;
+  int lo = min(c * h.stride, h.nk);
+  int len = min(h.stride, h.nk - lo);
+  while (len > 0) {
+    const int half = len >> 1;
+    if (__ldg(v.full + lo + half) < q) { lo += half + 1; len -= half + 1; } else { len = half; }
+  }
+  return lo;
+}
+
+// Key i (0-based among X[1..n-1]) of the table, from shared memory when the
+// whole table is staged, else from the global full keys.
+__device__ __forceinline__ uint64_t key_at(const StagedView& v, int i) {
+  return v.h->stride == 1 ? v.keys[i] : __ldg(v.full + i);
+}
+
+// Plain count of keys below q with the bucket directory (any occupancy).
+__device__ __forceinline__ int plain_bucket(const StagedView& v, uint64_t q) {
+  const BlobHdr& h = *v.h;
+  const int T = h.occ > 0 ? 32 - __clz(h.occ) : 0;
+  const int c = h.occ <= 1 ? search_bucket<1>(v.keys, v.dir, h.shift, h.base, h.nb, q)
+                           : search_bucket_bisect(v.keys, v.dir, h.shift, h.base, h.nb, T, q);
+  return finish_full(v, c, q);
+}
+
+__device__ __forceinline__ int plain_binary(const StagedView& v, uint64_t q) {
+  return finish_full(v, search_eyt_rt(v.eyt, v.h->D, q), q);
+}
+
+// Learned search: proposal p (count units), exact check that the answer lies
+// in [p-E, p+E], bounded bisection inside, plain bucket search otherwise.
+__device__ __forceinline__ int learned_count(const StagedView& v, int p, uint64_t q, int& fallbacks) {
+  const BlobHdr& h = *v.h;
+  const int lo = max(p - h.E, 0), hi = min(p + h.E, h.nk);
+  const bool ok = (lo == 0 || key_at(v, lo - 1) < q) && (hi == h.nk || key_at(v, hi) >= q);
+  if (!ok) {
+    ++fallbacks;
+    return plain_bucket(v, q);
+  }
+  int c = lo, len = hi - lo;
+  while (len > 0) {
+    const int half = len >> 1;
+    if (key_at(v, c + half) < q) { c += half + 1; len -= half + 1; } else { len = half; }
+  }
+  return c;
+}
+
+__device__ __forceinline__ int spline_count(const StagedView& v, uint64_t q, int& fallbacks) {
+  const BlobHdr& h = *v.h;
+  return learned_count(v, spline_propose(v.dir, h.shift, h.base, h.nb, q), q, fallbacks);
+}
+
+__device__ __forceinline__ int mlp_count(const StagedView& v, double t, uint64_t q, int& fallbacks) {
+  const BlobHdr& h = *v.h;
+  const MlpFeatScale sc{h.e_lo, h.e_scale};
+  return learned_count(v, mlp_propose(v.mlp, sc, h.n, t), q, fallbacks);
+}
+
+}  // namespace ss

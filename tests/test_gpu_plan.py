@@ -1,0 +1,251 @@
+"""GPU parity of plans (prepared tables, learned proposals, persistent
+batched kernel, CUDA graph, autotuner, save/load) against the CPU oracle."""
+import os
+import struct
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2112_03229_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+REL_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def ss():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2112_03229_gb300 as m
+    return m
+
+
+def run_plan_1d(ss, b, Y=None, **opts):
+    plan = ss.Plan.create_1d(b.X_off, b.X.to(DEV), **opts)
+    Yd = (b.Y if Y is None else Y).to(DEV)
+    out = torch.full((Yd.numel(),), -1, dtype=torch.int32, device=DEV)
+    stat = ss.new_stat()
+    plan.bind_1d(b.Y_off, Yd, out, stat=stat)
+    plan.execute()
+    return plan, out.cpu().numpy(), ss.read_stat(stat)
+
+
+def small_batch(seed=3, ntables=150, scale=0.003):
+    return wl.batched_1d(ntables=ntables, count_scale=scale, seed=seed)
+
+
+@pytest.mark.parametrize("model", ["none", "spline", "mlp"])
+@pytest.mark.parametrize("side", [0, 1])
+def test_plan_1d_batched_models(ss, model, side):
+    b = small_batch()
+    want = oracle.search_1d_batched(b.X_off.numpy(), b.X.numpy(), b.Y_off.numpy(), b.Y.numpy(), side)
+    plan, got, st = run_plan_1d(ss, b, model=model, side=side, mlp_epochs=150 if model == "mlp" else None)
+    np.testing.assert_array_equal(got, want)
+    assert st.flags == 0
+    inf = plan.info()
+    if model == "none":
+        assert inf.max_window == 0 and st.fallbacks == 0
+    else:
+        assert inf.max_window >= 1
+
+
+@pytest.mark.parametrize("algo", ["bucket", "binary", "ballot"])
+def test_plan_1d_plain_algorithms(ss, algo):
+    b = small_batch(seed=4)
+    want = oracle.search_1d_batched(b.X_off.numpy(), b.X.numpy(), b.Y_off.numpy(), b.Y.numpy())
+    _, got, st = run_plan_1d(ss, b, algo=algo)
+    np.testing.assert_array_equal(got, want)
+
+
+def sweep_batch(m_per=60_000):
+    """The table-size sweep (16, 256, 4096, 65536 clustered entries) as one batch."""
+    tabs = [wl.sweep_table(n) for n in (16, 256, 4096, 65536)]
+    X = torch.cat(tabs)
+    X_off = np.concatenate([[0], np.cumsum([len(t) for t in tabs])])
+    Ys = [wl.log_uniform(m_per, 0.5 * t[0].item(), 2 * t[-1].item(), seed=len(t)) for t in tabs]
+    Ys[-1][:2000] = tabs[-1][-2000:]                   # exact hits on the big table
+    Y = torch.cat(Ys)
+    Y_off = np.concatenate([[0], np.cumsum([len(y) for y in Ys])])
+    return wl.Batched1D(torch.as_tensor(X_off), X, torch.as_tensor(Y_off), Y, None, None)
+
+
+@pytest.mark.parametrize("model", ["none", "spline", "mlp"])
+def test_plan_table_size_sweep(ss, model):
+    b = sweep_batch()
+    want = oracle.search_1d_batched(b.X_off.numpy(), b.X.numpy(), b.Y_off.numpy(), b.Y.numpy())
+    plan, got, st = run_plan_1d(ss, b, model=model)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_plan_empty_tiny_tiles_and_misaligned(ss):
+    rng = np.random.default_rng(5)
+    sizes = [2, 3, 17, 300, 2000, 5]
+    counts = [0, 1, 63, 64, 65, 0, 1000, 3]
+    sizes = sizes + [40, 50]
+    tabs = [wl.log_spaced_table(n, 1e-3, 1e3, 0.1, seed=n) for n in sizes]
+    X = torch.cat(tabs)
+    X_off = np.concatenate([[0], np.cumsum(sizes)])
+    Y = torch.as_tensor(10 ** rng.uniform(-4, 4, sum(counts)))
+    Y_off = np.concatenate([[0], np.cumsum(counts)])
+    want = oracle.search_1d_batched(X_off, X.numpy(), Y_off, Y.numpy())
+    for model in ("none", "spline"):
+        for off in (0, 1, 3):
+            plan = ss.Plan.create_1d(X_off, X.to(DEV), model=model, tile=64)
+            ybuf = torch.zeros(len(Y) + 4, dtype=torch.float64, device=DEV)
+            ybuf[off:off + len(Y)] = Y.to(DEV)
+            obuf = torch.full((len(Y) + 4,), -5, dtype=torch.int32, device=DEV)
+            plan.bind_1d(Y_off, ybuf[off:off + len(Y)], obuf[off:off + len(Y)])
+            plan.execute()
+            o = obuf.cpu().numpy()
+            np.testing.assert_array_equal(o[off:off + len(Y)], want)
+            assert np.all(o[:off] == -5) and np.all(o[off + len(Y):] == -5)
+
+
+def test_plan_graph_replay_and_rebind(ss):
+    b = small_batch(seed=6)
+    plan = ss.Plan.create_1d(b.X_off, b.X.to(DEV), model="spline")
+    Yd = b.Y.to(DEV)
+    out = torch.empty(len(b.Y), dtype=torch.int32, device=DEV)
+    plan.bind_1d(b.Y_off, Yd, out)
+    plan.execute()
+    first = out.clone()
+    Yd.mul_(1.5)                                   # new targets in the bound buffer
+    plan.execute()
+    want2 = oracle.search_1d_batched(b.X_off.numpy(), b.X.numpy(), b.Y_off.numpy(), (b.Y * 1.5).numpy())
+    np.testing.assert_array_equal(out.cpu().numpy(), want2)
+    Yd.div_(1.5)
+    plan.execute()
+    assert torch.equal(out, first)
+
+
+def test_plan_not_sorted_rejected(ss):
+    X = torch.tensor([1.0, 2.0, 2.0, 3.0, 1.0, 5.0, 7.0], dtype=torch.float64, device=DEV)
+    with pytest.raises(ss.SSError) as e:
+        ss.Plan.create_1d([0, 4, 7], X)
+    assert e.value.code == 2
+
+
+def _blob_headers(raw):
+    """Parse a saved plan file: returns (positions of blob headers, blob data start)."""
+    pos = 8 + 4 * 3 + 48                      # magic, version/kind/ntables, options
+    def vec(pos, fmt, size):
+        n = struct.unpack_from("<q", raw, pos)[0]
+        return list(struct.unpack_from("<%d%s" % (n, fmt), raw, pos + 8)), pos + 8 + n * size
+    vals = {}
+    for name, fmt, size in (("sizes", "i", 4), ("sizes_t", "i", 4), ("X_off", "q", 8), ("dir_cap", "i", 4),
+                            ("algo", "i", 4), ("blob_off", "q", 8), ("grid_off", "q", 8)):
+        vals[name], pos = vec(pos, fmt, size)
+    pos += 3 * 8 * 4 + 4                      # bucket arrays, tuned
+    pos += 8                                  # blob_bytes
+    return vals["blob_off"], pos
+
+
+def test_plan_save_load_and_forced_fallback(ss, tmp_path):
+    b = small_batch(seed=7)
+    want = oracle.search_1d_batched(b.X_off.numpy(), b.X.numpy(), b.Y_off.numpy(), b.Y.numpy())
+    plan, got, st = run_plan_1d(ss, b, model="mlp", mlp_epochs=100)
+    np.testing.assert_array_equal(got, want)
+    path = tmp_path / "plan.bin"
+    plan.save(path)
+    re = ss.Plan.load(path)
+    out = torch.empty(len(b.Y), dtype=torch.int32, device=DEV)
+    re.bind_1d(b.Y_off, b.Y.to(DEV), out)
+    re.execute()
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
+    assert re.info().max_window == plan.info().max_window
+    # corrupt every model (scrambled weights) and set its window to zero: the
+    # exact check must reject the proposals and the plain search must take over
+    raw = bytearray(path.read_bytes())
+    offs, start = _blob_headers(bytes(raw))
+    rng = np.random.default_rng(0)
+    for o in offs:
+        h = start + o
+        struct.pack_into("<i", raw, h + 36, 0)                                     # E
+        off_mlp = struct.unpack_from("<i", raw, h + 48)[0]
+        struct.pack_into("<65f", raw, h + off_mlp, *rng.standard_normal(65).astype(np.float32))
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(bytes(raw))
+    re2 = ss.Plan.load(bad)
+    stat = ss.new_stat()
+    out.fill_(-1)
+    re2.bind_1d(b.Y_off, b.Y.to(DEV), out, stat=stat)
+    re2.execute()
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
+    st = ss.read_stat(stat)
+    assert st.fallbacks > len(b.Y) // 2
+
+
+def test_plan_autotune_and_cache(ss, tmp_path):
+    b = wl.batched_1d(ntables=60, count_scale=0.004, seed=8)
+    want = oracle.search_1d_batched(b.X_off.numpy(), b.X.numpy(), b.Y_off.numpy(), b.Y.numpy())
+    cache = str(tmp_path / "tune.json")
+    plan, got, _ = run_plan_1d(ss, b, autotune=True, tune_cache=cache)
+    np.testing.assert_array_equal(got, want)
+    inf = plan.info()
+    assert inf.tuned == 1 and os.path.exists(cache)
+    ch = plan.choices()
+    assert ch and all(a in ss.BLOB_ALGOS[:5] and t in (4096, 16384, 65536) for a, t, _ in ch.values())
+    text = open(cache).read()
+    assert '"buckets"' in text
+    plan2, got2, _ = run_plan_1d(ss, b, autotune=True, tune_cache=cache)
+    np.testing.assert_array_equal(got2, want)
+    assert plan2.choices() == ch
+
+
+def test_learned_gain(ss):
+    """What training buys: the trained MLP's fix-up window against the untrained
+    initialisation (same architecture) on the 65536-entry clustered table."""
+    X = wl.sweep_table(65536)
+    b = wl.Batched1D(torch.tensor([0, len(X)]), X, torch.tensor([0, 200_000]),
+                     wl.log_uniform(200_000, 0.5e-6, 2e4, seed=3), None, None)
+    want = oracle.search_1d_batched(b.X_off.numpy(), b.X.numpy(), b.Y_off.numpy(), b.Y.numpy())
+    trained, got_t, st_t = run_plan_1d(ss, b, model="mlp", mlp_epochs=400)
+    untrained, got_u, st_u = run_plan_1d(ss, b, model="mlp", mlp_epochs=0)
+    spline, got_s, st_s = run_plan_1d(ss, b, model="spline")
+    for g in (got_t, got_u, got_s):
+        np.testing.assert_array_equal(g, want)
+    Et, Eu = trained.info().max_window, untrained.info().max_window
+    assert Et * 8 < Eu, (Et, Eu)
+    assert trained.info().train_loss < 1e-3
+
+
+# ---------------------------------------------------------------- 2D plans
+
+@pytest.mark.parametrize("coherent", [False, True])
+@pytest.mark.parametrize("model", ["none", "spline", "mlp"])
+def test_plan_2d_batched(ss, model, coherent):
+    b = wl.batched_2d(ntables=12, pairs_per_table=4001, coherent=coherent, seed=9)
+    wi, wv = oracle.search_interp_2d_batched(b.R_off.numpy(), b.R.numpy(), b.T_off.numpy(), b.T.numpy(),
+                                             b.F_off.numpy(), b.F.numpy(), b.Y_off.numpy(), b.Y2.numpy())
+    plan = ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), model=model,
+                             mlp_epochs=150 if model == "mlp" else None)
+    m = b.Y2.shape[0]
+    idx = torch.empty((m, 2), dtype=torch.int32, device=DEV)
+    val = torch.empty(m, dtype=torch.float64, device=DEV)
+    stat = ss.new_stat()
+    plan.bind_2d(b.Y_off, b.Y2.to(DEV), idx, val, stat=stat)
+    plan.execute()
+    np.testing.assert_array_equal(idx.cpu().numpy(), wi)
+    rel = np.abs(val.cpu().numpy() - wv) / np.abs(wv)
+    assert rel.max() <= REL_TOL
+    assert ss.read_stat(stat).flags == 0
+
+
+def test_plan_2d_save_load_and_autotune(ss, tmp_path):
+    b = wl.batched_2d(ntables=6, pairs_per_table=3000, seed=10)
+    wi, wv = oracle.search_interp_2d_batched(b.R_off.numpy(), b.R.numpy(), b.T_off.numpy(), b.T.numpy(),
+                                             b.F_off.numpy(), b.F.numpy(), b.Y_off.numpy(), b.Y2.numpy())
+    plan = ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), autotune=True)
+    path = tmp_path / "p2.bin"
+    plan.save(path)
+    for p in (plan, ss.Plan.load(path)):
+        m = b.Y2.shape[0]
+        idx = torch.empty((m, 2), dtype=torch.int32, device=DEV)
+        val = torch.empty(m, dtype=torch.float64, device=DEV)
+        p.bind_2d(b.Y_off, b.Y2.to(DEV), idx, val)
+        p.execute()
+        np.testing.assert_array_equal(idx.cpu().numpy(), wi)
+        assert (np.abs(val.cpu().numpy() - wv) / np.abs(wv)).max() <= REL_TOL

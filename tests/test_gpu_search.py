@@ -130,16 +130,65 @@ def check_2d(idx, val, wi, wv):
     assert rel.max(initial=0.0) <= REL_TOL, rel.max()
 
 
-@pytest.mark.parametrize("algo", ["bucket", "binary"])
-def test_2d_config1_small(ss, algo):
+@pytest.mark.parametrize("algo,fp64", [("bucket", False), ("binary", False), ("bucket", True), ("binary", True)])
+def test_2d_config1_small(ss, algo, fp64):
     R, T, F, Y2 = wl.interp_2d(m=(1 << 20) + 1, seed=2)
     # add out-of-range, exact-node and NaN pairs
     extra = np.array([[R[0].item(), T[0].item()], [R[-1].item(), T[-1].item()], [1e-9, 1e9], [1e9, 1e-9],
                       [np.nan, 1.0], [1.0, np.nan], [-0.0, 0.0], [np.inf, -np.inf], [R[5].item(), T[7].item()]])
     Y2 = torch.cat([Y2, torch.as_tensor(extra)])
-    idx, val = ss.search_interp_2d(R.to(DEV), T.to(DEV), F.to(DEV), Y2.to(DEV), algo=algo)
+    stat = ss.new_stat()
+    idx, val = ss.search_interp_2d(R.to(DEV), T.to(DEV), F.to(DEV), Y2.to(DEV), algo=algo, fp64=fp64, stat=stat)
     wi, wv = oracle.search_interp_2d(R.numpy(), T.numpy(), F.numpy(), Y2.numpy())
     check_2d(idx.cpu().numpy(), val.cpu().numpy(), wi, wv)
+    st = ss.read_stat(stat)
+    assert st.flags == 0 and st.nan_targets == 2
+
+
+def test_2d_float_float_preconditions(ss):
+    """Axes or grids outside the float-float path's range fall back to fp64 and stay exact."""
+    rng = np.random.default_rng(4)
+    cases = []
+    R = np.sort(rng.uniform(-5, 5, 40)); T = np.sort(rng.uniform(1, 50, 30))        # negative axis
+    cases.append((R, T))
+    R = np.array([1e-30, 1e-10, 1.0, 1e10, 1e30]); T = np.array([1.0, 2.0, 3.0])      # cells over 2^10 wide
+    cases.append((R, T))
+    R = np.geomspace(1e-25, 1e-20, 50); T = np.geomspace(1.0, 1e3, 20)               # axis below 2^-70
+    cases.append((R, T))
+    for R, T in cases:
+        F = rng.uniform(0.5, 3.0, (len(R), len(T)))
+        Y2 = np.stack([rng.uniform(R[0] * 1.5 - 1, R[-1] * 1.1, 20000) if R[0] < 0 else
+                       np.exp(rng.uniform(np.log(R[0]) - 1, np.log(R[-1]) + 1, 20000)),
+                       rng.uniform(T[0] - 1, T[-1] + 1, 20000)], 1)
+        stat = ss.new_stat()
+        idx, val = ss.search_interp_2d(*(torch.as_tensor(a).to(DEV) for a in (R, T, F.reshape(-1), Y2)), stat=stat)
+        wi, wv = oracle.search_interp_2d(R, T, F, Y2)
+        check_2d(idx.cpu().numpy(), val.cpu().numpy(), wi, wv)
+        assert ss.read_stat(stat).flags & ss.FLAG_BAD_VALUE
+    # grid values outside the splittable range (and zeros, negatives) on a float-float table
+    R = wl.log_spaced_table(50, 1e-3, 1e3, 0.1, seed=1).numpy()
+    T = wl.log_spaced_table(40, 1e-2, 1e2, 0.1, seed=2).numpy()
+    F = rng.uniform(0.5, 3.0, (50, 40))
+    F[3, :] = 1e-200; F[7, 5] = 0.0; F[9, 9] = -2.0; F[11, :] = 1e250
+    Y2 = np.stack([np.exp(rng.uniform(np.log(1e-3), np.log(1e3), 50000)),
+                   np.exp(rng.uniform(np.log(1e-2), np.log(1e2), 50000))], 1)
+    idx, val = ss.search_interp_2d(*(torch.as_tensor(a).to(DEV) for a in (R, T, F.reshape(-1), Y2)))
+    wi, wv = oracle.search_interp_2d(R, T, F, Y2)
+    np.testing.assert_array_equal(idx.cpu().numpy(), wi)
+    v = val.cpu().numpy()
+    cr = np.minimum(wi[:, 0], 48)
+    ct = np.minimum(wi[:, 1], 38)
+    corners = np.abs(np.stack([F[cr, ct], F[cr, ct + 1], F[cr + 1, ct], F[cr + 1, ct + 1]], 1))
+    # a convex blend is good to the rounding of its largest term; all-positive cells keep the relative bar
+    assert np.all(np.abs(v - wv) <= 1e-12 * corners.max(1))
+    pos = (corners.min(1) > 0) & (np.min(np.stack([F[cr, ct], F[cr, ct + 1], F[cr + 1, ct], F[cr + 1, ct + 1]], 1), 1) > 0)
+    rel = np.abs(v - wv) / np.abs(wv)
+    worst = np.argmax(np.where(pos, rel, 0.0))
+    assert rel[worst] <= REL_TOL or not pos[worst], (
+        "pair %s idx %s corners %s want %r got %r" % (Y2[worst].tolist(), wi[worst].tolist(),
+                                                        [F[cr[worst], ct[worst]], F[cr[worst], ct[worst] + 1],
+                                                         F[cr[worst] + 1, ct[worst]], F[cr[worst] + 1, ct[worst] + 1]],
+                                                        wv[worst], v[worst]))
 
 
 def test_2d_ragged_misaligned_and_sizes(ss):
