@@ -247,9 +247,223 @@ class Plain1D(Workload):
         return ns / dt, "first %d of the %d targets (same table), single thread" % (ns, self.m)
 
 
+class PlanWorkload(Workload):
+    """Common driver of the plan-based workloads: tables prepared once (not
+    timed; Sec. 5.3 set-up), then each step is one graph launch of the
+    persistent batched kernel over the bound batch."""
+    kernel = "k_batched_1d"
+    bytes_per_target = 8 + 4
+    model = "spline"
+
+    def __init__(self, model=None, autotune=True):
+        if model is not None:
+            self.model = model
+        self.autotune = autotune
+        self.plans = {}
+
+    def make_plan(self, model):
+        import paper_2112_03229_gb300 as ss
+        return ss.Plan.create_1d(self.b.X_off, self.b.X_dev, model=model, autotune=self.autotune,
+                                 tune_cache=os.path.join(ROOT, "_build", "tune_%s_%s.json" % (self.name, model)))
+
+    def setup(self, dev, seed):
+        import paper_2112_03229_gb300 as ss
+        self.ss = ss
+        self.b = self.generate(dev, seed)
+        self.b.X_dev = self.b.X.to(dev)
+        self.Y = self.b.Y.to(dev)
+        self.out = torch.empty(self.Y.shape, dtype=torch.int32, device=dev)
+        t0 = time.perf_counter()
+        self.plan = self.make_plan(self.model)
+        self.plan.bind_1d(self.b.Y_off, self.Y, self.out)
+        torch.cuda.synchronize()
+        self.setup_s = time.perf_counter() - t0
+
+    def step(self):
+        self.plan.execute()
+        return 1
+
+    def targets(self):
+        return int(self.b.Y_off[-1])
+
+    def compare(self, stream, steps):
+        """Plain plan (model none, autotuned) on the same bound batch, timed the same way."""
+        plain = self.make_plan("none")
+        plain.bind_1d(self.b.Y_off, self.Y, self.out)
+        for _ in range(3):
+            plain.execute()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            plain.execute()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res = {"model": "none", "Gtargets_s": round(self.targets() / (ms / 1e3) / 1e9, 3),
+               "ms_per_step": round(ms, 4), "choices": plain.choices()}
+        self.plan.bind_1d(self.b.Y_off, self.Y, self.out)
+        return res
+
+    def e2e_setup(self):
+        self.hY = torch.empty(self.Y.shape, dtype=torch.float64, pin_memory=True)
+        self.hY.copy_(self.Y)
+        self.hO = torch.empty(self.out.shape, dtype=torch.int32, pin_memory=True)
+        return self.hY.numel() * 8, self.hO.numel() * 4
+
+    def e2e_step(self):
+        self.Y.copy_(self.hY, non_blocking=True)
+        self.step()
+        self.hO.copy_(self.out, non_blocking=True)
+
+    def cpu_sample(self, budget_s):
+        import oracle
+        X_off, Y_off = self.b.X_off.cpu().numpy(), self.b.Y_off.cpu().numpy()
+        X = self.b.X.cpu().numpy()
+        # first tables of the batch, up to a target budget scaled from a probe
+        probe_n = 1 << 20
+        j = int(np.searchsorted(Y_off, probe_n, side="right"))
+        j = max(1, min(j, len(Y_off) - 1))
+        Yp = self.Y[: Y_off[j]].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.search_1d_batched(X_off[: j + 1], X, Y_off[: j + 1], Yp)
+        rate = Y_off[j] / max(time.perf_counter() - t0, 1e-9)
+        want = rate * budget_s
+        j = int(np.searchsorted(Y_off, want, side="right"))
+        j = max(1, min(j, len(Y_off) - 1))
+        Ys = self.Y[: Y_off[j]].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.search_1d_batched(X_off[: j + 1], X, Y_off[: j + 1], Ys)
+        dt = time.perf_counter() - t0
+        return Y_off[j] / dt, "first %d tables (%d targets) of the batch, single thread" % (j, Y_off[j])
+
+
+class Batched1D(PlanWorkload):
+    """10,000 tables (sizes log-uniform 20..2000), Zipf(1.1) target counts on
+    [1e3, 1e6] (about 1.1B targets), learned (spline) proposals vs plain."""
+    name = "batched1d-10k-zipf"
+
+    def generate(self, dev, seed):
+        from paper_2112_03229_gb300 import workloads as wl
+        return wl.batched_1d(ntables=10_000, seed=5 + 1000 * seed, device=dev)
+
+
+class Sweep1D(PlanWorkload):
+    """Table-size sweep: clustered tables of 16, 256, 4096 and 65536 entries,
+    256M log-uniform targets per table, learned (spline) proposals vs plain."""
+    name = "sweep1d-16-65536-256M"
+
+    def __init__(self, per_table=256 << 20, **kw):
+        super().__init__(**kw)
+        self.per_table = per_table
+
+    def generate(self, dev, seed):
+        from paper_2112_03229_gb300 import workloads as wl
+        tabs = [wl.sweep_table(n, seed=4 + 1000 * seed) for n in (16, 256, 4096, 65536)]
+        Ys = [wl.log_uniform(self.per_table, 0.5 * t[0].item(), 2 * t[-1].item(), seed=7 + i + 1000 * seed,
+                             device=dev) for i, t in enumerate(tabs)]
+        X = torch.cat(tabs)
+        X_off = torch.tensor(np.concatenate([[0], np.cumsum([len(t) for t in tabs])]))
+        Y_off = torch.tensor(np.concatenate([[0], np.cumsum([len(y) for y in Ys])]))
+        return wl.Batched1D(X_off, X, Y_off, torch.cat(Ys), None, None)
+
+
+class Batched2D(PlanWorkload):
+    """1,000 2D tables (axes U{50..500} x U{30..300}), 1M (rho, T) pairs each
+    (1B pairs), learned (spline) proposals on both axes vs plain."""
+    name = "batched2d-1000-1B"
+    kernel = "k_batched_2d"
+    bytes_per_target = 16 + 8 + 8
+
+    def __init__(self, coherent=False, pairs=1_000_000, **kw):
+        super().__init__(**kw)
+        self.coherent = coherent
+        self.pairs = pairs
+        if coherent:
+            self.name = "batched2d-1000-1B-coherent"
+
+    def make_plan(self, model):
+        import paper_2112_03229_gb300 as ss
+        b = self.b
+        return ss.Plan.create_2d(b.R_off, b.R_dev, b.T_off, b.T_dev, b.F_off, b.F_dev, model=model,
+                                 autotune=self.autotune,
+                                 tune_cache=os.path.join(ROOT, "_build", "tune_%s_%s.json" % (self.name, model)))
+
+    def setup(self, dev, seed):
+        import paper_2112_03229_gb300 as ss
+        from paper_2112_03229_gb300 import workloads as wl
+        self.ss = ss
+        b = wl.batched_2d(ntables=1000, pairs_per_table=self.pairs, coherent=self.coherent, seed=6 + 1000 * seed,
+                          device=dev)
+        b.R_dev, b.T_dev, b.F_dev = b.R.to(dev), b.T.to(dev), b.F.to(dev)
+        self.b = b
+        self.Y = b.Y2
+        self.m = b.Y2.shape[0]
+        self.idx = torch.empty((self.m, 2), dtype=torch.int32, device=dev)
+        self.val = torch.empty(self.m, dtype=torch.float64, device=dev)
+        t0 = time.perf_counter()
+        self.plan = self.make_plan(self.model)
+        self.plan.bind_2d(b.Y_off, self.Y, self.idx, self.val)
+        torch.cuda.synchronize()
+        self.setup_s = time.perf_counter() - t0
+
+    def targets(self):
+        return self.m
+
+    def compare(self, stream, steps):
+        plain = self.make_plan("none")
+        plain.bind_2d(self.b.Y_off, self.Y, self.idx, self.val)
+        for _ in range(3):
+            plain.execute()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            plain.execute()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res = {"model": "none", "Gtargets_s": round(self.m / (ms / 1e3) / 1e9, 3), "ms_per_step": round(ms, 4),
+               "choices": plain.choices()}
+        self.plan.bind_2d(self.b.Y_off, self.Y, self.idx, self.val)
+        return res
+
+    def e2e_setup(self):
+        self.hY = torch.empty(self.Y.shape, dtype=torch.float64, pin_memory=True)
+        self.hY.copy_(self.Y)
+        self.hI = torch.empty(self.idx.shape, dtype=torch.int32, pin_memory=True)
+        self.hV = torch.empty(self.val.shape, dtype=torch.float64, pin_memory=True)
+        return self.hY.numel() * 8, self.hI.numel() * 4 + self.hV.numel() * 8
+
+    def e2e_step(self):
+        self.Y.copy_(self.hY, non_blocking=True)
+        self.step()
+        self.hI.copy_(self.idx, non_blocking=True)
+        self.hV.copy_(self.val, non_blocking=True)
+
+    def cpu_sample(self, budget_s):
+        import oracle
+        b = self.b
+        offs = [o.cpu().numpy() for o in (b.R_off, b.T_off, b.F_off, b.Y_off)]
+        R, T, F = b.R.cpu().numpy(), b.T.cpu().numpy(), b.F.cpu().numpy()
+        per = int(offs[3][1] - offs[3][0])
+        ntab = max(1, min(len(offs[3]) - 1, int(budget_s * 9e6 / max(per, 1))))
+        j = ntab
+        Y = self.Y[: offs[3][j]].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.search_interp_2d_batched(offs[0][: j + 1], R, offs[1][: j + 1], T, offs[2][: j + 1], F,
+                                        offs[3][: j + 1], Y)
+        dt = time.perf_counter() - t0
+        return offs[3][j] / dt, "first %d tables (%d pairs) of the batch, single thread" % (j, offs[3][j])
+
+
 WORKLOADS = {
     "interp2d": Interp2D,
     "plain1d": Plain1D,
+    "batched1d": Batched1D,
+    "sweep1d": Sweep1D,
+    "batched2d": Batched2D,
+    "batched2d-coherent": lambda: Batched2D(coherent=True),
 }
 DEFAULT_WORKLOAD = "interp2d"
 
@@ -315,12 +529,17 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--targets", type=int, default=0, help="override the workload's target count (profiling cases)")
+    ap.add_argument("--model", default=None, choices=["none", "spline", "mlp"],
+                    help="position model of the plan-based workloads (default spline)")
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain-plan comparison of plan workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     wl_obj = WORKLOADS[args.workload]()
     if args.targets:
         wl_obj.m = args.targets
+    if args.model is not None and isinstance(wl_obj, PlanWorkload):
+        wl_obj.model = args.model
     if args.impl == "reference":
         return run_reference(args, wl_obj)
 
@@ -385,6 +604,18 @@ def main():
         rate, sample = wl_obj.cpu_sample(args.cpu_budget)
         cpu = {"value": rate / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
 
+    extra = {}
+    if isinstance(wl_obj, PlanWorkload):
+        inf = wl_obj.plan.info()
+        extra["plan"] = {"model": wl_obj.model, "setup_s": round(wl_obj.setup_s, 2), "choices": wl_obj.plan.choices(),
+                         "max_window": inf.max_window, "mean_window": round(inf.mean_window, 2),
+                         "train_loss": inf.train_loss, "ntiles": inf.ntiles}
+        if world == 1 and not args.no_compare and wl_obj.model != "none":
+            pl = wl_obj.compare(stream, args.steps)
+            pl["frac"] = round(wl_obj.targets() * wl_obj.bytes_per_target / (pl["ms_per_step"] / 1e3) / 1e9 / peak, 4)
+            extra["plain"] = pl
+            extra["learned_over_plain"] = round(value / pl["Gtargets_s"], 3)
+
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": True,
@@ -395,6 +626,10 @@ def main():
                 "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "clocks": clk.summary()}
+        if isinstance(wl_obj, PlanWorkload):
+            line["config"]["model"] = wl_obj.model
+            line["config"]["setup"] = "tables prepared once before timing (plan creation, Sec. 5.3)"
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

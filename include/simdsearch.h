@@ -142,7 +142,7 @@ typedef struct ss_plan_opts {
   int32_t autotune;         /* 1: time the candidates of each table-size bucket and keep the fastest */
   int32_t tile;             /* targets per tile; 0: library default or tuned */
   int32_t mlp_epochs;       /* full-batch Adam steps of the MLP (default 400; 0 keeps the untrained initialisation) */
-  float mlp_lr;             /* Adam learning rate (default 1e-2) */
+  float mlp_lr;             /* peak Adam learning rate, cosine-decayed (default 2e-3) */
   int32_t dir_cap;          /* bucket-directory budget per table (0: 16 n clamped to [64, 8192]) */
   uint64_t seed;            /* seed of the counter-based sampler of training and probe targets */
   const char* tune_cache;   /* JSON file the autotuner reads and writes (NULL: none) */

@@ -28,7 +28,7 @@ constexpr int kMaxAxis2D = 4096;   // largest axis staged whole with its per-cel
 
 struct Axis2D {                    // shared-memory offsets of one axis
   Layout1D lay;
-  int cells;                       // CellFF[n-1]: X[c] bits and the float-float weight scale
+  int cells;                       // CellFF[n]: X[c] bits and the float-float weight scale (last: X[n-1] only)
   int rg;                          // double[n-1]: 1 / (X[c+1] - X[c]) for the fp64 path
   int aux;                         // AxisAux
 };
@@ -62,6 +62,7 @@ static __device__ void stage_cells(const double* __restrict__ X, int n, const Ax
   double* rg = reinterpret_cast<double*>(smem + ax.rg);
   AxisAux& aux = *reinterpret_cast<AxisAux*>(smem + ax.aux);
   bool ok = true;
+  if (threadIdx.x == 0) cells[n - 1] = CellFF{static_cast<uint64_t>(__double_as_longlong(__ldg(X + n - 1))), 0.0f, 0.0f};
   for (int c = threadIdx.x; c < n - 1; c += blockDim.x) {
     const double a = __ldg(X + c), b = __ldg(X + c + 1);
     const double gap = b - a;
@@ -127,11 +128,11 @@ __device__ __forceinline__ int axis_search(const AxisView& a, uint64_t k) {
   return search_eyt_rt(a.eyt, a.D, k);
 }
 
-// Float-float weight of a target with key k and bits u whose lower-bound index is i.
-__device__ __forceinline__ ff axis_weight_ff(const AxisView& a, int i, int c, uint64_t k, uint64_t u) {
-  if (i >= a.n - 1) return {1.0f, 0.0f};                 // above the last entry
-  if (i == 0 && k <= a.k0) return {0.0f, 0.0f};          // at or below the first entry
-  return ff_clamp01(cell_weight(u, a.cells[c]));
+// Float-float weights (w, 1 - w) of a target with key k and bits u whose lower-bound index is i.
+__device__ __forceinline__ Weights axis_weights_ff(const AxisView& a, int i, int c, uint64_t k, uint64_t u) {
+  if (i >= a.n - 1) return {{1.0f, 0.0f}, {0.0f, 0.0f}};          // above the last entry
+  if (i == 0 && k <= a.k0) return {{0.0f, 0.0f}, {1.0f, 0.0f}};   // at or below the first entry
+  return cell_weights(u, a.cells[c], a.cells[c + 1].xbits);
 }
 
 // Convex blend in fp64 (fallback path of a pair).
@@ -139,6 +140,12 @@ __device__ __forceinline__ double blend64(double wr, double wt, double f00, doub
   const double lo = (1.0 - wt) * f00 + wt * f01;
   const double hi = (1.0 - wt) * f10 + wt * f11;
   return (1.0 - wr) * lo + wr * hi;
+}
+
+// Same with both weights of each axis given.
+__device__ __forceinline__ double blend64w(double wr, double wrb, double wt, double wtb, double f00, double f01,
+                                          double f10, double f11) {
+  return wrb * (wtb * f00 + wt * f01) + wr * (wtb * f10 + wt * f11);
 }
 
 // One pair: indices and value.  MODE 0: both axes bucket with occupancy <= 1;
@@ -162,19 +169,18 @@ __device__ __forceinline__ void lookup_pair(const AxisView& vr, const AxisView& 
     v = blend64(wr, wt, f00, f01, f10, f11);
     return;
   }
-  const ff wr = axis_weight_ff(vr, ir, cr, kr, ur);
-  const ff wt = axis_weight_ff(vt, it, ct, kt, ut);
+  const Weights wr = axis_weights_ff(vr, ir, cr, kr, ur);
+  const Weights wt = axis_weights_ff(vt, it, ct, kt, ut);
   ff a00, a01, a10, a11;
   const bool ok = d2ff(f00, a00) & d2ff(f01, a01) & d2ff(f10, a10) & d2ff(f11, a11);
   if (nan) {
     v = __longlong_as_double(0x7FF8000000000000ll);
   } else if (ok) {
-    const ff omt = ff_one_minus(wt), omr = ff_one_minus(wr);
-    const ff lo = ff_add(ff_mul(omt, a00), ff_mul(wt, a01));
-    const ff hi = ff_add(ff_mul(omt, a10), ff_mul(wt, a11));
-    v = ff2d(ff_add(ff_mul(omr, lo), ff_mul(wr, hi)));
+    const ff lo = ff_add(ff_mul(wt.wbar, a00), ff_mul(wt.w, a01));
+    const ff hi = ff_add(ff_mul(wt.wbar, a10), ff_mul(wt.w, a11));
+    v = ff2d(ff_add(ff_mul(wr.wbar, lo), ff_mul(wr.w, hi)));
   } else {
-    v = blend64(ff2d(wr), ff2d(wt), f00, f01, f10, f11);
+    v = blend64w(ff2d(wr.w), ff2d(wr.wbar), ff2d(wt.w), ff2d(wt.wbar), f00, f01, f10, f11);
   }
 }
 
@@ -247,7 +253,7 @@ static Axis2D make_axis(int n, int algo, int offset) {
   ax.lay = make_layout_1d(n, bucket, !bucket, bucket ? default_dir_cap(n) : 0, offset);
   int off = ax.lay.bytes;
   auto take = [&](int bytes) { int o = off; off += (bytes + 15) & ~15; return o; };
-  ax.cells = take((n - 1) * (int)sizeof(CellFF));
+  ax.cells = take(n * (int)sizeof(CellFF));
   ax.rg = take((n - 1) * 8);
   ax.aux = take((int)sizeof(AxisAux));
   ax.lay.bytes = off;   // end of this axis' region

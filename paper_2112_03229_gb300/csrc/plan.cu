@@ -111,7 +111,7 @@ extern "C" void ss_plan_opts_default(ss_plan_opts* o) {
   o->autotune = 0;
   o->tile = 0;
   o->mlp_epochs = 400;
-  o->mlp_lr = 1e-2f;
+  o->mlp_lr = 2e-3f;
   o->dir_cap = 0;
   o->seed = 0x5EEDull;
   o->tune_cache = nullptr;

@@ -171,6 +171,30 @@ __global__ void __launch_bounds__(kTrainThreads) k_train_mlp(TrainArgs a) {
     ys[i] = (float)count_keys_below(v, q) * inv;
   }
   __syncthreads();
+  // Initialisation from the data: hinge k sits at the normalised log2
+  // coordinate z of the table entry at quantile k/16, and the output weights
+  // make the network the piecewise-linear interpolant of the 17 quantile
+  // points (slope changes at the hinges).  Adam then minimises the MSE.
+  if (threadIdx.x == 0) {
+    float zk[kHidden + 1], yk[kHidden + 1];
+    for (int q = 0; q <= kHidden; ++q) {
+      const int i = (int)(((int64_t)q * (nkeys - 1)) / kHidden);
+      zk[q] = xs[i][0] + h.e_scale * xs[i][1];
+      yk[q] = ys[i];
+    }
+    float prev = 0.0f;
+    for (int q = 0; q < kHidden; ++q) {
+      const float dz = zk[q + 1] - zk[q];
+      const float slope = dz > 0.0f ? (yk[q + 1] - yk[q]) / dz : 0.0f;
+      p[2 * q] = 1.0f;
+      p[2 * q + 1] = h.e_scale;
+      p[2 * kHidden + q] = -zk[q];
+      p[3 * kHidden + q] = slope - prev;
+      prev = slope;
+    }
+    p[4 * kHidden] = yk[0];
+  }
+  __syncthreads();
   float m1 = 0.0f, m2 = 0.0f;     // Adam moments of parameter threadIdx.x
   const float lr = a.lr, b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const float scale = 1.0f / (float)kTrainSamples;
@@ -185,14 +209,16 @@ __global__ void __launch_bounds__(kTrainThreads) k_train_mlp(TrainArgs a) {
     loss = red[0][kMlpParams] * scale;
     if (threadIdx.x < kMlpParams) {
       const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+      // cosine decay of the learning rate to 5% over the run
+      const float lr_t = lr * (0.05f + 0.475f * (1.0f + cospif((float)(step - 1) / (float)a.epochs)));
       float pv = p[threadIdx.x];
-      adam_update(pv, red[0][threadIdx.x], m1, m2, lr, b1, b2, eps, c1, c2);
+      adam_update(pv, red[0][threadIdx.x], m1, m2, lr_t, b1, b2, eps, c1, c2);
       p[threadIdx.x] = pv;
     }
     __syncthreads();
   }
   for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) gp[i] = p[i];
-  if (threadIdx.x == 0) gh->loss = loss;
+  if (threadIdx.x == 0) gh->loss = a.epochs > 0 ? loss : 0.0f;
 }
 
 // ---------------------------------------------------------------------------

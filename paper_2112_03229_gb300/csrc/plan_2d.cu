@@ -73,20 +73,23 @@ __device__ __forceinline__ int axis_count(const StagedView& v, double t, uint64_
   }
 }
 
-// Weight of a coordinate on an axis (float-float; fp64 division when the axis
-// is outside the float-float preconditions).
-__device__ __forceinline__ ff axis_weight(const StagedView& v, int i, int c, uint64_t k, double x) {
+// Weights (w, 1 - w) of a coordinate on an axis (float-float; fp64 division
+// when the axis is outside the float-float preconditions).
+__device__ __forceinline__ Weights axis_weights(const StagedView& v, int i, int c, uint64_t k, double x) {
   const BlobHdr& h = *v.h;
-  if (i >= h.n - 1) return {1.0f, 0.0f};
-  if (i == 0 && k <= h.k0) return {0.0f, 0.0f};
-  if (h.ffok) return ff_clamp01(cell_weight(static_cast<uint64_t>(__double_as_longlong(x)), v.cells[c]));
+  if (i >= h.n - 1) return {{1.0f, 0.0f}, {0.0f, 0.0f}};
+  if (i == 0 && k <= h.k0) return {{0.0f, 0.0f}, {1.0f, 0.0f}};
+  if (h.ffok) return cell_weights(static_cast<uint64_t>(__double_as_longlong(x)), v.cells[c], v.cells[c + 1].xbits);
   const double a = __longlong_as_double((long long)v.cells[c].xbits);
   const double b = __longlong_as_double((long long)v.cells[c + 1].xbits);
   double w = (x - a) / (b - a);
   w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
-  ff r;
-  r.hi = __double2float_rn(w);
-  r.lo = __double2float_rn(w - (double)r.hi);
+  const double wb = 1.0 - w;
+  Weights r;
+  r.w.hi = __double2float_rn(w);
+  r.w.lo = __double2float_rn(w - (double)r.w.hi);
+  r.wbar.hi = __double2float_rn(wb);
+  r.wbar.lo = __double2float_rn(wb - (double)r.wbar.hi);
   return r;
 }
 
@@ -102,20 +105,19 @@ __device__ __forceinline__ void pair_2d(const StagedView& vr, const StagedView& 
   const int cr = min(ir, vr.h->n - 2), ct = min(it, nt - 2);
   const int64_t o = (int64_t)cr * nt + ct;
   const float2 g00 = __ldg(G + o), g01 = __ldg(G + o + 1), g10 = __ldg(G + o + nt), g11 = __ldg(G + o + nt + 1);
-  const ff wr = axis_weight(vr, ir, cr, kr, rho);
-  const ff wt = axis_weight(vt, it, ct, kt, tem);
+  const Weights wr = axis_weights(vr, ir, cr, kr, rho);
+  const Weights wt = axis_weights(vt, it, ct, kt, tem);
   if (nan) {
     v = __longlong_as_double(0x7FF8000000000000ll);
   } else if (!(isnan(g00.x) | isnan(g01.x) | isnan(g10.x) | isnan(g11.x))) {
-    const ff omt = ff_one_minus(wt), omr = ff_one_minus(wr);
-    const ff lo = ff_add(ff_mul(omt, ff{g00.x, g00.y}), ff_mul(wt, ff{g01.x, g01.y}));
-    const ff hi = ff_add(ff_mul(omt, ff{g10.x, g10.y}), ff_mul(wt, ff{g11.x, g11.y}));
-    v = ff2d(ff_add(ff_mul(omr, lo), ff_mul(wr, hi)));
+    const ff lo = ff_add(ff_mul(wt.wbar, ff{g00.x, g00.y}), ff_mul(wt.w, ff{g01.x, g01.y}));
+    const ff hi = ff_add(ff_mul(wt.wbar, ff{g10.x, g10.y}), ff_mul(wt.w, ff{g11.x, g11.y}));
+    v = ff2d(ff_add(ff_mul(wr.wbar, lo), ff_mul(wr.w, hi)));
   } else {
-    const double w1 = ff2d(wr), w2 = ff2d(wt);
-    const double lo = (1.0 - w2) * G64[o] + w2 * G64[o + 1];
-    const double hi = (1.0 - w2) * G64[o + nt] + w2 * G64[o + nt + 1];
-    v = (1.0 - w1) * lo + w1 * hi;
+    const double w1 = ff2d(wr.w), w1b = ff2d(wr.wbar), w2 = ff2d(wt.w), w2b = ff2d(wt.wbar);
+    const double lo = w2b * G64[o] + w2 * G64[o + 1];
+    const double hi = w2b * G64[o + nt] + w2 * G64[o + nt + 1];
+    v = w1b * lo + w1 * hi;
   }
 }
 
@@ -270,7 +272,7 @@ ss_status plan_build_2d(ss_plan* p, const double* R, const double* T, const doub
     }
     if (o.model == SS_MODEL_MLP && o.mlp_epochs > 0) {
       TrainArgs ta{2 * nt, p->d_blobs, p->d_blob_off, o.mlp_epochs,
-                   o.mlp_lr > 0 ? o.mlp_lr : 1e-2f, o.seed};
+                   o.mlp_lr > 0 ? o.mlp_lr : 2e-3f, o.seed};
       k_train_mlp<<<2 * nt, 256, 0, stream>>>(ta);
       SS_CHECK_CUDA(cudaGetLastError());
     }

@@ -139,7 +139,7 @@ ss_status plan_build_1d(ss_plan* p, const double* X, cudaStream_t stream) {
          SS_CHECK_CUDA(cudaGetLastError());
          if (o.model == SS_MODEL_MLP && o.mlp_epochs > 0) {
            TrainArgs ta{nt, p->d_blobs, p->d_blob_off, o.mlp_epochs,
-                        o.mlp_lr > 0 ? o.mlp_lr : 1e-2f, o.seed};
+                        o.mlp_lr > 0 ? o.mlp_lr : 2e-3f, o.seed};
            k_train_mlp<<<nt, 256, 0, stream>>>(ta);
            SS_CHECK_CUDA(cudaGetLastError());
          }

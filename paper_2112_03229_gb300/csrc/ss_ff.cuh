@@ -111,15 +111,28 @@ struct CellFF {
   float ghi, glo;   // g_c = 2^(e_c - 1075) / (X[c+1] - X[c]) as float-float
 };
 
-// Weight of target x (bit pattern u, positive normal, X[c] < x <= X[c+1]) in cell c.
-__device__ __forceinline__ ff cell_weight(uint64_t u, const CellFF& cell) {
+// Both weights of target x (bit pattern u, positive normal, X[c] < x <= X[c+1])
+// in cell c: w = (x - X[c]) / gap and wbar = (X[c+1] - x) / gap.  Each
+// numerator is an exact integer (no cancellation), so wbar keeps full
+// relative precision when w is close to 1 instead of being formed as 1 - w.
+struct Weights {
+  ff w, wbar;
+};
+
+__device__ __forceinline__ Weights cell_weights(uint64_t u, const CellFF& cell, uint64_t next_bits) {
   const int ex = (int)((u >> 52) & 0x7FF);
   const int ec = (int)((cell.xbits >> 52) & 0x7FF);
-  const uint64_t Mx = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int en = (int)((next_bits >> 52) & 0x7FF);
+  const uint64_t Mx = ((u & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << (ex - ec);
   const uint64_t Mc = (cell.xbits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const uint64_t D = (Mx << (ex - ec)) - Mc;           // exact: x - X[c] in units of 2^(ec - 1075)
-  if (D == 0) return {0.0f, 0.0f};
-  return ff_mul(u64_to_ff(D), ff{cell.ghi, cell.glo});
+  const uint64_t Mn = ((next_bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << (en - ec);
+  const uint64_t D = Mx - Mc;          // x - X[c]    in units of 2^(ec - 1075)
+  const uint64_t Dn = Mn - Mx;         // X[c+1] - x  in the same units
+  const ff g{cell.ghi, cell.glo};
+  Weights r;
+  r.w = D == 0 ? ff{0.0f, 0.0f} : ff_mul(u64_to_ff(D), g);
+  r.wbar = Dn == 0 ? ff{0.0f, 0.0f} : ff_mul(u64_to_ff(Dn), g);
+  return r;
 }
 
 __device__ __forceinline__ ff ff_clamp01(ff w) {
