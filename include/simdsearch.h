@@ -205,6 +205,33 @@ ss_status ss_plan_load(ss_plan** plan, const char* path, cudaStream_t stream);
 void ss_plan_destroy(ss_plan* plan);
 
 /* ---------------------------------------------------------------------- */
+/* Batched search without device allocation                                */
+/* ---------------------------------------------------------------------- */
+
+/* The paper has no counterpart of this entry point; it exists for callers
+ * that may not allocate device memory themselves or through this library:
+ * code that works inside a fixed device-memory budget owned by a host
+ * framework, loops that cannot take cudaMalloc's implicit synchronisation,
+ * plug-ins that leave all device memory management to their host.
+ *
+ * Same result as a plan without a model (bucket search) over ntables tables:
+ * table k is X[X_off[k] .. X_off[k+1]) and its targets Y[Y_off[k] ..
+ * Y_off[k+1]) (X_off, Y_off host arrays of ntables+1 entries; X, Y,
+ * lowbounds device), answers at the same positions of lowbounds.  It calls
+ * no cudaMalloc/cudaFree: prepared tables, tile list and tile counter live in
+ * one 8 MiB array inside the library that every GPU loading the library
+ * holds until the process exits.  A batch whose working set exceeds 8 MiB is
+ * rejected with SS_EINVAL (about 250 tables of 2000 entries fit).  Every
+ * call reuses that array and clears what must start at zero, so calls whose
+ * work overlaps on the GPU (other streams or host threads) race: serialise
+ * them.  The first call on each device looks up the array's device address;
+ * make that first call before any stream capture.  A table that is not
+ * strictly increasing sets SS_FLAG_NOT_SORTED in *stat. */
+ss_status ss_search_1d_batched_static(int32_t ntables, const int64_t* X_off, const double* X,
+                                      const int64_t* Y_off, const double* Y, int32_t* lowbounds,
+                                      int32_t side, ss_devstat* stat, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------- */
 /* Status and diagnostics                                                  */
 /* ---------------------------------------------------------------------- */
 

@@ -318,3 +318,22 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def search_1d_batched_static(X_off, X, Y_off, Y, out=None, side=SIDE_LT, stat=None, stream=None):
+    """ss_search_1d_batched_static: batched bucket search that allocates no
+    device memory (its working set lives in a fixed 8 MiB array of the library)."""
+    L = lib()
+    if not hasattr(L, "_static_sig"):
+        L.ss_search_1d_batched_static.argtypes = [_i32, C.POINTER(C.c_int64), _vp, C.POINTER(C.c_int64), _vp, _vp,
+                                                  _i32, _vp, _vp]
+        L.ss_search_1d_batched_static.restype = _i32
+        L._static_sig = True
+    xo, xp = _offsets(X_off)
+    yo, yp = _offsets(Y_off)
+    if out is None:
+        out = torch.empty(Y.shape, dtype=torch.int32, device=Y.device)
+    _check(L.ss_search_1d_batched_static(len(xo) - 1, xp, _dev(X, torch.float64, "X"), yp,
+                                         _dev(Y, torch.float64, "Y"), _dev(out, torch.int32, "out"), side,
+                                         _statp(stat), _stream(stream)))
+    return out
