@@ -171,17 +171,17 @@ class Interp2D(Workload):
         return self.m
 
     def e2e_setup(self):
+        """Host arrays (page-locked) through ss_search_interp_2d_host, which
+        pipelines the copies and the search inside the library."""
         self.hY = torch.empty(self.Y2.shape, dtype=torch.float64, pin_memory=True)
         self.hY.copy_(self.Y2)
         self.hI = torch.empty(self.idx.shape, dtype=torch.int32, pin_memory=True)
         self.hV = torch.empty(self.val.shape, dtype=torch.float64, pin_memory=True)
+        self.hR, self.hT, self.hF = self.R.cpu(), self.T.cpu(), self.F.cpu()
         return self.hY.numel() * 8, self.hI.numel() * 4 + self.hV.numel() * 8
 
     def e2e_step(self):
-        self.Y2.copy_(self.hY, non_blocking=True)
-        self.step()
-        self.hI.copy_(self.idx, non_blocking=True)
-        self.hV.copy_(self.val, non_blocking=True)
+        self.ss.search_interp_2d_host(self.hR, self.hT, self.hF, self.hY, idx=self.hI, val=self.hV)
 
     def cpu_sample(self, budget_s):
         import oracle
@@ -205,7 +205,14 @@ class Plain1D(Workload):
     bytes_per_target = 8 + 4
 
     def __init__(self, m=1 << 30, algo="auto"):
-        self.m, self.algo = m, algo
+        self.m, self.algo, self.g = m, algo, 0
+
+    def set_algo(self, name):
+        kern = {"auto": "bucket", "ballot8": "ballot", "ballot16": "ballot"}.get(name, name)
+        self.kernel = "k_search_1d_" + kern
+        self.algo = "ballot" if name.startswith("ballot") else name
+        self.g = {"ballot8": 8, "ballot16": 16, "ballot": 32}.get(name, 0)
+        self.name = "plain1d-n64-1B-" + name
 
     def setup(self, dev, seed):
         from paper_2112_03229_gb300 import workloads as wl
@@ -215,22 +222,22 @@ class Plain1D(Workload):
         self.out = torch.empty((self.m,), dtype=torch.int32, device=dev)
 
     def step(self):
-        self.ss.search_1d(self.X, self.Y, out=self.out, algo=self.algo)
+        self.ss.search_1d(self.X, self.Y, out=self.out, algo=self.algo, ballot_g=self.g)
         return 1
 
     def targets(self):
         return self.m
 
     def e2e_setup(self):
+        """Host arrays (page-locked) through ss_search_1d_host."""
         self.hY = torch.empty(self.Y.shape, dtype=torch.float64, pin_memory=True)
         self.hY.copy_(self.Y)
         self.hO = torch.empty(self.out.shape, dtype=torch.int32, pin_memory=True)
+        self.hX = self.X.cpu()
         return self.hY.numel() * 8, self.hO.numel() * 4
 
     def e2e_step(self):
-        self.Y.copy_(self.hY, non_blocking=True)
-        self.step()
-        self.hO.copy_(self.out, non_blocking=True)
+        self.ss.search_1d_host(self.hX, self.hY, out=self.hO, algo=self.algo)
 
     def cpu_sample(self, budget_s):
         import oracle
@@ -340,12 +347,15 @@ class PlanWorkload(Workload):
 
 class Batched1D(PlanWorkload):
     """10,000 tables (sizes log-uniform 20..2000), Zipf(1.1) target counts on
-    [1e3, 1e6] (about 1.1B targets), learned (spline) proposals vs plain."""
+    [1e3, 1e6] (about 1.1B targets), learned (spline) proposals vs plain.
+    --targets scales the counts (profiling cases)."""
     name = "batched1d-10k-zipf"
+    m = 0
 
     def generate(self, dev, seed):
         from paper_2112_03229_gb300 import workloads as wl
-        return wl.batched_1d(ntables=10_000, seed=5 + 1000 * seed, device=dev)
+        scale = self.m / 1.1e9 if self.m else 1.0
+        return wl.batched_1d(ntables=10_000, seed=5 + 1000 * seed, count_scale=scale, device=dev)
 
 
 class Sweep1D(PlanWorkload):
@@ -366,6 +376,38 @@ class Sweep1D(PlanWorkload):
         X_off = torch.tensor(np.concatenate([[0], np.cumsum([len(t) for t in tabs])]))
         Y_off = torch.tensor(np.concatenate([[0], np.cumsum([len(y) for y in Ys])]))
         return wl.Batched1D(X_off, X, Y_off, torch.cat(Ys), None, None)
+
+
+def sweep_per_table(wl_obj, stream, steps):
+    """Per-table Gtargets/s of the sweep: one plan per table and model."""
+    import paper_2112_03229_gb300 as ss
+    b = wl_obj.b
+    X_off, Y_off = b.X_off.tolist(), b.Y_off.tolist()
+    res = {}
+    for k in range(len(X_off) - 1):
+        X = b.X_dev[X_off[k]:X_off[k + 1]]
+        Y = wl_obj.Y[Y_off[k]:Y_off[k + 1]]
+        out = wl_obj.out[Y_off[k]:Y_off[k + 1]]
+        row = {}
+        for model in ("none", "spline", "mlp"):
+            plan = ss.Plan.create_1d([0, X.numel()], X, model=model, autotune=(model == "none"))
+            plan.bind_1d([0, Y.numel()], Y, out)
+            for _ in range(3):
+                plan.execute()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                plan.execute()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            inf = plan.info()
+            row[model] = {"Gtargets_s": round(Y.numel() / (ms / 1e3) / 1e9, 2), "window": inf.max_window,
+                          "algo": list(plan.choices().values())[0][0]}
+        res[str(X.numel())] = row
+    wl_obj.plan.bind_1d(b.Y_off, wl_obj.Y, wl_obj.out)
+    return res
 
 
 class Batched2D(PlanWorkload):
@@ -519,12 +561,45 @@ def run_reference(args, wl_obj):
     print(json.dumps(line), flush=True)
 
 
+def small_m_latency(args):
+    """Per-call latency for small batches (the set-up-dominated regime of
+    Sec. 5.1 / 5.3): one-shot call (no set-up kept) vs a prepared plan
+    replayed as a CUDA graph, on the 64-entry table; medians of 50 calls."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2112_03229_gb300 as ss
+    from paper_2112_03229_gb300 import workloads as wl
+    dev = torch.device("cuda", 0)
+    X, Y = wl.plain_1d(m=1 << 20, seed=1, device=dev)
+    res = {}
+    for m in (1, 100, 10_000, 1_000_000):
+        y = Y[:m].contiguous()
+        out = torch.empty(m, dtype=torch.int32, device=dev)
+        plan = ss.Plan.create_1d([0, X.numel()], X)
+        plan.bind_1d([0, m], y, out)
+        row = {}
+        for name, fn in (("one_shot", lambda: ss.search_1d(X, y, out=out)), ("plan_graph", plan.execute)):
+            for _ in range(5):
+                fn()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(50):
+                t0 = time.perf_counter()
+                fn()
+                torch.cuda.synchronize()
+                ts.append((time.perf_counter() - t0) * 1e6)
+            row[name + "_us"] = round(statistics.median(ts), 2)
+        res[str(m)] = row
+    print(json.dumps({"metric": "per-call latency (us), small target batches", "unit": "us", "n_gpus": 1,
+                      "config": {"workload": "latency-n64", "table": 64}, "latency": res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["latency"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -532,14 +607,20 @@ def main():
     ap.add_argument("--model", default=None, choices=["none", "spline", "mlp"],
                     help="position model of the plan-based workloads (default spline)")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-plan comparison of plan workloads")
+    ap.add_argument("--algo", default=None, choices=["auto", "bucket", "binary", "branchy", "ballot", "ballot8", "ballot16"],
+                    help="in-block search of the plain1d workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "latency":
+        return small_m_latency(args)
     wl_obj = WORKLOADS[args.workload]()
     if args.targets:
         wl_obj.m = args.targets
     if args.model is not None and isinstance(wl_obj, PlanWorkload):
         wl_obj.model = args.model
+    if args.algo is not None and isinstance(wl_obj, Plain1D):
+        wl_obj.set_algo(args.algo)
     if args.impl == "reference":
         return run_reference(args, wl_obj)
 
@@ -583,13 +664,11 @@ def main():
         wl_obj.e2e_step()
     torch.cuda.synchronize()
     barrier(world)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    t0 = time.perf_counter()
     for _ in range(args.steps):
         wl_obj.e2e_step()
-    e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, world)
     e2e_value = wl_obj.targets() * args.steps * world / (e2e_ms / 1e3) / 1e9
 
     peak, peak_kind = hbm_peak()
@@ -615,6 +694,8 @@ def main():
             pl["frac"] = round(wl_obj.targets() * wl_obj.bytes_per_target / (pl["ms_per_step"] / 1e3) / 1e9 / peak, 4)
             extra["plain"] = pl
             extra["learned_over_plain"] = round(value / pl["Gtargets_s"], 3)
+        if isinstance(wl_obj, Sweep1D) and world == 1 and not args.no_compare:
+            extra["per_table"] = sweep_per_table(wl_obj, stream, args.steps)
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,

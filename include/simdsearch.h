@@ -111,6 +111,21 @@ ss_status ss_search_interp_2d(const double* R, int32_t nr, const double* T, int3
                               int32_t* lowbounds2, double* values, int32_t algo,
                               ss_devstat* stat, cudaStream_t stream);
 
+/* Host-array forms of the two calls above, for callers whose targets live
+ * in host memory (EOSPAC's callers pass host arrays, Sec. 1 and 2.2).  Every
+ * pointer is host memory.  The library streams the targets through the GPU
+ * in chunks, overlapping host-to-device copies, the search and
+ * device-to-host copies on two streams; page-locked buffers give link-speed
+ * copies, pageable ones work through the driver's staging.  Synchronous: the
+ * results are in host memory when the call returns.  Device staging memory is
+ * allocated on first use per device and kept; calls on one device are
+ * serialised. */
+ss_status ss_search_1d_host(const double* X, int32_t n, const double* Y, int64_t m, int32_t* lowbounds,
+                            int32_t side, int32_t algo);
+ss_status ss_search_interp_2d_host(const double* R, int32_t nr, const double* T, int32_t nt,
+                                   const double* F, const double* Y2, int64_t m, int32_t* lowbounds2,
+                                   double* values, int32_t algo);
+
 /* ---------------------------------------------------------------------- */
 /* Plans: set-up once per set of loaded tables, then many searches.        */
 /* EOSPAC loads its tables once at program start, so search set-up is paid  */

@@ -337,3 +337,51 @@ def search_1d_batched_static(X_off, X, Y_off, Y, out=None, side=SIDE_LT, stat=No
                                          _dev(Y, torch.float64, "Y"), _dev(out, torch.int32, "out"), side,
                                          _statp(stat), _stream(stream)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Host-array forms (pipelined copies + search inside the library)
+# ---------------------------------------------------------------------------
+def _host(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError("%s must be a host (CPU) tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s" % (name, dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return C.c_void_p(t.data_ptr())
+
+
+def _host_lib():
+    L = lib()
+    if not hasattr(L, "_host_sig"):
+        L.ss_search_1d_host.argtypes = [_vp, _i32, _vp, _i64, _vp, _i32, _i32]
+        L.ss_search_interp_2d_host.argtypes = [_vp, _i32, _vp, _i32, _vp, _vp, _i64, _vp, _vp, _i32]
+        L.ss_search_1d_host.restype = _i32
+        L.ss_search_interp_2d_host.restype = _i32
+        L._host_sig = True
+    return L
+
+
+def search_1d_host(X, Y, out=None, side=SIDE_LT, algo="auto"):
+    """ss_search_1d_host: all arrays in host memory (pin them for full copy speed)."""
+    L = _host_lib()
+    if out is None:
+        out = torch.empty(Y.shape, dtype=torch.int32)
+    _check(L.ss_search_1d_host(_host(X, torch.float64, "X"), X.numel(), _host(Y, torch.float64, "Y"), Y.numel(),
+                               _host(out, torch.int32, "out"), side, _algo(algo)))
+    return out
+
+
+def search_interp_2d_host(R, T, F, Y2, idx=None, val=None, algo="auto"):
+    """ss_search_interp_2d_host: all arrays in host memory."""
+    L = _host_lib()
+    m = Y2.numel() // 2
+    if idx is None:
+        idx = torch.empty((m, 2), dtype=torch.int32)
+    if val is None:
+        val = torch.empty((m,), dtype=torch.float64)
+    _check(L.ss_search_interp_2d_host(_host(R, torch.float64, "R"), R.numel(), _host(T, torch.float64, "T"), T.numel(),
+                                      _host(F, torch.float64, "F"), _host(Y2, torch.float64, "Y2"), m,
+                                      _host(idx, torch.int32, "idx"), _host(val, torch.float64, "val"), _algo(algo)))
+    return idx, val

@@ -9,7 +9,7 @@
 //  * float-float (default): exact integer weight numerators and a
 //    float-float blend on the fp32 pipe (ss_ff.cuh); needs positive axes
 //    with entries in [2^-70, 2^101) and cells spanning at most 2^10.
-//    A pair whose four grid values are not splittable (zero excepted) is
+//    A pair whose four grid values are not positive and in that range is
 //    finished in fp64.
 //  * fp64: weights (x - X[c]) * (1 / gap) and the blend in double.
 // Both agree with an fp64 evaluation of the formula to well within 1e-12
@@ -28,8 +28,8 @@ constexpr int kMaxAxis2D = 4096;   // largest axis staged whole with its per-cel
 
 struct Axis2D {                    // shared-memory offsets of one axis
   Layout1D lay;
-  int cells;                       // CellFF[n]: X[c] bits and the float-float weight scale (last: X[n-1] only)
-  int rg;                          // double[n-1]: 1 / (X[c+1] - X[c]) for the fp64 path
+  int cells;                       // CellW[n-1]: exact weight numerators' data and scale
+  int rg;                          // double[n-1]: 1 / (X[c+1] - X[c]) for the fp64 path (X[c] read from global)
   int aux;                         // AxisAux
 };
 
@@ -52,35 +52,23 @@ struct Args2D {
   int64_t np2;      // pairs in the vector body, in units of 2 pairs
   int algo;         // SS_ALGO_BUCKET or SS_ALGO_BINARY
   int force_fp64;   // 1: skip the float-float path
+  int grid_smem;    // offset of the float-float grid in shared memory (-1: grid stays in global memory)
   Axis2D ar, at;
   ss_devstat* stat;
 };
 
 // Per-cell data and the float-float eligibility of one axis.
 static __device__ void stage_cells(const double* __restrict__ X, int n, const Axis2D& ax, unsigned char* smem) {
-  CellFF* cells = reinterpret_cast<CellFF*>(smem + ax.cells);
+  CellW* cells = reinterpret_cast<CellW*>(smem + ax.cells);
   double* rg = reinterpret_cast<double*>(smem + ax.rg);
   AxisAux& aux = *reinterpret_cast<AxisAux*>(smem + ax.aux);
   bool ok = true;
-  if (threadIdx.x == 0) cells[n - 1] = CellFF{static_cast<uint64_t>(__double_as_longlong(__ldg(X + n - 1))), 0.0f, 0.0f};
   for (int c = threadIdx.x; c < n - 1; c += blockDim.x) {
     const double a = __ldg(X + c), b = __ldg(X + c + 1);
-    const double gap = b - a;
-    rg[c] = 1.0 / gap;
-    const uint64_t ua = static_cast<uint64_t>(__double_as_longlong(a));
-    const uint64_t ub = static_cast<uint64_t>(__double_as_longlong(b));
-    const int ea = (int)((ua >> 52) & 0x7FF), eb = (int)((ub >> 52) & 0x7FF);
-    const bool cell_ok = (ua >> 63) == 0 && ea >= kFFMinExp && eb <= kFFMaxExp && eb - ea <= kMaxCellOctaves &&
-                         gap > 0.0;
-    double g = 0.0;
-    float ghi = 0.0f, glo = 0.0f;
-    if (cell_ok) {
-      g = ldexp(1.0, ea - 1075) / gap;
-      ghi = __double2float_rn(g);
-      glo = __double2float_rn(g - (double)ghi);
-    }
-    ok &= cell_ok && ghi != 0.0f && isfinite(ghi) && fabsf(ghi) >= 1.0e-36f;
-    cells[c] = CellFF{ua, ghi, glo};
+    rg[c] = 1.0 / (b - a);
+    CellW w;
+    ok &= make_cell(a, b, w);
+    cells[c] = w;
   }
   ok = __syncthreads_and(ok);
   if (threadIdx.x == 0) {
@@ -96,7 +84,8 @@ struct AxisView {
   const uint64_t* keys;
   const uint64_t* eyt;
   const int* dir;
-  const CellFF* cells;
+  const CellW* cells;
+  const double* x;           // the axis in global memory
   const double* rg;
   int shift, nb, T, D, n;
   uint64_t base, k0;
@@ -109,7 +98,7 @@ __device__ __forceinline__ AxisView view_of(const Axis2D& ax, const unsigned cha
   v.keys = ax.lay.keys >= 0 ? reinterpret_cast<const uint64_t*>(smem + ax.lay.keys) : nullptr;
   v.eyt = ax.lay.eyt >= 0 ? reinterpret_cast<const uint64_t*>(smem + ax.lay.eyt) : nullptr;
   v.dir = ax.lay.dir >= 0 ? reinterpret_cast<const int*>(smem + ax.lay.dir) : nullptr;
-  v.cells = reinterpret_cast<const CellFF*>(smem + ax.cells);
+  v.cells = reinterpret_cast<const CellW*>(smem + ax.cells);
   v.rg = reinterpret_cast<const double*>(smem + ax.rg);
   v.shift = h.shift;
   v.nb = h.nb;
@@ -132,7 +121,7 @@ __device__ __forceinline__ int axis_search(const AxisView& a, uint64_t k) {
 __device__ __forceinline__ Weights axis_weights_ff(const AxisView& a, int i, int c, uint64_t k, uint64_t u) {
   if (i >= a.n - 1) return {{1.0f, 0.0f}, {0.0f, 0.0f}};          // above the last entry
   if (i == 0 && k <= a.k0) return {{0.0f, 0.0f}, {1.0f, 0.0f}};   // at or below the first entry
-  return cell_weights(u, a.cells[c], a.cells[c + 1].xbits);
+  return cell_weights(u, a.cells[c]);
 }
 
 // Convex blend in fp64 (fallback path of a pair).
@@ -149,10 +138,14 @@ __device__ __forceinline__ double blend64w(double wr, double wrb, double wt, dou
 }
 
 // One pair: indices and value.  MODE 0: both axes bucket with occupancy <= 1;
-// 1: bucket with bounded bisection; 2: breadth-first binary.  FF: arithmetic path.
-template <int MODE, bool FF>
+// 1: bucket with bounded bisection; 2: breadth-first binary.  FF: arithmetic
+// path.  SG: the value grid is staged in shared memory as float-float (a NaN
+// high part marks a value the split does not cover; that pair is finished in
+// fp64 from the caller's grid).
+template <int MODE, bool FF, bool SG>
 __device__ __forceinline__ void lookup_pair(const AxisView& vr, const AxisView& vt, const double* __restrict__ F,
-                                            int nt, double rho, double tem, int& ir, int& it, double& v, int& nans) {
+                                            const float2* __restrict__ Gs, int nt, double rho, double tem, int& ir,
+                                            int& it, double& v, int& nans) {
   const uint64_t ur = static_cast<uint64_t>(__double_as_longlong(rho));
   const uint64_t ut = static_cast<uint64_t>(__double_as_longlong(tem));
   const uint64_t kr = order_key(rho), kt = order_key(tem);
@@ -161,38 +154,50 @@ __device__ __forceinline__ void lookup_pair(const AxisView& vr, const AxisView& 
   ir = axis_search<MODE>(vr, kr);
   it = axis_search<MODE>(vt, kt);
   const int cr = min(ir, vr.n - 2), ct = min(it, nt - 2);
-  const double* f = F + (int64_t)cr * nt + ct;
-  const double f00 = __ldg(f), f01 = __ldg(f + 1), f10 = __ldg(f + nt), f11 = __ldg(f + nt + 1);
+  const int64_t o = (int64_t)cr * nt + ct;
   if (!FF) {
-    const double wr = clamp01((rho - __longlong_as_double((long long)vr.cells[cr].xbits)) * vr.rg[cr]);
-    const double wt = clamp01((tem - __longlong_as_double((long long)vt.cells[ct].xbits)) * vt.rg[ct]);
+    const double* f = F + o;
+    const double f00 = __ldg(f), f01 = __ldg(f + 1), f10 = __ldg(f + nt), f11 = __ldg(f + nt + 1);
+    const double wr = clamp01((rho - __ldg(vr.x + cr)) * vr.rg[cr]);
+    const double wt = clamp01((tem - __ldg(vt.x + ct)) * vt.rg[ct]);
     v = blend64(wr, wt, f00, f01, f10, f11);
     return;
   }
+  ff a00, a01, a10, a11;
+  bool ok;
+  if (SG) {
+    const float2 g00 = Gs[o], g01 = Gs[o + 1], g10 = Gs[o + nt], g11 = Gs[o + nt + 1];
+    a00 = {g00.x, g00.y}; a01 = {g01.x, g01.y}; a10 = {g10.x, g10.y}; a11 = {g11.x, g11.y};
+    ok = !(isnan(g00.x) | isnan(g01.x) | isnan(g10.x) | isnan(g11.x));
+  } else {
+    const double* f = F + o;
+    ok = d2ff(__ldg(f), a00) & d2ff(__ldg(f + 1), a01) & d2ff(__ldg(f + nt), a10) & d2ff(__ldg(f + nt + 1), a11);
+  }
   const Weights wr = axis_weights_ff(vr, ir, cr, kr, ur);
   const Weights wt = axis_weights_ff(vt, it, ct, kt, ut);
-  ff a00, a01, a10, a11;
-  const bool ok = d2ff(f00, a00) & d2ff(f01, a01) & d2ff(f10, a10) & d2ff(f11, a11);
   if (nan) {
     v = __longlong_as_double(0x7FF8000000000000ll);
   } else if (ok) {
-    const ff lo = ff_add(ff_mul(wt.wbar, a00), ff_mul(wt.w, a01));
-    const ff hi = ff_add(ff_mul(wt.wbar, a10), ff_mul(wt.w, a11));
-    v = ff2d(ff_add(ff_mul(wr.wbar, lo), ff_mul(wr.w, hi)));
+    const ff lo = ff_add_u(ff_mul_u(wt.wbar, a00), ff_mul_u(wt.w, a01));
+    const ff hi = ff_add_u(ff_mul_u(wt.wbar, a10), ff_mul_u(wt.w, a11));
+    v = ff2d(ff_add_u(ff_mul_u(wr.wbar, lo), ff_mul_u(wr.w, hi)));
   } else {
-    v = blend64w(ff2d(wr.w), ff2d(wr.wbar), ff2d(wt.w), ff2d(wt.wbar), f00, f01, f10, f11);
+    const double* f = F + o;
+    v = blend64w(ff2d(wr.w), ff2d(wr.wbar), ff2d(wt.w), ff2d(wt.wbar), __ldg(f), __ldg(f + 1), __ldg(f + nt),
+                 __ldg(f + nt + 1));
   }
 }
 
-template <int MODE, bool FF>
-__device__ __forceinline__ int stream_pairs(const Args2D& a, const AxisView& vr, const AxisView& vt) {
+template <int MODE, bool FF, bool SG>
+__device__ __forceinline__ int stream_pairs(const Args2D& a, const AxisView& vr, const AxisView& vt,
+                                            const float2* Gs) {
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gs = (int64_t)gridDim.x * blockDim.x;
   int nans = 0;
   auto scalar = [&](int64_t i) {
     int ir, it;
     double v;
-    lookup_pair<MODE, FF>(vr, vt, a.F, a.nt, a.Y2[2 * i], a.Y2[2 * i + 1], ir, it, v, nans);
+    lookup_pair<MODE, FF, SG>(vr, vt, a.F, Gs, a.nt, a.Y2[2 * i], a.Y2[2 * i + 1], ir, it, v, nans);
     a.idx[2 * i] = ir;
     a.idx[2 * i + 1] = it;
     a.val[i] = v;
@@ -205,8 +210,8 @@ __device__ __forceinline__ int stream_pairs(const Args2D& a, const AxisView& vr,
     const double2 p0 = ld_stream(Y + 2 * g), p1 = ld_stream(Y + 2 * g + 1);
     int i0, j0, i1, j1;
     double v0, v1;
-    lookup_pair<MODE, FF>(vr, vt, a.F, a.nt, p0.x, p0.y, i0, j0, v0, nans);
-    lookup_pair<MODE, FF>(vr, vt, a.F, a.nt, p1.x, p1.y, i1, j1, v1, nans);
+    lookup_pair<MODE, FF, SG>(vr, vt, a.F, Gs, a.nt, p0.x, p0.y, i0, j0, v0, nans);
+    lookup_pair<MODE, FF, SG>(vr, vt, a.F, Gs, a.nt, p1.x, p1.y, i1, j1, v1, nans);
     st_stream(I4 + g, make_int4(i0, j0, i1, j1));
     st_stream(V2 + g, make_double2(v0, v1));
   }
@@ -214,14 +219,26 @@ __device__ __forceinline__ int stream_pairs(const Args2D& a, const AxisView& vr,
   return nans;
 }
 
-__global__ void __launch_bounds__(kNumThreads) k_search_interp_2d(Args2D a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+template <bool SG>
+__device__ __forceinline__ void interp_body(const Args2D& a, unsigned char* smem) {
   stage_table_1d(a.R, a.nr, a.ar.lay, smem);
   stage_table_1d(a.T, a.nt, a.at.lay, smem);
   stage_cells(a.R, a.nr, a.ar, smem);
   stage_cells(a.T, a.nt, a.at, smem);
+  float2* Gs = nullptr;
+  if (SG) {
+    // the value grid as float-float, once per block
+    Gs = reinterpret_cast<float2*>(smem + a.grid_smem);
+    const int64_t cnt = (int64_t)a.nr * a.nt;
+    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+      ff r;
+      Gs[i] = d2ff(__ldg(a.F + i), r) ? make_float2(r.hi, r.lo) : make_float2(__int_as_float(0x7FC00000), 0.0f);
+    }
+  }
   __syncthreads();
-  const AxisView vr = view_of(a.ar, smem), vt = view_of(a.at, smem);
+  AxisView vr = view_of(a.ar, smem), vt = view_of(a.at, smem);
+  vr.x = a.R;
+  vt.x = a.T;
   const TableHdr& hr = *reinterpret_cast<const TableHdr*>(smem + a.ar.lay.hdr);
   const TableHdr& ht = *reinterpret_cast<const TableHdr*>(smem + a.at.lay.hdr);
   const bool ff = !a.force_fp64 && reinterpret_cast<const AxisAux*>(smem + a.ar.aux)->ffok &&
@@ -229,11 +246,11 @@ __global__ void __launch_bounds__(kNumThreads) k_search_interp_2d(Args2D a) {
   const int mode = a.algo == SS_ALGO_BINARY ? 2 : (hr.occ <= 1 && ht.occ <= 1) ? 0 : 1;
   int nans;
   if (ff) {
-    nans = mode == 0 ? stream_pairs<0, true>(a, vr, vt)
-         : mode == 1 ? stream_pairs<1, true>(a, vr, vt) : stream_pairs<2, true>(a, vr, vt);
+    nans = mode == 0 ? stream_pairs<0, true, SG>(a, vr, vt, Gs)
+         : mode == 1 ? stream_pairs<1, true, SG>(a, vr, vt, Gs) : stream_pairs<2, true, SG>(a, vr, vt, Gs);
   } else {
-    nans = mode == 0 ? stream_pairs<0, false>(a, vr, vt)
-         : mode == 1 ? stream_pairs<1, false>(a, vr, vt) : stream_pairs<2, false>(a, vr, vt);
+    nans = mode == 0 ? stream_pairs<0, false, false>(a, vr, vt, Gs)
+         : mode == 1 ? stream_pairs<1, false, false>(a, vr, vt, Gs) : stream_pairs<2, false, false>(a, vr, vt, Gs);
   }
   nans = __reduce_add_sync(0xFFFFFFFFu, nans);
   if (a.stat != nullptr) {
@@ -245,6 +262,20 @@ __global__ void __launch_bounds__(kNumThreads) k_search_interp_2d(Args2D a) {
   }
 }
 
+// Grid in global memory (L2-resident): 256 threads, several blocks per SM.
+__global__ void __launch_bounds__(kNumThreads) k_search_interp_2d(Args2D a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  interp_body<false>(a, smem);
+}
+
+// Grid staged in shared memory as float-float: one 1024-thread block per SM,
+// the four corner gathers become shared-memory loads.
+constexpr int kSgThreads = 1024;
+__global__ void __launch_bounds__(kSgThreads, 1) k_search_interp_2d_sg(Args2D a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  interp_body<true>(a, smem);
+}
+
 int default_dir_cap(int n);
 
 static Axis2D make_axis(int n, int algo, int offset) {
@@ -253,7 +284,7 @@ static Axis2D make_axis(int n, int algo, int offset) {
   ax.lay = make_layout_1d(n, bucket, !bucket, bucket ? default_dir_cap(n) : 0, offset);
   int off = ax.lay.bytes;
   auto take = [&](int bytes) { int o = off; off += (bytes + 15) & ~15; return o; };
-  ax.cells = take(n * (int)sizeof(CellFF));
+  ax.cells = take((n - 1) * (int)sizeof(CellW));
   ax.rg = take((n - 1) * 8);
   ax.aux = take((int)sizeof(AxisAux));
   ax.lay.bytes = off;   // end of this axis' region
@@ -288,16 +319,22 @@ ss_status search_interp_2d(const double* R, int32_t nr, const double* T, int32_t
     if (ok) { a.head = h; a.np2 = (m - h) / 2; break; }
   }
   if (smem > max_smem_optin()) return fail(SS_EUNSUPPORTED, "ss_search_interp_2d: axes too large for shared memory");
-  const void* k = reinterpret_cast<const void*>(&k_search_interp_2d);
-  SS_CHECK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  // stage the grid too when it fits beside the axes (and the float-float path is not disabled)
+  const int64_t gbytes = (int64_t)nr * nt * 8;
+  const bool sg = !force_fp64 && smem + gbytes + 16 <= (int64_t)max_smem_optin();
+  a.grid_smem = sg ? ((smem + 15) & ~15) : -1;
+  const int threads = sg ? kSgThreads : kNumThreads;
+  const int smem_all = sg ? a.grid_smem + (int)gbytes : smem;
+  const void* k = sg ? reinterpret_cast<const void*>(&k_search_interp_2d_sg) : reinterpret_cast<const void*>(&k_search_interp_2d);
+  SS_CHECK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_all));
   int per_sm = 0;
-  SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kNumThreads, smem));
+  SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem_all));
   if (per_sm < 1) return fail(SS_EUNSUPPORTED, "ss_search_interp_2d: kernel does not fit on an SM");
   const int64_t items = a.np2 > 0 ? a.np2 + (m - 2 * a.np2) : m;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((items + kNumThreads - 1) / kNumThreads,
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((items + threads - 1) / threads,
                                                                 (int64_t)num_sms() * per_sm));
   void* args[1] = {&a};
-  cudaError_t err = cudaLaunchKernel(k, dim3(grid), dim3(kNumThreads), args, (size_t)smem, stream);
+  cudaError_t err = cudaLaunchKernel(k, dim3(grid), dim3(threads), args, (size_t)smem_all, stream);
   if (err != cudaSuccess) return cuda_fail(err, "k_search_interp_2d");
   return SS_OK;
 }

@@ -95,6 +95,19 @@ std::vector<Tile> make_tiles(const std::vector<int64_t>& Y_off, const std::vecto
   return tiles;
 }
 
+// Automatic tile size: about six tiles per resident block for balance, and
+// at least 16x the staged table bytes in target traffic so that staging a
+// table costs under ~6% of streaming its tile; scaled by the tuned multiple.
+int auto_tile(int64_t total, int blocks, int staged_bytes, float mult) {
+  int64_t t = total / std::max<int64_t>(1, (int64_t)blocks * 6);
+  t = std::max<int64_t>(t, 8192);
+  t = std::max<int64_t>(t, (int64_t)staged_bytes * 16 / 12);
+  t = std::min<int64_t>(t, 1 << 20);
+  t = (int64_t)((double)t * mult);
+  t = std::max<int64_t>(1024, std::min<int64_t>(t, 1 << 22));
+  return (int)(t & ~(int64_t)255);
+}
+
 }  // namespace ss
 
 using namespace ss;

@@ -5,6 +5,9 @@
 
 namespace ss {
 
+// Bucket budget of the fine directory of a sampled table (all keys, global memory).
+__host__ __device__ inline int fine_dir_cap(int nk) { return nk < (1 << 16) ? 4 * nk : (1 << 18); }
+
 __host__ __device__ inline BlobGeom blob_geom_dev(int n, int dir_cap, bool cells) {
   BlobGeom g{};
   const int nk = n - 1;
@@ -19,10 +22,10 @@ __host__ __device__ inline BlobGeom blob_geom_dev(int n, int dir_cap, bool cells
   g.off_keys = off; off += (g.ns + kPad) * 8;
   g.off_eyt = off;  off += g.P * 8;
   g.off_cells = -1;
-  if (cells) { g.off_cells = off; off += ((n * (int)sizeof(CellFF)) + 15) & ~15; }
+  if (cells) { g.off_cells = off; off += (((n - 1) * (int)sizeof(CellW)) + 15) & ~15; }
   g.staged_end = off;
   g.off_full = g.stride > 1 ? off : -1;
-  g.bytes = g.stride > 1 ? (int64_t)off + (int64_t)(nk + kPad) * 8 : off;
+  g.bytes = g.stride > 1 ? (int64_t)off + (int64_t)(nk + kPad) * 8 + (int64_t)(fine_dir_cap(nk) + 1) * 4 : off;
   g.bytes = (g.bytes + 15) & ~(int64_t)15;
   return g;
 }
@@ -92,7 +95,7 @@ struct BatchArgs2D {
 __global__ void k_prep_1d(PrepArgs a);
 __global__ void k_train_mlp(TrainArgs a);
 __global__ void k_window(WindowArgs a);
-const void* batched_1d_kernel(bool le);
+const void* batched_1d_kernel(bool le, int family);   // family: 0 plain, 1 +spline, 2 +mlp
 __global__ void k_batched_2d(BatchArgs2D a);
 __global__ void k_grid_to_ff(const double* F, float2* G, int64_t count, unsigned* bad);
 __global__ void k_prep_cells(PrepArgs a);

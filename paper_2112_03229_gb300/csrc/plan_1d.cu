@@ -76,6 +76,29 @@ __global__ void __launch_bounds__(256) k_prep_1d(PrepArgs a) {
   for (int b = tid; b < nb; b += nt) occ = max(occ, dir[b + 1] - dir[b]);
   occ = __reduce_max_sync(0xFFFFFFFFu, occ);
   if ((tid & 31) == 0) atomicMax(&s_occ, occ);
+  // fine directory over all keys for sampled tables (global memory)
+  __shared__ int s_gshift, s_gnb;
+  __shared__ uint64_t s_gbase;
+  if (full != nullptr) {
+    int* gdir = reinterpret_cast<int*>(blob + g.off_full + (int64_t)(nk + kPad) * 8);
+    const int cap = fine_dir_cap(nk);
+    __syncthreads();
+    if (tid == 0) {
+      const uint64_t k0 = full[0], k1 = full[nk - 1];
+      int s2 = 0;
+      while (s2 < 63 && ((k1 >> s2) - (k0 >> s2)) >= (uint64_t)cap) ++s2;
+      s_gshift = s2;
+      s_gbase = k0 >> s2;
+      s_gnb = (int)min((k1 >> s2) - (k0 >> s2) + 1, (uint64_t)cap);
+    }
+    __syncthreads();
+    for (int b = tid; b <= s_gnb; b += nt)
+      gdir[b] = b == s_gnb ? nk : lower_count(full, nk, (s_gbase + (uint64_t)b) << s_gshift);
+  } else if (tid == 0) {
+    s_gshift = 0;
+    s_gnb = 0;
+    s_gbase = 0;
+  }
   // MLP feature scaling and initial parameters: hinge units spread evenly over
   // the normalised log2 coordinate z = x0 + e_scale * x1 of the table's range
   const uint64_t u0 = static_cast<uint64_t>(__double_as_longlong(X[0]));
@@ -100,7 +123,7 @@ __global__ void __launch_bounds__(256) k_prep_1d(PrepArgs a) {
     hh.algo = a.algo[k];
     hh.D = g.D;
     hh.shift = shift; hh.nb = nb; hh.occ = s_occ;
-    hh.E = s_occ;                              // spline window: the bucket occupancy bounds its error
+    hh.E = s_occ * g.stride;                   // spline window: the bucket occupancy bounds its error
     int S0 = 1;
     const int G = hh.algo == BL_BALLOT8 ? 8 : hh.algo == BL_BALLOT16 ? 16 : 32;
     while ((int64_t)S0 * (G + 1) < (int64_t)g.ns + 1) S0 *= (G + 1);
@@ -115,6 +138,9 @@ __global__ void __launch_bounds__(256) k_prep_1d(PrepArgs a) {
     hh.loss = 0.0f;
     hh.off_cells = g.off_cells;
     hh.ffok = 0;
+    hh.gshift = s_gshift;
+    hh.gnb = s_gnb;
+    hh.gbase = s_gbase;
     *h = hh;
     if (s_bad) atomicOr(a.bad_flag, 1u);
   }
@@ -145,10 +171,11 @@ __global__ void __launch_bounds__(kTrainThreads) k_train_mlp(TrainArgs a) {
   for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) p[i] = gp[i];
   // global view of the blob for labelling (no staging needed: reads hit L2)
   StagedView v;
-  v.h = gh;
+  v.h = h;
   v.dir = reinterpret_cast<const int*>(blob + h.off_dir);
   v.keys = reinterpret_cast<const uint64_t*>(blob + h.off_keys);
   v.full = h.off_full >= 0 ? reinterpret_cast<const uint64_t*>(blob + h.off_full) : nullptr;
+  v.gdir = h.gnb > 0 ? reinterpret_cast<const int*>(blob + h.off_full + (int64_t)(h.nk + kPad) * 8) : nullptr;
   const MlpFeatScale sc{h.e_lo, h.e_scale};
   const uint64_t k0 = h.k0, k1 = h.stride == 1 ? v.keys[h.nk - 1] : v.full[h.nk - 1];
   const int nkeys = min(h.n, kTrainSamples / 2);
@@ -233,11 +260,12 @@ __global__ void __launch_bounds__(256) k_window(WindowArgs a) {
   const BlobHdr h = *gh;
   if (h.algo != BL_SPLINE && h.algo != BL_MLP) return;
   StagedView v;
-  v.h = gh;
+  v.h = h;
   v.mlp = reinterpret_cast<const float*>(blob + h.off_mlp);
   v.dir = reinterpret_cast<const int*>(blob + h.off_dir);
   v.keys = reinterpret_cast<const uint64_t*>(blob + h.off_keys);
   v.full = h.off_full >= 0 ? reinterpret_cast<const uint64_t*>(blob + h.off_full) : nullptr;
+  v.gdir = h.gnb > 0 ? reinterpret_cast<const int*>(blob + h.off_full + (int64_t)(h.nk + kPad) * 8) : nullptr;
   const MlpFeatScale sc{h.e_lo, h.e_scale};
   __shared__ int s_err;
   if (threadIdx.x == 0) s_err = 0;
@@ -251,7 +279,7 @@ __global__ void __launch_bounds__(256) k_window(WindowArgs a) {
     else q = k0 + (uint64_t)((double)(splitmix64(a.seed ^ ((uint64_t)k << 40) ^ (uint64_t)i) >> 11) * 0x1.0p-53 *
                              (double)(k1 - k0));
     const int c = plain_bucket(v, q);
-    const int prop = h.algo == BL_SPLINE ? spline_propose(v.dir, h.shift, h.base, h.nb, q)
+    const int prop = h.algo == BL_SPLINE ? spline_proposal(v, q)
                                          : mlp_propose(v.mlp, sc, h.n, key_to_double(q));
     err = max(err, abs(prop - c));
   }
@@ -267,14 +295,18 @@ __global__ void __launch_bounds__(256) k_window(WindowArgs a) {
 // it differs from the one already in shared memory, and streams the tile's
 // targets.  Targets of a tile are contiguous in Y / out.
 // ---------------------------------------------------------------------------
-template <bool LE>
+// Algorithm families compiled into one instance of the batched kernel: the
+// plain searches only, plus the spline, plus the MLP.  A plan launches the
+// smallest family that covers its tables, which keeps registers (and so
+// resident warps) at the level the plain searches need.
+enum : int { FAM_PLAIN = 0, FAM_SPLINE = 1, FAM_MLP = 2 };
+
+template <int FAM>
 __device__ __forceinline__ int count_for(const StagedView& v, int algo, double t, uint64_t q, int& fallbacks) {
-  switch (algo) {
-    case BL_BINARY: return plain_binary(v, q);
-    case BL_SPLINE: return spline_count(v, q, fallbacks);
-    case BL_MLP: return mlp_count(v, t, q, fallbacks);
-    default: return plain_bucket(v, q);
-  }
+  if (FAM >= FAM_MLP && algo == BL_MLP) return mlp_count(v, t, q, fallbacks);
+  if (FAM >= FAM_SPLINE && algo == BL_SPLINE) return spline_count(v, q, fallbacks);
+  if (algo == BL_BINARY) return plain_binary(v, q);
+  return plain_bucket(v, q);
 }
 
 template <int G>
@@ -282,7 +314,7 @@ __device__ __forceinline__ void ballot_tile(const StagedView& v, const double* _
                                             int64_t b, int cnt, uint64_t le, int& nans) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int gbase = lane & ~(G - 1);
-  const BlobHdr& h = *v.h;
+  const BlobHdr& h = v.h;
   for (int base = w * 32; base < cnt; base += nw * 32) {
     const int i = base + lane;
     const bool ok = i < cnt;
@@ -302,8 +334,8 @@ __device__ __forceinline__ void ballot_tile(const StagedView& v, const double* _
   }
 }
 
-template <bool LE>
-__global__ void __launch_bounds__(kNumThreads) k_batched_1d(BatchArgs1D a) {
+template <bool LE, int FAM>
+__global__ void __launch_bounds__(kNumThreads, FAM == FAM_MLP ? 2 : 4) k_batched_1d(BatchArgs1D a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
   __shared__ int s_tile;
@@ -331,7 +363,7 @@ __global__ void __launch_bounds__(kNumThreads) k_batched_1d(BatchArgs1D a) {
       cur_table = tile.table;
       if (!ok) break;
     }
-    const int algo = v.h->algo;
+    const int algo = v.h.algo;
     const int64_t b = tile.begin;
     const int cnt = tile.count;
     if (algo >= BL_BALLOT8 && algo <= BL_BALLOT32) {
@@ -347,27 +379,37 @@ __global__ void __launch_bounds__(kNumThreads) k_batched_1d(BatchArgs1D a) {
       const double y = a.Y[b + i];
       const uint64_t k = order_key(y);
       nans += k < 0x0010000000000000ull;
-      a.out[b + i] = count_for<LE>(v, algo, y, k + le, fallbacks);
+      a.out[b + i] = count_for<FAM>(v, algo, y, k + le, fallbacks);
     }
     const double2* Y2 = reinterpret_cast<const double2*>(a.Y + b + head);
     int4* O4 = reinterpret_cast<int4*>(a.out + b + head);
-    for (int g = threadIdx.x; g < nq; g += blockDim.x) {
+    // two quads in flight per thread: both loads issue before any search
+    for (int g = threadIdx.x; g < nq; g += 2 * blockDim.x) {
+      const int g2 = g + blockDim.x;
+      const bool two = g2 < nq;
       const double2 p0 = ld_stream(Y2 + 2 * g), p1 = ld_stream(Y2 + 2 * g + 1);
-      const double y[4] = {p0.x, p0.y, p1.x, p1.y};
-      int r[4];
+      double2 p2 = make_double2(0.0, 0.0), p3 = p2;
+      if (two) {
+        p2 = ld_stream(Y2 + 2 * g2);
+        p3 = ld_stream(Y2 + 2 * g2 + 1);
+      }
+      const double y[8] = {p0.x, p0.y, p1.x, p1.y, p2.x, p2.y, p3.x, p3.y};
+      int r[8];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < 8; ++j) {
+        if (j >= 4 && !two) break;
         const uint64_t k = order_key(y[j]);
         nans += k < 0x0010000000000000ull;
-        r[j] = count_for<LE>(v, algo, y[j], k + le, fallbacks);
+        r[j] = count_for<FAM>(v, algo, y[j], k + le, fallbacks);
       }
       st_stream(O4 + g, make_int4(r[0], r[1], r[2], r[3]));
+      if (two) st_stream(O4 + g2, make_int4(r[4], r[5], r[6], r[7]));
     }
     for (int i = head + 4 * nq + threadIdx.x; i < cnt; i += blockDim.x) {
       const double y = a.Y[b + i];
       const uint64_t k = order_key(y);
       nans += k < 0x0010000000000000ull;
-      a.out[b + i] = count_for<LE>(v, algo, y, k + le, fallbacks);
+      a.out[b + i] = count_for<FAM>(v, algo, y, k + le, fallbacks);
     }
   }
   if (!ok && threadIdx.x == 0) s_err = 1;
@@ -382,8 +424,13 @@ __global__ void __launch_bounds__(kNumThreads) k_batched_1d(BatchArgs1D a) {
 }
 
 // Kernel entry of the batched search (template stubs stay local to this unit).
-const void* batched_1d_kernel(bool le) {
-  return le ? reinterpret_cast<const void*>(&k_batched_1d<true>) : reinterpret_cast<const void*>(&k_batched_1d<false>);
+const void* batched_1d_kernel(bool le, int family) {
+  if (family >= FAM_MLP)
+    return le ? reinterpret_cast<const void*>(&k_batched_1d<true, FAM_MLP>) : reinterpret_cast<const void*>(&k_batched_1d<false, FAM_MLP>);
+  if (family == FAM_SPLINE)
+    return le ? reinterpret_cast<const void*>(&k_batched_1d<true, FAM_SPLINE>)
+              : reinterpret_cast<const void*>(&k_batched_1d<false, FAM_SPLINE>);
+  return le ? reinterpret_cast<const void*>(&k_batched_1d<true, FAM_PLAIN>) : reinterpret_cast<const void*>(&k_batched_1d<false, FAM_PLAIN>);
 }
 
 }  // namespace ss

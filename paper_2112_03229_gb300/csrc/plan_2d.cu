@@ -14,7 +14,7 @@ namespace ss {
 
 int default_dir_cap(int n);
 
-// Per-cell data of one axis blob (n cells: the last one only holds X[n-1]).
+// Per-cell data of one axis blob and its float-float eligibility.
 __global__ void __launch_bounds__(256) k_prep_cells(PrepArgs a) {
   const int k = blockIdx.x;
   if (k >= a.ntables) return;
@@ -22,35 +22,20 @@ __global__ void __launch_bounds__(256) k_prep_cells(PrepArgs a) {
   const int n = (int)(a.X_off[k + 1] - a.X_off[k]);
   unsigned char* blob = a.blobs + a.blob_off[k];
   BlobHdr* h = reinterpret_cast<BlobHdr*>(blob);
-  CellFF* cells = reinterpret_cast<CellFF*>(blob + h->off_cells);
+  CellW* cells = reinterpret_cast<CellW*>(blob + h->off_cells);
   bool ok = true;
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    const double lo = X[c];
-    const uint64_t ua = static_cast<uint64_t>(__double_as_longlong(lo));
-    float ghi = 0.0f, glo = 0.0f;
-    if (c < n - 1) {
-      const double hi = X[c + 1];
-      const double gap = hi - lo;
-      const uint64_t ub = static_cast<uint64_t>(__double_as_longlong(hi));
-      const int ea = (int)((ua >> 52) & 0x7FF), eb = (int)((ub >> 52) & 0x7FF);
-      const bool cell_ok = (ua >> 63) == 0 && ea >= kFFMinExp && eb <= kFFMaxExp && eb - ea <= kMaxCellOctaves &&
-                           gap > 0.0;
-      if (cell_ok) {
-        const double g = ldexp(1.0, ea - 1075) / gap;
-        ghi = __double2float_rn(g);
-        glo = __double2float_rn(g - (double)ghi);
-      }
-      ok &= cell_ok && isfinite(ghi) && fabsf(ghi) >= 1.0e-36f;
-    }
-    cells[c] = CellFF{ua, ghi, glo};
+  for (int c = threadIdx.x; c < n - 1; c += blockDim.x) {
+    CellW w;
+    ok &= make_cell(X[c], X[c + 1], w);
+    cells[c] = w;
   }
   ok = __syncthreads_and(ok);
   if (threadIdx.x == 0) h->ffok = ok ? 1 : 0;
 }
 
-// Value grid to float-float; values that cannot be split (outside
-// [2^-70, 2^101) in magnitude, not zero) are marked with a NaN high part and
-// set *bad so the plan keeps an fp64 copy for them.
+// Value grid to float-float; values the split does not cover (zero,
+// negative, or outside [2^-70, 2^101)) are marked with a NaN high part and set
+// *bad so the plan keeps an fp64 copy for them.
 __global__ void k_grid_to_ff(const double* __restrict__ F, float2* __restrict__ G, int64_t count, unsigned* bad) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
     ff r;
@@ -65,7 +50,7 @@ __global__ void k_grid_to_ff(const double* __restrict__ F, float2* __restrict__ 
 
 // Exact count for one axis with the axis' algorithm.
 __device__ __forceinline__ int axis_count(const StagedView& v, double t, uint64_t q, int& fallbacks) {
-  switch (v.h->algo) {
+  switch (v.h.algo) {
     case BL_BINARY: return plain_binary(v, q);
     case BL_SPLINE: return spline_count(v, q, fallbacks);
     case BL_MLP: return mlp_count(v, t, q, fallbacks);
@@ -75,13 +60,18 @@ __device__ __forceinline__ int axis_count(const StagedView& v, double t, uint64_
 
 // Weights (w, 1 - w) of a coordinate on an axis (float-float; fp64 division
 // when the axis is outside the float-float preconditions).
+__device__ __forceinline__ double entry_value(const StagedView& v, int j) {
+  const uint64_t k = j == 0 ? v.h.k0 : key_at(v, j - 1);
+  const uint64_t u = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : (0ull - k);
+  return __longlong_as_double((long long)u);
+}
+
 __device__ __forceinline__ Weights axis_weights(const StagedView& v, int i, int c, uint64_t k, double x) {
-  const BlobHdr& h = *v.h;
+  const BlobHdr& h = v.h;
   if (i >= h.n - 1) return {{1.0f, 0.0f}, {0.0f, 0.0f}};
   if (i == 0 && k <= h.k0) return {{0.0f, 0.0f}, {1.0f, 0.0f}};
-  if (h.ffok) return cell_weights(static_cast<uint64_t>(__double_as_longlong(x)), v.cells[c], v.cells[c + 1].xbits);
-  const double a = __longlong_as_double((long long)v.cells[c].xbits);
-  const double b = __longlong_as_double((long long)v.cells[c + 1].xbits);
+  if (h.ffok) return cell_weights(static_cast<uint64_t>(__double_as_longlong(x)), v.cells[c]);
+  const double a = entry_value(v, c), b = entry_value(v, c + 1);
   double w = (x - a) / (b - a);
   w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
   const double wb = 1.0 - w;
@@ -101,8 +91,8 @@ __device__ __forceinline__ void pair_2d(const StagedView& vr, const StagedView& 
   nans += (kr < 0x0010000000000000ull) + (kt < 0x0010000000000000ull);
   ir = axis_count(vr, rho, kr, fallbacks);
   it = axis_count(vt, tem, kt, fallbacks);
-  const int nt = vt.h->n;
-  const int cr = min(ir, vr.h->n - 2), ct = min(it, nt - 2);
+  const int nt = vt.h.n;
+  const int cr = min(ir, vr.h.n - 2), ct = min(it, nt - 2);
   const int64_t o = (int64_t)cr * nt + ct;
   const float2 g00 = __ldg(G + o), g01 = __ldg(G + o + 1), g10 = __ldg(G + o + nt), g11 = __ldg(G + o + nt + 1);
   const Weights wr = axis_weights(vr, ir, cr, kr, rho);
@@ -110,9 +100,9 @@ __device__ __forceinline__ void pair_2d(const StagedView& vr, const StagedView& 
   if (nan) {
     v = __longlong_as_double(0x7FF8000000000000ll);
   } else if (!(isnan(g00.x) | isnan(g01.x) | isnan(g10.x) | isnan(g11.x))) {
-    const ff lo = ff_add(ff_mul(wt.wbar, ff{g00.x, g00.y}), ff_mul(wt.w, ff{g01.x, g01.y}));
-    const ff hi = ff_add(ff_mul(wt.wbar, ff{g10.x, g10.y}), ff_mul(wt.w, ff{g11.x, g11.y}));
-    v = ff2d(ff_add(ff_mul(wr.wbar, lo), ff_mul(wr.w, hi)));
+    const ff lo = ff_add_u(ff_mul_u(wt.wbar, ff{g00.x, g00.y}), ff_mul_u(wt.w, ff{g01.x, g01.y}));
+    const ff hi = ff_add_u(ff_mul_u(wt.wbar, ff{g10.x, g10.y}), ff_mul_u(wt.w, ff{g11.x, g11.y}));
+    v = ff2d(ff_add_u(ff_mul_u(wr.wbar, lo), ff_mul_u(wr.w, hi)));
   } else {
     const double w1 = ff2d(wr.w), w1b = ff2d(wr.wbar), w2 = ff2d(wt.w), w2b = ff2d(wt.wbar);
     const double lo = w2b * G64[o] + w2 * G64[o + 1];

@@ -183,6 +183,35 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
   unbind(p);
   std::vector<int> bucket_of(p->ntables);
   for (int k = 0; k < p->ntables; ++k) bucket_of[k] = size_bucket(std::max(p->sizes[k], p->kind == 2 ? p->sizes_t[k] : 0));
+  // dynamic shared memory: the largest staged table (both axes for 2D), also per bucket
+  int smem = 0;
+  int smem_b[kNumBuckets] = {0};
+  for (int k = 0; k < p->ntables; ++k) {
+    int need;
+    if (p->kind == 1) {
+      need = staged_bytes(p->sizes[k], p->dir_cap[k], false, p->algo[k]);
+    } else {
+      const int a = (staged_bytes(p->sizes[k], p->dir_cap[2 * k], true, p->algo[2 * k]) + 127) & ~127;
+      need = a + staged_bytes(p->sizes_t[k], p->dir_cap[2 * k + 1], true, p->algo[2 * k + 1]);
+    }
+    smem = std::max(smem, need);
+    smem_b[bucket_of[k]] = std::max(smem_b[bucket_of[k]], need);
+  }
+  smem = (smem + 127) & ~127;
+  if (smem > max_smem_optin()) return fail(SS_EUNSUPPORTED, "plan: staged tables exceed shared memory");
+  const void* kern;
+  int family = 0;
+  for (int a : p->algo) family = std::max(family, a == BL_MLP ? 2 : a == BL_SPLINE ? 1 : 0);
+  if (p->kind == 1) kern = batched_1d_kernel(p->opts.side == SS_SIDE_LE, family);
+  else kern = reinterpret_cast<const void*>(&k_batched_2d);
+  SS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int per_sm = 0;
+  SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNumThreads, smem));
+  if (per_sm < 1) return fail(SS_EUNSUPPORTED, "plan: kernel does not fit on an SM");
+  const int resident = num_sms() * per_sm;
+  const int64_t total_targets = Y_off.back() - Y_off.front();
+  for (int b = 0; b < kNumBuckets; ++b)
+    p->bucket_tile[b] = p->opts.tile > 0 ? p->opts.tile : auto_tile(total_targets, resident, smem_b[b], p->bucket_mult[b]);
   int64_t total = 0;
   std::vector<Tile> tiles = make_tiles(Y_off, bucket_of, p->bucket_tile, total);
   if (tiles.size() > (size_t)0x7FFFFFFF) return fail(SS_EUNSUPPORTED, "plan: too many tiles");
@@ -192,28 +221,8 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
     SS_CHECK_CUDA(cudaMalloc(&p->d_tiles, tiles.size() * sizeof(Tile)));
     SS_CHECK_CUDA(cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
   }
-  // dynamic shared memory: the largest staged table (both axes for 2D)
-  int smem = 0;
-  for (int k = 0; k < p->ntables; ++k) {
-    if (p->kind == 1) {
-      smem = std::max(smem, staged_bytes(p->sizes[k], p->dir_cap[k], false, p->algo[k]));
-    } else {
-      const int a = (staged_bytes(p->sizes[k], p->dir_cap[2 * k], true, p->algo[2 * k]) + 127) & ~127;
-      const int b = staged_bytes(p->sizes_t[k], p->dir_cap[2 * k + 1], true, p->algo[2 * k + 1]);
-      smem = std::max(smem, a + b);
-    }
-  }
-  smem = (smem + 127) & ~127;
-  if (smem > max_smem_optin()) return fail(SS_EUNSUPPORTED, "plan: staged tables exceed shared memory");
-  const void* kern;
-  if (p->kind == 1) kern = batched_1d_kernel(p->opts.side == SS_SIDE_LE);
-  else kern = reinterpret_cast<const void*>(&k_batched_2d);
-  SS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  int per_sm = 0;
-  SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNumThreads, smem));
-  if (per_sm < 1) return fail(SS_EUNSUPPORTED, "plan: kernel does not fit on an SM");
   p->smem_bytes = smem;
-  p->grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms() * per_sm, p->ntiles));
+  p->grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)resident, p->ntiles));
   if (p->ntiles == 0) {
     p->bound = true;
     return SS_OK;
@@ -274,12 +283,14 @@ static bool read_cache(ss_plan* p, const std::string& dev) {
   int found = 0;
   size_t pos = 0;
   while ((pos = s.find("{\"bucket\": ", pos)) != std::string::npos) {
-    int b = -1, tile = 0;
+    int b = -1;
+    float mult = 0.0f;
     char name[32] = {0};
-    if (std::sscanf(s.c_str() + pos, "{\"bucket\": %d, \"algo\": \"%31[^\"]\", \"tile\": %d}", &b, name, &tile) == 3 &&
-        b >= 0 && b < kNumBuckets && algo_from_name(name) >= 0 && tile > 0) {
+    if (std::sscanf(s.c_str() + pos, "{\"bucket\": %d, \"algo\": \"%31[^\"]\", \"tile_multiple\": %f}", &b, name,
+                    &mult) == 3 &&
+        b >= 0 && b < kNumBuckets && algo_from_name(name) >= 0 && mult > 0.0f) {
       p->bucket_algo[b] = algo_from_name(name);
-      p->bucket_tile[b] = tile;
+      p->bucket_mult[b] = mult;
       ++found;
     }
     pos += 10;
@@ -298,8 +309,8 @@ static void write_cache(const ss_plan* p, const std::string& dev) {
     if (p->bucket_tables[b] == 0) continue;
     if (!first) f << ",\n";
     first = false;
-    f << " {\"bucket\": " << b << ", \"algo\": \"" << algo_name(p->bucket_algo[b]) << "\", \"tile\": "
-      << p->bucket_tile[b] << "}";
+    f << " {\"bucket\": " << b << ", \"algo\": \"" << algo_name(p->bucket_algo[b]) << "\", \"tile_multiple\": "
+      << p->bucket_mult[b] << "}";
   }
   f << "\n]}\n";
 }
@@ -325,9 +336,9 @@ ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
   else if (p->opts.model == SS_MODEL_MLP) cands = {BL_MLP};
   else if (p->kind == 1) cands = {BL_BUCKET, BL_BINARY, BL_BALLOT8, BL_BALLOT16, BL_BALLOT32};
   else cands = {BL_BUCKET, BL_BINARY};
-  const std::vector<int> tile_cands = {4096, 16384, 65536};
+  const std::vector<float> mult_cands = {0.25f, 1.0f, 4.0f};
   const int kReps = 8;
-  const int64_t kPerRep = 1 << 19;
+  const int64_t kPerRep = 1 << 22;
   cudaEvent_t e0, e1;
   SS_CHECK_CUDA(cudaEventCreate(&e0));
   SS_CHECK_CUDA(cudaEventCreate(&e1));
@@ -389,16 +400,16 @@ ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
       }
       Y_off[p->ntables] = acc;
     }
-    auto time_config = [&](int algo, int tile, float& ms) -> ss_status {
+    auto time_config = [&](int algo, float mult, float& ms) -> ss_status {
       for (int r : reps) {
         if (p->kind == 1) p->algo[r] = algo;
         else p->algo[2 * r] = p->algo[2 * r + 1] = algo;
       }
       if (ss_status s2 = plan_set_algos(p, stream)) return s2;
-      const int saved_tile = p->bucket_tile[b];
-      p->bucket_tile[b] = tile;
+      const float saved = p->bucket_mult[b];
+      p->bucket_mult[b] = mult;
       ss_status s2 = plan_bind(p, Y_off, d_Y, d_out, d_val, nullptr, stream);
-      p->bucket_tile[b] = saved_tile;
+      p->bucket_mult[b] = saved;
       if (s2 != SS_OK) return s2;
       float best = 1e30f;
       for (int rep = 0; rep < 4; ++rep) {
@@ -417,24 +428,24 @@ ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
     float best_ms = 1e30f;
     for (int a : cands) {
       float ms = 0;
-      ss_status s2 = time_config(a, p->bucket_tile[b], ms);
+      ss_status s2 = time_config(a, 1.0f, ms);
       if (s2 == SS_EUNSUPPORTED) continue;     // e.g. staged tables too large for this variant
       if (s2 != SS_OK) { st = s2; break; }
       if (ms < best_ms) { best_ms = ms; best_algo = a; }
     }
     if (st != SS_OK) break;
-    int best_tile = p->bucket_tile[b];
+    float best_mult = 1.0f;
     if (p->opts.tile <= 0) {
       best_ms = 1e30f;
-      for (int t : tile_cands) {
+      for (float mu : mult_cands) {
         float ms = 0;
-        if ((st = time_config(best_algo, t, ms)) != SS_OK) break;
-        if (ms < best_ms) { best_ms = ms; best_tile = t; }
+        if ((st = time_config(best_algo, mu, ms)) != SS_OK) break;
+        if (ms < best_ms) { best_ms = ms; best_mult = mu; }
       }
       if (st != SS_OK) break;
     }
     p->bucket_algo[b] = best_algo;
-    p->bucket_tile[b] = best_tile;
+    p->bucket_mult[b] = best_mult;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

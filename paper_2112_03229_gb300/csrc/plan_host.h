@@ -19,6 +19,7 @@ int staged_bytes(int n, int dir_cap, bool cells, int algo);
 int initial_algo(const ss_plan_opts& o);
 std::vector<Tile> make_tiles(const std::vector<int64_t>& Y_off, const std::vector<int>& bucket_of,
                              const int* bucket_tile, int64_t& total);
+int auto_tile(int64_t total, int blocks, int staged_bytes, float mult);
 void free_dev(void* p);
 
 struct PlanBase {
@@ -42,7 +43,8 @@ struct PlanBase {
   std::vector<int64_t> grid_off;
   // autotuner choices per table-size bucket
   int bucket_algo[kNumBuckets] = {0};
-  int bucket_tile[kNumBuckets] = {0};
+  int bucket_tile[kNumBuckets] = {0};      // targets per tile used by the bound batch
+  float bucket_mult[kNumBuckets] = {1, 1, 1, 1, 1, 1, 1, 1};   // tuned multiple of the automatic tile
   int bucket_tables[kNumBuckets] = {0};
   int tuned = 0;
   // bound batch

@@ -15,7 +15,7 @@ using namespace ss;
 namespace {
 
 constexpr char kMagic[8] = {'S', 'S', 'P', 'L', 'A', 'N', 0, 1};
-constexpr int32_t kVersion = 1;
+constexpr int32_t kVersion = 2;
 
 struct Writer {
   FILE* f;
@@ -85,7 +85,7 @@ extern "C" ss_status ss_plan_save(const ss_plan* p, const char* path) {
   w.vec(p->blob_off);
   w.vec(p->grid_off);
   w.raw(p->bucket_algo, sizeof(p->bucket_algo));
-  w.raw(p->bucket_tile, sizeof(p->bucket_tile));
+  w.raw(p->bucket_mult, sizeof(p->bucket_mult));
   w.raw(p->bucket_tables, sizeof(p->bucket_tables));
   w.val<int32_t>(p->tuned);
   w.val<int64_t>(p->blob_bytes);
@@ -132,7 +132,7 @@ extern "C" ss_status ss_plan_load(ss_plan** out, const char* path, cudaStream_t 
   r.vec(p->blob_off);
   r.vec(p->grid_off);
   r.raw(p->bucket_algo, sizeof(p->bucket_algo));
-  r.raw(p->bucket_tile, sizeof(p->bucket_tile));
+  r.raw(p->bucket_mult, sizeof(p->bucket_mult));
   r.raw(p->bucket_tables, sizeof(p->bucket_tables));
   r.val(p->tuned);
   r.val(p->blob_bytes);

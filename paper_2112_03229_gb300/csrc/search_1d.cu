@@ -261,7 +261,10 @@ static const void* binary_kernel(int D) {
   }
 }
 
-int default_dir_cap(int n) { return std::min(8192, std::max(64, 16 * n)); }
+// Bucket budget: about four buckets per entry keeps the occupancy of a
+// log-spaced table at one or two; sampled (two-level) tables take the largest
+// directory so that it also serves as a fine spline.
+int default_dir_cap(int n) { return n - 1 > kMaxSmemKeys ? 8192 : std::min(4096, std::max(64, 4 * n)); }
 
 ss_status search_1d(const double* X, int32_t n, const double* Y, int64_t m, int32_t* out, int32_t side,
                     int32_t algo, ss_devstat* stat, cudaStream_t stream, int dir_cap_override, int ballot_g) {

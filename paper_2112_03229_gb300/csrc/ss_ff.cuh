@@ -9,10 +9,12 @@
 // are split into hi + lo with integer bit operations, so the hot loop issues
 // no fp64 arithmetic except one final add per output value.
 //
-// The interpolation weights are formed exactly: for a target x in cell
-// [X_c, X_c+1] whose binary exponents differ by at most kMaxCellOctaves,
-// x - X_c is an integer multiple of 2^(e_c - 1075) computed exactly in 64-bit
-// integers; it is then scaled by the per-cell factor g_c = 2^(e_c-1075) / gap_c.
+// The interpolation weights are formed from exact integers: for a target x in
+// cell [X_c, X_c+1] whose binary exponents differ by at most kMaxCellOctaves,
+// x - X_c and X_c+1 - x are integer multiples of 2^(e_c - 1075) computed in
+// 64-bit integers, then scaled by the per-cell factor 1 / (X_c+1 - X_c) in the
+// same units.  Both weights keep full relative precision (none is formed as
+// 1 - w).
 #pragma once
 
 #include "ss_common.cuh"
@@ -50,95 +52,103 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b) {
   return fast_two_sum(p, e);
 }
 
-// 1 - w for w in [0, 1]
-__device__ __forceinline__ ff ff_one_minus(ff w) {
-  const ff s = two_sum(1.0f, -w.hi);
-  return fast_two_sum(s.hi, s.lo - w.lo);
-}
-
 constexpr int kMaxCellOctaves = 10;   // exact integer weights when a cell spans at most 2^10
 constexpr int kFFMinExp = 1023 - 70;  // doubles split into float-float must lie in [2^-70, 2^101)
 constexpr int kFFMaxExp = 1023 + 100;
 
-// Float whose value is the power of two 2^k (k in the normal range).
-__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+// Products and sums that feed further float-float arithmetic are left
+// unnormalised (the pair still sums exactly to the represented value).
+__device__ __forceinline__ ff ff_mul_u(ff a, ff b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return {p, e};
+}
 
-// Split a finite double with biased exponent in [kFFMinExp, kFFMaxExp] (or
-// zero) into hi + lo exactly up to 2^-48 relative.  Returns false (and
-// leaves hi/lo zero) for anything else.
+__device__ __forceinline__ ff ff_add_u(ff a, ff b) {
+  const ff s = two_sum(a.hi, b.hi);
+  return {s.hi, s.lo + (a.lo + b.lo)};
+}
+
+// Split a positive double with biased exponent in [kFFMinExp, kFFMaxExp] into
+// hi (its top 24 significant bits, truncated) + lo (the other 29 bits rounded
+// to 24), exact up to 2^-48 relative.  Integer bit operations and one int to
+// float conversion.  Returns false for zero, negative or out-of-range values.
 __device__ __forceinline__ bool d2ff(double d, ff& r) {
   const uint64_t u = static_cast<uint64_t>(__double_as_longlong(d));
-  const int e = (int)((u >> 52) & 0x7FF);
-  const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
-  r.hi = 0.0f;
-  r.lo = 0.0f;
-  if ((u << 1) == 0) return true;                      // +-0
-  if (e < kFFMinExp || e > kFFMaxExp) return false;
-  const uint64_t M = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);   // 53-bit significand
-  // hi: top 24 bits, exponent e-1023; lo: the remaining 29 bits (rounded to 24)
-  r.hi = __int_as_float((int)(sign | ((uint32_t)(e - 1023 + 127) << 23) | (uint32_t)((M >> 29) & 0x7FFFFF)));
-  const float rem = (float)(uint32_t)(M & 0x1FFFFFFFull) * pow2f(e - 1075);
-  r.lo = sign ? -rem : rem;
+  const uint32_t hw = (uint32_t)(u >> 32);
+  const bool ok = (hw - ((uint32_t)kFFMinExp << 20)) < ((uint32_t)(kFFMaxExp + 1 - kFFMinExp) << 20);
+  const uint32_t hb = (uint32_t)((u - (896ull << 52)) >> 29);        // float bits: exponent rebiased
+  r.hi = __uint_as_float(hb);
+  const float unit = __uint_as_float((hb & 0x7F800000u) - (52u << 23));  // 2^(e - 1075)
+  r.lo = (float)((uint32_t)u & 0x1FFFFFFFu) * unit;
+  return ok;
+}
+
+// Exact widening of a float (zero and subnormals give 0: below 2^-126).
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t b = __float_as_uint(f);
+  if ((b & 0x7F800000u) == 0) return 0.0;
+  const uint64_t w = ((uint64_t)(b & 0x80000000u) << 32) | (((uint64_t)(b & 0x7FFFFFFFu) << 29) + (896ull << 52));
+  return __longlong_as_double((long long)w);
+}
+
+// Double nearest to hi + lo (one fp64 add rounds the exact sum).
+__device__ __forceinline__ double ff2d(ff a) { return widen(a.hi) + widen(a.lo); }
+
+// Per-cell data for the float-float weights (32 bytes).
+struct CellW {
+  uint64_t Mc;      // significand of X[c] (53 bits with the implicit one)
+  uint64_t MnS;     // significand of X[c+1] shifted left by e(X[c+1]) - e(X[c])
+  int ec;           // biased exponent of X[c]
+  int pad;
+  float ghi, glo;   // 2^48 / (MnS - Mc) as float-float
+};
+
+// Cell data of [a, b]; false if the cell is outside the float-float preconditions.
+__device__ __forceinline__ bool make_cell(double a, double b, CellW& c) {
+  const uint64_t ua = static_cast<uint64_t>(__double_as_longlong(a));
+  const uint64_t ub = static_cast<uint64_t>(__double_as_longlong(b));
+  const int ea = (int)((ua >> 52) & 0x7FF), eb = (int)((ub >> 52) & 0x7FF);
+  c = CellW{0, 0, ea, 0, 0.0f, 0.0f};
+  if ((ua >> 63) != 0 || ea < kFFMinExp || eb > kFFMaxExp || eb - ea > kMaxCellOctaves || !(b > a)) return false;
+  c.Mc = (ua & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  c.MnS = ((ub & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << (eb - ea);
+  const double g = 0x1.0p48 / (double)(c.MnS - c.Mc);
+  c.ghi = __double2float_rn(g);
+  c.glo = __double2float_rn(g - (double)c.ghi);
   return true;
 }
 
-// Double nearest to hi + lo (the float-to-double widening is exact and done
-// with integer operations; one fp64 add rounds the sum).
-__device__ __forceinline__ double widen(float f) {
-  const uint32_t b = (uint32_t)__float_as_int(f);
-  const uint32_t ef = (b >> 23) & 0xFF;
-  if (ef == 0) return 0.0;                              // zero (subnormal parts dropped: < 2^-126)
-  const uint64_t hi = ((uint64_t)(b & 0x80000000u) << 32) | ((uint64_t)(ef - 127 + 1023) << 52) |
-                      ((uint64_t)(b & 0x7FFFFFu) << 29);
-  return __longlong_as_double((long long)hi);
+// Integer 0 < v < 2^63 as a float pair scaled by 2^-48: v is normalised so
+// that its leading one sits at bit 47 (shift k, either way), the 48 bits are
+// split into two 24-bit halves, and 2^(k-48) is folded into them.  The low
+// half is then below one unit of the high half's last place, so products
+// with it stay accurate to 2^-47 whatever the magnitude of v.
+__device__ __forceinline__ ff numerator(uint64_t v) {
+  const int k = 16 - __clzll((long long)v);                  // position of bit 47 relative to the leading one
+  const uint64_t t = k >= 0 ? v >> k : v << -k;              // in [2^47, 2^48)
+  const float sc = __int_as_float((127 + k - 48) << 23);      // 2^(k - 48)
+  return {(float)(uint32_t)(t >> 24) * (16777216.0f * sc), (float)((uint32_t)t & 0xFFFFFFu) * sc};
 }
 
-__device__ __forceinline__ double ff2d(ff a) { return widen(a.hi) + widen(a.lo); }
-
-// Unsigned 64-bit integer D > 0 as float-float, exact up to 2^-47 relative.
-__device__ __forceinline__ ff u64_to_ff(uint64_t D) {
-  const int lz = __clzll((long long)D);
-  const uint64_t N = D << lz;                           // leading one at bit 63
-  ff r;
-  r.hi = __int_as_float((int)(((uint32_t)(127 + 63 - lz) << 23) | (uint32_t)((N >> 40) & 0x7FFFFF)));
-  r.lo = (float)(uint32_t)((N >> 16) & 0xFFFFFF) * pow2f(16 - lz);
-  return r;
-}
-
-// Per-cell data staged in shared memory for the float-float path.
-struct CellFF {
-  uint64_t xbits;   // bit pattern of X[c] (positive normal)
-  float ghi, glo;   // g_c = 2^(e_c - 1075) / (X[c+1] - X[c]) as float-float
-};
-
-// Both weights of target x (bit pattern u, positive normal, X[c] < x <= X[c+1])
-// in cell c: w = (x - X[c]) / gap and wbar = (X[c+1] - x) / gap.  Each
-// numerator is an exact integer (no cancellation), so wbar keeps full
-// relative precision when w is close to 1 instead of being formed as 1 - w.
+// Both weights of target x (bit pattern u, X[c] < x <= X[c+1]) in cell c:
+// w = (x - X[c]) / gap and wbar = (X[c+1] - x) / gap, each numerator exact
+// and normalised on its own (so a small wbar keeps its relative precision).
 struct Weights {
   ff w, wbar;
 };
 
-__device__ __forceinline__ Weights cell_weights(uint64_t u, const CellFF& cell, uint64_t next_bits) {
+__device__ __forceinline__ Weights cell_weights(uint64_t u, const CellW& c) {
   const int ex = (int)((u >> 52) & 0x7FF);
-  const int ec = (int)((cell.xbits >> 52) & 0x7FF);
-  const int en = (int)((next_bits >> 52) & 0x7FF);
-  const uint64_t Mx = ((u & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << (ex - ec);
-  const uint64_t Mc = (cell.xbits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const uint64_t Mn = ((next_bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << (en - ec);
-  const uint64_t D = Mx - Mc;          // x - X[c]    in units of 2^(ec - 1075)
-  const uint64_t Dn = Mn - Mx;         // X[c+1] - x  in the same units
-  const ff g{cell.ghi, cell.glo};
+  const uint64_t MxS = ((u & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << (ex - c.ec);
+  const ff g{c.ghi, c.glo};
+  const uint64_t D = MxS - c.Mc, Dn = c.MnS - MxS;
   Weights r;
-  r.w = D == 0 ? ff{0.0f, 0.0f} : ff_mul(u64_to_ff(D), g);
-  r.wbar = Dn == 0 ? ff{0.0f, 0.0f} : ff_mul(u64_to_ff(Dn), g);
+  r.w = D == 0 ? ff{0.0f, 0.0f} : ff_mul_u(numerator(D), g);
+  r.wbar = Dn == 0 ? ff{0.0f, 0.0f} : ff_mul_u(numerator(Dn), g);
   return r;
-}
-
-__device__ __forceinline__ ff ff_clamp01(ff w) {
-  if (w.hi < 0.0f) return {0.0f, 0.0f};
-  if (w.hi > 1.0f || (w.hi == 1.0f && w.lo > 0.0f)) return {1.0f, 0.0f};
-  return w;
 }
 
 }  // namespace ss

@@ -34,17 +34,17 @@ struct __align__(16) BlobHdr {
   int dir_cap;
   int off_mlp, off_dir, off_keys, off_eyt;   // staged sections
   int staged_end;            // end of the staged part
-  int pad0;
+  int gshift;                // fine directory over all keys (sampled tables): bucket shift
   int64_t off_full;          // full keys (global)
   uint64_t base;             // bucket of keys[0]
   uint64_t k0;               // key of X[0]
   float e_lo, e_scale;       // MLP feature scaling
   float loss;                // final training loss of the MLP (diagnostic)
-  int pad1;
+  int gnb;                   // fine directory: bucket count (0: none)
   // 2D axes only: per-cell float-float data follows the staged part
-  int off_cells;             // CellFF[n-1] (staged with the axis), -1 for 1D
+  int off_cells;             // CellW[n-1] (staged with the axis), -1 for 1D
   int ffok;                  // cells usable by the float-float path
-  int pad2[2];
+  uint64_t gbase;            // fine directory: bucket of the first key
 };
 static_assert(sizeof(BlobHdr) == 128, "blob header must stay 128 bytes");
 
@@ -109,13 +109,14 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 
 // View of a staged blob in shared memory.
 struct StagedView {
-  const BlobHdr* h;
+  BlobHdr h;                 // header fields, held in registers
   const float* mlp;
   const int* dir;
   const uint64_t* keys;
   const uint64_t* eyt;
-  const CellFF* cells;
+  const CellW* cells;
   const uint64_t* full;      // global full keys (stride > 1)
+  const int* gdir;           // global fine directory over all keys (stride > 1)
 };
 
 // Stage blob `src` (global) into smem at `dst`: header, then the range the
@@ -146,19 +147,20 @@ __device__ __forceinline__ StagedView stage_blob(const unsigned char* __restrict
   phase ^= 1u;
   const int shift_off = (int)sizeof(BlobHdr) - lo;     // smem position of blob offset o is o + shift_off
   StagedView v;
-  v.h = reinterpret_cast<const BlobHdr*>(dst);
+  v.h = hdr;
   v.mlp = reinterpret_cast<const float*>(dst + hdr.off_mlp + shift_off);
   v.dir = reinterpret_cast<const int*>(dst + hdr.off_dir + shift_off);
   v.keys = reinterpret_cast<const uint64_t*>(dst + hdr.off_keys + shift_off);
   v.eyt = reinterpret_cast<const uint64_t*>(dst + hdr.off_eyt + shift_off);
-  v.cells = hdr.off_cells >= 0 ? reinterpret_cast<const CellFF*>(dst + hdr.off_cells + shift_off) : nullptr;
+  v.cells = hdr.off_cells >= 0 ? reinterpret_cast<const CellW*>(dst + hdr.off_cells + shift_off) : nullptr;
   v.full = hdr.off_full >= 0 ? reinterpret_cast<const uint64_t*>(src + hdr.off_full) : nullptr;
+  v.gdir = hdr.gnb > 0 ? reinterpret_cast<const int*>(src + hdr.off_full + (int64_t)(hdr.nk + kPad) * 8) : nullptr;
   return v;
 }
 
 // Count over the full searched set after the staged count c (two-level tables).
 __device__ __forceinline__ int finish_full(const StagedView& v, int c, uint64_t q) {
-  const BlobHdr& h = *v.h;
+  const BlobHdr& h = v.h;
   if (h.stride == 1) return c;
   int lo = min(c * h.stride, h.nk);
   int len = min(h.stride, h.nk - lo);
@@ -172,12 +174,12 @@ __device__ __forceinline__ int finish_full(const StagedView& v, int c, uint64_t 
 // Key i (0-based among X[1..n-1]) of the table, from shared memory when the
 // whole table is staged, else from the global full keys.
 __device__ __forceinline__ uint64_t key_at(const StagedView& v, int i) {
-  return v.h->stride == 1 ? v.keys[i] : __ldg(v.full + i);
+  return v.h.stride == 1 ? v.keys[i] : __ldg(v.full + i);
 }
 
 // Plain count of keys below q with the bucket directory (any occupancy).
 __device__ __forceinline__ int plain_bucket(const StagedView& v, uint64_t q) {
-  const BlobHdr& h = *v.h;
+  const BlobHdr& h = v.h;
   const int T = h.occ > 0 ? 32 - __clz(h.occ) : 0;
   const int c = h.occ <= 1 ? search_bucket<1>(v.keys, v.dir, h.shift, h.base, h.nb, q)
                            : search_bucket_bisect(v.keys, v.dir, h.shift, h.base, h.nb, T, q);
@@ -185,34 +187,67 @@ __device__ __forceinline__ int plain_bucket(const StagedView& v, uint64_t q) {
 }
 
 __device__ __forceinline__ int plain_binary(const StagedView& v, uint64_t q) {
-  return finish_full(v, search_eyt_rt(v.eyt, v.h->D, q), q);
+  return finish_full(v, search_eyt_rt(v.eyt, v.h.D, q), q);
 }
 
 // Learned search: proposal p (count units), exact check that the answer lies
-// in [p-E, p+E], bounded bisection inside, plain bucket search otherwise.
-__device__ __forceinline__ int learned_count(const StagedView& v, int p, uint64_t q, int& fallbacks) {
-  const BlobHdr& h = *v.h;
-  const int lo = max(p - h.E, 0), hi = min(p + h.E, h.nk);
-  const bool ok = (lo == 0 || key_at(v, lo - 1) < q) && (hi == h.nk || key_at(v, hi) >= q);
-  if (!ok) {
-    ++fallbacks;
-    return plain_bucket(v, q);
+// in [p-E, p+E], then the count inside the window; plain bucket search if the
+// check fails.  Windows of at most 6 keys are scanned with independent loads
+// (one memory round trip), wider ones bisected.  KEYS reads the keys from
+// shared memory (whole table staged) or global memory (sampled table).
+template <class KEYS>
+__device__ __forceinline__ int window_count(KEYS key, int nk, int E, int p, uint64_t q, bool& ok) {
+  const int lo = max(p - E, 0), hi = min(p + E, nk);
+  ok = (lo == 0 || key(lo - 1) < q) && (hi == nk || key(hi) >= q);
+  if (E <= 3) {
+    int c = lo;
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+      if (lo + j < hi) c += key(lo + j) < q ? 1 : 0;
+    return c;
   }
   int c = lo, len = hi - lo;
   while (len > 0) {
     const int half = len >> 1;
-    if (key_at(v, c + half) < q) { c += half + 1; len -= half + 1; } else { len = half; }
+    if (key(c + half) < q) { c += half + 1; len -= half + 1; } else { len = half; }
   }
   return c;
 }
 
+__device__ __forceinline__ int learned_count(const StagedView& v, int p, uint64_t q, int& fallbacks) {
+  const BlobHdr& h = v.h;
+  bool ok;
+  int c;
+  if (h.stride == 1) {
+    const uint64_t* keys = v.keys;
+    c = window_count([keys](int i) { return keys[i]; }, h.nk, h.E, p, q, ok);
+  } else {
+    const uint64_t* full = v.full;
+    c = window_count([full](int i) { return __ldg(full + i); }, h.nk, h.E, p, q, ok);
+  }
+  if (!ok) {
+    ++fallbacks;
+    return plain_bucket(v, q);
+  }
+  return c;
+}
+
+// Spline proposal in count units of the whole table.  A sampled (two-level)
+// table uses its fine directory over all keys, kept in global memory (two
+// L2 loads), so the proposal is as sharp as for a staged table.
+__device__ __forceinline__ int spline_proposal(const StagedView& v, uint64_t q) {
+  const BlobHdr& h = v.h;
+  if (h.stride > 1 && h.gnb > 0) return min((int)rintf(spline_position(v.gdir, h.gshift, h.gbase, h.gnb, q)), h.nk);
+  const float pos = spline_position(v.dir, h.shift, h.base, h.nb, q);
+  return min((int)rintf(pos * (float)h.stride), h.nk);
+}
+
 __device__ __forceinline__ int spline_count(const StagedView& v, uint64_t q, int& fallbacks) {
-  const BlobHdr& h = *v.h;
-  return learned_count(v, spline_propose(v.dir, h.shift, h.base, h.nb, q), q, fallbacks);
+  return learned_count(v, spline_proposal(v, q), q, fallbacks);
 }
 
 __device__ __forceinline__ int mlp_count(const StagedView& v, double t, uint64_t q, int& fallbacks) {
-  const BlobHdr& h = *v.h;
+  const BlobHdr& h = v.h;
   const MlpFeatScale sc{h.e_lo, h.e_scale};
   return learned_count(v, mlp_propose(v.mlp, sc, h.n, t), q, fallbacks);
 }

@@ -183,11 +183,23 @@ __device__ __forceinline__ int search_eyt_rt(const uint64_t* __restrict__ eyt, i
 // Bucket directory + fixed-length scan (occupancy <= SCAN, Sec. 3.5's
 // linear search inside a bin).  Keys past the bucket are larger than q (they
 // sit in later buckets) or are sentinels, so scanning them adds nothing.
+// Bucket of query key q, clamped to [0, nb-1].  Shifts of 32 or more (the
+// common case: buckets no finer than 2^-20 of an octave) need only the key's
+// high word; the branch is uniform across the block.
+__device__ __forceinline__ int bucket_index(uint64_t q, int shift, uint64_t base, int nb) {
+  if (shift >= 32) {
+    const uint32_t hb = (uint32_t)(q >> 32) >> (shift - 32);
+    const uint32_t d = hb - (uint32_t)base;                 // base < 2^32 here
+    return hb < (uint32_t)base ? 0 : (int)min(d, (uint32_t)(nb - 1));
+  }
+  const uint64_t hb = q >> shift;
+  return hb < base ? 0 : (int)min(hb - base, (uint64_t)(nb - 1));
+}
+
 template <int SCAN>
 __device__ __forceinline__ int search_bucket(const uint64_t* __restrict__ keys, const int* __restrict__ dir,
                                              int shift, uint64_t base, int nb, uint64_t q) {
-  const uint64_t hb = q >> shift;
-  const int b = hb < base ? 0 : (int)min(hb - base, (uint64_t)(nb - 1));
+  const int b = bucket_index(q, shift, base, nb);
   const int lo = dir[b];
   int c = lo;
 #pragma unroll
@@ -199,8 +211,7 @@ __device__ __forceinline__ int search_bucket(const uint64_t* __restrict__ keys, 
 // the largest occupancy).
 __device__ __forceinline__ int search_bucket_bisect(const uint64_t* __restrict__ keys, const int* __restrict__ dir,
                                                     int shift, uint64_t base, int nb, int T, uint64_t q) {
-  const uint64_t hb = q >> shift;
-  const int b = hb < base ? 0 : (int)min(hb - base, (uint64_t)(nb - 1));
+  const int b = bucket_index(q, shift, base, nb);
   int lo = dir[b], len = dir[b + 1] - lo;
   for (int it = 0; it < T; ++it) {
     const int half = len >> 1;

@@ -120,7 +120,7 @@ extern "C" ss_status ss_search_1d_batched_static(int32_t ntables, const int64_t*
   k_prep_1d<<<ntables, 256, 0, stream>>>(pa);
   SS_CHECK_CUDA(cudaGetLastError());
   if (tiles.empty()) return SS_OK;
-  const void* kern = batched_1d_kernel(side == SS_SIDE_LE);
+  const void* kern = batched_1d_kernel(side == SS_SIDE_LE, 0);
   SS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int per_sm = 0;
   SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNumThreads, smem));

@@ -187,12 +187,12 @@ def test_plan_autotune_and_cache(ss, tmp_path):
     inf = plan.info()
     assert inf.tuned == 1 and os.path.exists(cache)
     ch = plan.choices()
-    assert ch and all(a in ss.BLOB_ALGOS[:5] and t in (4096, 16384, 65536) for a, t, _ in ch.values())
+    assert ch and all(a in ss.BLOB_ALGOS[:5] and t >= 1024 for a, t, _ in ch.values())
     text = open(cache).read()
-    assert '"buckets"' in text
+    assert '"buckets"' in text and '"tile_multiple"' in text
     plan2, got2, _ = run_plan_1d(ss, b, autotune=True, tune_cache=cache)
     np.testing.assert_array_equal(got2, want)
-    assert plan2.choices() == ch
+    assert {k: v[0] for k, v in plan2.choices().items()} == {k: v[0] for k, v in ch.items()}
 
 
 def test_learned_gain(ss):

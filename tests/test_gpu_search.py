@@ -251,3 +251,20 @@ def test_2d_full_size_sampled(ss):
     sample = torch.randint(0, m, (1_000_000,), device=DEV)
     wi, wv = oracle.search_interp_2d(R.cpu().numpy(), T.cpu().numpy(), F.cpu().numpy(), Y2[sample].cpu().numpy())
     check_2d(idx[sample].cpu().numpy(), val[sample].cpu().numpy(), wi, wv)
+
+
+# ---------------------------------------------------------------- host-array entry points
+
+def test_host_entry_points_match_device_calls(ss):
+    X, Y = wl.plain_1d(m=(1 << 24) + (1 << 23) + 5, seed=3)     # 1.5 chunks + ragged tail
+    Yp = Y.pin_memory()
+    got = ss.search_1d_host(X, Yp, out=torch.empty(len(Y), dtype=torch.int32).pin_memory())
+    np.testing.assert_array_equal(got.numpy(), ss.search_1d(X.to(DEV), Y.to(DEV)).cpu().numpy())
+    # pageable buffers work too
+    got2 = ss.search_1d_host(X, Y[:1001].clone(), side=1)
+    np.testing.assert_array_equal(got2.numpy(), oracle.search_1d(X.numpy(), Y[:1001].numpy(), side=1))
+    R, T, F, Y2 = wl.interp_2d(m=(1 << 23) + 77, seed=4)
+    idx, val = ss.search_interp_2d_host(R, T, F, Y2.pin_memory())
+    di, dv = ss.search_interp_2d(R.to(DEV), T.to(DEV), F.to(DEV), Y2.to(DEV))
+    np.testing.assert_array_equal(idx.numpy(), di.cpu().numpy())
+    np.testing.assert_array_equal(val.numpy(), dv.cpu().numpy())

@@ -46,7 +46,7 @@ def test_static_matches_plan_on_two_calls_in_a_row(ss):
 
 
 def test_static_rejects_a_batch_over_its_limit(ss):
-    b = wl.batched_1d(ntables=600, count_scale=0.0002, seed=23)
+    b = wl.batched_1d(ntables=4000, count_scale=0.00005, seed=23)
     with pytest.raises(ss.SSError) as e:
         ss.search_1d_batched_static(b.X_off, b.X.to(DEV), b.Y_off, b.Y.to(DEV))
     assert e.value.code == 1 and "bytes" in str(e.value)
