@@ -6,7 +6,11 @@ python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ou
 Prints ONE JSON line (rank 0).  A step is one pass of the hot path over one
 batch of synthetic input that is already resident in HBM; `value` is the
 whole-job throughput in Gtargets/s (a 2D (rho, T) pair counts as one
-target).  Inputs are larger than L2, so no flush is needed between steps.
+target).  The default workload is the batched plain-vs-learned case: 10,000
+tables of 20..2000 entries, Zipf(1.1) target counts (about 1.1B targets),
+one graph launch of the persistent plan kernel per step; the timed form is
+the autotuned plain search, and the spline and MLP proposal forms are timed
+on the same batch beside it.  Inputs are larger than L2, so no flush is needed between steps.
 `e2e` is the same metric with the inputs copied in from pinned host memory
 and the outputs copied back inside the timed region.  `--impl reference`
 times the plain CPU oracle on host cores on a bounded sample of the same
@@ -260,7 +264,7 @@ class PlanWorkload(Workload):
     persistent batched kernel over the bound batch."""
     kernel = "k_batched_1d"
     bytes_per_target = 8 + 4
-    model = "spline"
+    model = "none"
 
     def __init__(self, model=None, autotune=True):
         if model is not None:
@@ -268,9 +272,11 @@ class PlanWorkload(Workload):
         self.autotune = autotune
         self.plans = {}
 
+    tile = 0
+
     def make_plan(self, model):
         import paper_2112_03229_gb300 as ss
-        return ss.Plan.create_1d(self.b.X_off, self.b.X_dev, model=model, autotune=self.autotune,
+        return ss.Plan.create_1d(self.b.X_off, self.b.X_dev, model=model, autotune=self.autotune, tile=self.tile,
                                  tune_cache=os.path.join(ROOT, "_build", "tune_%s_%s.json" % (self.name, model)))
 
     def setup(self, dev, seed):
@@ -293,23 +299,33 @@ class PlanWorkload(Workload):
     def targets(self):
         return int(self.b.Y_off[-1])
 
-    def compare(self, stream, steps):
-        """Plain plan (model none, autotuned) on the same bound batch, timed the same way."""
-        plain = self.make_plan("none")
-        plain.bind_1d(self.b.Y_off, self.Y, self.out)
+    def bind(self, plan):
+        plan.bind_1d(self.b.Y_off, self.Y, self.out)
+
+    def setup_reference(self, max_targets):
+        """CPU-only inputs for the oracle arm: the first tables of the batch."""
+        self.b = self.generate("cpu", 0, max_targets=max_targets)
+        self.Y = self.b.Y
+
+    def compare(self, stream, steps, model):
+        """A plan with another position model (or none) on the same bound batch, timed the same way."""
+        other = self.make_plan(model)
+        self.bind(other)
         for _ in range(3):
-            plain.execute()
+            other.execute()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
-            plain.execute()
+            other.execute()
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
-        res = {"model": "none", "Gtargets_s": round(self.targets() / (ms / 1e3) / 1e9, 3),
-               "ms_per_step": round(ms, 4), "choices": plain.choices()}
-        self.plan.bind_1d(self.b.Y_off, self.Y, self.out)
+        inf = other.info()
+        res = {"model": model, "Gtargets_s": round(self.targets() / (ms / 1e3) / 1e9, 3),
+               "ms_per_step": round(ms, 4), "choices": other.choices(), "max_window": inf.max_window,
+               "mean_window": round(inf.mean_window, 2), "train_loss": inf.train_loss}
+        self.bind(self.plan)
         return res
 
     def e2e_setup(self):
@@ -352,10 +368,11 @@ class Batched1D(PlanWorkload):
     name = "batched1d-10k-zipf"
     m = 0
 
-    def generate(self, dev, seed):
+    def generate(self, dev, seed, max_targets=None):
         from paper_2112_03229_gb300 import workloads as wl
         scale = self.m / 1.1e9 if self.m else 1.0
-        return wl.batched_1d(ntables=10_000, seed=5 + 1000 * seed, count_scale=scale, device=dev)
+        return wl.batched_1d(ntables=10_000, seed=5 + 1000 * seed, count_scale=scale, device=dev,
+                             max_targets=max_targets)
 
 
 class Sweep1D(PlanWorkload):
@@ -367,10 +384,11 @@ class Sweep1D(PlanWorkload):
         super().__init__(**kw)
         self.per_table = per_table
 
-    def generate(self, dev, seed):
+    def generate(self, dev, seed, max_targets=None):
         from paper_2112_03229_gb300 import workloads as wl
         tabs = [wl.sweep_table(n, seed=4 + 1000 * seed) for n in (16, 256, 4096, 65536)]
-        Ys = [wl.log_uniform(self.per_table, 0.5 * t[0].item(), 2 * t[-1].item(), seed=7 + i + 1000 * seed,
+        per = self.per_table if max_targets is None else max(1, max_targets // 4)
+        Ys = [wl.log_uniform(per, 0.5 * t[0].item(), 2 * t[-1].item(), seed=7 + i + 1000 * seed,
                              device=dev) for i, t in enumerate(tabs)]
         X = torch.cat(tabs)
         X_off = torch.tensor(np.concatenate([[0], np.cumsum([len(t) for t in tabs])]))
@@ -428,7 +446,7 @@ class Batched2D(PlanWorkload):
         import paper_2112_03229_gb300 as ss
         b = self.b
         return ss.Plan.create_2d(b.R_off, b.R_dev, b.T_off, b.T_dev, b.F_off, b.F_dev, model=model,
-                                 autotune=self.autotune,
+                                 autotune=self.autotune, tile=self.tile,
                                  tune_cache=os.path.join(ROOT, "_build", "tune_%s_%s.json" % (self.name, model)))
 
     def setup(self, dev, seed):
@@ -452,23 +470,14 @@ class Batched2D(PlanWorkload):
     def targets(self):
         return self.m
 
-    def compare(self, stream, steps):
-        plain = self.make_plan("none")
-        plain.bind_2d(self.b.Y_off, self.Y, self.idx, self.val)
-        for _ in range(3):
-            plain.execute()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            plain.execute()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
-        res = {"model": "none", "Gtargets_s": round(self.m / (ms / 1e3) / 1e9, 3), "ms_per_step": round(ms, 4),
-               "choices": plain.choices()}
-        self.plan.bind_2d(self.b.Y_off, self.Y, self.idx, self.val)
-        return res
+    def bind(self, plan):
+        plan.bind_2d(self.b.Y_off, self.Y, self.idx, self.val)
+
+    def setup_reference(self, max_targets):
+        from paper_2112_03229_gb300 import workloads as wl
+        nt = max(1, min(1000, max_targets // self.pairs))
+        self.b = wl.batched_2d(ntables=nt, pairs_per_table=self.pairs, coherent=self.coherent, seed=6, device="cpu")
+        self.Y = self.b.Y2
 
     def e2e_setup(self):
         self.hY = torch.empty(self.Y.shape, dtype=torch.float64, pin_memory=True)
@@ -507,7 +516,7 @@ WORKLOADS = {
     "batched2d": Batched2D,
     "batched2d-coherent": lambda: Batched2D(coherent=True),
 }
-DEFAULT_WORKLOAD = "interp2d"
+DEFAULT_WORKLOAD = "batched1d"
 
 
 # ---------------------------------------------------------------------------
@@ -542,10 +551,12 @@ def run_reference(args, wl_obj):
     rank, world, _ = dist_setup(args.gpus)
     if rank != 0:
         return
-    dev = "cpu"
-    # build the workload's inputs on the CPU at a bounded size
-    wl_obj.m = min(wl_obj.m, 1 << 23)
-    wl_obj.setup(dev, 0)
+    # build the workload's inputs on the CPU at a bounded size (a prefix of the same workload)
+    if isinstance(wl_obj, PlanWorkload):
+        wl_obj.setup_reference(max_targets=1 << 24)
+    else:
+        wl_obj.m = min(wl_obj.m, 1 << 23)
+        wl_obj.setup("cpu", 0)
     times = []
     for s in range(args.warmup + args.steps):
         rate, sample = wl_obj.cpu_sample(budget_s=2.0)
@@ -605,8 +616,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--targets", type=int, default=0, help="override the workload's target count (profiling cases)")
     ap.add_argument("--model", default=None, choices=["none", "spline", "mlp"],
-                    help="position model of the plan-based workloads (default spline)")
+                    help="position model of the timed plan (default none: plain search; the learned forms are "
+                         "timed beside it)")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-plan comparison of plan workloads")
+    ap.add_argument("--tile", type=int, default=0, help="fixed targets per tile for plan workloads (0: tuned)")
     ap.add_argument("--algo", default=None, choices=["auto", "bucket", "binary", "branchy", "ballot", "ballot8", "ballot16"],
                     help="in-block search of the plain1d workload")
     args = ap.parse_args()
@@ -619,6 +632,8 @@ def main():
         wl_obj.m = args.targets
     if args.model is not None and isinstance(wl_obj, PlanWorkload):
         wl_obj.model = args.model
+    if args.tile and isinstance(wl_obj, PlanWorkload):
+        wl_obj.tile = args.tile
     if args.algo is not None and isinstance(wl_obj, Plain1D):
         wl_obj.set_algo(args.algo)
     if args.impl == "reference":
@@ -689,11 +704,23 @@ def main():
         extra["plan"] = {"model": wl_obj.model, "setup_s": round(wl_obj.setup_s, 2), "choices": wl_obj.plan.choices(),
                          "max_window": inf.max_window, "mean_window": round(inf.mean_window, 2),
                          "train_loss": inf.train_loss, "ntiles": inf.ntiles}
-        if world == 1 and not args.no_compare and wl_obj.model != "none":
-            pl = wl_obj.compare(stream, args.steps)
-            pl["frac"] = round(wl_obj.targets() * wl_obj.bytes_per_target / (pl["ms_per_step"] / 1e3) / 1e9 / peak, 4)
-            extra["plain"] = pl
-            extra["learned_over_plain"] = round(value / pl["Gtargets_s"], 3)
+        if world == 1 and not args.no_compare:
+            def frac_of(r):
+                return round(wl_obj.targets() * wl_obj.bytes_per_target / (r["ms_per_step"] / 1e3) / 1e9 / peak, 4)
+            if wl_obj.model == "none":
+                # the timed form is the plain search; the learned forms on the same batch
+                learned = {}
+                for model in ("spline", "mlp"):
+                    r = wl_obj.compare(stream, args.steps, model)
+                    r["frac"] = frac_of(r)
+                    learned[model] = r
+                extra["learned"] = learned
+                extra["learned_over_plain"] = {k: round(v["Gtargets_s"] / value, 3) for k, v in learned.items()}
+            else:
+                r = wl_obj.compare(stream, args.steps, "none")
+                r["frac"] = frac_of(r)
+                extra["plain"] = r
+                extra["learned_over_plain"] = round(value / r["Gtargets_s"], 3)
         if isinstance(wl_obj, Sweep1D) and world == 1 and not args.no_compare:
             extra["per_table"] = sweep_per_table(wl_obj, stream, args.steps)
 

@@ -215,15 +215,20 @@ class Batched1D:
 
 
 def batched_1d(ntables: int = 10_000, seed: int = 5, count_lo: int = 1000, count_hi: int = 1_000_000,
-               count_scale: float = 1.0, device="cpu") -> Batched1D:
+               count_scale: float = 1.0, device="cpu", max_targets: int | None = None) -> Batched1D:
     """Many uneven tables: sizes round(log-uniform[20,2000]), ranges
     min 10^U(-8,-2) with span 10^U(4,12), Zipf(1.1) target counts on
-    [count_lo, count_hi] (scaled by count_scale for small test cases)."""
+    [count_lo, count_hi] (scaled by count_scale for small test cases).
+    max_targets keeps the targets of the first tables only (a prefix of the
+    same batch: later tables get none)."""
     rng = np.random.default_rng(seed)
     sizes = np.rint(10 ** rng.uniform(math.log10(20), math.log10(2000), ntables)).astype(np.int64)
     lo = 10 ** rng.uniform(-8, -2, ntables)
     hi = lo * 10 ** rng.uniform(4, 12, ntables)
     counts = np.maximum(0, np.rint(zipf_counts(ntables, 1.1, count_lo, count_hi, rng) * count_scale)).astype(np.int64)
+    if max_targets is not None:
+        keep = np.cumsum(counts) <= max_targets
+        counts = np.where(keep, counts, 0)
     X_off = np.concatenate([[0], np.cumsum(sizes)])
     Y_off = np.concatenate([[0], np.cumsum(counts)])
     X = torch.cat([log_spaced_table(int(sizes[k]), float(lo[k]), float(hi[k]), 0.1, seed * 100003 + k)
