@@ -301,12 +301,59 @@ __global__ void __launch_bounds__(256) k_window(WindowArgs a) {
 // resident warps) at the level the plain searches need.
 enum : int { FAM_PLAIN = 0, FAM_SPLINE = 1, FAM_MLP = 2 };
 
-template <int FAM>
-__device__ __forceinline__ int count_for(const StagedView& v, int algo, double t, uint64_t q, int& fallbacks) {
-  if (FAM >= FAM_MLP && algo == BL_MLP) return mlp_count(v, t, q, fallbacks);
-  if (FAM >= FAM_SPLINE && algo == BL_SPLINE) return spline_count(v, q, fallbacks);
-  if (algo == BL_BINARY) return plain_binary(v, q);
-  return plain_bucket(v, q);
+constexpr uint64_t kKeyNegInf = 0x0010000000000000ull;   // image of -inf; NaNs map below it
+
+// Streams one tile's targets through count(y, q): a scalar head up to a
+// 4-target boundary, then 128-bit quads two at a time (both loads issue
+// before any search, and the eight searches are independent code, so their
+// shared-memory round trips overlap), one last quad, and a scalar tail.
+template <class F>
+__device__ __forceinline__ void stream_tile(const double* __restrict__ Y, int32_t* __restrict__ out, int64_t b,
+                                            int cnt, bool vec, uint64_t le, int& nans, F&& count) {
+  const int bs = blockDim.x;
+  const int head = vec ? min(cnt, (int)((-b) & 3)) : cnt;
+  const int nq = (cnt - head) >> 2;
+  for (int i = threadIdx.x; i < head; i += bs) {
+    const double y = Y[b + i];
+    const uint64_t k = order_key(y);
+    nans += k < kKeyNegInf;
+    out[b + i] = count(y, k + le);
+  }
+  const double2* Y2 = reinterpret_cast<const double2*>(Y + b + head);
+  int4* O4 = reinterpret_cast<int4*>(out + b + head);
+  int g = threadIdx.x;
+  for (; g + bs < nq; g += 2 * bs) {
+    const double2 p0 = ld_stream(Y2 + 2 * g), p1 = ld_stream(Y2 + 2 * g + 1);
+    const double2 p2 = ld_stream(Y2 + 2 * (g + bs)), p3 = ld_stream(Y2 + 2 * (g + bs) + 1);
+    const double y[8] = {p0.x, p0.y, p1.x, p1.y, p2.x, p2.y, p3.x, p3.y};
+    int r[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint64_t k = order_key(y[j]);
+      nans += k < kKeyNegInf;
+      r[j] = count(y[j], k + le);
+    }
+    st_stream(O4 + g, make_int4(r[0], r[1], r[2], r[3]));
+    st_stream(O4 + g + bs, make_int4(r[4], r[5], r[6], r[7]));
+  }
+  if (g < nq) {
+    const double2 p0 = ld_stream(Y2 + 2 * g), p1 = ld_stream(Y2 + 2 * g + 1);
+    const double y[4] = {p0.x, p0.y, p1.x, p1.y};
+    int r[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint64_t k = order_key(y[j]);
+      nans += k < kKeyNegInf;
+      r[j] = count(y[j], k + le);
+    }
+    st_stream(O4 + g, make_int4(r[0], r[1], r[2], r[3]));
+  }
+  for (int i = head + 4 * nq + threadIdx.x; i < cnt; i += bs) {
+    const double y = Y[b + i];
+    const uint64_t k = order_key(y);
+    nans += k < kKeyNegInf;
+    out[b + i] = count(y, k + le);
+  }
 }
 
 template <int G>
@@ -321,7 +368,7 @@ __device__ __forceinline__ void ballot_tile(const StagedView& v, const double* _
     uint64_t q = 0;
     if (ok) {
       const uint64_t k = order_key(Y[b + i]);
-      nans += k < 0x0010000000000000ull;
+      nans += k < kKeyNegInf;
       q = k + le;
     }
     int r = 0;
@@ -363,7 +410,8 @@ __global__ void __launch_bounds__(kNumThreads, FAM == FAM_MLP ? 2 : 4) k_batched
       cur_table = tile.table;
       if (!ok) break;
     }
-    const int algo = v.h.algo;
+    const BlobHdr& h = v.h;
+    const int algo = h.algo;
     const int64_t b = tile.begin;
     const int cnt = tile.count;
     if (algo >= BL_BALLOT8 && algo <= BL_BALLOT32) {
@@ -372,44 +420,28 @@ __global__ void __launch_bounds__(kNumThreads, FAM == FAM_MLP ? 2 : 4) k_batched
       else ballot_tile<32>(v, a.Y, a.out, b, cnt, le, nans);
       continue;
     }
-    // scalar head up to a 4-target boundary, quads with 128-bit I/O, scalar tail
-    const int head = a.vec ? min(cnt, (int)((-b) & 3)) : cnt;
-    const int nq = (cnt - head) >> 2;
-    for (int i = threadIdx.x; i < head; i += blockDim.x) {
-      const double y = a.Y[b + i];
-      const uint64_t k = order_key(y);
-      nans += k < 0x0010000000000000ull;
-      a.out[b + i] = count_for<FAM>(v, algo, y, k + le, fallbacks);
-    }
-    const double2* Y2 = reinterpret_cast<const double2*>(a.Y + b + head);
-    int4* O4 = reinterpret_cast<int4*>(a.out + b + head);
-    // two quads in flight per thread: both loads issue before any search
-    for (int g = threadIdx.x; g < nq; g += 2 * blockDim.x) {
-      const int g2 = g + blockDim.x;
-      const bool two = g2 < nq;
-      const double2 p0 = ld_stream(Y2 + 2 * g), p1 = ld_stream(Y2 + 2 * g + 1);
-      double2 p2 = make_double2(0.0, 0.0), p3 = p2;
-      if (two) {
-        p2 = ld_stream(Y2 + 2 * g2);
-        p3 = ld_stream(Y2 + 2 * g2 + 1);
-      }
-      const double y[8] = {p0.x, p0.y, p1.x, p1.y, p2.x, p2.y, p3.x, p3.y};
-      int r[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        if (j >= 4 && !two) break;
-        const uint64_t k = order_key(y[j]);
-        nans += k < 0x0010000000000000ull;
-        r[j] = count_for<FAM>(v, algo, y[j], k + le, fallbacks);
-      }
-      st_stream(O4 + g, make_int4(r[0], r[1], r[2], r[3]));
-      if (two) st_stream(O4 + g2, make_int4(r[4], r[5], r[6], r[7]));
-    }
-    for (int i = head + 4 * nq + threadIdx.x; i < cnt; i += blockDim.x) {
-      const double y = a.Y[b + i];
-      const uint64_t k = order_key(y);
-      nans += k < 0x0010000000000000ull;
-      a.out[b + i] = count_for<FAM>(v, algo, y, k + le, fallbacks);
+    // one uniform branch per tile picks the search; inside the tile the
+    // searches are branch-free straight-line code where the table allows it
+    const bool vec = a.vec != 0;
+    if (FAM >= FAM_MLP && algo == BL_MLP) {
+      stream_tile(a.Y, a.out, b, cnt, vec, le, nans, [&](double y, uint64_t q) { return mlp_count(v, y, q, fallbacks); });
+    } else if (FAM >= FAM_SPLINE && algo == BL_SPLINE) {
+      stream_tile(a.Y, a.out, b, cnt, vec, le, nans, [&](double, uint64_t q) { return spline_count(v, q, fallbacks); });
+    } else if (algo == BL_BINARY) {
+      stream_tile(a.Y, a.out, b, cnt, vec, le, nans, [&](double, uint64_t q) { return plain_binary(v, q); });
+    } else if (h.stride == 1 && h.occ <= 2) {
+      const uint64_t* keys = v.keys;
+      const int* dir = v.dir;
+      const int shift = h.shift, nb = h.nb;
+      const uint64_t base = h.base;
+      if (h.occ <= 1)
+        stream_tile(a.Y, a.out, b, cnt, vec, le, nans,
+                    [&](double, uint64_t q) { return search_bucket<1>(keys, dir, shift, base, nb, q); });
+      else
+        stream_tile(a.Y, a.out, b, cnt, vec, le, nans,
+                    [&](double, uint64_t q) { return search_bucket<2>(keys, dir, shift, base, nb, q); });
+    } else {
+      stream_tile(a.Y, a.out, b, cnt, vec, le, nans, [&](double, uint64_t q) { return plain_bucket(v, q); });
     }
   }
   if (!ok && threadIdx.x == 0) s_err = 1;
