@@ -133,6 +133,72 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# The CPU oracle, timed as it stands (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def _batched_tables(Y_off, lo, hi):
+    """Tables t0..t1-1 whose target ranges meet [lo, hi), and their offsets clipped to it."""
+    t0 = max(int(np.searchsorted(Y_off, lo, side="right")) - 1, 0)
+    t1 = max(int(np.searchsorted(Y_off, hi, side="left")), t0 + 1)
+    return t0, t1, np.clip(Y_off[t0:t1 + 1], lo, hi) - lo
+
+
+def _oracle_call(kind, a, lo, hi):
+    """One oracle call on units [lo, hi) of a sample (targets, or pairs for 2D)."""
+    import oracle
+    if kind == "1d":
+        oracle.search_1d(a["X"], a["Y"][lo:hi])
+    elif kind == "2d":
+        oracle.search_interp_2d(a["R"], a["T"], a["F"], a["Y2"][lo:hi])
+    elif kind == "1d_batched":
+        t0, t1, yo = _batched_tables(a["Y_off"], lo, hi)
+        xo = a["X_off"][t0:t1 + 1]
+        oracle.search_1d_batched(xo - xo[0], a["X"][xo[0]:xo[-1]], yo, a["Y"][lo:hi])
+    else:
+        t0, t1, yo = _batched_tables(a["Y_off"], lo, hi)
+        ro, to, fo = (a[k][t0:t1 + 1] for k in ("R_off", "T_off", "F_off"))
+        oracle.search_interp_2d_batched(ro - ro[0], a["R"][ro[0]:ro[-1]], to - to[0], a["T"][to[0]:to[-1]],
+                                        fo - fo[0], a["F"][fo[0]:fo[-1]], yo, a["Y2"][lo:hi])
+
+
+def oracle_rate_1thread(kind, a, n):
+    t0 = time.perf_counter()
+    _oracle_call(kind, a, 0, n)
+    return n / max(time.perf_counter() - t0, 1e-9)
+
+
+class OracleTimer:
+    """Runs the oracle on a sample in one thread, and split over one thread
+    per host core.  The oracle is C called through ctypes, which releases the
+    interpreter lock for the call, so the threads run in parallel on shared
+    arrays (no copies, no processes)."""
+
+    def __init__(self):
+        from concurrent.futures import ThreadPoolExecutor
+        self.cores = os.cpu_count() or 1
+        self.pool = ThreadPoolExecutor(self.cores)
+
+    def parallel(self, kind, a, n):
+        cuts = np.linspace(0, n, self.cores + 1).astype(np.int64)
+        parts = [(int(cuts[i]), int(cuts[i + 1])) for i in range(self.cores) if cuts[i + 1] > cuts[i]]
+        t0 = time.perf_counter()
+        list(self.pool.map(lambda r: _oracle_call(kind, a, r[0], r[1]), parts))
+        return n / max(time.perf_counter() - t0, 1e-9)
+
+    def baseline(self, wl_obj, budget_s, reps=3):
+        """cpu_baseline: all host cores (median of reps) on a sample of about
+        budget_s seconds of single-thread work, plus the single-thread rate."""
+        kind, a, n, desc = wl_obj.cpu_spec(budget_s)
+        one = oracle_rate_1thread(kind, a, n)
+        par = statistics.median([self.parallel(kind, a, n) for _ in range(reps)])
+        return {"value": par / 1e9, "unit": UNIT, "cores": self.cores, "kind": "oracle",
+                "sample": "%s, split over %d threads" % (desc, self.cores),
+                "single_thread": {"value": one / 1e9, "cores": 1}}
+
+    def close(self):
+        self.pool.shutdown()
+
+
+# ---------------------------------------------------------------------------
 # Workloads
 # ---------------------------------------------------------------------------
 class Workload:
@@ -187,19 +253,13 @@ class Interp2D(Workload):
     def e2e_step(self):
         self.ss.search_interp_2d_host(self.hR, self.hT, self.hF, self.hY, idx=self.hI, val=self.hV)
 
-    def cpu_sample(self, budget_s):
-        import oracle
-        R, T, F = self.R.cpu().numpy(), self.T.cpu().numpy(), self.F.cpu().numpy()
-        probe = self.Y2[: 1 << 18].cpu().numpy()
-        t0 = time.perf_counter()
-        oracle.search_interp_2d(R, T, F, probe)
-        rate = probe.shape[0] / (time.perf_counter() - t0)
+    def cpu_spec(self, budget_s):
+        a = {"R": self.R.cpu().numpy(), "T": self.T.cpu().numpy(), "F": self.F.cpu().numpy(),
+             "Y2": self.Y2[: 1 << 18].cpu().numpy()}
+        rate = oracle_rate_1thread("2d", a, 1 << 18)
         ns = int(min(self.m, max(1 << 18, rate * budget_s)))
-        Y = self.Y2[:ns].cpu().numpy()
-        t0 = time.perf_counter()
-        oracle.search_interp_2d(R, T, F, Y)
-        dt = time.perf_counter() - t0
-        return ns / dt, "first %d of the %d pairs (same tables), single thread" % (ns, self.m)
+        a["Y2"] = self.Y2[:ns].cpu().numpy()
+        return "2d", a, ns, "first %d of the %d pairs (same tables)" % (ns, self.m)
 
 
 class Plain1D(Workload):
@@ -243,19 +303,12 @@ class Plain1D(Workload):
     def e2e_step(self):
         self.ss.search_1d_host(self.hX, self.hY, out=self.hO, algo=self.algo)
 
-    def cpu_sample(self, budget_s):
-        import oracle
-        X = self.X.cpu().numpy()
-        probe = self.Y[: 1 << 20].cpu().numpy()
-        t0 = time.perf_counter()
-        oracle.search_1d(X, probe)
-        rate = probe.shape[0] / (time.perf_counter() - t0)
+    def cpu_spec(self, budget_s):
+        a = {"X": self.X.cpu().numpy(), "Y": self.Y[: 1 << 20].cpu().numpy()}
+        rate = oracle_rate_1thread("1d", a, 1 << 20)
         ns = int(min(self.m, max(1 << 20, rate * budget_s)))
-        Y = self.Y[:ns].cpu().numpy()
-        t0 = time.perf_counter()
-        oracle.search_1d(X, Y)
-        dt = time.perf_counter() - t0
-        return ns / dt, "first %d of the %d targets (same table), single thread" % (ns, self.m)
+        a["Y"] = self.Y[:ns].cpu().numpy()
+        return "1d", a, ns, "first %d of the %d targets (same table)" % (ns, self.m)
 
 
 class PlanWorkload(Workload):
@@ -339,26 +392,15 @@ class PlanWorkload(Workload):
         self.step()
         self.hO.copy_(self.out, non_blocking=True)
 
-    def cpu_sample(self, budget_s):
-        import oracle
+    def cpu_spec(self, budget_s):
         X_off, Y_off = self.b.X_off.cpu().numpy(), self.b.Y_off.cpu().numpy()
-        X = self.b.X.cpu().numpy()
-        # first tables of the batch, up to a target budget scaled from a probe
-        probe_n = 1 << 20
-        j = int(np.searchsorted(Y_off, probe_n, side="right"))
-        j = max(1, min(j, len(Y_off) - 1))
-        Yp = self.Y[: Y_off[j]].cpu().numpy()
-        t0 = time.perf_counter()
-        oracle.search_1d_batched(X_off[: j + 1], X, Y_off[: j + 1], Yp)
-        rate = Y_off[j] / max(time.perf_counter() - t0, 1e-9)
-        want = rate * budget_s
-        j = int(np.searchsorted(Y_off, want, side="right"))
-        j = max(1, min(j, len(Y_off) - 1))
-        Ys = self.Y[: Y_off[j]].cpu().numpy()
-        t0 = time.perf_counter()
-        oracle.search_1d_batched(X_off[: j + 1], X, Y_off[: j + 1], Ys)
-        dt = time.perf_counter() - t0
-        return Y_off[j] / dt, "first %d tables (%d targets) of the batch, single thread" % (j, Y_off[j])
+        probe = int(min(Y_off[-1], 1 << 20))
+        a = {"X_off": X_off, "X": self.b.X.cpu().numpy(), "Y_off": Y_off, "Y": self.Y[:probe].cpu().numpy()}
+        rate = oracle_rate_1thread("1d_batched", a, probe)
+        ns = int(min(Y_off[-1], max(probe, rate * budget_s)))
+        a["Y"] = self.Y[:ns].cpu().numpy()
+        ntab = int(np.searchsorted(Y_off, ns, side="left"))
+        return "1d_batched", a, ns, "first %d targets (first %d tables) of the batch" % (ns, ntab)
 
 
 class Batched1D(PlanWorkload):
@@ -492,20 +534,19 @@ class Batched2D(PlanWorkload):
         self.hI.copy_(self.idx, non_blocking=True)
         self.hV.copy_(self.val, non_blocking=True)
 
-    def cpu_sample(self, budget_s):
-        import oracle
+    def cpu_spec(self, budget_s):
         b = self.b
-        offs = [o.cpu().numpy() for o in (b.R_off, b.T_off, b.F_off, b.Y_off)]
-        R, T, F = b.R.cpu().numpy(), b.T.cpu().numpy(), b.F.cpu().numpy()
-        per = int(offs[3][1] - offs[3][0])
-        ntab = max(1, min(len(offs[3]) - 1, int(budget_s * 9e6 / max(per, 1))))
-        j = ntab
-        Y = self.Y[: offs[3][j]].cpu().numpy()
-        t0 = time.perf_counter()
-        oracle.search_interp_2d_batched(offs[0][: j + 1], R, offs[1][: j + 1], T, offs[2][: j + 1], F,
-                                        offs[3][: j + 1], Y)
-        dt = time.perf_counter() - t0
-        return offs[3][j] / dt, "first %d tables (%d pairs) of the batch, single thread" % (j, offs[3][j])
+        a = {"R_off": b.R_off.cpu().numpy(), "R": b.R.cpu().numpy(), "T_off": b.T_off.cpu().numpy(),
+             "T": b.T.cpu().numpy(), "F_off": b.F_off.cpu().numpy(), "F": b.F.cpu().numpy(),
+             "Y_off": b.Y_off.cpu().numpy()}
+        total = int(a["Y_off"][-1])
+        probe = int(min(total, 1 << 18))
+        a["Y2"] = self.Y[:probe].cpu().numpy()
+        rate = oracle_rate_1thread("2d_batched", a, probe)
+        ns = int(min(total, max(probe, rate * budget_s)))
+        a["Y2"] = self.Y[:ns].cpu().numpy()
+        ntab = int(np.searchsorted(a["Y_off"], ns, side="left"))
+        return "2d_batched", a, ns, "first %d pairs (first %d tables) of the batch" % (ns, ntab)
 
 
 WORKLOADS = {
@@ -557,17 +598,17 @@ def run_reference(args, wl_obj):
     else:
         wl_obj.m = min(wl_obj.m, 1 << 23)
         wl_obj.setup("cpu", 0)
-    times = []
-    for s in range(args.warmup + args.steps):
-        rate, sample = wl_obj.cpu_sample(budget_s=2.0)
-        times.append(rate)
-    rates = times[args.warmup:]
+    timer = OracleTimer()
+    kind, a, n, desc = wl_obj.cpu_spec(budget_s=4.0)
+    rates = [timer.parallel(kind, a, n) for _ in range(args.warmup + args.steps)][args.warmup:]
+    timer.close()
     value = statistics.median(rates) / 1e9
+    sample = "%s, split over %d threads" % (desc, timer.cores)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": n / (value * 1e9) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl_obj.name},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": timer.cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -695,8 +736,9 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, sample = wl_obj.cpu_sample(args.cpu_budget)
-        cpu = {"value": rate / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        timer = OracleTimer()
+        cpu = timer.baseline(wl_obj, args.cpu_budget)
+        timer.close()
 
     extra = {}
     if isinstance(wl_obj, PlanWorkload):

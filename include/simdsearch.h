@@ -158,7 +158,7 @@ typedef struct ss_plan_opts {
   int32_t tile;             /* targets per tile; 0: library default or tuned */
   int32_t mlp_epochs;       /* full-batch Adam steps of the MLP (default 400; 0 keeps the untrained initialisation) */
   float mlp_lr;             /* peak Adam learning rate, cosine-decayed (default 2e-3) */
-  int32_t dir_cap;          /* bucket-directory budget per table (0: 16 n clamped to [64, 8192]) */
+  int32_t dir_cap;          /* bucket-directory budget per table (0: 4 n clamped to [64, 4096]; 8192 above 8128 entries) */
   uint64_t seed;            /* seed of the counter-based sampler of training and probe targets */
   const char* tune_cache;   /* JSON file the autotuner reads and writes (NULL: none) */
 } ss_plan_opts;
@@ -218,6 +218,32 @@ ss_status ss_plan_save(const ss_plan* plan, const char* path);
 ss_status ss_plan_load(ss_plan** plan, const char* path, cudaStream_t stream);
 
 void ss_plan_destroy(ss_plan* plan);
+
+/* One-shot batched forms: the search of Sec. 1 (and the 2D lookup of
+ * Sec. 2.2) over many tables in one call, with the same results as a plan
+ * without a model.  Table k is X[X_off[k] .. X_off[k+1]) with targets
+ * Y[Y_off[k] .. Y_off[k+1]); X_off and Y_off are host arrays of ntables+1
+ * entries (Y_off non-decreasing, empty tables allowed), X, Y and lowbounds
+ * device arrays; table k's answers go to the same positions of lowbounds.
+ * The call prepares the tables, runs the batch as one persistent launch on
+ * `stream`, waits for it and releases the device memory it allocated, so the
+ * results are written when it returns.  SS_ENOTSORTED if a table is not
+ * strictly increasing (nothing is written then).  Callers that search the
+ * same tables again should keep a plan: its preparation is paid once. */
+ss_status ss_search_1d_batched(int32_t ntables, const int64_t* X_off, const double* X,
+                               const int64_t* Y_off, const double* Y, int32_t* lowbounds,
+                               int32_t side, ss_devstat* stat, cudaStream_t stream);
+
+/* 2D: table k has axes R[R_off[k] ..], T[T_off[k] ..] and the row-major
+ * nr_k x nt_k grid F[F_off[k] ..]; its pairs are Y2[2 Y_off[k] ..
+ * 2 Y_off[k+1]) interleaved (rho, T); lowbounds2 receives interleaved index
+ * pairs and values one double per pair.  Offsets are host arrays, the rest
+ * device arrays; synchronous like the 1D form. */
+ss_status ss_search_interp_2d_batched(int32_t ntables, const int64_t* R_off, const double* R,
+                                      const int64_t* T_off, const double* T, const int64_t* F_off,
+                                      const double* F, const int64_t* Y_off, const double* Y2,
+                                      int32_t* lowbounds2, double* values, ss_devstat* stat,
+                                      cudaStream_t stream);
 
 /* ---------------------------------------------------------------------- */
 /* Batched search without device allocation                                */

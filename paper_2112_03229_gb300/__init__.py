@@ -320,6 +320,51 @@ class Plan:
             pass
 
 
+def _batched_lib():
+    L = lib()
+    if not hasattr(L, "_batched_sig"):
+        P64 = C.POINTER(C.c_int64)
+        L.ss_search_1d_batched.argtypes = [_i32, P64, _vp, P64, _vp, _vp, _i32, _vp, _vp]
+        L.ss_search_interp_2d_batched.argtypes = [_i32, P64, _vp, P64, _vp, P64, _vp, P64, _vp, _vp, _vp, _vp, _vp]
+        L.ss_search_1d_batched.restype = _i32
+        L.ss_search_interp_2d_batched.restype = _i32
+        L._batched_sig = True
+    return L
+
+
+def search_1d_batched(X_off, X, Y_off, Y, out=None, side=SIDE_LT, stat=None, stream=None):
+    """ss_search_1d_batched: one call over many tables (table k = X[X_off[k]:X_off[k+1]],
+    its targets Y[Y_off[k]:Y_off[k+1]]); synchronous."""
+    L = _batched_lib()
+    xo, xp = _offsets(X_off)
+    yo, yp = _offsets(Y_off)
+    if out is None:
+        out = torch.empty(Y.shape, dtype=torch.int32, device=Y.device)
+    _check(L.ss_search_1d_batched(len(xo) - 1, xp, _dev(X, torch.float64, "X"), yp, _dev(Y, torch.float64, "Y"),
+                                  _dev(out, torch.int32, "out"), side, _statp(stat), _stream(stream)))
+    return out
+
+
+def search_interp_2d_batched(R_off, R, T_off, T, F_off, F, Y_off, Y2, idx=None, val=None, stat=None, stream=None):
+    """ss_search_interp_2d_batched: the 2D lookup over many tables in one call; synchronous.
+    Returns (idx [m, 2] int32, val [m] float64)."""
+    L = _batched_lib()
+    ro, rp = _offsets(R_off)
+    to, tp = _offsets(T_off)
+    fo, fp = _offsets(F_off)
+    yo, yp = _offsets(Y_off)
+    m = Y2.numel() // 2
+    if idx is None:
+        idx = torch.empty((m, 2), dtype=torch.int32, device=Y2.device)
+    if val is None:
+        val = torch.empty((m,), dtype=torch.float64, device=Y2.device)
+    _check(L.ss_search_interp_2d_batched(len(ro) - 1, rp, _dev(R, torch.float64, "R"), tp, _dev(T, torch.float64, "T"),
+                                         fp, _dev(F, torch.float64, "F"), yp, _dev(Y2, torch.float64, "Y2"),
+                                         _dev(idx, torch.int32, "idx"), _dev(val, torch.float64, "val"),
+                                         _statp(stat), _stream(stream)))
+    return idx, val
+
+
 def search_1d_batched_static(X_off, X, Y_off, Y, out=None, side=SIDE_LT, stat=None, stream=None):
     """ss_search_1d_batched_static: batched bucket search that allocates no
     device memory (its working set lives in a fixed 8 MiB array of the library)."""

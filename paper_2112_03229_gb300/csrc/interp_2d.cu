@@ -114,6 +114,7 @@ template <int MODE>
 __device__ __forceinline__ int axis_search(const AxisView& a, uint64_t k) {
   if (MODE == 0) return search_bucket<1>(a.keys, a.dir, a.shift, a.base, a.nb, k);
   if (MODE == 1) return search_bucket_bisect(a.keys, a.dir, a.shift, a.base, a.nb, a.T, k);
+  if (MODE == 3) return search_bucket<2>(a.keys, a.dir, a.shift, a.base, a.nb, k);
   return search_eyt_rt(a.eyt, a.D, k);
 }
 
@@ -138,7 +139,8 @@ __device__ __forceinline__ double blend64w(double wr, double wrb, double wt, dou
 }
 
 // One pair: indices and value.  MODE 0: both axes bucket with occupancy <= 1;
-// 1: bucket with bounded bisection; 2: breadth-first binary.  FF: arithmetic
+// 3: occupancy <= 2 (a branch-free two-key scan); 1: bucket with bounded
+// bisection; 2: breadth-first binary.  FF: arithmetic
 // path.  SG: the value grid is staged in shared memory as float-float (a NaN
 // high part marks a value the split does not cover; that pair is finished in
 // fp64 from the caller's grid).
@@ -243,14 +245,15 @@ __device__ __forceinline__ void interp_body(const Args2D& a, unsigned char* smem
   const TableHdr& ht = *reinterpret_cast<const TableHdr*>(smem + a.at.lay.hdr);
   const bool ff = !a.force_fp64 && reinterpret_cast<const AxisAux*>(smem + a.ar.aux)->ffok &&
                   reinterpret_cast<const AxisAux*>(smem + a.at.aux)->ffok;
-  const int mode = a.algo == SS_ALGO_BINARY ? 2 : (hr.occ <= 1 && ht.occ <= 1) ? 0 : 1;
+  const int mode = a.algo == SS_ALGO_BINARY ? 2 : (hr.occ <= 1 && ht.occ <= 1) ? 0 : (hr.occ <= 2 && ht.occ <= 2) ? 3 : 1;
   int nans;
   if (ff) {
     nans = mode == 0 ? stream_pairs<0, true, SG>(a, vr, vt, Gs)
+         : mode == 3 ? stream_pairs<3, true, SG>(a, vr, vt, Gs)
          : mode == 1 ? stream_pairs<1, true, SG>(a, vr, vt, Gs) : stream_pairs<2, true, SG>(a, vr, vt, Gs);
   } else {
     nans = mode == 0 ? stream_pairs<0, false, false>(a, vr, vt, Gs)
-         : mode == 1 ? stream_pairs<1, false, false>(a, vr, vt, Gs) : stream_pairs<2, false, false>(a, vr, vt, Gs);
+         : mode == 2 ? stream_pairs<2, false, false>(a, vr, vt, Gs) : stream_pairs<1, false, false>(a, vr, vt, Gs);
   }
   nans = __reduce_add_sync(0xFFFFFFFFu, nans);
   if (a.stat != nullptr) {

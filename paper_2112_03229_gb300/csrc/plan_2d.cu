@@ -83,14 +83,19 @@ __device__ __forceinline__ Weights axis_weights(const StagedView& v, int i, int 
   return r;
 }
 
+constexpr uint64_t kKeyNegInf = 0x0010000000000000ull;   // image of -inf; NaNs map below it
+
+// One pair: the two axis counts (CR, CT: the searches the tile dispatched),
+// four gathers from the grid, and the blend.
+template <class CR, class CT>
 __device__ __forceinline__ void pair_2d(const StagedView& vr, const StagedView& vt, const float2* __restrict__ G,
                                         const double* __restrict__ G64, double rho, double tem, int& ir, int& it,
-                                        double& v, int& nans, int& fallbacks) {
+                                        double& v, int& nans, CR&& count_r, CT&& count_t) {
   const uint64_t kr = order_key(rho), kt = order_key(tem);
-  const bool nan = (kr < 0x0010000000000000ull) | (kt < 0x0010000000000000ull);
-  nans += (kr < 0x0010000000000000ull) + (kt < 0x0010000000000000ull);
-  ir = axis_count(vr, rho, kr, fallbacks);
-  it = axis_count(vt, tem, kt, fallbacks);
+  const bool nan = (kr < kKeyNegInf) | (kt < kKeyNegInf);
+  nans += (kr < kKeyNegInf) + (kt < kKeyNegInf);
+  ir = count_r(rho, kr);
+  it = count_t(tem, kt);
   const int nt = vt.h.n;
   const int cr = min(ir, vr.h.n - 2), ct = min(it, nt - 2);
   const int64_t o = (int64_t)cr * nt + ct;
@@ -109,6 +114,40 @@ __device__ __forceinline__ void pair_2d(const StagedView& vr, const StagedView& 
     const double hi = w2b * G64[o + nt] + w2 * G64[o + nt + 1];
     v = w1b * lo + w1 * hi;
   }
+}
+
+// Streams one tile's pairs: scalar head to an even pair, two pairs per
+// thread with 128-bit loads and stores, scalar tail.
+template <class CR, class CT>
+__device__ __forceinline__ void stream_pairs(const BatchArgs2D& a, const StagedView& vr, const StagedView& vt,
+                                             const float2* __restrict__ G, const double* __restrict__ G64,
+                                             const Tile& tile, int& nans, CR&& count_r, CT&& count_t) {
+  const int64_t b = tile.begin;
+  const int cnt = tile.count;
+  auto scalar = [&](int i) {
+    int ir, it;
+    double v;
+    pair_2d(vr, vt, G, G64, a.Y2[2 * (b + i)], a.Y2[2 * (b + i) + 1], ir, it, v, nans, count_r, count_t);
+    a.idx[2 * (b + i)] = ir;
+    a.idx[2 * (b + i) + 1] = it;
+    a.val[b + i] = v;
+  };
+  const int head = a.vec ? min(cnt, (int)(b & 1)) : cnt;
+  const int np2 = (cnt - head) >> 1;
+  for (int i = threadIdx.x; i < head; i += blockDim.x) scalar(i);
+  const double2* Y = reinterpret_cast<const double2*>(a.Y2) + b + head;
+  int4* I4 = reinterpret_cast<int4*>(a.idx + 2 * (b + head));
+  double2* V2 = reinterpret_cast<double2*>(a.val + b + head);
+  for (int g = threadIdx.x; g < np2; g += blockDim.x) {
+    const double2 p0 = ld_stream(Y + 2 * g), p1 = ld_stream(Y + 2 * g + 1);
+    int i0, j0, i1, j1;
+    double v0, v1;
+    pair_2d(vr, vt, G, G64, p0.x, p0.y, i0, j0, v0, nans, count_r, count_t);
+    pair_2d(vr, vt, G, G64, p1.x, p1.y, i1, j1, v1, nans, count_r, count_t);
+    st_stream(I4 + g, make_int4(i0, j0, i1, j1));
+    st_stream(V2 + g, make_double2(v0, v1));
+  }
+  for (int i = head + 2 * np2 + threadIdx.x; i < cnt; i += blockDim.x) scalar(i);
 }
 
 __global__ void __launch_bounds__(kNumThreads) k_batched_2d(BatchArgs2D a) {
@@ -150,32 +189,26 @@ __global__ void __launch_bounds__(kNumThreads) k_batched_2d(BatchArgs2D a) {
     }
     const float2* G = a.grid + a.grid_off[tile.table];
     const double* G64 = a.grid64 != nullptr ? a.grid64 + a.grid_off[tile.table] : nullptr;
-    const int64_t b = tile.begin;
-    const int cnt = tile.count;
-    auto scalar = [&](int i) {
-      int ir, it;
-      double v;
-      pair_2d(vr, vt, G, G64, a.Y2[2 * (b + i)], a.Y2[2 * (b + i) + 1], ir, it, v, nans, fallbacks);
-      a.idx[2 * (b + i)] = ir;
-      a.idx[2 * (b + i) + 1] = it;
-      a.val[b + i] = v;
+    // one uniform branch per tile: both axes plain bucket searches over whole
+    // staged tables with at most two keys per bucket (the common case) take a
+    // branch-free two-key scan; every other combination the generic dispatch
+    auto generic = [&](const StagedView& v) {
+      return [&v, &fallbacks](double t, uint64_t q) { return axis_count(v, t, q, fallbacks); };
     };
-    const int head = a.vec ? min(cnt, (int)(b & 1)) : cnt;
-    const int np2 = (cnt - head) >> 1;
-    for (int i = threadIdx.x; i < head; i += blockDim.x) scalar(i);
-    const double2* Y = reinterpret_cast<const double2*>(a.Y2) + b + head;
-    int4* I4 = reinterpret_cast<int4*>(a.idx + 2 * (b + head));
-    double2* V2 = reinterpret_cast<double2*>(a.val + b + head);
-    for (int g = threadIdx.x; g < np2; g += blockDim.x) {
-      const double2 p0 = ld_stream(Y + 2 * g), p1 = ld_stream(Y + 2 * g + 1);
-      int i0, j0, i1, j1;
-      double v0, v1;
-      pair_2d(vr, vt, G, G64, p0.x, p0.y, i0, j0, v0, nans, fallbacks);
-      pair_2d(vr, vt, G, G64, p1.x, p1.y, i1, j1, v1, nans, fallbacks);
-      st_stream(I4 + g, make_int4(i0, j0, i1, j1));
-      st_stream(V2 + g, make_double2(v0, v1));
-    }
-    for (int i = head + 2 * np2 + threadIdx.x; i < cnt; i += blockDim.x) scalar(i);
+    auto scan2 = [](const StagedView& v) {
+      const uint64_t* keys = v.keys;
+      const int* dir = v.dir;
+      const int shift = v.h.shift, nb = v.h.nb;
+      const uint64_t base = v.h.base;
+      return [=](double, uint64_t q) { return search_bucket<2>(keys, dir, shift, base, nb, q); };
+    };
+    auto fast = [](const StagedView& v) {
+      return v.h.algo == BL_BUCKET && v.h.stride == 1 && v.h.occ <= 2;
+    };
+    if (fast(vr) && fast(vt))
+      stream_pairs(a, vr, vt, G, G64, tile, nans, scan2(vr), scan2(vt));
+    else
+      stream_pairs(a, vr, vt, G, G64, tile, nans, generic(vr), generic(vt));
   }
   nans = __reduce_add_sync(0xFFFFFFFFu, nans);
   fallbacks = __reduce_add_sync(0xFFFFFFFFu, fallbacks);

@@ -249,3 +249,46 @@ def test_plan_2d_save_load_and_autotune(ss, tmp_path):
         p.execute()
         np.testing.assert_array_equal(idx.cpu().numpy(), wi)
         assert (np.abs(val.cpu().numpy() - wv) / np.abs(wv)).max() <= REL_TOL
+
+
+@pytest.mark.parametrize("side", [0, 1])
+def test_oneshot_batched_1d(ss, side):
+    # the one-call batched form: same answers as the oracle on ragged
+    # per-table counts, and with target and output arrays off 16-byte alignment
+    b = small_batch(seed=11, ntables=40, scale=0.002)
+    want = oracle.search_1d_batched(b.X_off.numpy(), b.X.numpy(), b.Y_off.numpy(), b.Y.numpy(), side)
+    got = ss.search_1d_batched(b.X_off, b.X.to(DEV), b.Y_off, b.Y.to(DEV), side=side)
+    np.testing.assert_array_equal(got.cpu().numpy(), want)
+    # misaligned: drop the first target and shift every table's range by one
+    Yd = torch.empty(b.Y.numel() + 1, dtype=torch.float64, device=DEV)
+    Yd[1:] = b.Y.to(DEV)
+    out = torch.full((b.Y.numel() + 1,), -1, dtype=torch.int32, device=DEV)
+    stat = ss.new_stat()
+    ss.search_1d_batched(b.X_off, b.X.to(DEV), b.Y_off, Yd[1:], out=out[1:], side=side, stat=stat)
+    np.testing.assert_array_equal(out[1:].cpu().numpy(), want)
+    assert int(out[0]) == -1
+    assert ss.read_stat(stat).flags == 0
+
+
+def test_oneshot_batched_1d_empty_tables_and_unsorted(ss):
+    X = torch.tensor([1.0, 2.0, 3.0, 10.0, 20.0, 30.0, 40.0], dtype=torch.float64)
+    Y = torch.tensor([0.5, 2.5, 25.0, 45.0], dtype=torch.float64)
+    got = ss.search_1d_batched([0, 3, 7], X.to(DEV), [0, 0, 4], Y.to(DEV))   # table 0 has no targets
+    want = oracle.search_1d_batched(np.array([0, 3, 7]), X.numpy(), np.array([0, 0, 4]), Y.numpy())
+    np.testing.assert_array_equal(got.cpu().numpy(), want)
+    bad = torch.tensor([1.0, 2.0, 2.0, 3.0, 1.0, 5.0, 7.0], dtype=torch.float64, device=DEV)
+    with pytest.raises(ss.SSError) as e:
+        ss.search_1d_batched([0, 4, 7], bad, [0, 2, 4], Y.to(DEV))
+    assert e.value.code == 2
+
+
+def test_oneshot_batched_2d(ss):
+    b = wl.batched_2d(ntables=9, pairs_per_table=3001, seed=12)
+    wi, wv = oracle.search_interp_2d_batched(b.R_off.numpy(), b.R.numpy(), b.T_off.numpy(), b.T.numpy(),
+                                             b.F_off.numpy(), b.F.numpy(), b.Y_off.numpy(), b.Y2.numpy())
+    stat = ss.new_stat()
+    idx, val = ss.search_interp_2d_batched(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV),
+                                           b.Y_off, b.Y2.to(DEV), stat=stat)
+    np.testing.assert_array_equal(idx.cpu().numpy(), wi)
+    assert (np.abs(val.cpu().numpy() - wv) / np.abs(wv)).max() <= REL_TOL
+    assert ss.read_stat(stat).flags == 0
