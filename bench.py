@@ -219,7 +219,7 @@ class Workload:
 class Interp2D(Workload):
     """Fused 2D search + bilinear: 200 x 100 axes, 64M (rho, T) pairs (one table)."""
     name = "interp2d-200x100-64M"
-    kernel = "k_search_interp_2d"
+    kernel = "k_search_interp_2d_sg"     # the grid fits shared memory: the staged-grid variant runs
     bytes_per_target = 16 + 8 + 8      # pair in, index pair out, value out
 
     def __init__(self, m=64 << 20):

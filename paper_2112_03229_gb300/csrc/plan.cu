@@ -59,6 +59,7 @@ PlanBase::~PlanBase() {
   free_dev(d_grid);
   free_dev(d_grid64);
   free_dev(d_grid_off);
+  free_dev(d_cell_off);
   if (cap_stream) cudaStreamDestroy(cap_stream);
 }
 

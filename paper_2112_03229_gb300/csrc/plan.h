@@ -79,9 +79,10 @@ struct BatchArgs1D {
 struct BatchArgs2D {
   const unsigned char* blobs;
   const int64_t* blob_off;      // [2*ntables]: rho axis, T axis
-  const float2* grid;           // float-float values of all tables
-  const double* grid64;         // the caller's fp64 values (fallback)
-  const int64_t* grid_off;      // [ntables]
+  const float4* cells;          // per cell of every table: two float4 = four float-float corners
+  const double* grid64;         // the caller's fp64 values, row-major (fallback)
+  const int64_t* grid_off;      // [ntables] value offsets of grid64
+  const int64_t* cell_off;      // [ntables] cell offsets of cells (in cells)
   const Tile* tiles;
   int ntiles;
   int* counter;

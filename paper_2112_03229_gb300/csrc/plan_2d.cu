@@ -33,19 +33,37 @@ __global__ void __launch_bounds__(256) k_prep_cells(PrepArgs a) {
   if (threadIdx.x == 0) h->ffok = ok ? 1 : 0;
 }
 
-// Value grid to float-float; values the split does not cover (zero,
-// negative, or outside [2^-70, 2^101)) are marked with a NaN high part and set
-// *bad so the plan keeps an fp64 copy for them.
-__global__ void k_grid_to_ff(const double* __restrict__ F, float2* __restrict__ G, int64_t count, unsigned* bad) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+// Value grids to per-cell corner records: cell (i, j) of a table holds
+// F[i][j], F[i][j+1], F[i+1][j], F[i+1][j+1] as float-float in 32 bytes, so
+// the four gathers of a lookup are two 16-byte loads from one 32-byte sector.
+// Values the split does not cover (zero, negative, or outside
+// [2^-70, 2^101)) get a NaN high part and set *bad, so the plan keeps the
+// caller's fp64 grid for them.  One block per table.
+__global__ void __launch_bounds__(256) k_grid_cells(const double* __restrict__ F, const int64_t* __restrict__ F_off,
+                                                    const int64_t* __restrict__ R_off,
+                                                    const int64_t* __restrict__ T_off,
+                                                    const int64_t* __restrict__ cell_off, float4* __restrict__ cells,
+                                                    unsigned* bad) {
+  const int k = blockIdx.x;
+  const int nr = (int)(R_off[k + 1] - R_off[k]), nt = (int)(T_off[k + 1] - T_off[k]);
+  const double* f = F + F_off[k];
+  float4* out = cells + 2 * cell_off[k];
+  const int64_t ncell = (int64_t)(nr - 1) * (nt - 1);
+  bool ok = true;
+  auto split = [&ok](double v) {
     ff r;
-    if (d2ff(F[i], r)) {
-      G[i] = make_float2(r.hi, r.lo);
-    } else {
-      G[i] = make_float2(__int_as_float(0x7FC00000), 0.0f);
-      atomicOr(bad, 1u);
-    }
+    if (d2ff(v, r)) return r;
+    ok = false;
+    return ff{__int_as_float(0x7FC00000), 0.0f};
+  };
+  for (int64_t c = threadIdx.x; c < ncell; c += blockDim.x) {
+    const int64_t i = c / (nt - 1), j = c - i * (nt - 1);
+    const double* q = f + i * nt + j;
+    const ff a00 = split(q[0]), a01 = split(q[1]), a10 = split(q[nt]), a11 = split(q[nt + 1]);
+    out[2 * c] = make_float4(a00.hi, a00.lo, a01.hi, a01.lo);
+    out[2 * c + 1] = make_float4(a10.hi, a10.lo, a11.hi, a11.lo);
   }
+  if (!ok) atomicOr(bad, 1u);
 }
 
 // Exact count for one axis with the axis' algorithm.
@@ -88,7 +106,7 @@ constexpr uint64_t kKeyNegInf = 0x0010000000000000ull;   // image of -inf; NaNs 
 // One pair: the two axis counts (CR, CT: the searches the tile dispatched),
 // four gathers from the grid, and the blend.
 template <class CR, class CT>
-__device__ __forceinline__ void pair_2d(const StagedView& vr, const StagedView& vt, const float2* __restrict__ G,
+__device__ __forceinline__ void pair_2d(const StagedView& vr, const StagedView& vt, const float4* __restrict__ G,
                                         const double* __restrict__ G64, double rho, double tem, int& ir, int& it,
                                         double& v, int& nans, CR&& count_r, CT&& count_t) {
   const uint64_t kr = order_key(rho), kt = order_key(tem);
@@ -98,8 +116,10 @@ __device__ __forceinline__ void pair_2d(const StagedView& vr, const StagedView& 
   it = count_t(tem, kt);
   const int nt = vt.h.n;
   const int cr = min(ir, vr.h.n - 2), ct = min(it, nt - 2);
-  const int64_t o = (int64_t)cr * nt + ct;
-  const float2 g00 = __ldg(G + o), g01 = __ldg(G + o + 1), g10 = __ldg(G + o + nt), g11 = __ldg(G + o + nt + 1);
+  const int64_t cell = (int64_t)cr * (nt - 1) + ct;
+  const float4 q0 = __ldg(G + 2 * cell), q1 = __ldg(G + 2 * cell + 1);
+  const float2 g00 = make_float2(q0.x, q0.y), g01 = make_float2(q0.z, q0.w);
+  const float2 g10 = make_float2(q1.x, q1.y), g11 = make_float2(q1.z, q1.w);
   const Weights wr = axis_weights(vr, ir, cr, kr, rho);
   const Weights wt = axis_weights(vt, it, ct, kt, tem);
   if (nan) {
@@ -109,6 +129,7 @@ __device__ __forceinline__ void pair_2d(const StagedView& vr, const StagedView& 
     const ff hi = ff_add_u(ff_mul_u(wt.wbar, ff{g10.x, g10.y}), ff_mul_u(wt.w, ff{g11.x, g11.y}));
     v = ff2d(ff_add_u(ff_mul_u(wr.wbar, lo), ff_mul_u(wr.w, hi)));
   } else {
+    const int64_t o = (int64_t)cr * nt + ct;
     const double w1 = ff2d(wr.w), w1b = ff2d(wr.wbar), w2 = ff2d(wt.w), w2b = ff2d(wt.wbar);
     const double lo = w2b * G64[o] + w2 * G64[o + 1];
     const double hi = w2b * G64[o + nt] + w2 * G64[o + nt + 1];
@@ -120,7 +141,7 @@ __device__ __forceinline__ void pair_2d(const StagedView& vr, const StagedView& 
 // thread with 128-bit loads and stores, scalar tail.
 template <class CR, class CT>
 __device__ __forceinline__ void stream_pairs(const BatchArgs2D& a, const StagedView& vr, const StagedView& vt,
-                                             const float2* __restrict__ G, const double* __restrict__ G64,
+                                             const float4* __restrict__ G, const double* __restrict__ G64,
                                              const Tile& tile, int& nans, CR&& count_r, CT&& count_t) {
   const int64_t b = tile.begin;
   const int cnt = tile.count;
@@ -187,7 +208,7 @@ __global__ void __launch_bounds__(kNumThreads) k_batched_2d(BatchArgs2D a) {
       cur = tile.table;
       if (!ok) break;
     }
-    const float2* G = a.grid + a.grid_off[tile.table];
+    const float4* G = a.cells + 2 * a.cell_off[tile.table];
     const double* G64 = a.grid64 != nullptr ? a.grid64 + a.grid_off[tile.table] : nullptr;
     // one uniform branch per tile: both axes plain bucket searches over whole
     // staged tables with at most two keys per bucket (the common case) take a
@@ -219,6 +240,12 @@ __global__ void __launch_bounds__(kNumThreads) k_batched_2d(BatchArgs2D a) {
   if (a.stat != nullptr && threadIdx.x == 0 && !ok) atomicOr(&a.stat->flags, SS_FLAG_STAGING_TIMEOUT);
 }
 
+void plan_cell_offsets(PlanBase* p) {
+  p->cell_off.assign(p->ntables + 1, 0);
+  for (int k = 0; k < p->ntables; ++k)
+    p->cell_off[k + 1] = p->cell_off[k] + (int64_t)(p->sizes[k] - 1) * (p->sizes_t[k] - 1);
+}
+
 ss_status plan_build_2d(ss_plan* p, const double* R, const double* T, const double* F, cudaStream_t stream) {
   const int nt = p->ntables;
   const ss_plan_opts& o = p->opts;
@@ -243,6 +270,8 @@ ss_status plan_build_2d(ss_plan* p, const double* R, const double* T, const doub
   }
   for (int k = 0; k < nt; ++k) p->bucket_tables[size_bucket(std::max(p->sizes[k], p->sizes_t[k]))]++;
   const int64_t gcount = p->grid_off[nt];
+  plan_cell_offsets(p);
+  const int64_t ncells = p->cell_off[nt];
   std::vector<int64_t> offR(nt), offT(nt), axR(nt + 1), axT(nt + 1);
   for (int k = 0; k < nt; ++k) { offR[k] = p->blob_off[2 * k]; offT[k] = p->blob_off[2 * k + 1]; }
   for (int k = 0; k <= nt; ++k) { axR[k] = p->X_off[k]; axT[k] = p->X_off[nt + 1 + k]; }
@@ -261,15 +290,17 @@ ss_status plan_build_2d(ss_plan* p, const double* R, const double* T, const doub
   };
   auto cleanup = [&]() { for (void* d : temps) cudaFree(d); };
   if (cudaMalloc(&p->d_blobs, p->blob_bytes) != cudaSuccess ||
-      cudaMalloc(&p->d_grid, std::max<int64_t>(gcount, 1) * sizeof(float2)) != cudaSuccess) {
+      cudaMalloc(&p->d_grid, std::max<int64_t>(ncells, 1) * 4 * sizeof(float2)) != cudaSuccess) {
     return fail(SS_ENOMEM, "plan: device allocation failed");
   }
-  p->device_bytes = p->blob_bytes + gcount * (int64_t)sizeof(float2);
+  p->device_bytes = p->blob_bytes + ncells * 4 * (int64_t)sizeof(float2);
   ss_status st = [&]() -> ss_status {
     SS_CHECK_CUDA(cudaMalloc(&p->d_blob_off, 2 * nt * sizeof(int64_t)));
     SS_CHECK_CUDA(cudaMemcpy(p->d_blob_off, p->blob_off.data(), 2 * nt * sizeof(int64_t), cudaMemcpyHostToDevice));
     SS_CHECK_CUDA(cudaMalloc(&p->d_grid_off, (nt + 1) * sizeof(int64_t)));
     SS_CHECK_CUDA(cudaMemcpy(p->d_grid_off, p->grid_off.data(), (nt + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    SS_CHECK_CUDA(cudaMalloc(&p->d_cell_off, (nt + 1) * sizeof(int64_t)));
+    SS_CHECK_CUDA(cudaMemcpy(p->d_cell_off, p->cell_off.data(), (nt + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
     auto* dR = (int64_t*)dev_copy(offR.data(), nt * 8);
     auto* dT = (int64_t*)dev_copy(offT.data(), nt * 8);
     auto* dAR = (int64_t*)dev_copy(axR.data(), (nt + 1) * 8);
@@ -288,11 +319,9 @@ ss_status plan_build_2d(ss_plan* p, const double* R, const double* T, const doub
     k_prep_cells<<<nt, 256, 0, stream>>>(pr);
     k_prep_cells<<<nt, 256, 0, stream>>>(pt);
     SS_CHECK_CUDA(cudaGetLastError());
-    if (gcount > 0) {
-      const int grid = (int)std::min<int64_t>((gcount + 255) / 256, (int64_t)num_sms() * 16);
-      k_grid_to_ff<<<grid, 256, 0, stream>>>(F, p->d_grid, gcount, dBad + 1);
-      SS_CHECK_CUDA(cudaGetLastError());
-    }
+    k_grid_cells<<<nt, 256, 0, stream>>>(F, p->d_grid_off, dAR, dAT, p->d_cell_off,
+                                          reinterpret_cast<float4*>(p->d_grid), dBad + 1);
+    SS_CHECK_CUDA(cudaGetLastError());
     if (o.model == SS_MODEL_MLP && o.mlp_epochs > 0) {
       TrainArgs ta{2 * nt, p->d_blobs, p->d_blob_off, o.mlp_epochs,
                    o.mlp_lr > 0 ? o.mlp_lr : 2e-3f, o.seed};

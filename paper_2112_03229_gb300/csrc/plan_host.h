@@ -36,11 +36,15 @@ struct PlanBase {
   int64_t blob_bytes = 0;
   unsigned char* d_blobs = nullptr;
   int64_t* d_blob_off = nullptr;
-  // 2D value grids (float-float) and their fp64 copies for tables that need them
+  // 2D value grids: per cell its four corners as float-float (CellCorners,
+  // cell offsets cell_off), and the caller's fp64 grids, row-major (grid_off),
+  // kept only when some value needs the fp64 blend
   float2* d_grid = nullptr;
   double* d_grid64 = nullptr;
   int64_t* d_grid_off = nullptr;
+  int64_t* d_cell_off = nullptr;
   std::vector<int64_t> grid_off;
+  std::vector<int64_t> cell_off;
   // autotuner choices per table-size bucket
   int bucket_algo[kNumBuckets] = {0};
   int bucket_tile[kNumBuckets] = {0};      // targets per tile used by the bound batch
@@ -71,6 +75,7 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
 ss_status plan_set_algos(ss_plan* p, cudaStream_t stream);
 ss_status plan_tune(ss_plan* p, cudaStream_t stream);
 ss_status plan_window_stats(ss_plan* p);
+void plan_cell_offsets(PlanBase* p);   // cell_off from the axis sizes (2D)
 
 }  // namespace ss
 

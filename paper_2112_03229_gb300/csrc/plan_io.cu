@@ -15,7 +15,7 @@ using namespace ss;
 namespace {
 
 constexpr char kMagic[8] = {'S', 'S', 'P', 'L', 'A', 'N', 0, 1};
-constexpr int32_t kVersion = 2;
+constexpr int32_t kVersion = 3;
 
 struct Writer {
   FILE* f;
@@ -91,9 +91,10 @@ extern "C" ss_status ss_plan_save(const ss_plan* p, const char* path) {
   w.val<int64_t>(p->blob_bytes);
   ss_status st = copy_out(w, p->d_blobs, p->blob_bytes);
   const int64_t gcount = p->kind == 2 ? p->grid_off.back() : 0;
+  const int64_t ccount = p->kind == 2 ? 4 * p->cell_off.back() : 0;     // float-float corners
   if (st == SS_OK && p->kind == 2) {
-    w.val<int64_t>(gcount);
-    st = copy_out(w, p->d_grid, gcount * (int64_t)sizeof(float2));
+    w.val<int64_t>(ccount);
+    st = copy_out(w, p->d_grid, ccount * (int64_t)sizeof(float2));
     const int32_t has64 = p->d_grid64 != nullptr;
     w.val(has64);
     if (st == SS_OK && has64) st = copy_out(w, p->d_grid64, gcount * (int64_t)sizeof(double));
@@ -149,12 +150,17 @@ extern "C" ss_status ss_plan_load(ss_plan** out, const char* path, cudaStream_t 
     SS_CHECK_CUDA(cudaMemcpy(p->d_blob_off, p->blob_off.data(), nblobs * sizeof(int64_t), cudaMemcpyHostToDevice));
     p->device_bytes = p->blob_bytes;
     if (kind == 2) {
-      int64_t gcount = 0;
-      r.val(gcount);
-      if (!r.ok || gcount != p->grid_off.back()) return fail(SS_EINVAL, "ss_plan_load: corrupt plan file");
-      if (cudaMalloc(&p->d_grid, std::max<int64_t>(gcount, 1) * sizeof(float2)) != cudaSuccess)
+      if (p->sizes_t.size() != (size_t)ntables) return fail(SS_EINVAL, "ss_plan_load: corrupt plan file");
+      for (int k = 0; k < ntables; ++k)
+        if (p->sizes[k] < 2 || p->sizes_t[k] < 2) return fail(SS_EINVAL, "ss_plan_load: corrupt plan file");
+      plan_cell_offsets(p);
+      const int64_t gcount = p->grid_off.back();
+      int64_t ccount = 0;
+      r.val(ccount);
+      if (!r.ok || ccount != 4 * p->cell_off.back()) return fail(SS_EINVAL, "ss_plan_load: corrupt plan file");
+      if (cudaMalloc(&p->d_grid, std::max<int64_t>(ccount, 1) * sizeof(float2)) != cudaSuccess)
         return fail(SS_ENOMEM, "ss_plan_load: device allocation failed");
-      if (ss_status s2 = copy_in(r, p->d_grid, gcount * (int64_t)sizeof(float2))) return s2;
+      if (ss_status s2 = copy_in(r, p->d_grid, ccount * (int64_t)sizeof(float2))) return s2;
       int32_t has64 = 0;
       r.val(has64);
       if (has64) {
@@ -164,7 +170,9 @@ extern "C" ss_status ss_plan_load(ss_plan** out, const char* path, cudaStream_t 
       }
       SS_CHECK_CUDA(cudaMalloc(&p->d_grid_off, (ntables + 1) * sizeof(int64_t)));
       SS_CHECK_CUDA(cudaMemcpy(p->d_grid_off, p->grid_off.data(), (ntables + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
-      p->device_bytes += gcount * (int64_t)(sizeof(float2) + (has64 ? sizeof(double) : 0));
+      SS_CHECK_CUDA(cudaMalloc(&p->d_cell_off, (ntables + 1) * sizeof(int64_t)));
+      SS_CHECK_CUDA(cudaMemcpy(p->d_cell_off, p->cell_off.data(), (ntables + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+      p->device_bytes += ccount * (int64_t)sizeof(float2) + (has64 ? gcount * (int64_t)sizeof(double) : 0);
     }
     return plan_window_stats(p);
   }();
