@@ -449,7 +449,7 @@ def sweep_per_table(wl_obj, stream, steps):
         Y = wl_obj.Y[Y_off[k]:Y_off[k + 1]]
         out = wl_obj.out[Y_off[k]:Y_off[k + 1]]
         row = {}
-        for model in ("none", "spline", "mlp"):
+        for model in ("none", "spline", "mlp", "loghash"):
             plan = ss.Plan.create_1d([0, X.numel()], X, model=model, autotune=(model == "none"))
             plan.bind_1d([0, Y.numel()], Y, out)
             for _ in range(3):
@@ -656,7 +656,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--targets", type=int, default=0, help="override the workload's target count (profiling cases)")
-    ap.add_argument("--model", default=None, choices=["none", "spline", "mlp"],
+    ap.add_argument("--model", default=None, choices=["none", "spline", "mlp", "loghash"],
                     help="position model of the timed plan (default none: plain search; the learned forms are "
                          "timed beside it)")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-plan comparison of plan workloads")
@@ -752,7 +752,7 @@ def main():
             if wl_obj.model == "none":
                 # the timed form is the plain search; the learned forms on the same batch
                 learned = {}
-                for model in ("spline", "mlp"):
+                for model in ("spline", "mlp", "loghash"):
                     r = wl_obj.compare(stream, args.steps, model)
                     r["frac"] = frac_of(r)
                     learned[model] = r

@@ -147,7 +147,8 @@ typedef struct ss_plan ss_plan;
 typedef enum ss_model {
   SS_MODEL_NONE = 0,    /* plain search only */
   SS_MODEL_SPLINE = 1,  /* piecewise-linear map of the target's key, knots = bucket directory */
-  SS_MODEL_MLP = 2      /* 2-16-1 fp32 MLP on the target's exponent and mantissa, trained on the GPU */
+  SS_MODEL_MLP = 2,     /* 2-16-1 fp32 MLP on the target's exponent and mantissa, trained on the GPU */
+  SS_MODEL_LOGHASH = 3  /* no training: the logarithm hash of Sec. 3.4 (Eqs. 1-2), base fitted to the end points */
 } ss_model;
 
 typedef struct ss_plan_opts {
@@ -171,7 +172,7 @@ typedef struct ss_plan_info {
   float mean_window;
   float train_loss;         /* mean final training loss of the MLP (MLP model only) */
   int32_t nbuckets;         /* table-size buckets [2,16) [16,64) [64,256) ... */
-  int32_t bucket_algo[8];   /* chosen algorithm per bucket: 0 bucket, 1 binary, 2-4 ballot 8/16/32, 5 spline, 6 mlp */
+  int32_t bucket_algo[8];   /* chosen algorithm per bucket: 0 bucket, 1 binary, 2-4 ballot 8/16/32, 5 spline, 6 mlp, 7 loghash */
   int32_t bucket_tile[8];   /* chosen targets per tile per bucket */
   int32_t bucket_tables[8]; /* tables per bucket */
   int64_t ntiles;           /* tiles of the bound batch */

@@ -23,7 +23,8 @@ int size_bucket(int n) {
 }
 
 const char* algo_name(int a) {
-  static const char* names[BL_NUM] = {"bucket", "binary", "ballot8", "ballot16", "ballot32", "spline", "mlp"};
+  static const char* names[BL_NUM] = {"bucket", "binary", "ballot8", "ballot16", "ballot32", "spline", "mlp",
+                                              "loghash"};
   return a >= 0 && a < BL_NUM ? names[a] : "?";
 }
 
@@ -133,7 +134,7 @@ extern "C" void ss_plan_opts_default(ss_plan_opts* o) {
 
 static ss_status check_opts(const ss_plan_opts* o) {
   if (o->side != SS_SIDE_LT && o->side != SS_SIDE_LE) return fail(SS_EINVAL, "plan: bad side");
-  if (o->model < SS_MODEL_NONE || o->model > SS_MODEL_MLP) return fail(SS_EINVAL, "plan: bad model");
+  if (o->model < SS_MODEL_NONE || o->model > SS_MODEL_LOGHASH) return fail(SS_EINVAL, "plan: bad model");
   if (o->algo < SS_ALGO_AUTO || o->algo > SS_ALGO_BALLOT) return fail(SS_EINVAL, "plan: algo must be auto, binary, bucket or ballot");
   if (o->tile < 0 || o->mlp_epochs < 0 || o->dir_cap < 0) return fail(SS_EINVAL, "plan: negative option");
   return SS_OK;
@@ -143,6 +144,7 @@ static ss_status check_opts(const ss_plan_opts* o) {
 int ss::initial_algo(const ss_plan_opts& o) {
   if (o.model == SS_MODEL_SPLINE) return BL_SPLINE;
   if (o.model == SS_MODEL_MLP) return BL_MLP;
+  if (o.model == SS_MODEL_LOGHASH) return BL_LOGHASH;
   if (o.algo == SS_ALGO_BINARY) return BL_BINARY;
   if (o.algo == SS_ALGO_BALLOT) return BL_BALLOT32;
   return BL_BUCKET;

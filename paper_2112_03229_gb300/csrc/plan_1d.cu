@@ -115,6 +115,13 @@ __global__ void __launch_bounds__(256) k_prep_1d(PrepArgs a) {
   if (tid == kHidden) {
     mlp[4 * kHidden] = 0.5f;
     for (int i = kMlpParams; i < kMlpBytes / 4; ++i) mlp[i] = 0.0f;
+    // logarithm-hash coefficients (Eqs. 1-2: n-1 steps of base b between the end points)
+    const double x0 = X[0], x1 = X[nk];
+    if (x0 > 0.0 && isfinite(x1)) {
+      const double steps_per_log2 = (double)nk / (log2(x1) - log2(x0));
+      mlp[kMlpParams] = (float)steps_per_log2;
+      mlp[kMlpParams + 1] = (float)(-log2(x0) * steps_per_log2);
+    }
   }
   __syncthreads();
   if (tid == 0) {
@@ -258,7 +265,7 @@ __global__ void __launch_bounds__(256) k_window(WindowArgs a) {
   unsigned char* blob = a.blobs + a.blob_off[k];
   BlobHdr* gh = reinterpret_cast<BlobHdr*>(blob);
   const BlobHdr h = *gh;
-  if (h.algo != BL_SPLINE && h.algo != BL_MLP) return;
+  if (h.algo != BL_SPLINE && h.algo != BL_MLP && h.algo != BL_LOGHASH) return;
   StagedView v;
   v.h = h;
   v.mlp = reinterpret_cast<const float*>(blob + h.off_mlp);
@@ -279,8 +286,10 @@ __global__ void __launch_bounds__(256) k_window(WindowArgs a) {
     else q = k0 + (uint64_t)((double)(splitmix64(a.seed ^ ((uint64_t)k << 40) ^ (uint64_t)i) >> 11) * 0x1.0p-53 *
                              (double)(k1 - k0));
     const int c = plain_bucket(v, q);
-    const int prop = h.algo == BL_SPLINE ? spline_proposal(v, q)
-                                         : mlp_propose(v.mlp, sc, h.n, key_to_double(q));
+    const int prop = h.algo == BL_SPLINE    ? spline_proposal(v, q)
+                     : h.algo == BL_LOGHASH ? loghash_propose(v.mlp[kMlpParams], v.mlp[kMlpParams + 1], h.nk,
+                                                              key_to_double(q))
+                                            : mlp_propose(v.mlp, sc, h.n, key_to_double(q));
     err = max(err, abs(prop - c));
   }
   err = __reduce_max_sync(0xFFFFFFFFu, err);
@@ -296,7 +305,7 @@ __global__ void __launch_bounds__(256) k_window(WindowArgs a) {
 // targets.  Targets of a tile are contiguous in Y / out.
 // ---------------------------------------------------------------------------
 // Algorithm families compiled into one instance of the batched kernel: the
-// plain searches only, plus the spline, plus the MLP.  A plan launches the
+// plain searches only, plus the spline and the logarithm hash, plus the MLP.  A plan launches the
 // smallest family that covers its tables, which keeps registers (and so
 // resident warps) at the level the plain searches need.
 enum : int { FAM_PLAIN = 0, FAM_SPLINE = 1, FAM_MLP = 2 };
@@ -427,6 +436,11 @@ __global__ void __launch_bounds__(kNumThreads, FAM == FAM_MLP ? 2 : 4) k_batched
       stream_tile(a.Y, a.out, b, cnt, vec, le, nans, [&](double y, uint64_t q) { return mlp_count(v, y, q, fallbacks); });
     } else if (FAM >= FAM_SPLINE && algo == BL_SPLINE) {
       stream_tile(a.Y, a.out, b, cnt, vec, le, nans, [&](double, uint64_t q) { return spline_count(v, q, fallbacks); });
+    } else if (FAM >= FAM_SPLINE && algo == BL_LOGHASH) {
+      const float la = v.mlp[kMlpParams], lc = v.mlp[kMlpParams + 1];
+      const int nk = h.nk;
+      stream_tile(a.Y, a.out, b, cnt, vec, le, nans,
+                  [&](double y, uint64_t q) { return learned_count(v, loghash_propose(la, lc, nk, y), q, fallbacks); });
     } else if (algo == BL_BINARY) {
       stream_tile(a.Y, a.out, b, cnt, vec, le, nans, [&](double, uint64_t q) { return plain_binary(v, q); });
     } else if (h.stride == 1 && h.occ <= 2) {

@@ -72,6 +72,7 @@ __device__ __forceinline__ int axis_count(const StagedView& v, double t, uint64_
     case BL_BINARY: return plain_binary(v, q);
     case BL_SPLINE: return spline_count(v, q, fallbacks);
     case BL_MLP: return mlp_count(v, t, q, fallbacks);
+    case BL_LOGHASH: return loghash_count(v, t, q, fallbacks);
     default: return plain_bucket(v, q);
   }
 }
@@ -370,7 +371,7 @@ extern "C" ss_status ss_plan_create_2d(ss_plan** out, int32_t ntables, const int
   ss_plan_opts_default(&o);
   if (opts_in) o = *opts_in;
   if (o.side != SS_SIDE_LT) return fail(SS_EINVAL, "ss_plan_create_2d: the 2D lookup uses side SS_SIDE_LT");
-  if (o.model < SS_MODEL_NONE || o.model > SS_MODEL_MLP || o.algo == SS_ALGO_BALLOT || o.algo == SS_ALGO_BRANCHY ||
+  if (o.model < SS_MODEL_NONE || o.model > SS_MODEL_LOGHASH || o.algo == SS_ALGO_BALLOT || o.algo == SS_ALGO_BRANCHY ||
       o.algo < 0 || o.algo > SS_ALGO_BALLOT)
     return fail(SS_EINVAL, "ss_plan_create_2d: algo must be auto, binary or bucket");
   auto* p = new ss_plan();

@@ -76,7 +76,7 @@ ss_status plan_window_stats(ss_plan* p) {
   double sw = 0, sl = 0;
   int mw = 0, cnt = 0;
   for (const auto& h : hs) {
-    if (h.algo == BL_SPLINE || h.algo == BL_MLP) {
+    if (h.algo == BL_SPLINE || h.algo == BL_MLP || h.algo == BL_LOGHASH) {
       mw = std::max(mw, h.E);
       sw += h.E;
       sl += h.loss;
@@ -201,7 +201,7 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
   if (smem > max_smem_optin()) return fail(SS_EUNSUPPORTED, "plan: staged tables exceed shared memory");
   const void* kern;
   int family = 0;
-  for (int a : p->algo) family = std::max(family, a == BL_MLP ? 2 : a == BL_SPLINE ? 1 : 0);
+  for (int a : p->algo) family = std::max(family, a == BL_MLP ? 2 : (a == BL_SPLINE || a == BL_LOGHASH) ? 1 : 0);
   if (p->kind == 1) kern = batched_1d_kernel(p->opts.side == SS_SIDE_LE, family);
   else kern = reinterpret_cast<const void*>(&k_batched_2d);
   SS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -335,6 +335,7 @@ ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
   std::vector<int> cands;
   if (p->opts.model == SS_MODEL_SPLINE) cands = {BL_SPLINE};
   else if (p->opts.model == SS_MODEL_MLP) cands = {BL_MLP};
+  else if (p->opts.model == SS_MODEL_LOGHASH) cands = {BL_LOGHASH};
   else if (p->kind == 1) cands = {BL_BUCKET, BL_BINARY, BL_BALLOT8, BL_BALLOT16, BL_BALLOT32};
   else cands = {BL_BUCKET, BL_BINARY};
   const std::vector<float> mult_cands = {0.25f, 1.0f, 4.0f};

@@ -105,6 +105,27 @@ __device__ __forceinline__ float spline_position(const int* __restrict__ dir, in
   return (float)lo + frac * (float)(hi - lo);
 }
 
+// Logarithm hash of Sec. 3.4 as a position proposal (no training).  With the
+// base b fitted so that the table's range spans n-1 steps (Eq. 1) and the
+// offset of Eq. 2, hash(t) = floor(log_b t - log_b X[0]) is the count of
+// entries below t for an exactly log-spaced table.  log2 t is taken from the
+// bits of t: the unbiased exponent plus log2 of the significand's top 23
+// bits (fp32).  a = 1 / log2 b, c = -log2(X[0]) / log2 b; a table without a
+// positive range has a = c = 0 (every proposal is 0, the window covers the
+// table).  Negative targets propose 0; NaN proposes 0 through fmaxf.
+__device__ __forceinline__ float log2_of_bits(double t) {
+  const uint64_t u = static_cast<uint64_t>(__double_as_longlong(t));
+  const int e = (int)((u >> 52) & 0x7FF) - 1023;
+  const float m = __int_as_float(0x3F800000 | (int)((u >> 29) & 0x7FFFFF));   // significand in [1, 2)
+  return (float)e + __log2f(m);
+}
+
+__device__ __forceinline__ int loghash_propose(float a, float c, int nk, double t) {
+  if (__double_as_longlong(t) < 0) return 0;
+  const float p = floorf(fmaf(a, log2_of_bits(t), c));
+  return (int)fminf(fmaxf(p, 0.0f), (float)nk);
+}
+
 __device__ __forceinline__ int spline_propose(const int* __restrict__ dir, int shift, uint64_t base, int nb,
                                               uint64_t q) {
   return (int)rintf(spline_position(dir, shift, base, nb, q));

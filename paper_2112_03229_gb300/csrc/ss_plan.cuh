@@ -22,7 +22,7 @@
 namespace ss {
 
 enum BlobAlgo : int { BL_BUCKET = 0, BL_BINARY = 1, BL_BALLOT8 = 2, BL_BALLOT16 = 3, BL_BALLOT32 = 4,
-                      BL_SPLINE = 5, BL_MLP = 6, BL_NUM = 7 };
+                      BL_SPLINE = 5, BL_MLP = 6, BL_LOGHASH = 7, BL_NUM = 8 };
 
 struct __align__(16) BlobHdr {
   int n, nk, ns, stride;     // table length, searched keys, staged keys, sample stride
@@ -61,7 +61,7 @@ __host__ __device__ inline void staged_range(const BlobHdr& h, int& lo, int& hi)
   switch (h.algo) {
     case BL_BINARY: lo = h.off_eyt; hi = h.off_eyt + (1 << h.D) * 8; break;
     case BL_BALLOT8: case BL_BALLOT16: case BL_BALLOT32: lo = h.off_keys; hi = h.off_keys + (h.ns + kPad) * 8; break;
-    default: lo = h.off_mlp; hi = h.off_keys + (h.ns + kPad) * 8; break;   // bucket, spline, mlp
+    default: lo = h.off_mlp; hi = h.off_keys + (h.ns + kPad) * 8; break;   // bucket, spline, mlp, loghash
   }
   if (h.off_cells >= 0) hi = h.staged_end;   // 2D axes keep their cells right after
   lo &= ~15;
@@ -244,6 +244,11 @@ __device__ __forceinline__ int spline_proposal(const StagedView& v, uint64_t q) 
 
 __device__ __forceinline__ int spline_count(const StagedView& v, uint64_t q, int& fallbacks) {
   return learned_count(v, spline_proposal(v, q), q, fallbacks);
+}
+
+// Logarithm-hash proposal: its two coefficients sit after the MLP parameters.
+__device__ __forceinline__ int loghash_count(const StagedView& v, double t, uint64_t q, int& fallbacks) {
+  return learned_count(v, loghash_propose(v.mlp[kMlpParams], v.mlp[kMlpParams + 1], v.h.nk, t), q, fallbacks);
 }
 
 __device__ __forceinline__ int mlp_count(const StagedView& v, double t, uint64_t q, int& fallbacks) {

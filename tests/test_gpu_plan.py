@@ -37,7 +37,7 @@ def small_batch(seed=3, ntables=150, scale=0.003):
     return wl.batched_1d(ntables=ntables, count_scale=scale, seed=seed)
 
 
-@pytest.mark.parametrize("model", ["none", "spline", "mlp"])
+@pytest.mark.parametrize("model", ["none", "spline", "mlp", "loghash"])
 @pytest.mark.parametrize("side", [0, 1])
 def test_plan_1d_batched_models(ss, model, side):
     b = small_batch()
@@ -72,7 +72,7 @@ def sweep_batch(m_per=60_000):
     return wl.Batched1D(torch.as_tensor(X_off), X, torch.as_tensor(Y_off), Y, None, None)
 
 
-@pytest.mark.parametrize("model", ["none", "spline", "mlp"])
+@pytest.mark.parametrize("model", ["none", "spline", "mlp", "loghash"])
 def test_plan_table_size_sweep(ss, model):
     b = sweep_batch()
     want = oracle.search_1d_batched(b.X_off.numpy(), b.X.numpy(), b.Y_off.numpy(), b.Y.numpy())
@@ -212,10 +212,36 @@ def test_learned_gain(ss):
     assert trained.info().train_loss < 1e-3
 
 
+def test_loghash_proposal(ss):
+    """The logarithm hash of Sec. 3.4 (Eqs. 1-2) as an untrained proposal: on
+    exactly log-spaced tables it is off by at most a step or two (rounding of
+    the fp32 logarithm), on a table with no positive range it proposes 0 and
+    the window spans the table; the indices are exact in both cases."""
+    tabs = [wl.log_spaced_table(n, 1e-6, 1e4, 0.0, seed=n) for n in (17, 300, 2001)]
+    counts = [5000, 7001, 9003]
+    Y = torch.cat([wl.log_uniform(c, 0.5e-6, 2e4, seed=i) for i, c in enumerate(counts)])
+    X_off = torch.tensor(np.concatenate([[0], np.cumsum([len(t) for t in tabs])]))
+    Y_off = torch.tensor(np.concatenate([[0], np.cumsum(counts)]))
+    b = wl.Batched1D(X_off, torch.cat(tabs), Y_off, Y, None, None)
+    want = oracle.search_1d_batched(b.X_off.numpy(), b.X.numpy(), b.Y_off.numpy(), b.Y.numpy())
+    plan, got, st = run_plan_1d(ss, b, model="loghash")
+    np.testing.assert_array_equal(got, want)
+    assert 1 <= plan.info().max_window <= 3, plan.info().max_window
+    assert st.fallbacks == 0
+    # a table through zero: no positive range, a = c = 0
+    Xn = torch.linspace(-5.0, 5.0, 64, dtype=torch.float64)
+    Yn = torch.linspace(-6.0, 6.0, 1001, dtype=torch.float64)
+    bn = wl.Batched1D(torch.tensor([0, 64]), Xn, torch.tensor([0, 1001]), Yn, None, None)
+    want = oracle.search_1d_batched(bn.X_off.numpy(), bn.X.numpy(), bn.Y_off.numpy(), bn.Y.numpy())
+    plan, got, st = run_plan_1d(ss, bn, model="loghash")
+    np.testing.assert_array_equal(got, want)
+    assert plan.info().max_window == 64 and st.fallbacks == 0
+
+
 # ---------------------------------------------------------------- 2D plans
 
 @pytest.mark.parametrize("coherent", [False, True])
-@pytest.mark.parametrize("model", ["none", "spline", "mlp"])
+@pytest.mark.parametrize("model", ["none", "spline", "mlp", "loghash"])
 def test_plan_2d_batched(ss, model, coherent):
     b = wl.batched_2d(ntables=12, pairs_per_table=4001, coherent=coherent, seed=9)
     wi, wv = oracle.search_interp_2d_batched(b.R_off.numpy(), b.R.numpy(), b.T_off.numpy(), b.T.numpy(),
