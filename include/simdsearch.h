@@ -113,12 +113,14 @@ ss_status ss_search_interp_2d(const double* R, int32_t nr, const double* T, int3
 
 /* Host-array forms of the two calls above, for callers whose targets live
  * in host memory (EOSPAC's callers pass host arrays, Sec. 1 and 2.2).  Every
- * pointer is host memory.  The library streams the targets through the GPU
- * in chunks, overlapping host-to-device copies, the search and
- * device-to-host copies on two streams; page-locked buffers give link-speed
- * copies, pageable ones work through the driver's staging.  Synchronous: the
- * results are in host memory when the call returns.  Device staging memory is
- * allocated on first use per device and kept; calls on one device are
+ * pointer is host memory.  When the target and result buffers are
+ * page-locked (cudaHostAlloc / cudaHostRegister) the search kernels read and
+ * write them directly over the host link, reads and writes in flight
+ * together, with no staging copy; pageable buffers are moved in chunks,
+ * overlapping host-to-device copies, the search and device-to-host copies
+ * on two streams.  Synchronous: the results are in host memory when the call
+ * returns.  Device memory (the tables, and the chunks of the pageable path)
+ * is allocated on first use per device and kept; calls on one device are
  * serialised. */
 ss_status ss_search_1d_host(const double* X, int32_t n, const double* Y, int64_t m, int32_t* lowbounds,
                             int32_t side, int32_t algo);
@@ -199,7 +201,9 @@ ss_status ss_plan_create_2d(ss_plan** plan, int32_t ntables, const int64_t* R_of
 /* Bind a batch: table k's targets are Y[Y_off[k] .. Y_off[k+1]) (Y_off host,
  * non-decreasing; empty tables allowed) and its results go to the same
  * positions of lowbounds.  Builds the tile queue and captures the launch in a
- * CUDA graph; buffers must stay valid while the plan executes. */
+ * CUDA graph; buffers must stay valid while the plan executes.  Y and
+ * lowbounds (and the 2D buffers below) are device memory or page-locked host
+ * memory; the latter is streamed over the host link by the kernel itself. */
 ss_status ss_plan_bind_1d(ss_plan* plan, const int64_t* Y_off, const double* Y, int32_t* lowbounds,
                           ss_devstat* stat, cudaStream_t stream);
 

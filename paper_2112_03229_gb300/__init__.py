@@ -93,6 +93,20 @@ def _dev(t, dtype, name):
     return C.c_void_p(t.data_ptr())
 
 
+def _dev_or_pinned(t, dtype, name):
+    """A CUDA tensor, or a page-locked host tensor (mapped into the device's
+    address space: the kernels stream it over the host link)."""
+    if isinstance(t, torch.Tensor) and not t.is_cuda:
+        if not t.is_pinned():
+            raise TypeError("%s must be a CUDA tensor or a page-locked host tensor" % name)
+        if t.dtype != dtype:
+            raise TypeError("%s must be %s" % (name, dtype))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        return C.c_void_p(t.data_ptr())
+    return _dev(t, dtype, name)
+
+
 def _algo(a):
     return ALGOS[a] if isinstance(a, str) else int(a)
 
@@ -283,14 +297,15 @@ class Plan:
     def bind_1d(self, Y_off, Y, out, stat=None, stream=None):
         off, offp = _offsets(Y_off)
         self._keep = (Y, out, stat)
-        _check(lib().ss_plan_bind_1d(self._h, offp, _dev(Y, torch.float64, "Y"), _dev(out, torch.int32, "out"),
-                                     _statp(stat), _stream(stream)))
+        _check(lib().ss_plan_bind_1d(self._h, offp, _dev_or_pinned(Y, torch.float64, "Y"),
+                                     _dev_or_pinned(out, torch.int32, "out"), _statp(stat), _stream(stream)))
 
     def bind_2d(self, Y_off, Y2, idx, val, stat=None, stream=None):
         off, offp = _offsets(Y_off)
         self._keep = (Y2, idx, val, stat)
-        _check(lib().ss_plan_bind_2d(self._h, offp, _dev(Y2, torch.float64, "Y2"), _dev(idx, torch.int32, "idx"),
-                                     _dev(val, torch.float64, "val"), _statp(stat), _stream(stream)))
+        _check(lib().ss_plan_bind_2d(self._h, offp, _dev_or_pinned(Y2, torch.float64, "Y2"),
+                                     _dev_or_pinned(idx, torch.int32, "idx"), _dev_or_pinned(val, torch.float64, "val"),
+                                     _statp(stat), _stream(stream)))
 
     def execute(self, stream=None):
         _check(lib().ss_plan_execute(self._h, _stream(stream)))

@@ -1,13 +1,18 @@
 // host_api.cu -- the one-shot searches over host-resident arrays.
 //
-// EOSPAC's callers hand over host arrays of targets (Sec. 1, 2.2).  These
-// entry points move them through the GPU in chunks, with the host-to-device
-// copy of chunk c+1, the search of chunk c and the device-to-host copy of
-// chunk c-1 running at the same time on two streams, so the copy engines and
-// the kernels overlap.  The device staging buffers are allocated on first use
-// and kept per device (grown on demand); calls on one device are serialised.
-// With page-locked host buffers the copies run at link speed; pageable
-// buffers work too, through the driver's staging copies.
+// EOSPAC's callers hand over host arrays of targets (Sec. 1, 2.2).  Two ways
+// through the GPU:
+//  * page-locked target and result buffers are mapped into the device's
+//    address space, so the search kernels stream them directly over the
+//    host link: reads of targets and writes of results are in flight
+//    together and no staging copy is made (the tables, a few KB, are copied
+//    to the device first);
+//  * pageable buffers move in chunks, with the host-to-device copy of chunk
+//    c+1, the search of chunk c and the device-to-host copy of chunk c-1
+//    running at the same time on two streams.
+// The device buffers (tables, and the chunks of the pageable path) are
+// allocated on first use and kept per device (grown on demand); calls on one
+// device are serialised.
 #include <algorithm>
 #include <mutex>
 
@@ -59,6 +64,21 @@ ss_status workspace(size_t bytes, Workspace** out) {
 
 size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Device address of page-locked, mapped host memory [p, p + bytes), or
+// nullptr if either end is not such memory (pageable, device, unregistered).
+template <class T>
+T* mapped(T* p, size_t bytes) {
+  if (p == nullptr || bytes == 0) return nullptr;
+  cudaPointerAttributes a{}, b{};
+  const unsigned char* last = reinterpret_cast<const unsigned char*>(p) + bytes - 1;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+    cudaGetLastError();   // clear the query's error state
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return nullptr;
+  return static_cast<T*>(a.devicePointer);
+}
+
 }  // namespace
 }  // namespace ss
 
@@ -72,10 +92,19 @@ extern "C" ss_status ss_search_1d_host(const double* X, int32_t n, const double*
   std::lock_guard<std::mutex> lock(g_mu);
   const size_t tab = up256((size_t)n * 8);
   const size_t cin = up256((size_t)kChunk1D * 8), cout = up256((size_t)kChunk1D * 4);
+  const double* mY = mapped(Y, (size_t)m * 8);
+  int32_t* mO = mapped(lowbounds, (size_t)m * 4);
+  const bool direct = mY != nullptr && mO != nullptr;
   Workspace* w = nullptr;
-  if (ss_status st = workspace(tab + 2 * (cin + cout), &w)) return st;
+  if (ss_status st = workspace(direct ? tab : tab + 2 * (cin + cout), &w)) return st;
   double* dX = reinterpret_cast<double*>(w->buf);
   SS_CHECK_CUDA(cudaMemcpyAsync(dX, X, (size_t)n * 8, cudaMemcpyHostToDevice, w->st[0]));
+  if (direct) {
+    // page-locked buffers: one launch streams them over the link
+    if (ss_status st = search_1d(dX, n, mY, m, mO, side, algo, nullptr, w->st[0], 0, 0)) return st;
+    SS_CHECK_CUDA(cudaStreamSynchronize(w->st[0]));
+    return SS_OK;
+  }
   SS_CHECK_CUDA(cudaEventRecord(w->ready, w->st[0]));
   SS_CHECK_CUDA(cudaStreamWaitEvent(w->st[1], w->ready, 0));
   for (int64_t off = 0, c = 0; off < m; off += kChunk1D, ++c) {
@@ -103,14 +132,23 @@ extern "C" ss_status ss_search_interp_2d_host(const double* R, int32_t nr, const
   const size_t tr = up256((size_t)nr * 8), tt = up256((size_t)nt * 8), tf = up256((size_t)nr * nt * 8);
   const size_t cin = up256((size_t)kChunk2D * 16), cidx = up256((size_t)kChunk2D * 8), cval = up256((size_t)kChunk2D * 8);
   const size_t chunk = cin + cidx + cval;
+  const double* mY = mapped(Y2, (size_t)m * 16);
+  int32_t* mI = mapped(lowbounds2, (size_t)m * 8);
+  double* mV = mapped(values, (size_t)m * 8);
+  const bool direct = mY != nullptr && mI != nullptr && mV != nullptr;
   Workspace* w = nullptr;
-  if (ss_status st = workspace(tr + tt + tf + 2 * chunk, &w)) return st;
+  if (ss_status st = workspace(direct ? tr + tt + tf : tr + tt + tf + 2 * chunk, &w)) return st;
   double* dR = reinterpret_cast<double*>(w->buf);
   double* dT = reinterpret_cast<double*>(w->buf + tr);
   double* dF = reinterpret_cast<double*>(w->buf + tr + tt);
   SS_CHECK_CUDA(cudaMemcpyAsync(dR, R, (size_t)nr * 8, cudaMemcpyHostToDevice, w->st[0]));
   SS_CHECK_CUDA(cudaMemcpyAsync(dT, T, (size_t)nt * 8, cudaMemcpyHostToDevice, w->st[0]));
   SS_CHECK_CUDA(cudaMemcpyAsync(dF, F, (size_t)nr * nt * 8, cudaMemcpyHostToDevice, w->st[0]));
+  if (direct) {
+    if (ss_status st = search_interp_2d(dR, nr, dT, nt, dF, mY, m, mI, mV, algo, 0, nullptr, w->st[0])) return st;
+    SS_CHECK_CUDA(cudaStreamSynchronize(w->st[0]));
+    return SS_OK;
+  }
   SS_CHECK_CUDA(cudaEventRecord(w->ready, w->st[0]));
   SS_CHECK_CUDA(cudaStreamWaitEvent(w->st[1], w->ready, 0));
   unsigned char* base = w->buf + tr + tt + tf;

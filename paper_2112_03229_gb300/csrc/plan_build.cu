@@ -339,8 +339,11 @@ ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
   else if (p->kind == 1) cands = {BL_BUCKET, BL_BINARY, BL_BALLOT8, BL_BALLOT16, BL_BALLOT32};
   else cands = {BL_BUCKET, BL_BINARY};
   const std::vector<float> mult_cands = {0.25f, 1.0f, 4.0f};
+  // up to 8 representative tables per size bucket share 64M synthetic
+  // targets, enough tiles to keep every block of the GPU busy, so each
+  // candidate is timed in the regime the real batch runs in
   const int kReps = 8;
-  const int64_t kPerRep = 1 << 22;
+  const int64_t kTuneTargets = int64_t(1) << 26;
   cudaEvent_t e0, e1;
   SS_CHECK_CUDA(cudaEventCreate(&e0));
   SS_CHECK_CUDA(cudaEventCreate(&e1));
@@ -351,9 +354,9 @@ ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
   int64_t* d_yoff = nullptr;
   const int64_t per_pair = p->kind == 2 ? 2 : 1;
   ss_status st = SS_OK;
-  if (cudaMalloc(&d_Y, kReps * kPerRep * 8 * per_pair) != cudaSuccess ||
-      cudaMalloc(&d_out, kReps * kPerRep * 4 * per_pair) != cudaSuccess ||
-      cudaMalloc(&d_val, kReps * kPerRep * 8) != cudaSuccess || cudaMalloc(&d_tab, kReps * sizeof(int)) != cudaSuccess ||
+  if (cudaMalloc(&d_Y, kTuneTargets * 8 * per_pair) != cudaSuccess ||
+      cudaMalloc(&d_out, kTuneTargets * 4 * per_pair) != cudaSuccess ||
+      cudaMalloc(&d_val, kTuneTargets * 8) != cudaSuccess || cudaMalloc(&d_tab, kReps * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&d_yoff, (kReps + 1) * sizeof(int64_t)) != cudaSuccess) {
     st = fail(SS_ENOMEM, "autotune: device allocation failed");
   }
@@ -365,6 +368,7 @@ ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
     for (int k = 0; k < p->ntables && (int)reps.size() < kReps; ++k)
       if (size_bucket(std::max(p->sizes[k], p->kind == 2 ? p->sizes_t[k] : 0)) == b) reps.push_back(k);
     const int nr = (int)reps.size();
+    const int64_t kPerRep = kTuneTargets / nr;
     std::vector<int64_t> yoff_r(nr + 1);
     for (int r = 0; r <= nr; ++r) yoff_r[r] = r * kPerRep;
     std::vector<int> blob_of_rep(nr);
@@ -380,7 +384,7 @@ ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
       int* d_tab_t = nullptr;
       double* d_tmp = nullptr;
       cudaMalloc(&d_tab_t, nr * sizeof(int));
-      cudaMalloc(&d_tmp, kReps * kPerRep * 8);
+      cudaMalloc(&d_tmp, kTuneTargets * 8);
       cudaMemcpy(d_tab_t, tab_t.data(), nr * sizeof(int), cudaMemcpyHostToDevice);
       k_synth_1d<<<nr, 256, 0, stream>>>(p->d_blobs, p->d_blob_off, d_tab, d_yoff, d_tmp, p->opts.seed ^ 0x7E57ull);
       cudaMemcpy2DAsync(d_Y, 16, d_tmp, 8, 8, nr * kPerRep, cudaMemcpyDeviceToDevice, stream);

@@ -121,6 +121,34 @@ def test_plan_graph_replay_and_rebind(ss):
     assert torch.equal(out, first)
 
 
+def test_plan_bound_to_page_locked_host_buffers(ss):
+    """A plan bound to page-locked host buffers: the kernel streams targets in
+    and indices out over the host link; same answers as device buffers."""
+    b = small_batch(seed=13)
+    want = oracle.search_1d_batched(b.X_off.numpy(), b.X.numpy(), b.Y_off.numpy(), b.Y.numpy())
+    plan = ss.Plan.create_1d(b.X_off, b.X.to(DEV))
+    hY = b.Y.clone().pin_memory()
+    hO = torch.full((b.Y.numel(),), -1, dtype=torch.int32).pin_memory()
+    plan.bind_1d(b.Y_off, hY, hO)
+    plan.execute()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(hO.numpy(), want)
+    with pytest.raises(TypeError):
+        plan.bind_1d(b.Y_off, b.Y.clone(), hO)          # pageable host memory is refused
+    b2 = wl.batched_2d(ntables=5, pairs_per_table=2001, seed=14)
+    wi, wv = oracle.search_interp_2d_batched(b2.R_off.numpy(), b2.R.numpy(), b2.T_off.numpy(), b2.T.numpy(),
+                                             b2.F_off.numpy(), b2.F.numpy(), b2.Y_off.numpy(), b2.Y2.numpy())
+    p2 = ss.Plan.create_2d(b2.R_off, b2.R.to(DEV), b2.T_off, b2.T.to(DEV), b2.F_off, b2.F.to(DEV))
+    m = b2.Y2.shape[0]
+    hI = torch.empty((m, 2), dtype=torch.int32).pin_memory()
+    hV = torch.empty(m, dtype=torch.float64).pin_memory()
+    p2.bind_2d(b2.Y_off, b2.Y2.clone().pin_memory(), hI, hV)
+    p2.execute()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(hI.numpy(), wi)
+    assert (np.abs(hV.numpy() - wv) / np.abs(wv)).max() <= REL_TOL
+
+
 def test_plan_not_sorted_rejected(ss):
     X = torch.tensor([1.0, 2.0, 2.0, 3.0, 1.0, 5.0, 7.0], dtype=torch.float64, device=DEV)
     with pytest.raises(ss.SSError) as e:

@@ -268,3 +268,33 @@ def test_host_entry_points_match_device_calls(ss):
     di, dv = ss.search_interp_2d(R.to(DEV), T.to(DEV), F.to(DEV), Y2.to(DEV))
     np.testing.assert_array_equal(idx.numpy(), di.cpu().numpy())
     np.testing.assert_array_equal(val.numpy(), dv.cpu().numpy())
+
+
+def test_host_entry_points_both_paths(ss):
+    """Page-locked target and result buffers are streamed by the kernels over
+    the host link; pageable (or mixed) ones go through the chunked copies.
+    Both give the device call's answers, across chunk boundaries and at
+    offsets that are not 16-byte aligned."""
+    X, Y = wl.plain_1d(m=(1 << 24) + (1 << 23) + 3, seed=5)
+    want = ss.search_1d(X.to(DEV), Y.to(DEV)).cpu().numpy()
+    Yp = torch.empty(len(Y) + 1, dtype=torch.float64).pin_memory()
+    Yp[1:] = Y
+    Op = torch.full((len(Y) + 1,), -1, dtype=torch.int32).pin_memory()
+    ss.search_1d_host(X, Yp[1:], out=Op[1:])                      # mapped, misaligned by 8 / 4 bytes
+    np.testing.assert_array_equal(Op[1:].numpy(), want)
+    assert int(Op[0]) == -1
+    got = ss.search_1d_host(X, Y.clone())                          # pageable, 1.5 chunks
+    np.testing.assert_array_equal(got.numpy(), want)
+    got = ss.search_1d_host(X, Yp[1:], out=torch.empty(len(Y), dtype=torch.int32))   # mixed: chunked
+    np.testing.assert_array_equal(got.numpy(), want)
+    R, T, F, Y2 = wl.interp_2d(m=(1 << 23) + (1 << 22) + 9, seed=6)
+    di, dv = ss.search_interp_2d(R.to(DEV), T.to(DEV), F.to(DEV), Y2.to(DEV))
+    m = Y2.shape[0]
+    Ip = torch.empty((m, 2), dtype=torch.int32).pin_memory()
+    Vp = torch.empty(m, dtype=torch.float64).pin_memory()
+    ss.search_interp_2d_host(R, T, F, Y2.pin_memory(), idx=Ip, val=Vp)   # mapped
+    np.testing.assert_array_equal(Ip.numpy(), di.cpu().numpy())
+    np.testing.assert_array_equal(Vp.numpy(), dv.cpu().numpy())
+    idx, val = ss.search_interp_2d_host(R, T, F, Y2.clone())       # pageable, 1.5 chunks
+    np.testing.assert_array_equal(idx.numpy(), di.cpu().numpy())
+    np.testing.assert_array_equal(val.numpy(), dv.cpu().numpy())
