@@ -111,6 +111,28 @@ ss_status ss_search_interp_2d(const double* R, int32_t nr, const double* T, int3
                               int32_t* lowbounds2, double* values, int32_t algo,
                               ss_devstat* stat, cudaStream_t stream);
 
+/* Interpolation options of the 2D lookup.  The paper prints no
+ * interpolation formula (Sec. 1, 2.2); the default is bilinear in linear
+ * axis coordinates with weights clamped to [0, 1] (constant extrapolation
+ * beyond the grid).  extrap = 1 drops the clamp: targets outside an axis are
+ * extrapolated linearly from its edge cell.  logspace = 1 takes each weight
+ * in natural-log axis coordinates, w = (ln x - ln X[c]) / (ln X[c+1] -
+ * ln X[c]) (a coordinate <= 0 gives a weight of -inf or NaN, which the clamp
+ * and the NaN rule then handle).  Pairs that need either option are
+ * evaluated in fp64; logspace = 1 evaluates every pair in fp64. */
+typedef struct ss_interp_opts {
+  int32_t algo;       /* ss_algo of both axis searches (AUTO, BUCKET or BINARY) */
+  int32_t extrap;     /* 0: clamp the weights (default); 1: linear extrapolation */
+  int32_t logspace;   /* 0: linear axis coordinates (default); 1: natural-log coordinates */
+  int32_t fp64;       /* 1: fp64 weights and blend for every pair */
+} ss_interp_opts;
+
+/* ss_search_interp_2d with interpolation options (NULL opts: the defaults). */
+ss_status ss_search_interp_2d_ex(const double* R, int32_t nr, const double* T, int32_t nt,
+                                 const double* F, const double* Y2, int64_t m,
+                                 int32_t* lowbounds2, double* values, const ss_interp_opts* opts,
+                                 ss_devstat* stat, cudaStream_t stream);
+
 /* Host-array forms of the two calls above, for callers whose targets live
  * in host memory (EOSPAC's callers pass host arrays, Sec. 1 and 2.2).  Every
  * pointer is host memory.  When the target and result buffers are
@@ -164,6 +186,8 @@ typedef struct ss_plan_opts {
   int32_t dir_cap;          /* bucket-directory budget per table (0: 4 n clamped to [64, 4096]; 8192 above 8128 entries) */
   uint64_t seed;            /* seed of the counter-based sampler of training and probe targets */
   const char* tune_cache;   /* JSON file the autotuner reads and writes (NULL: none) */
+  int32_t extrap;           /* 2D plans: interpolation options as in ss_interp_opts */
+  int32_t logspace;
 } ss_plan_opts;
 
 typedef struct ss_plan_info {

@@ -33,6 +33,10 @@ def lib():
         L.oracle_search_1d_batched.argtypes = [C.c_int32, _i64p, _f64p, _i64p, _f64p, C.c_int32, _i32p]
         L.oracle_search_interp_2d_batched.argtypes = [C.c_int32, _i64p, _f64p, _i64p, _f64p, _i64p, _f64p,
                                                       _i64p, _f64p, _i32p, _f64p]
+        L.oracle_search_interp_2d_opts.argtypes = [_f64p, C.c_int32, _f64p, C.c_int32, _f64p, _f64p,
+                                                   C.c_int64, C.c_int32, C.c_int32, _i32p, _f64p]
+        L.oracle_search_interp_2d_batched_opts.argtypes = [C.c_int32, _i64p, _f64p, _i64p, _f64p, _i64p, _f64p,
+                                                           _i64p, _f64p, C.c_int32, C.c_int32, _i32p, _f64p]
         L.oracle_order_key.argtypes = [C.c_double]
         L.oracle_order_key.restype = C.c_uint64
         L.oracle_bucket_directory.argtypes = [_f64p, C.c_int32, C.c_int32, _u64p, _i32p, C.c_int64]
@@ -79,15 +83,22 @@ def search_1d_sampled(X, Y, sample, side=SIDE_LT):
     return out
 
 
-def search_interp_2d(R, T, F, Y2):
-    """Per (rho, T) pair: the two lower-bound indices and the bilinear value."""
+def search_interp_2d(R, T, F, Y2, extrap=0, logspace=0):
+    """Per (rho, T) pair: the two lower-bound indices and the bilinear value.
+    extrap=1: linear extrapolation (no weight clamp); logspace=1: weights in
+    log axis coordinates (reading R6 of the C source)."""
     R, T, F, Y2 = _f64(R), _f64(T), _f64(F), _f64(Y2).reshape(-1)
     assert F.size == R.shape[0] * T.shape[0]
     m = Y2.shape[0] // 2
     idx = np.empty(2 * m, dtype=np.int32)
     val = np.empty(m, dtype=np.float64)
-    lib().oracle_search_interp_2d(_p(R, _f64p), R.shape[0], _p(T, _f64p), T.shape[0], _p(F, _f64p),
-                                  _p(Y2, _f64p), m, _p(idx, _i32p), _p(val, _f64p))
+    if extrap or logspace:
+        lib().oracle_search_interp_2d_opts(_p(R, _f64p), R.shape[0], _p(T, _f64p), T.shape[0], _p(F, _f64p),
+                                           _p(Y2, _f64p), m, int(extrap), int(logspace), _p(idx, _i32p),
+                                           _p(val, _f64p))
+    else:
+        lib().oracle_search_interp_2d(_p(R, _f64p), R.shape[0], _p(T, _f64p), T.shape[0], _p(F, _f64p),
+                                      _p(Y2, _f64p), m, _p(idx, _i32p), _p(val, _f64p))
     return idx.reshape(m, 2), val
 
 
@@ -113,16 +124,16 @@ def search_1d_batched(X_off, X, Y_off, Y, side=SIDE_LT):
     return out
 
 
-def search_interp_2d_batched(R_off, R, T_off, T, F_off, F, Y_off, Y2):
+def search_interp_2d_batched(R_off, R, T_off, T, F_off, F, Y_off, Y2, extrap=0, logspace=0):
     offs = [np.ascontiguousarray(o, dtype=np.int64) for o in (R_off, T_off, F_off, Y_off)]
     R, T, F, Y2 = _f64(R), _f64(T), _f64(F), _f64(Y2).reshape(-1)
     m = Y2.shape[0] // 2
     idx = np.empty(2 * m, dtype=np.int32)
     val = np.empty(m, dtype=np.float64)
-    lib().oracle_search_interp_2d_batched(offs[0].shape[0] - 1, _p(offs[0], _i64p), _p(R, _f64p),
-                                          _p(offs[1], _i64p), _p(T, _f64p), _p(offs[2], _i64p),
-                                          _p(F, _f64p), _p(offs[3], _i64p), _p(Y2, _f64p),
-                                          _p(idx, _i32p), _p(val, _f64p))
+    lib().oracle_search_interp_2d_batched_opts(offs[0].shape[0] - 1, _p(offs[0], _i64p), _p(R, _f64p),
+                                               _p(offs[1], _i64p), _p(T, _f64p), _p(offs[2], _i64p),
+                                               _p(F, _f64p), _p(offs[3], _i64p), _p(Y2, _f64p),
+                                               int(extrap), int(logspace), _p(idx, _i32p), _p(val, _f64p))
     return idx.reshape(m, 2), val
 
 

@@ -27,6 +27,12 @@
  *       bilinear in linear coordinates on cell c = min(i, n-2) of each axis,
  *       with weights clamped to [0,1] and the convex form
  *       (1-w)((1-u)F00 + u F01) + w((1-u)F10 + u F11).
+ *   R6  Interpolation options (the paper is silent; EOSPAC-style table
+ *       libraries offer both): extrap 1 drops the clamp of R4 (linear
+ *       extrapolation from the edge cell); logspace 1 takes the weights in
+ *       natural-log axis coordinates, w = (ln x - ln X[c]) / (ln X[c+1] -
+ *       ln X[c]), with C's log (so x = 0 gives -inf and x < 0 NaN, which the
+ *       clamp and R2 then treat like any other value).
  *   R5  The exponent hash of Sec. 3.5 is taken as the top bits of an
  *       order-preserving integer image of the double; with a shift of 52 on
  *       positive doubles it is exactly the IEEE-754 base-2 exponent.  The
@@ -91,15 +97,23 @@ static double clamp01(double w) {
   return w;                          /* NaN passes through (reading R2) */
 }
 
-static void interp_one(const double* R, int32_t nr, const double* T, int32_t nt,
-                       const double* F, double rho, double tem,
-                       int32_t* ir_out, int32_t* it_out, double* v_out) {
+/* Weight of coordinate x in cell [X[c], X[c+1]] (readings R4 and R6). */
+static double axis_weight(const double* X, int32_t c, double x, int extrap, int logspace) {
+  double w;
+  if (logspace) w = (log(x) - log(X[c])) / (log(X[c + 1]) - log(X[c]));
+  else w = (x - X[c]) / (X[c + 1] - X[c]);
+  return extrap ? w : clamp01(w);
+}
+
+static void interp_one_opts(const double* R, int32_t nr, const double* T, int32_t nt,
+                            const double* F, double rho, double tem, int extrap, int logspace,
+                            int32_t* ir_out, int32_t* it_out, double* v_out) {
   int32_t ir = lower_bound_index(R, nr, rho, 0);
   int32_t it = lower_bound_index(T, nt, tem, 0);
   int32_t cr = ir < nr - 2 ? ir : nr - 2;
   int32_t ct = it < nt - 2 ? it : nt - 2;
-  double wr = clamp01((rho - R[cr]) / (R[cr + 1] - R[cr]));
-  double wt = clamp01((tem - T[ct]) / (T[ct + 1] - T[ct]));
+  double wr = axis_weight(R, cr, rho, extrap, logspace);
+  double wt = axis_weight(T, ct, tem, extrap, logspace);
   double f00 = F[(int64_t)cr * nt + ct];
   double f01 = F[(int64_t)cr * nt + ct + 1];
   double f10 = F[(int64_t)(cr + 1) * nt + ct];
@@ -109,6 +123,22 @@ static void interp_one(const double* R, int32_t nr, const double* T, int32_t nt,
   *ir_out = ir;
   *it_out = it;
   *v_out = (1.0 - wr) * lo_row + wr * hi_row;
+}
+
+static void interp_one(const double* R, int32_t nr, const double* T, int32_t nt,
+                       const double* F, double rho, double tem,
+                       int32_t* ir_out, int32_t* it_out, double* v_out) {
+  interp_one_opts(R, nr, T, nt, F, rho, tem, 0, 0, ir_out, it_out, v_out);
+}
+
+/* The 2D lookup with the interpolation options of reading R6. */
+void oracle_search_interp_2d_opts(const double* R, int32_t nr, const double* T, int32_t nt,
+                                  const double* F, const double* Y2, int64_t m,
+                                  int32_t extrap, int32_t logspace,
+                                  int32_t* lowbounds2, double* values) {
+  for (int64_t i = 0; i < m; ++i)
+    interp_one_opts(R, nr, T, nt, F, Y2[2 * i], Y2[2 * i + 1], extrap, logspace,
+                    &lowbounds2[2 * i], &lowbounds2[2 * i + 1], &values[i]);
 }
 
 void oracle_search_interp_2d(const double* R, int32_t nr, const double* T, int32_t nt,
@@ -145,20 +175,31 @@ void oracle_search_1d_batched(int32_t ntables, const int64_t* X_off, const doubl
   }
 }
 
+void oracle_search_interp_2d_batched_opts(int32_t ntables,
+                                          const int64_t* R_off, const double* R,
+                                          const int64_t* T_off, const double* T,
+                                          const int64_t* F_off, const double* F,
+                                          const int64_t* Y_off, const double* Y2,
+                                          int32_t extrap, int32_t logspace,
+                                          int32_t* lowbounds2, double* values) {
+  for (int32_t k = 0; k < ntables; ++k) {
+    int32_t nr = (int32_t)(R_off[k + 1] - R_off[k]);
+    int32_t nt = (int32_t)(T_off[k + 1] - T_off[k]);
+    int64_t y0 = Y_off[k];
+    oracle_search_interp_2d_opts(R + R_off[k], nr, T + T_off[k], nt, F + F_off[k],
+                                 Y2 + 2 * y0, Y_off[k + 1] - y0, extrap, logspace,
+                                 lowbounds2 + 2 * y0, values + y0);
+  }
+}
+
 void oracle_search_interp_2d_batched(int32_t ntables,
                                      const int64_t* R_off, const double* R,
                                      const int64_t* T_off, const double* T,
                                      const int64_t* F_off, const double* F,
                                      const int64_t* Y_off, const double* Y2,
                                      int32_t* lowbounds2, double* values) {
-  for (int32_t k = 0; k < ntables; ++k) {
-    int32_t nr = (int32_t)(R_off[k + 1] - R_off[k]);
-    int32_t nt = (int32_t)(T_off[k + 1] - T_off[k]);
-    int64_t y0 = Y_off[k];
-    oracle_search_interp_2d(R + R_off[k], nr, T + T_off[k], nt, F + F_off[k],
-                            Y2 + 2 * y0, Y_off[k + 1] - y0,
-                            lowbounds2 + 2 * y0, values + y0);
-  }
+  oracle_search_interp_2d_batched_opts(ntables, R_off, R, T_off, T, F_off, F, Y_off, Y2, 0, 0,
+                                       lowbounds2, values);
 }
 
 /* ------------------------------------------------------------------------ */

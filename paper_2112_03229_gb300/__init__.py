@@ -140,9 +140,16 @@ def search_1d(X: torch.Tensor, Y: torch.Tensor, out: torch.Tensor | None = None,
     return out
 
 
-def search_interp_2d(R, T, F, Y2, idx=None, val=None, algo="auto", stat=None, stream=None, fp64=False):
+class InterpOpts(C.Structure):
+    _fields_ = [("algo", C.c_int32), ("extrap", C.c_int32), ("logspace", C.c_int32), ("fp64", C.c_int32)]
+
+
+def search_interp_2d(R, T, F, Y2, idx=None, val=None, algo="auto", stat=None, stream=None, fp64=False,
+                     extrap=False, logspace=False):
     """ss_search_interp_2d: per (rho, T) pair the index pair and the bilinear value.
-    fp64=True calls ss_search_interp_2d_fp64 (fp64 weights and blend)."""
+    fp64=True calls ss_search_interp_2d_fp64 (fp64 weights and blend); extrap /
+    logspace select linear extrapolation / log-coordinate weights
+    (ss_search_interp_2d_ex)."""
     m = Y2.numel() // 2
     if F.numel() != R.numel() * T.numel():
         raise ValueError("F must hold len(R) * len(T) values")
@@ -150,6 +157,17 @@ def search_interp_2d(R, T, F, Y2, idx=None, val=None, algo="auto", stat=None, st
         idx = torch.empty((m, 2), dtype=torch.int32, device=Y2.device)
     if val is None:
         val = torch.empty((m,), dtype=torch.float64, device=Y2.device)
+    if extrap or logspace:
+        L = lib()
+        L.ss_search_interp_2d_ex.argtypes = [_vp, _i32, _vp, _i32, _vp, _vp, _i64, _vp, _vp,
+                                             C.POINTER(InterpOpts), _vp, _vp]
+        L.ss_search_interp_2d_ex.restype = _i32
+        o = InterpOpts(_algo(algo), int(bool(extrap)), int(bool(logspace)), int(bool(fp64)))
+        _check(L.ss_search_interp_2d_ex(_dev(R, torch.float64, "R"), R.numel(), _dev(T, torch.float64, "T"),
+                                        T.numel(), _dev(F, torch.float64, "F"), _dev(Y2, torch.float64, "Y2"), m,
+                                        _dev(idx, torch.int32, "idx"), _dev(val, torch.float64, "val"),
+                                        C.byref(o), _statp(stat), _stream(stream)))
+        return idx, val
     fn = lib().ss_search_interp_2d_fp64 if fp64 else lib().ss_search_interp_2d
     _check(fn(_dev(R, torch.float64, "R"), R.numel(), _dev(T, torch.float64, "T"), T.numel(),
                                      _dev(F, torch.float64, "F"), _dev(Y2, torch.float64, "Y2"), m,
@@ -195,7 +213,7 @@ BLOB_ALGOS = ["bucket", "binary", "ballot8", "ballot16", "ballot32", "spline", "
 class PlanOpts(C.Structure):
     _fields_ = [("side", C.c_int32), ("algo", C.c_int32), ("model", C.c_int32), ("autotune", C.c_int32),
                 ("tile", C.c_int32), ("mlp_epochs", C.c_int32), ("mlp_lr", C.c_float), ("dir_cap", C.c_int32),
-                ("seed", C.c_uint64), ("tune_cache", C.c_char_p)]
+                ("seed", C.c_uint64), ("tune_cache", C.c_char_p), ("extrap", C.c_int32), ("logspace", C.c_int32)]
 
 
 class PlanInfo(C.Structure):
@@ -232,7 +250,7 @@ def _offsets(off):
 
 
 def plan_opts(side=SIDE_LT, algo="auto", model="none", autotune=False, tile=0, mlp_epochs=None, mlp_lr=0.0,
-              dir_cap=0, seed=0x5EED, tune_cache=None) -> PlanOpts:
+              dir_cap=0, seed=0x5EED, tune_cache=None, extrap=False, logspace=False) -> PlanOpts:
     o = PlanOpts()
     L = lib()
     if not hasattr(L, "_plan_sigs"):
@@ -251,6 +269,8 @@ def plan_opts(side=SIDE_LT, algo="auto", model="none", autotune=False, tile=0, m
     o.dir_cap = dir_cap
     o.seed = seed
     o.tune_cache = tune_cache.encode() if tune_cache else None
+    o.extrap = int(bool(extrap))
+    o.logspace = int(bool(logspace))
     return o
 
 

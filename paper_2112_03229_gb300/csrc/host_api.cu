@@ -24,7 +24,7 @@ ss_status search_1d(const double* X, int32_t n, const double* Y, int64_t m, int3
                     int32_t algo, ss_devstat* stat, cudaStream_t stream, int dir_cap_override, int ballot_g);
 ss_status search_interp_2d(const double* R, int32_t nr, const double* T, int32_t nt, const double* F,
                            const double* Y2, int64_t m, int32_t* idx, double* val, int32_t algo, int force_fp64,
-                           ss_devstat* stat, cudaStream_t stream);
+                           ss_devstat* stat, cudaStream_t stream, int extrap, int logspace);
 
 namespace {
 
@@ -145,7 +145,7 @@ extern "C" ss_status ss_search_interp_2d_host(const double* R, int32_t nr, const
   SS_CHECK_CUDA(cudaMemcpyAsync(dT, T, (size_t)nt * 8, cudaMemcpyHostToDevice, w->st[0]));
   SS_CHECK_CUDA(cudaMemcpyAsync(dF, F, (size_t)nr * nt * 8, cudaMemcpyHostToDevice, w->st[0]));
   if (direct) {
-    if (ss_status st = search_interp_2d(dR, nr, dT, nt, dF, mY, m, mI, mV, algo, 0, nullptr, w->st[0])) return st;
+    if (ss_status st = search_interp_2d(dR, nr, dT, nt, dF, mY, m, mI, mV, algo, 0, nullptr, w->st[0], 0, 0)) return st;
     SS_CHECK_CUDA(cudaStreamSynchronize(w->st[0]));
     return SS_OK;
   }
@@ -160,7 +160,7 @@ extern "C" ss_status ss_search_interp_2d_host(const double* R, int32_t nr, const
     int32_t* dI = reinterpret_cast<int32_t*>(b + cin);
     double* dV = reinterpret_cast<double*>(b + cin + cidx);
     SS_CHECK_CUDA(cudaMemcpyAsync(dY, Y2 + 2 * off, (size_t)cnt * 16, cudaMemcpyHostToDevice, s));
-    if (ss_status st = search_interp_2d(dR, nr, dT, nt, dF, dY, cnt, dI, dV, algo, 0, nullptr, s)) return st;
+    if (ss_status st = search_interp_2d(dR, nr, dT, nt, dF, dY, cnt, dI, dV, algo, 0, nullptr, s, 0, 0)) return st;
     SS_CHECK_CUDA(cudaMemcpyAsync(lowbounds2 + 2 * off, dI, (size_t)cnt * 8, cudaMemcpyDeviceToHost, s));
     SS_CHECK_CUDA(cudaMemcpyAsync(values + off, dV, (size_t)cnt * 8, cudaMemcpyDeviceToHost, s));
   }

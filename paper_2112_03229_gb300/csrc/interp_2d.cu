@@ -15,6 +15,11 @@
 // Both agree with an fp64 evaluation of the formula to well within 1e-12
 // relative for positive grids.
 //
+// Interpolation options: linear extrapolation (no weight clamp) sends the
+// pairs outside either axis to the fp64 path with unclamped weights; log
+// coordinates (weights (ln x - ln X[c]) / (ln X[c+1] - ln X[c]), per-entry
+// logarithms staged with the axis) run every pair on the fp64 path.
+//
 // The value grid stays in global memory (L2-resident for the sizes of
 // interest); axes, bucket directories and per-cell data live in shared memory.
 #include <algorithm>
@@ -29,7 +34,9 @@ constexpr int kMaxAxis2D = 4096;   // largest axis staged whole with its per-cel
 struct Axis2D {                    // shared-memory offsets of one axis
   Layout1D lay;
   int cells;                       // CellW[n-1]: exact weight numerators' data and scale
-  int rg;                          // double[n-1]: 1 / (X[c+1] - X[c]) for the fp64 path (X[c] read from global)
+  int rg;                          // double[n-1]: 1 / (X[c+1] - X[c]) for the fp64 path (X[c] read from global);
+                                   // in log coordinates 1 / (ln X[c+1] - ln X[c])
+  int lx;                          // double[n]: ln X[j] (log coordinates only, else -1)
   int aux;                         // AxisAux
 };
 
@@ -52,6 +59,8 @@ struct Args2D {
   int64_t np2;      // pairs in the vector body, in units of 2 pairs
   int algo;         // SS_ALGO_BUCKET or SS_ALGO_BINARY
   int force_fp64;   // 1: skip the float-float path
+  int extrap;       // 1: linear extrapolation (weights not clamped)
+  int logspace;     // 1: weights in natural-log axis coordinates (fp64 path)
   int grid_smem;    // offset of the float-float grid in shared memory (-1: grid stays in global memory)
   Axis2D ar, at;
   ss_devstat* stat;
@@ -61,11 +70,19 @@ struct Args2D {
 static __device__ void stage_cells(const double* __restrict__ X, int n, const Axis2D& ax, unsigned char* smem) {
   CellW* cells = reinterpret_cast<CellW*>(smem + ax.cells);
   double* rg = reinterpret_cast<double*>(smem + ax.rg);
+  double* lx = ax.lx >= 0 ? reinterpret_cast<double*>(smem + ax.lx) : nullptr;
   AxisAux& aux = *reinterpret_cast<AxisAux*>(smem + ax.aux);
   bool ok = true;
   for (int c = threadIdx.x; c < n - 1; c += blockDim.x) {
     const double a = __ldg(X + c), b = __ldg(X + c + 1);
-    rg[c] = 1.0 / (b - a);
+    if (lx != nullptr) {
+      const double la = log(a), lb = log(b);
+      lx[c] = la;
+      if (c == n - 2) lx[n - 1] = lb;
+      rg[c] = 1.0 / (lb - la);
+    } else {
+      rg[c] = 1.0 / (b - a);
+    }
     CellW w;
     ok &= make_cell(a, b, w);
     cells[c] = w;
@@ -87,6 +104,8 @@ struct AxisView {
   const CellW* cells;
   const double* x;           // the axis in global memory
   const double* rg;
+  const double* lx;          // ln X[j] (log coordinates), else nullptr
+  int extrap;                // 1: weights not clamped
   int shift, nb, T, D, n;
   uint64_t base, k0;
 };
@@ -100,6 +119,8 @@ __device__ __forceinline__ AxisView view_of(const Axis2D& ax, const unsigned cha
   v.dir = ax.lay.dir >= 0 ? reinterpret_cast<const int*>(smem + ax.lay.dir) : nullptr;
   v.cells = reinterpret_cast<const CellW*>(smem + ax.cells);
   v.rg = reinterpret_cast<const double*>(smem + ax.rg);
+  v.lx = ax.lx >= 0 ? reinterpret_cast<const double*>(smem + ax.lx) : nullptr;
+  v.extrap = 0;
   v.shift = h.shift;
   v.nb = h.nb;
   v.T = h.occ > 0 ? 32 - __clz(h.occ) : 0;
@@ -123,6 +144,13 @@ __device__ __forceinline__ Weights axis_weights_ff(const AxisView& a, int i, int
   if (i >= a.n - 1) return {{1.0f, 0.0f}, {0.0f, 0.0f}};          // above the last entry
   if (i == 0 && k <= a.k0) return {{0.0f, 0.0f}, {1.0f, 0.0f}};   // at or below the first entry
   return cell_weights(u, a.cells[c]);
+}
+
+// fp64 weight of coordinate x in cell c: linear or log coordinates, clamped
+// to [0, 1] unless the axis extrapolates.
+__device__ __forceinline__ double weight64(const AxisView& a, int c, double x) {
+  const double w = a.lx != nullptr ? (log(x) - a.lx[c]) * a.rg[c] : (x - __ldg(a.x + c)) * a.rg[c];
+  return a.extrap ? w : clamp01(w);
 }
 
 // Convex blend in fp64 (fallback path of a pair).
@@ -160,10 +188,18 @@ __device__ __forceinline__ void lookup_pair(const AxisView& vr, const AxisView& 
   if (!FF) {
     const double* f = F + o;
     const double f00 = __ldg(f), f01 = __ldg(f + 1), f10 = __ldg(f + nt), f11 = __ldg(f + nt + 1);
-    const double wr = clamp01((rho - __ldg(vr.x + cr)) * vr.rg[cr]);
-    const double wt = clamp01((tem - __ldg(vt.x + ct)) * vt.rg[ct]);
-    v = blend64(wr, wt, f00, f01, f10, f11);
+    v = blend64(weight64(vr, cr, rho), weight64(vt, ct, tem), f00, f01, f10, f11);
     return;
+  }
+  if (vr.extrap) {
+    // linear extrapolation: a pair outside either axis takes the fp64 path with unclamped weights
+    const bool outside = (ir >= vr.n - 1) | (ir == 0 && kr <= vr.k0) | (it >= vt.n - 1) | (it == 0 && kt <= vt.k0);
+    if (outside) {
+      const double* f = F + o;
+      v = blend64(weight64(vr, cr, rho), weight64(vt, ct, tem), __ldg(f), __ldg(f + 1), __ldg(f + nt),
+                  __ldg(f + nt + 1));
+      return;
+    }
   }
   ff a00, a01, a10, a11;
   bool ok;
@@ -241,9 +277,10 @@ __device__ __forceinline__ void interp_body(const Args2D& a, unsigned char* smem
   AxisView vr = view_of(a.ar, smem), vt = view_of(a.at, smem);
   vr.x = a.R;
   vt.x = a.T;
+  vr.extrap = vt.extrap = a.extrap;
   const TableHdr& hr = *reinterpret_cast<const TableHdr*>(smem + a.ar.lay.hdr);
   const TableHdr& ht = *reinterpret_cast<const TableHdr*>(smem + a.at.lay.hdr);
-  const bool ff = !a.force_fp64 && reinterpret_cast<const AxisAux*>(smem + a.ar.aux)->ffok &&
+  const bool ff = !a.force_fp64 && !a.logspace && reinterpret_cast<const AxisAux*>(smem + a.ar.aux)->ffok &&
                   reinterpret_cast<const AxisAux*>(smem + a.at.aux)->ffok;
   const int mode = a.algo == SS_ALGO_BINARY ? 2 : (hr.occ <= 1 && ht.occ <= 1) ? 0 : (hr.occ <= 2 && ht.occ <= 2) ? 3 : 1;
   int nans;
@@ -260,7 +297,7 @@ __device__ __forceinline__ void interp_body(const Args2D& a, unsigned char* smem
     if ((threadIdx.x & 31) == 0 && nans) atomicAdd(&a.stat->nan_targets, (unsigned long long)nans);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       if (hr.bad | ht.bad) atomicOr(&a.stat->flags, SS_FLAG_NOT_SORTED);
-      if (!ff && !a.force_fp64) atomicOr(&a.stat->flags, SS_FLAG_BAD_VALUE);
+      if (!ff && !a.force_fp64 && !a.logspace) atomicOr(&a.stat->flags, SS_FLAG_BAD_VALUE);
     }
   }
 }
@@ -281,7 +318,7 @@ __global__ void __launch_bounds__(kSgThreads, 1) k_search_interp_2d_sg(Args2D a)
 
 int default_dir_cap(int n);
 
-static Axis2D make_axis(int n, int algo, int offset) {
+static Axis2D make_axis(int n, int algo, int offset, bool logspace) {
   Axis2D ax{};
   const bool bucket = algo == SS_ALGO_BUCKET;
   ax.lay = make_layout_1d(n, bucket, !bucket, bucket ? default_dir_cap(n) : 0, offset);
@@ -289,6 +326,7 @@ static Axis2D make_axis(int n, int algo, int offset) {
   auto take = [&](int bytes) { int o = off; off += (bytes + 15) & ~15; return o; };
   ax.cells = take((n - 1) * (int)sizeof(CellW));
   ax.rg = take((n - 1) * 8);
+  ax.lx = logspace ? take(n * 8) : -1;
   ax.aux = take((int)sizeof(AxisAux));
   ax.lay.bytes = off;   // end of this axis' region
   return ax;
@@ -296,7 +334,7 @@ static Axis2D make_axis(int n, int algo, int offset) {
 
 ss_status search_interp_2d(const double* R, int32_t nr, const double* T, int32_t nt, const double* F,
                            const double* Y2, int64_t m, int32_t* idx, double* val, int32_t algo, int force_fp64,
-                           ss_devstat* stat, cudaStream_t stream) {
+                           ss_devstat* stat, cudaStream_t stream, int extrap, int logspace) {
   if (R == nullptr || T == nullptr || F == nullptr || (m > 0 && (Y2 == nullptr || idx == nullptr || val == nullptr)))
     return fail(SS_EINVAL, "ss_search_interp_2d: null pointer");
   if (nr < 2 || nt < 2) return fail(SS_EINVAL, "ss_search_interp_2d: each axis needs >= 2 entries");
@@ -310,9 +348,11 @@ ss_status search_interp_2d(const double* R, int32_t nr, const double* T, int32_t
   if (m == 0) return SS_OK;
   Args2D a{};
   a.R = R; a.nr = nr; a.T = T; a.nt = nt; a.F = F; a.Y2 = Y2; a.m = m; a.idx = idx; a.val = val;
-  a.algo = algo; a.force_fp64 = force_fp64; a.stat = stat;
-  a.ar = make_axis(nr, algo, 0);
-  a.at = make_axis(nt, algo, a.ar.lay.bytes);
+  a.algo = algo; a.force_fp64 = force_fp64 | logspace; a.stat = stat;
+  a.extrap = extrap ? 1 : 0;
+  a.logspace = logspace ? 1 : 0;
+  a.ar = make_axis(nr, algo, 0, logspace);
+  a.at = make_axis(nt, algo, a.ar.lay.bytes, logspace);
   const int smem = a.at.lay.bytes;
   // vector body: two pairs per item, needs 16-byte alignment of pair, index pair-of-pairs and value pair
   a.head = m;
@@ -324,7 +364,7 @@ ss_status search_interp_2d(const double* R, int32_t nr, const double* T, int32_t
   if (smem > max_smem_optin()) return fail(SS_EUNSUPPORTED, "ss_search_interp_2d: axes too large for shared memory");
   // stage the grid too when it fits beside the axes (and the float-float path is not disabled)
   const int64_t gbytes = (int64_t)nr * nt * 8;
-  const bool sg = !force_fp64 && smem + gbytes + 16 <= (int64_t)max_smem_optin();
+  const bool sg = !a.force_fp64 && smem + gbytes + 16 <= (int64_t)max_smem_optin();
   a.grid_smem = sg ? ((smem + 15) & ~15) : -1;
   const int threads = sg ? kSgThreads : kNumThreads;
   const int smem_all = sg ? a.grid_smem + (int)gbytes : smem;
@@ -349,7 +389,17 @@ extern "C" {
 ss_status ss_search_interp_2d(const double* R, int32_t nr, const double* T, int32_t nt, const double* F,
                               const double* Y2, int64_t m, int32_t* lowbounds2, double* values, int32_t algo,
                               ss_devstat* stat, cudaStream_t stream) {
-  return ss::search_interp_2d(R, nr, T, nt, F, Y2, m, lowbounds2, values, algo, 0, stat, stream);
+  return ss::search_interp_2d(R, nr, T, nt, F, Y2, m, lowbounds2, values, algo, 0, stat, stream, 0, 0);
+}
+
+ss_status ss_search_interp_2d_ex(const double* R, int32_t nr, const double* T, int32_t nt, const double* F,
+                                 const double* Y2, int64_t m, int32_t* lowbounds2, double* values,
+                                 const ss_interp_opts* opts, ss_devstat* stat, cudaStream_t stream) {
+  const ss_interp_opts o = opts != nullptr ? *opts : ss_interp_opts{SS_ALGO_AUTO, 0, 0, 0};
+  if ((o.extrap != 0 && o.extrap != 1) || (o.logspace != 0 && o.logspace != 1) || (o.fp64 != 0 && o.fp64 != 1))
+    return ss::fail(SS_EINVAL, "ss_search_interp_2d_ex: extrap, logspace and fp64 must be 0 or 1");
+  return ss::search_interp_2d(R, nr, T, nt, F, Y2, m, lowbounds2, values, o.algo, o.fp64, stat, stream, o.extrap,
+                              o.logspace);
 }
 
 // Same lookup with the float-float path disabled (fp64 weights and blend);
@@ -357,7 +407,7 @@ ss_status ss_search_interp_2d(const double* R, int32_t nr, const double* T, int3
 ss_status ss_search_interp_2d_fp64(const double* R, int32_t nr, const double* T, int32_t nt, const double* F,
                                    const double* Y2, int64_t m, int32_t* lowbounds2, double* values, int32_t algo,
                                    ss_devstat* stat, cudaStream_t stream) {
-  return ss::search_interp_2d(R, nr, T, nt, F, Y2, m, lowbounds2, values, algo, 1, stat, stream);
+  return ss::search_interp_2d(R, nr, T, nt, F, Y2, m, lowbounds2, values, algo, 1, stat, stream, 0, 0);
 }
 
 }  // extern "C"

@@ -83,6 +83,8 @@ struct BatchArgs2D {
   const double* grid64;         // the caller's fp64 values, row-major (fallback)
   const int64_t* grid_off;      // [ntables] value offsets of grid64
   const int64_t* cell_off;      // [ntables] cell offsets of cells (in cells)
+  int extrap;                   // 1: linear extrapolation (pairs outside an axis in fp64, unclamped)
+  int logspace;                 // 1: weights in natural-log coordinates (every pair in fp64)
   const Tile* tiles;
   int ntiles;
   int* counter;

@@ -106,10 +106,19 @@ constexpr uint64_t kKeyNegInf = 0x0010000000000000ull;   // image of -inf; NaNs 
 
 // One pair: the two axis counts (CR, CT: the searches the tile dispatched),
 // four gathers from the grid, and the blend.
+// fp64 weight of coordinate x in cell c for the interpolation options:
+// linear or natural-log coordinates, clamped to [0, 1] unless extrapolating.
+__device__ __forceinline__ double option_weight(const StagedView& v, int c, double x, int extrap, int logspace) {
+  const double a = entry_value(v, c), b = entry_value(v, c + 1);
+  const double w = logspace ? (log(x) - log(a)) / (log(b) - log(a)) : (x - a) / (b - a);
+  return extrap ? w : (w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w));
+}
+
 template <class CR, class CT>
 __device__ __forceinline__ void pair_2d(const StagedView& vr, const StagedView& vt, const float4* __restrict__ G,
                                         const double* __restrict__ G64, double rho, double tem, int& ir, int& it,
-                                        double& v, int& nans, CR&& count_r, CT&& count_t) {
+                                        double& v, int& nans, CR&& count_r, CT&& count_t, int extrap = 0,
+                                        int logspace = 0) {
   const uint64_t kr = order_key(rho), kt = order_key(tem);
   const bool nan = (kr < kKeyNegInf) | (kt < kKeyNegInf);
   nans += (kr < kKeyNegInf) + (kt < kKeyNegInf);
@@ -121,6 +130,17 @@ __device__ __forceinline__ void pair_2d(const StagedView& vr, const StagedView& 
   const float4 q0 = __ldg(G + 2 * cell), q1 = __ldg(G + 2 * cell + 1);
   const float2 g00 = make_float2(q0.x, q0.y), g01 = make_float2(q0.z, q0.w);
   const float2 g10 = make_float2(q1.x, q1.y), g11 = make_float2(q1.z, q1.w);
+  if (logspace | extrap) {
+    const bool outside = (ir >= vr.h.n - 1) | (ir == 0 && kr <= vr.h.k0) | (it >= nt - 1) | (it == 0 && kt <= vt.h.k0);
+    if (logspace | outside) {
+      const int64_t o = (int64_t)cr * nt + ct;
+      const double w1 = option_weight(vr, cr, rho, extrap, logspace), w2 = option_weight(vt, ct, tem, extrap, logspace);
+      const double lo = (1.0 - w2) * G64[o] + w2 * G64[o + 1];
+      const double hi = (1.0 - w2) * G64[o + nt] + w2 * G64[o + nt + 1];
+      v = (1.0 - w1) * lo + w1 * hi;
+      return;
+    }
+  }
   const Weights wr = axis_weights(vr, ir, cr, kr, rho);
   const Weights wt = axis_weights(vt, it, ct, kt, tem);
   if (nan) {
@@ -149,7 +169,8 @@ __device__ __forceinline__ void stream_pairs(const BatchArgs2D& a, const StagedV
   auto scalar = [&](int i) {
     int ir, it;
     double v;
-    pair_2d(vr, vt, G, G64, a.Y2[2 * (b + i)], a.Y2[2 * (b + i) + 1], ir, it, v, nans, count_r, count_t);
+    pair_2d(vr, vt, G, G64, a.Y2[2 * (b + i)], a.Y2[2 * (b + i) + 1], ir, it, v, nans, count_r, count_t, a.extrap,
+            a.logspace);
     a.idx[2 * (b + i)] = ir;
     a.idx[2 * (b + i) + 1] = it;
     a.val[b + i] = v;
@@ -164,8 +185,8 @@ __device__ __forceinline__ void stream_pairs(const BatchArgs2D& a, const StagedV
     const double2 p0 = ld_stream(Y + 2 * g), p1 = ld_stream(Y + 2 * g + 1);
     int i0, j0, i1, j1;
     double v0, v1;
-    pair_2d(vr, vt, G, G64, p0.x, p0.y, i0, j0, v0, nans, count_r, count_t);
-    pair_2d(vr, vt, G, G64, p1.x, p1.y, i1, j1, v1, nans, count_r, count_t);
+    pair_2d(vr, vt, G, G64, p0.x, p0.y, i0, j0, v0, nans, count_r, count_t, a.extrap, a.logspace);
+    pair_2d(vr, vt, G, G64, p1.x, p1.y, i1, j1, v1, nans, count_r, count_t, a.extrap, a.logspace);
     st_stream(I4 + g, make_int4(i0, j0, i1, j1));
     st_stream(V2 + g, make_double2(v0, v1));
   }
@@ -338,8 +359,9 @@ ss_status plan_build_2d(ss_plan* p, const double* R, const double* T, const doub
     unsigned bad[2];
     SS_CHECK_CUDA(cudaMemcpy(bad, dBad, 8, cudaMemcpyDeviceToHost));
     if (bad[0]) return fail(SS_ENOTSORTED, "ss_plan_create_2d: an axis is not strictly increasing (or holds NaN)");
-    if (bad[1]) {
-      // some values need the fp64 blend: keep a copy of the caller's grids
+    if (bad[1] || o.extrap || o.logspace) {
+      // some values need the fp64 blend (values outside the float-float
+      // range, or the interpolation options): keep a copy of the caller's grids
       SS_CHECK_CUDA(cudaMalloc(&p->d_grid64, gcount * sizeof(double)));
       SS_CHECK_CUDA(cudaMemcpy(p->d_grid64, F, gcount * sizeof(double), cudaMemcpyDeviceToDevice));
       p->device_bytes += gcount * (int64_t)sizeof(double);
@@ -371,6 +393,8 @@ extern "C" ss_status ss_plan_create_2d(ss_plan** out, int32_t ntables, const int
   ss_plan_opts_default(&o);
   if (opts_in) o = *opts_in;
   if (o.side != SS_SIDE_LT) return fail(SS_EINVAL, "ss_plan_create_2d: the 2D lookup uses side SS_SIDE_LT");
+  if ((o.extrap != 0 && o.extrap != 1) || (o.logspace != 0 && o.logspace != 1))
+    return fail(SS_EINVAL, "ss_plan_create_2d: extrap and logspace must be 0 or 1");
   if (o.model < SS_MODEL_NONE || o.model > SS_MODEL_LOGHASH || o.algo == SS_ALGO_BALLOT || o.algo == SS_ALGO_BRANCHY ||
       o.algo < 0 || o.algo > SS_ALGO_BALLOT)
     return fail(SS_EINVAL, "ss_plan_create_2d: algo must be auto, binary or bucket");

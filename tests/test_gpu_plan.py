@@ -1,5 +1,6 @@
 """GPU parity of plans (prepared tables, learned proposals, persistent
 batched kernel, CUDA graph, autotuner, save/load) against the CPU oracle."""
+import ctypes
 import os
 import struct
 
@@ -8,6 +9,7 @@ import pytest
 import torch
 
 import oracle
+from paper_2112_03229_gb300 import PlanOpts
 from paper_2112_03229_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -158,7 +160,7 @@ def test_plan_not_sorted_rejected(ss):
 
 def _blob_headers(raw):
     """Parse a saved plan file: returns (positions of blob headers, blob data start)."""
-    pos = 8 + 4 * 3 + 48                      # magic, version/kind/ntables, options
+    pos = 8 + 4 * 3 + ctypes.sizeof(PlanOpts)  # magic, version/kind/ntables, options
     def vec(pos, fmt, size):
         n = struct.unpack_from("<q", raw, pos)[0]
         return list(struct.unpack_from("<%d%s" % (n, fmt), raw, pos + 8)), pos + 8 + n * size
@@ -286,6 +288,45 @@ def test_plan_2d_batched(ss, model, coherent):
     rel = np.abs(val.cpu().numpy() - wv) / np.abs(wv)
     assert rel.max() <= REL_TOL
     assert ss.read_stat(stat).flags == 0
+
+
+@pytest.mark.parametrize("extrap,logspace", [(1, 0), (0, 1), (1, 1)])
+def test_plan_2d_interpolation_options(ss, extrap, logspace):
+    """2D plans with linear extrapolation / log-coordinate weights: pairs
+    spread beyond the axes by up to a factor e^2 either way."""
+    b = wl.batched_2d(ntables=7, pairs_per_table=3001, seed=15)
+    rng = np.random.default_rng(16)
+    Y2 = b.Y2.numpy() * np.exp(rng.uniform(-2.0, 2.0, size=b.Y2.shape))
+    args = (b.R_off.numpy(), b.R.numpy(), b.T_off.numpy(), b.T.numpy(), b.F_off.numpy(), b.F.numpy(), b.Y_off.numpy())
+    wi, wv = oracle.search_interp_2d_batched(*args, Y2, extrap=extrap, logspace=logspace)
+    plan = ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), extrap=bool(extrap),
+                             logspace=bool(logspace))
+    m = Y2.shape[0]
+    idx = torch.empty((m, 2), dtype=torch.int32, device=DEV)
+    val = torch.empty(m, dtype=torch.float64, device=DEV)
+    plan.bind_2d(b.Y_off, torch.from_numpy(Y2).to(DEV), idx, val)
+    plan.execute()
+    np.testing.assert_array_equal(idx.cpu().numpy(), wi)
+    val = val.cpu().numpy()
+    for k in range(7):
+        r0, r1 = int(b.R_off[k]), int(b.R_off[k + 1])
+        t0, t1 = int(b.T_off[k]), int(b.T_off[k + 1])
+        f0, f1 = int(b.F_off[k]), int(b.F_off[k + 1])
+        y0, y1 = int(b.Y_off[k]), int(b.Y_off[k + 1])
+        R, T, F = b.R.numpy()[r0:r1], b.T.numpy()[t0:t1], b.F.numpy()[f0:f1]
+        nr, nt = len(R), len(T)
+        cr = np.minimum(wi[y0:y1, 0], nr - 2)
+        ct = np.minimum(wi[y0:y1, 1], nt - 2)
+        def w(X, c, x):
+            if logspace:
+                return np.abs((np.log(x) - np.log(X[c])) / (np.log(X[c + 1]) - np.log(X[c])))
+            return np.abs((x - X[c]) / (X[c + 1] - X[c]))
+        wr, wt = w(R, cr, Y2[y0:y1, 0]), w(T, ct, Y2[y0:y1, 1])
+        F2 = F.reshape(nr, nt)
+        lo = np.abs(1 - wt) * np.abs(F2[cr, ct]) + wt * np.abs(F2[cr, ct + 1])
+        hi = np.abs(1 - wt) * np.abs(F2[cr + 1, ct]) + wt * np.abs(F2[cr + 1, ct + 1])
+        scale = np.abs(1 - wr) * lo + wr * hi
+        assert (np.abs(val[y0:y1] - wv[y0:y1]) <= REL_TOL * scale).all()
 
 
 def test_plan_2d_save_load_and_autotune(ss, tmp_path):

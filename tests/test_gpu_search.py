@@ -226,6 +226,49 @@ def test_2d_affine_field_exact(ss):
 # ---------------------------------------------------------------- full sizes, sampled
 
 @pytest.mark.slow
+def option_scale(R, T, F, Y, idx, logspace):
+    """Per pair, the sum of |weight x corner| terms of the blend (unclamped
+    weights): the size of the numbers the value is formed from, against
+    which the 1e-12 bound is taken where extrapolation can cancel."""
+    nr, nt = len(R), len(T)
+    F2 = F.reshape(nr, nt)
+    cr = np.minimum(idx[:, 0], nr - 2)
+    ct = np.minimum(idx[:, 1], nt - 2)
+    def w(X, c, x):
+        if logspace:
+            return (np.log(x) - np.log(X[c])) / (np.log(X[c + 1]) - np.log(X[c]))
+        return (x - X[c]) / (X[c + 1] - X[c])
+    wr, wt = np.abs(w(R, cr, Y[:, 0])), np.abs(w(T, ct, Y[:, 1]))
+    lo = np.abs(1 - wt) * np.abs(F2[cr, ct]) + wt * np.abs(F2[cr, ct + 1])
+    hi = np.abs(1 - wt) * np.abs(F2[cr + 1, ct]) + wt * np.abs(F2[cr + 1, ct + 1])
+    return np.abs(1 - wr) * lo + wr * hi
+
+
+@pytest.mark.parametrize("extrap,logspace", [(1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("fp64", [False, True])
+def test_2d_interpolation_options(ss, extrap, logspace, fp64):
+    """Linear extrapolation and log-coordinate weights against the oracle:
+    indices exact, values within 1e-12 of the terms they are formed from,
+    with pairs spread to 8x beyond both axes."""
+    R, T, F, _ = wl.interp_2d(m=4, seed=21)
+    Y = wl.pairs_log_uniform(300_001, float(R[0]) / 8, float(R[-1]) * 8, float(T[0]) / 8, float(T[-1]) * 8,
+                             seed=22)
+    Rn, Tn, Fn, Yn = R.numpy(), T.numpy(), F.numpy(), Y.numpy()
+    wi, wv = oracle.search_interp_2d(Rn, Tn, Fn, Yn, extrap=extrap, logspace=logspace)
+    idx, val = ss.search_interp_2d(R.to(DEV), T.to(DEV), F.to(DEV), Y.to(DEV), fp64=fp64, extrap=bool(extrap),
+                                   logspace=bool(logspace))
+    idx, val = idx.cpu().numpy(), val.cpu().numpy()
+    np.testing.assert_array_equal(idx, wi)
+    scale = option_scale(Rn, Tn, Fn, Yn, wi, logspace)
+    err = np.abs(val - wv)
+    assert (err <= REL_TOL * scale).all(), err.max()
+    if extrap and not logspace:
+        # inside the grid nothing changes: the default lookup's values, bit for bit
+        inside = (Yn[:, 0] >= Rn[0]) & (Yn[:, 0] <= Rn[-1]) & (Yn[:, 1] >= Tn[0]) & (Yn[:, 1] <= Tn[-1])
+        _, dv = ss.search_interp_2d(R.to(DEV), T.to(DEV), F.to(DEV), Y.to(DEV), fp64=fp64)
+        np.testing.assert_array_equal(val[inside], dv.cpu().numpy()[inside])
+
+
 def test_1d_one_billion_sampled(ss):
     """The bench-size 1D run (1B targets, bucket search) checked at 2M sampled positions."""
     m = 1 << 30

@@ -269,6 +269,57 @@ def test_interp_nodes_bounds_and_clamp():
     assert np.all(np.isnan(v)) and idx[0, 0] == 0 and idx[1, 1] == 0
 
 
+def test_interp_linear_extrapolation_reproduces_affine():
+    """Reading R6, extrap=1: without the clamp, bilinear interpolation on the
+    edge cell continues the affine field a + b rho + c T + d rho T exactly
+    beyond the grid; inside the grid nothing changes."""
+    R = wl.log_spaced_table(30, 1e-3, 1e3, 0.1, seed=11).numpy()
+    T = wl.log_spaced_table(20, 1e-2, 1e2, 0.1, seed=12).numpy()
+    a, b, c, d = 3.0, 0.25, 1.5, 0.125
+    F = a + b * R[:, None] + c * T[None, :] + d * R[:, None] * T[None, :]
+    Y = wl.pairs_log_uniform(20_000, R[0] / 4, R[-1] * 4, T[0] / 4, T[-1] * 4, seed=13).numpy()
+    idx, val = oracle.search_interp_2d(R, T, F, Y, extrap=1)
+    want = a + b * Y[:, 0] + c * Y[:, 1] + d * Y[:, 0] * Y[:, 1]
+    scale = abs(a) + abs(b * Y[:, 0]) + abs(c * Y[:, 1]) + abs(d * Y[:, 0] * Y[:, 1])
+    assert (np.abs(val - want) <= 1e-12 * scale).all()
+    outside = (Y[:, 0] < R[0]) | (Y[:, 0] > R[-1]) | (Y[:, 1] < T[0]) | (Y[:, 1] > T[-1])
+    assert outside.sum() > 5000
+    _, clamped = oracle.search_interp_2d(R, T, F, Y)
+    np.testing.assert_array_equal(val[~outside], clamped[~outside])
+    assert (np.abs(clamped[outside] - want[outside]) > 1e-6 * scale[outside]).any()
+    np.testing.assert_array_equal(idx, oracle.search_interp_2d(R, T, F, Y)[0])
+
+
+def test_interp_log_space_reproduces_log_affine():
+    """Reading R6, logspace=1: weights in log coordinates reproduce a field
+    that is bilinear in (ln rho, ln T); nodes are exact; outside the grid the
+    clamp gives the edge value and extrap=1 continues the field."""
+    R = wl.log_spaced_table(30, 1e-3, 1e3, 0.1, seed=14).numpy()
+    T = wl.log_spaced_table(20, 1e-2, 1e2, 0.1, seed=15).numpy()
+    a, b, c, d = 30.0, 0.5, -1.25, 0.2
+    lr, lt = np.log(R), np.log(T)
+    F = a + b * lr[:, None] + c * lt[None, :] + d * lr[:, None] * lt[None, :]
+    Y = wl.pairs_log_uniform(20_000, R[0], R[-1], T[0], T[-1], seed=16).numpy()
+    _, val = oracle.search_interp_2d(R, T, F, Y, logspace=1)
+    ly0, ly1 = np.log(Y[:, 0]), np.log(Y[:, 1])
+    want = a + b * ly0 + c * ly1 + d * ly0 * ly1
+    scale = abs(a) + abs(b * ly0) + abs(c * ly1) + abs(d * ly0 * ly1)
+    assert (np.abs(val - want) <= 1e-12 * scale).all()
+    _, lin = oracle.search_interp_2d(R, T, F, Y)
+    assert (np.abs(lin - want) > 1e-4 * scale).any()          # linear weights do not reproduce it
+    nodes = np.array([[r, t] for r in R for t in T])
+    np.testing.assert_array_equal(oracle.search_interp_2d(R, T, F, nodes, logspace=1)[1], F.reshape(-1))
+    Yo = wl.pairs_log_uniform(5_000, R[0] / 10, R[-1] * 10, T[0] / 10, T[-1] * 10, seed=17).numpy()
+    _, ext = oracle.search_interp_2d(R, T, F, Yo, extrap=1, logspace=1)
+    ly0, ly1 = np.log(Yo[:, 0]), np.log(Yo[:, 1])
+    want = a + b * ly0 + c * ly1 + d * ly0 * ly1
+    scale = abs(a) + abs(b * ly0) + abs(c * ly1) + abs(d * ly0 * ly1)
+    assert (np.abs(ext - want) <= 1e-12 * scale).all()
+    Yc = np.stack([np.clip(Yo[:, 0], R[0], R[-1]), np.clip(Yo[:, 1], T[0], T[-1])], 1)
+    np.testing.assert_allclose(oracle.search_interp_2d(R, T, F, Yo, logspace=1)[1],
+                               oracle.search_interp_2d(R, T, F, Yc, logspace=1)[1], rtol=1e-15)
+
+
 def test_batched_equals_per_table():
     b = wl.batched_1d(ntables=12, count_scale=0.002, seed=3)
     got = oracle.search_1d_batched(b.X_off.numpy(), b.X.numpy(), b.Y_off.numpy(), b.Y.numpy())
