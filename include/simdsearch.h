@@ -198,7 +198,7 @@ typedef struct ss_plan_info {
   float mean_window;
   float train_loss;         /* mean final training loss of the MLP (MLP model only) */
   int32_t nbuckets;         /* table-size buckets [2,16) [16,64) [64,256) ... */
-  int32_t bucket_algo[8];   /* chosen algorithm per bucket: 0 bucket, 1 binary, 2-4 ballot 8/16/32, 5 spline, 6 mlp, 7 loghash */
+  int32_t bucket_algo[8];   /* chosen algorithm per bucket: 0 bucket, 1 binary, 2-4 ballot 8/16/32, 5 spline, 6 mlp, 7 loghash, 8 wide */
   int32_t bucket_tile[8];   /* chosen targets per tile per bucket */
   int32_t bucket_tables[8]; /* tables per bucket */
   int64_t ntiles;           /* tiles of the bound batch */

@@ -207,7 +207,7 @@ def mlp_adam_step(params, grad, m1, m2, step, lr, beta1=0.9, beta2=0.999, eps=1e
 # ---------------------------------------------------------------------------
 MODEL_NONE, MODEL_SPLINE, MODEL_MLP, MODEL_LOGHASH = 0, 1, 2, 3
 MODELS = {"none": MODEL_NONE, "spline": MODEL_SPLINE, "mlp": MODEL_MLP, "loghash": MODEL_LOGHASH}
-BLOB_ALGOS = ["bucket", "binary", "ballot8", "ballot16", "ballot32", "spline", "mlp", "loghash"]
+BLOB_ALGOS = ["bucket", "binary", "ballot8", "ballot16", "ballot32", "spline", "mlp", "loghash", "wide"]
 
 
 class PlanOpts(C.Structure):

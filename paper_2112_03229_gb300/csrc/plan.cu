@@ -24,7 +24,7 @@ int size_bucket(int n) {
 
 const char* algo_name(int a) {
   static const char* names[BL_NUM] = {"bucket", "binary", "ballot8", "ballot16", "ballot32", "spline", "mlp",
-                                              "loghash"};
+                                              "loghash", "wide"};
   return a >= 0 && a < BL_NUM ? names[a] : "?";
 }
 

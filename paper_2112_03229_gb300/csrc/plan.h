@@ -5,9 +5,6 @@
 
 namespace ss {
 
-// Bucket budget of the fine directory of a sampled table (all keys, global memory).
-__host__ __device__ inline int fine_dir_cap(int nk) { return nk < (1 << 16) ? 4 * nk : (1 << 18); }
-
 __host__ __device__ inline BlobGeom blob_geom_dev(int n, int dir_cap, bool cells) {
   BlobGeom g{};
   const int nk = n - 1;
@@ -25,8 +22,12 @@ __host__ __device__ inline BlobGeom blob_geom_dev(int n, int dir_cap, bool cells
   if (cells) { g.off_cells = off; off += (((n - 1) * (int)sizeof(CellW)) + 15) & ~15; }
   g.staged_end = off;
   g.off_full = g.stride > 1 ? off : -1;
-  g.bytes = g.stride > 1 ? (int64_t)off + (int64_t)(nk + kPad) * 8 + (int64_t)(fine_dir_cap(nk) + 1) * 4 : off;
-  g.bytes = (g.bytes + 15) & ~(int64_t)15;
+  g.bytes = g.stride > 1 ? wide_offset(off, nk) : ((off + 15) & ~15);
+  g.off_wide = -1;
+  if (!cells && g.stride > 1 && wide_eligible(nk)) {   // 1D tables only
+    g.off_wide = g.bytes;
+    g.bytes += wide_geom(nk).bytes;
+  }
   return g;
 }
 
@@ -98,7 +99,9 @@ struct BatchArgs2D {
 __global__ void k_prep_1d(PrepArgs a);
 __global__ void k_train_mlp(TrainArgs a);
 __global__ void k_window(WindowArgs a);
-const void* batched_1d_kernel(bool le, int family);   // family: 0 plain, 1 +spline, 2 +mlp
+const void* batched_1d_kernel(bool le, int family);   // family: 0 plain, 1 +spline/loghash, 2 +mlp
+const void* batched_1d_wide_kernel(bool le);          // tables searched through their wide section
+constexpr int kWideThreads = 1024;
 __global__ void k_batched_2d(BatchArgs2D a);
 __global__ void k_grid_to_ff(const double* F, float2* G, int64_t count, unsigned* bad);
 __global__ void k_prep_cells(PrepArgs a);

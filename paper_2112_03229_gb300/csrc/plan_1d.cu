@@ -124,6 +124,57 @@ __global__ void __launch_bounds__(256) k_prep_1d(PrepArgs a) {
     }
   }
   __syncthreads();
+  // wide section (tables too large for shared memory as 8-byte keys): leaf
+  // samples, per-leaf shifts and 16-bit offsets, directory over the samples
+  if (g.off_wide >= 0) {
+    const WideGeom wg = wide_geom(nk);
+    unsigned char* sec = blob + g.off_wide;
+    int* wdir = reinterpret_cast<int*>(sec + wg.off_dir);
+    uint64_t* ws = reinterpret_cast<uint64_t*>(sec + wg.off_samples);
+    uint8_t* wsh = sec + wg.off_shift;
+    uint16_t* wl = reinterpret_cast<uint16_t*>(sec + wg.off_leaf);
+    __shared__ int s_wshift, s_wnb, s_wocc;
+    __shared__ uint64_t s_wbase;
+    for (int s = tid; s < wg.L + kPad; s += nt) ws[s] = s < wg.L ? full[min((s + 1) * kLeaf, nk) - 1] : kKeyMax;
+    __syncthreads();
+    const uint64_t kx0 = order_key(X[0]);
+    for (int s = tid; s < wg.L; s += nt) {
+      const uint64_t b = s > 0 ? ws[s - 1] : kx0;
+      const uint64_t d = ws[s] - b;                          // > 0 for a strictly increasing table
+      const int sh = max(0, 64 - __clzll((long long)d) - 16);
+      wsh[s] = (uint8_t)sh;
+      for (int j = 0; j < kLeaf; ++j) {
+        const int i = s * kLeaf + j;
+        wl[i] = i < nk ? (uint16_t)((full[i] - b) >> sh) : (uint16_t)0xFFFF;
+      }
+    }
+    if (tid == 0) {
+      const uint64_t a0 = ws[0], a1 = ws[wg.L - 1];
+      int sft = 0;
+      while (sft < 63 && ((a1 >> sft) - (a0 >> sft)) >= (uint64_t)wg.dcap) ++sft;
+      s_wshift = sft;
+      s_wbase = a0 >> sft;
+      s_wnb = (int)min((a1 >> sft) - (a0 >> sft) + 1, (uint64_t)wg.dcap);
+      s_wocc = 0;
+    }
+    __syncthreads();
+    for (int b = tid; b <= s_wnb; b += nt)
+      wdir[b] = b == s_wnb ? wg.L : lower_count(ws, wg.L, (s_wbase + (uint64_t)b) << s_wshift);
+    __syncthreads();
+    int oc = 0;
+    for (int b = tid; b < s_wnb; b += nt) oc = max(oc, wdir[b + 1] - wdir[b]);
+    oc = __reduce_max_sync(0xFFFFFFFFu, oc);
+    if ((tid & 31) == 0) atomicMax(&s_wocc, oc);
+    __syncthreads();
+    if (tid == 0) {
+      WideHdr wh{};
+      wh.base = s_wbase;
+      wh.shift = s_wshift; wh.nb = s_wnb; wh.occ = s_wocc;
+      wh.L = wg.L; wh.dcap = wg.dcap;
+      wh.off_dir = wg.off_dir; wh.off_samples = wg.off_samples; wh.off_shift = wg.off_shift; wh.off_leaf = wg.off_leaf;
+      *reinterpret_cast<WideHdr*>(sec) = wh;
+    }
+  }
   if (tid == 0) {
     BlobHdr hh{};
     hh.n = n; hh.nk = nk; hh.ns = g.ns; hh.stride = g.stride;
@@ -467,6 +518,58 @@ __global__ void __launch_bounds__(kNumThreads, FAM == FAM_MLP ? 2 : 4) k_batched
     if (fallbacks) atomicAdd(&a.stat->fallbacks, (unsigned long long)fallbacks);
   }
   if (a.stat != nullptr && threadIdx.x == 0 && s_err) atomicOr(&a.stat->flags, SS_FLAG_STAGING_TIMEOUT);
+}
+
+// Persistent batched search over tables with a wide section: one block of
+// 1024 threads per SM holds a whole wide section (up to 224 KB) in shared
+// memory; otherwise the same tile loop as k_batched_1d.
+template <bool LE>
+__global__ void __launch_bounds__(kWideThreads, 1) k_batched_1d_wide(BatchArgs1D a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bar;
+  __shared__ int s_tile;
+  __shared__ int s_err;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    s_err = 0;
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  int cur_table = -1;
+  StagedView v{};
+  bool ok = true;
+  int nans = 0;
+  const uint64_t le = LE ? 1 : 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int t = s_tile;
+    __syncthreads();
+    if (t >= a.ntiles) break;
+    const Tile tile = a.tiles[t];
+    if (tile.table != cur_table) {
+      v = stage_blob(a.blobs + a.blob_off[tile.table], smem, &bar, phase, ok);
+      cur_table = tile.table;
+      if (!ok) break;
+    }
+    const WideView wv = wide_view(smem + sizeof(BlobHdr), v);
+    if (wv.w.occ <= 1)
+      stream_tile(a.Y, a.out, tile.begin, tile.count, a.vec != 0, le, nans,
+                  [&](double, uint64_t q) { return wide_count<true>(wv, q); });
+    else
+      stream_tile(a.Y, a.out, tile.begin, tile.count, a.vec != 0, le, nans,
+                  [&](double, uint64_t q) { return wide_count<false>(wv, q); });
+  }
+  if (!ok && threadIdx.x == 0) s_err = 1;
+  __syncthreads();
+  nans = __reduce_add_sync(0xFFFFFFFFu, nans);
+  if (a.stat != nullptr && (threadIdx.x & 31) == 0 && nans) atomicAdd(&a.stat->nan_targets, (unsigned long long)nans);
+  if (a.stat != nullptr && threadIdx.x == 0 && s_err) atomicOr(&a.stat->flags, SS_FLAG_STAGING_TIMEOUT);
+}
+
+const void* batched_1d_wide_kernel(bool le) {
+  return le ? reinterpret_cast<const void*>(&k_batched_1d_wide<true>)
+            : reinterpret_cast<const void*>(&k_batched_1d_wide<false>);
 }
 
 // Kernel entry of the batched search (template stubs stay local to this unit).

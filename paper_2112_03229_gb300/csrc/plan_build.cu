@@ -89,11 +89,23 @@ ss_status plan_window_stats(ss_plan* p) {
   return SS_OK;
 }
 
+// The algorithm a 1D table of n entries runs for a requested one: the wide
+// search needs a wide section; tables without one keep the plain search
+// that suits their layout.
+int table_algo(int algo, int n) {
+  if (algo != BL_WIDE || wide_eligible(n - 1)) return algo;
+  return n - 1 > kMaxSmemKeys ? BL_BINARY : BL_BUCKET;
+}
+
 ss_status plan_build_1d(ss_plan* p, const double* X, cudaStream_t stream) {
   const int nt = p->ntables;
   const ss_plan_opts& o = p->opts;
   p->dir_cap.resize(nt);
   p->algo.assign(nt, initial_algo(o));
+  // without a model and an explicit algorithm, tables with a wide section use it
+  if (o.model == SS_MODEL_NONE && o.algo == SS_ALGO_AUTO)
+    for (int k = 0; k < nt; ++k)
+      if (wide_eligible(p->sizes[k] - 1)) p->algo[k] = BL_WIDE;
   p->blob_off.resize(nt);
   int64_t off = 0;
   for (int k = 0; k < nt; ++k) {
@@ -108,7 +120,10 @@ ss_status plan_build_1d(ss_plan* p, const double* X, cudaStream_t stream) {
     p->bucket_tile[b] = o.tile > 0 ? o.tile : kDefaultTile;
     p->bucket_tables[b] = 0;
   }
-  for (int k = 0; k < nt; ++k) p->bucket_tables[size_bucket(p->sizes[k])]++;
+  for (int k = 0; k < nt; ++k) {
+    p->bucket_tables[size_bucket(p->sizes[k])]++;
+    if (p->algo[k] == BL_WIDE) p->bucket_algo[size_bucket(p->sizes[k])] = BL_WIDE;
+  }
   if (cudaMalloc(&p->d_blobs, p->blob_bytes) != cudaSuccess) return fail(SS_ENOMEM, "plan: device allocation failed");
   p->device_bytes = p->blob_bytes;
   int64_t* d_X_off = nullptr;
@@ -183,8 +198,13 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
   unbind(p);
   std::vector<int> bucket_of(p->ntables);
   for (int k = 0; k < p->ntables; ++k) bucket_of[k] = size_bucket(std::max(p->sizes[k], p->kind == 2 ? p->sizes_t[k] : 0));
+  // 1D tables searched through their wide section run in their own kernel
+  std::vector<char> wide(p->ntables, 0);
+  bool any_wide = false;
+  if (p->kind == 1)
+    for (int k = 0; k < p->ntables; ++k) any_wide |= (wide[k] = p->algo[k] == BL_WIDE) != 0;
   // dynamic shared memory: the largest staged table (both axes for 2D), also per bucket
-  int smem = 0;
+  int smem = 0, smem_w = 0;
   int smem_b[kNumBuckets] = {0};
   for (int k = 0; k < p->ntables; ++k) {
     int need;
@@ -194,11 +214,14 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
       const int a = (staged_bytes(p->sizes[k], p->dir_cap[2 * k], true, p->algo[2 * k]) + 127) & ~127;
       need = a + staged_bytes(p->sizes_t[k], p->dir_cap[2 * k + 1], true, p->algo[2 * k + 1]);
     }
-    smem = std::max(smem, need);
+    if (wide[k]) smem_w = std::max(smem_w, need);
+    else smem = std::max(smem, need);
     smem_b[bucket_of[k]] = std::max(smem_b[bucket_of[k]], need);
   }
   smem = (smem + 127) & ~127;
-  if (smem > max_smem_optin()) return fail(SS_EUNSUPPORTED, "plan: staged tables exceed shared memory");
+  smem_w = (smem_w + 127) & ~127;
+  if (smem > max_smem_optin() || smem_w > max_smem_optin())
+    return fail(SS_EUNSUPPORTED, "plan: staged tables exceed shared memory");
   const void* kern;
   int family = 0;
   for (int a : p->algo) family = std::max(family, a == BL_MLP ? 2 : (a == BL_SPLINE || a == BL_LOGHASH) ? 1 : 0);
@@ -209,33 +232,61 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
   SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNumThreads, smem));
   if (per_sm < 1) return fail(SS_EUNSUPPORTED, "plan: kernel does not fit on an SM");
   const int resident = num_sms() * per_sm;
-  const int64_t total_targets = Y_off.back() - Y_off.front();
-  for (int b = 0; b < kNumBuckets; ++b)
-    p->bucket_tile[b] = p->opts.tile > 0 ? p->opts.tile : auto_tile(total_targets, resident, smem_b[b], p->bucket_mult[b]);
+  const void* kern_w = nullptr;
+  int resident_w = 0;
+  if (any_wide) {
+    kern_w = batched_1d_wide_kernel(p->opts.side == SS_SIDE_LE);
+    SS_CHECK_CUDA(cudaFuncSetAttribute(kern_w, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_w));
+    int per_sm_w = 0;
+    SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_w, kern_w, kWideThreads, smem_w));
+    if (per_sm_w < 1) return fail(SS_EUNSUPPORTED, "plan: wide kernel does not fit on an SM");
+    resident_w = num_sms() * per_sm_w;
+  }
+  // tiles: the regular tables' first, then the wide tables'; each kernel has its own counter
+  int64_t total_reg = 0, total_w = 0;
+  for (int k = 0; k < p->ntables; ++k) (wide[k] ? total_w : total_reg) += Y_off[k + 1] - Y_off[k];
+  for (int b = 0; b < kNumBuckets; ++b) {
+    const bool wb = any_wide && [&] { for (int k = 0; k < p->ntables; ++k) if (bucket_of[k] == b && wide[k]) return true; return false; }();
+    p->bucket_tile[b] = p->opts.tile > 0 ? p->opts.tile
+                                         : auto_tile(wb ? total_w : total_reg, wb ? resident_w : resident, smem_b[b],
+                                                     p->bucket_mult[b]);
+  }
   int64_t total = 0;
   std::vector<Tile> tiles = make_tiles(Y_off, bucket_of, p->bucket_tile, total);
-  if (tiles.size() > (size_t)0x7FFFFFFF) return fail(SS_EUNSUPPORTED, "plan: too many tiles");
-  p->ntiles = (int64_t)tiles.size();
-  if (p->d_counter == nullptr) SS_CHECK_CUDA(cudaMalloc(&p->d_counter, sizeof(int)));
-  if (!tiles.empty()) {
-    SS_CHECK_CUDA(cudaMalloc(&p->d_tiles, tiles.size() * sizeof(Tile)));
-    SS_CHECK_CUDA(cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+  std::vector<Tile> reg, wtiles;
+  for (const Tile& t : tiles) (wide[t.table] ? wtiles : reg).push_back(t);
+  const int64_t nreg = (int64_t)reg.size(), nw = (int64_t)wtiles.size();
+  reg.insert(reg.end(), wtiles.begin(), wtiles.end());
+  if (reg.size() > (size_t)0x7FFFFFFF) return fail(SS_EUNSUPPORTED, "plan: too many tiles");
+  p->ntiles = (int64_t)reg.size();
+  if (p->d_counter == nullptr) SS_CHECK_CUDA(cudaMalloc(&p->d_counter, 2 * sizeof(int)));
+  if (!reg.empty()) {
+    SS_CHECK_CUDA(cudaMalloc(&p->d_tiles, reg.size() * sizeof(Tile)));
+    SS_CHECK_CUDA(cudaMemcpy(p->d_tiles, reg.data(), reg.size() * sizeof(Tile), cudaMemcpyHostToDevice));
   }
   p->smem_bytes = smem;
-  p->grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)resident, p->ntiles));
+  p->grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)resident, nreg));
+  const int grid_w = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)resident_w, nw));
   if (p->ntiles == 0) {
     p->bound = true;
     return SS_OK;
   }
   if (p->cap_stream == nullptr) SS_CHECK_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
   SS_CHECK_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = cudaMemsetAsync(p->d_counter, 0, sizeof(int), p->cap_stream);
+  cudaError_t e = cudaMemsetAsync(p->d_counter, 0, 2 * sizeof(int), p->cap_stream);
   if (e == cudaSuccess) {
     if (p->kind == 1) {
-      BatchArgs1D a{p->d_blobs, p->d_blob_off, p->d_tiles, (int)p->ntiles, p->d_counter, Y, out,
-                    (aligned(Y, 16) && aligned(out, 16)) ? 1 : 0, stat};
-      void* args[1] = {&a};
-      e = cudaLaunchKernel(kern, dim3(p->grid_blocks), dim3(kNumThreads), args, (size_t)smem, p->cap_stream);
+      const int vec = (aligned(Y, 16) && aligned(out, 16)) ? 1 : 0;
+      if (nreg > 0) {
+        BatchArgs1D a{p->d_blobs, p->d_blob_off, p->d_tiles, (int)nreg, p->d_counter, Y, out, vec, stat};
+        void* args[1] = {&a};
+        e = cudaLaunchKernel(kern, dim3(p->grid_blocks), dim3(kNumThreads), args, (size_t)smem, p->cap_stream);
+      }
+      if (e == cudaSuccess && nw > 0) {
+        BatchArgs1D a{p->d_blobs, p->d_blob_off, p->d_tiles + nreg, (int)nw, p->d_counter + 1, Y, out, vec, stat};
+        void* args[1] = {&a};
+        e = cudaLaunchKernel(kern_w, dim3(grid_w), dim3(kWideThreads), args, (size_t)smem_w, p->cap_stream);
+      }
     } else {
       BatchArgs2D a{p->d_blobs, p->d_blob_off, reinterpret_cast<const float4*>(p->d_grid), p->d_grid64,
                     p->d_grid_off, p->d_cell_off, p->opts.extrap, p->opts.logspace, p->d_tiles, (int)p->ntiles,
@@ -320,7 +371,7 @@ static void write_cache(const ss_plan* p, const std::string& dev) {
 static ss_status apply_buckets(ss_plan* p, cudaStream_t stream) {
   for (int k = 0; k < p->ntables; ++k) {
     const int b = size_bucket(std::max(p->sizes[k], p->kind == 2 ? p->sizes_t[k] : 0));
-    if (p->kind == 1) p->algo[k] = p->bucket_algo[b];
+    if (p->kind == 1) p->algo[k] = table_algo(p->bucket_algo[b], p->sizes[k]);
     else p->algo[2 * k] = p->algo[2 * k + 1] = p->bucket_algo[b];
   }
   return plan_set_algos(p, stream);
@@ -336,7 +387,7 @@ ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
   if (p->opts.model == SS_MODEL_SPLINE) cands = {BL_SPLINE};
   else if (p->opts.model == SS_MODEL_MLP) cands = {BL_MLP};
   else if (p->opts.model == SS_MODEL_LOGHASH) cands = {BL_LOGHASH};
-  else if (p->kind == 1) cands = {BL_BUCKET, BL_BINARY, BL_BALLOT8, BL_BALLOT16, BL_BALLOT32};
+  else if (p->kind == 1) cands = {BL_BUCKET, BL_BINARY, BL_BALLOT8, BL_BALLOT16, BL_BALLOT32, BL_WIDE};
   else cands = {BL_BUCKET, BL_BINARY};
   const std::vector<float> mult_cands = {0.25f, 1.0f, 4.0f};
   // up to 8 representative tables per size bucket share 64M synthetic
@@ -408,7 +459,7 @@ ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
     }
     auto time_config = [&](int algo, float mult, float& ms) -> ss_status {
       for (int r : reps) {
-        if (p->kind == 1) p->algo[r] = algo;
+        if (p->kind == 1) p->algo[r] = table_algo(algo, p->sizes[r]);
         else p->algo[2 * r] = p->algo[2 * r + 1] = algo;
       }
       if (ss_status s2 = plan_set_algos(p, stream)) return s2;
@@ -433,6 +484,7 @@ ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
     int best_algo = cands[0];
     float best_ms = 1e30f;
     for (int a : cands) {
+      if (a == BL_WIDE && table_algo(a, p->sizes[reps[0]]) != BL_WIDE) continue;   // no wide section here
       float ms = 0;
       ss_status s2 = time_config(a, 1.0f, ms);
       if (s2 == SS_EUNSUPPORTED) continue;     // e.g. staged tables too large for this variant

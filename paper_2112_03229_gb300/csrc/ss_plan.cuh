@@ -10,9 +10,20 @@
 // Blob layout (all offsets from the blob start, 16-byte aligned):
 //   [BlobHdr 128 B][mlp 65 floats, padded to 272 B][dir (cap+1) int32]
 //   [keys (ns + kPad) uint64][eyt P uint64]           <- staged part
-//   [full keys nk + kPad uint64]                      <- global only (stride > 1)
+//   [full keys nk + kPad uint64][fine dir]             <- global only (stride > 1)
+//   [wide section]                                    <- tables of 8129 .. ~76K keys
 // keys hold the images of X[1..n-1] (sampled every `stride` entries for big
 // tables, see ss_table.cuh); full keys hold all of them.
+//
+// Wide section (a table too large for shared memory as 8-byte keys, but not
+// as 16-bit ones): the keys form leaves of 16; per leaf, its last key (the
+// sample), a shift, and the 16 keys as offsets from the previous leaf's
+// last key, shifted right until they fit 16 bits.  A target's leaf comes
+// from a bucket directory over the samples; inside the leaf a 16-bit
+// comparison decides every key except those whose offset equals the
+// target's, which are compared in full from global memory (rare: the
+// truncation would have to land on the same 16-bit step).  Everything else
+// is one shared-memory stage of about 2.5 bytes per key.
 #pragma once
 
 #include "ss_ff.cuh"
@@ -22,7 +33,7 @@
 namespace ss {
 
 enum BlobAlgo : int { BL_BUCKET = 0, BL_BINARY = 1, BL_BALLOT8 = 2, BL_BALLOT16 = 3, BL_BALLOT32 = 4,
-                      BL_SPLINE = 5, BL_MLP = 6, BL_LOGHASH = 7, BL_NUM = 8 };
+                      BL_SPLINE = 5, BL_MLP = 6, BL_LOGHASH = 7, BL_WIDE = 8, BL_NUM = 9 };
 
 struct __align__(16) BlobHdr {
   int n, nk, ns, stride;     // table length, searched keys, staged keys, sample stride
@@ -53,11 +64,61 @@ constexpr int kMlpBytes = 272;
 struct BlobGeom {
   int ns, stride, P, D;
   int off_mlp, off_dir, off_keys, off_eyt, off_cells, staged_end;
-  int64_t off_full, bytes;
+  int64_t off_full, off_wide, bytes;   // off_wide: -1 without a wide section
 };
+
+// Bucket budget of the fine directory of a sampled table (all keys, global memory).
+__host__ __device__ inline int fine_dir_cap(int nk) { return nk < (1 << 16) ? 4 * nk : (1 << 18); }
+
+// Wide section geometry (offsets from the section start, 16-byte aligned).
+constexpr int kLeaf = 16;                         // keys per leaf
+constexpr int kWideSmemBudget = 224 * 1024;       // header + section, staged whole
+
+struct WideHdr {                                  // first 48 bytes of the section
+  uint64_t base;                                  // bucket of samples[0]
+  int shift, nb, occ;                             // bucket directory over the samples
+  int L;                                          // leaves (= samples)
+  int dcap;
+  int off_dir, off_samples, off_shift, off_leaf;
+  int pad;
+};
+static_assert(sizeof(WideHdr) == 48, "wide header size");
+
+struct WideGeom {
+  int L, dcap, off_dir, off_samples, off_shift, off_leaf, bytes;
+};
+
+__host__ __device__ inline WideGeom wide_geom(int nk) {
+  WideGeom w{};
+  w.L = (nk + kLeaf - 1) / kLeaf;
+  w.dcap = w.L * 2 < 64 ? 64 : (w.L * 2 > 8192 ? 8192 : w.L * 2);
+  int off = (int)sizeof(WideHdr);
+  w.off_dir = off;     off += (((w.dcap + 1) * 4) + 15) & ~15;
+  w.off_samples = off; off += (((w.L + kPad) * 8) + 15) & ~15;
+  w.off_shift = off;   off += (w.L + 15) & ~15;
+  w.off_leaf = off;    off += w.L * kLeaf * 2;
+  w.bytes = off;
+  return w;
+}
+
+// A table gets a wide section when its keys exceed shared memory as 8-byte
+// keys and the section (with the blob header) fits the budget.
+__host__ __device__ inline bool wide_eligible(int nk) {
+  return nk > kMaxSmemKeys && (int64_t)sizeof(BlobHdr) + wide_geom(nk).bytes <= kWideSmemBudget;
+}
+
+// Blob offset of the wide section: after the global-only keys and fine directory.
+__host__ __device__ inline int64_t wide_offset(int64_t off_full, int nk) {
+  return (off_full + (int64_t)(nk + kPad) * 8 + (int64_t)(fine_dir_cap(nk) + 1) * 4 + 15) & ~(int64_t)15;
+}
 
 // Byte range of the staged part that an algorithm needs: [lo, hi) besides the header.
 __host__ __device__ inline void staged_range(const BlobHdr& h, int& lo, int& hi) {
+  if (h.algo == BL_WIDE) {
+    lo = (int)wide_offset(h.off_full, h.nk);
+    hi = lo + wide_geom(h.nk).bytes;
+    return;
+  }
   switch (h.algo) {
     case BL_BINARY: lo = h.off_eyt; hi = h.off_eyt + (1 << h.D) * 8; break;
     case BL_BALLOT8: case BL_BALLOT16: case BL_BALLOT32: lo = h.off_keys; hi = h.off_keys + (h.ns + kPad) * 8; break;
@@ -156,6 +217,58 @@ __device__ __forceinline__ StagedView stage_blob(const unsigned char* __restrict
   v.full = hdr.off_full >= 0 ? reinterpret_cast<const uint64_t*>(src + hdr.off_full) : nullptr;
   v.gdir = hdr.gnb > 0 ? reinterpret_cast<const int*>(src + hdr.off_full + (int64_t)(hdr.nk + kPad) * 8) : nullptr;
   return v;
+}
+
+// Staged wide section (shared memory, right after the staged header).
+struct WideView {
+  WideHdr w;                    // directory parameters, in registers
+  const int* dir;
+  const uint64_t* samples;      // last key of each leaf, then kPad sentinels
+  const uint8_t* shifts;
+  const uint16_t* leaf;         // 16 offsets per leaf
+  const uint64_t* full;         // all keys, global memory (ties)
+  uint64_t k0;                  // key of X[0]: the base of leaf 0
+  int nk;
+};
+
+__device__ __forceinline__ WideView wide_view(const unsigned char* sec, const StagedView& v) {
+  WideView wv;
+  wv.w = *reinterpret_cast<const WideHdr*>(sec);
+  wv.dir = reinterpret_cast<const int*>(sec + wv.w.off_dir);
+  wv.samples = reinterpret_cast<const uint64_t*>(sec + wv.w.off_samples);
+  wv.shifts = sec + wv.w.off_shift;
+  wv.leaf = reinterpret_cast<const uint16_t*>(sec + wv.w.off_leaf);
+  wv.full = v.full;
+  wv.k0 = v.h.k0;
+  wv.nk = v.h.nk;
+  return wv;
+}
+
+// Count of keys below q on a wide section: the leaf from the sample
+// directory (SCAN1: at most one sample per bucket), then a branchless lower
+// bound of the target's 16-bit offset among the leaf's 16 (offsets below it
+// belong to smaller keys, above it to larger ones), then the keys whose
+// offset equals the target's, compared in full.
+template <bool SCAN1>
+__device__ __forceinline__ int wide_count(const WideView& wv, uint64_t q) {
+  const int s = SCAN1 ? search_bucket<1>(wv.samples, wv.dir, wv.w.shift, wv.w.base, wv.w.nb, q)
+                      : search_bucket_bisect(wv.samples, wv.dir, wv.w.shift, wv.w.base, wv.w.nb,
+                                             32 - __clz(wv.w.occ), q);
+  if (s >= wv.w.L) return wv.nk;
+  const uint64_t base = s > 0 ? wv.samples[s - 1] : wv.k0;
+  if (q <= base) return kLeaf * s;               // only below X[0] (leaf 0)
+  const uint32_t tq = (uint32_t)((q - base) >> wv.shifts[s]);   // < 2^16: q <= samples[s]
+  const uint16_t* t = wv.leaf + kLeaf * s;
+  int c = 0;
+#pragma unroll
+  for (int step = kLeaf / 2; step > 0; step >>= 1) c += t[c + step - 1] < tq ? step : 0;
+  c += t[c] < tq ? 1 : 0;
+  while (c < kLeaf && t[c] == tq) {
+    const int j = kLeaf * s + c;
+    if (j >= wv.nk || __ldg(wv.full + j) >= q) break;
+    ++c;
+  }
+  return kLeaf * s + c;
 }
 
 // Count over the full searched set after the staged count c (two-level tables).

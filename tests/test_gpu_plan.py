@@ -82,6 +82,40 @@ def test_plan_table_size_sweep(ss, model):
     np.testing.assert_array_equal(got, want)
 
 
+def test_plan_wide_section_with_ties(ss):
+    """Tables of 8129..~76K entries search a wide section (16-bit offsets in
+    shared memory).  Runs of consecutive doubles inside a leaf whose other
+    keys are far apart truncate to equal offsets, so targets at and next to
+    those keys take the full-key comparison; both sides, indices exact."""
+    rng = np.random.default_rng(21)
+    base = np.logspace(0, 10, 10_000)
+    runs = []
+    for x in rng.choice(base[100:-100], 25, replace=False):
+        v = x
+        for _ in range(12):
+            v = np.nextafter(v, np.inf)
+            runs.append(v)
+    X = np.unique(np.concatenate([base, runs]))
+    assert np.all(np.diff(X) > 0) and len(X) > 8200
+    near = np.concatenate([X, np.nextafter(X, np.inf), np.nextafter(X, -np.inf)])
+    Y = np.concatenate([near, 10 ** rng.uniform(-1, 11, 200_000), [np.nan, -0.0, np.inf, -np.inf]])
+    Xt, Yt = torch.from_numpy(X), torch.from_numpy(Y)
+    b = wl.Batched1D(torch.tensor([0, len(X)]), Xt, torch.tensor([0, len(Y)]), Yt, None, None)
+    for side in (0, 1):
+        want = oracle.search_1d(X, Y, side)
+        plan, got, st = run_plan_1d(ss, b, side=side)
+        assert "wide" in [c[0] for c in plan.choices().values()]
+        np.testing.assert_array_equal(got, want)
+        assert st.flags == 0 and st.nan_targets == 1
+    # the 65536-entry clustered table of the size sweep, through the wide section
+    X = wl.sweep_table(65536)
+    Y = wl.log_uniform(300_000, 0.5e-6, 2e4, seed=22)
+    b = wl.Batched1D(torch.tensor([0, len(X)]), X, torch.tensor([0, len(Y)]), Y, None, None)
+    plan, got, st = run_plan_1d(ss, b)
+    assert plan.choices()[7][0] == "wide"
+    np.testing.assert_array_equal(got, oracle.search_1d(X.numpy(), Y.numpy()))
+
+
 def test_plan_empty_tiny_tiles_and_misaligned(ss):
     rng = np.random.default_rng(5)
     sizes = [2, 3, 17, 300, 2000, 5]
