@@ -350,7 +350,14 @@ class PlanWorkload(Workload):
 
     def step(self):
         self.plan.execute()
-        return 1
+        return self.kernels_per_step
+
+    @property
+    def kernels_per_step(self):
+        """Kernels in the bound graph (read once; the binding used for timing does not change)."""
+        if getattr(self, "_kps", None) is None:
+            self._kps = self.plan.info().kernels
+        return self._kps
 
     def targets(self):
         return int(self.b.Y_off[-1])

@@ -203,6 +203,7 @@ typedef struct ss_plan_info {
   int32_t bucket_tables[8]; /* tables per bucket */
   int64_t ntiles;           /* tiles of the bound batch */
   int32_t tuned;            /* 1 if the autotuner (or its cache) set the choices */
+  int32_t kernels;          /* kernels one ss_plan_execute launches for the bound batch (0, 1 or 2) */
 } ss_plan_info;
 
 /* Fill *opts with the defaults. */

@@ -220,7 +220,8 @@ class PlanInfo(C.Structure):
     _fields_ = [("kind", C.c_int32), ("ntables", C.c_int32), ("device_bytes", C.c_int64),
                 ("max_window", C.c_int32), ("mean_window", C.c_float), ("train_loss", C.c_float),
                 ("nbuckets", C.c_int32), ("bucket_algo", C.c_int32 * 8), ("bucket_tile", C.c_int32 * 8),
-                ("bucket_tables", C.c_int32 * 8), ("ntiles", C.c_int64), ("tuned", C.c_int32)]
+                ("bucket_tables", C.c_int32 * 8), ("ntiles", C.c_int64), ("tuned", C.c_int32),
+                ("kernels", C.c_int32)]
 
 
 def _plan_sigs(L):

@@ -222,6 +222,7 @@ extern "C" ss_status ss_plan_info_get(const ss_plan* p, ss_plan_info* out) {
   }
   out->ntiles = p->ntiles;
   out->tuned = p->tuned;
+  out->kernels = p->kernels;
   return SS_OK;
 }
 

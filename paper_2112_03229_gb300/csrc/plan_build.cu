@@ -190,6 +190,7 @@ static void unbind(ss_plan* p) {
   free_dev(p->d_tiles);
   p->d_tiles = nullptr;
   p->ntiles = 0;
+  p->kernels = 0;
   p->bound = false;
 }
 
@@ -265,6 +266,7 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
     SS_CHECK_CUDA(cudaMemcpy(p->d_tiles, reg.data(), reg.size() * sizeof(Tile), cudaMemcpyHostToDevice));
   }
   p->smem_bytes = smem;
+  p->kernels = p->kind == 2 ? (p->ntiles > 0 ? 1 : 0) : (nreg > 0 ? 1 : 0) + (nw > 0 ? 1 : 0);
   p->grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)resident, nreg));
   const int grid_w = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)resident_w, nw));
   if (p->ntiles == 0) {

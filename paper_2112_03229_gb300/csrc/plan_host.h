@@ -60,6 +60,7 @@ struct PlanBase {
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cap_stream = nullptr;
   int grid_blocks = 0;
+  int kernels = 0;                    // kernels in the bound graph
   int smem_bytes = 0;
   // diagnostics
   int64_t device_bytes = 0;
