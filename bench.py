@@ -674,7 +674,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--targets", type=int, default=0, help="override the workload's target count (profiling cases)")
-    ap.add_argument("--model", default=None, choices=["none", "spline", "mlp", "loghash"],
+    ap.add_argument("--model", default=None, choices=["none", "spline", "mlp", "loghash", "hunt"],
                     help="position model of the timed plan (default none: plain search; the learned forms are "
                          "timed beside it)")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-plan comparison of plan workloads")
@@ -772,7 +772,8 @@ def main():
             if wl_obj.model == "none":
                 # the timed form is the plain search; the learned forms on the same batch
                 learned = {}
-                for model in ("spline", "mlp", "loghash"):
+                models = ("spline", "mlp", "loghash") + (("hunt",) if isinstance(wl_obj, Batched2D) else ())
+                for model in models:
                     r = wl_obj.compare(stream, args.steps, model)
                     r["frac"] = frac_of(r)
                     learned[model] = r

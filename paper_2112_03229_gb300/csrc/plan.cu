@@ -134,7 +134,8 @@ extern "C" void ss_plan_opts_default(ss_plan_opts* o) {
 
 static ss_status check_opts(const ss_plan_opts* o) {
   if (o->side != SS_SIDE_LT && o->side != SS_SIDE_LE) return fail(SS_EINVAL, "plan: bad side");
-  if (o->model < SS_MODEL_NONE || o->model > SS_MODEL_LOGHASH) return fail(SS_EINVAL, "plan: bad model");
+  if (o->model < SS_MODEL_NONE || o->model > SS_MODEL_LOGHASH)
+    return fail(SS_EINVAL, o->model == SS_MODEL_HUNT ? "plan: the hunt applies to 2D plans only" : "plan: bad model");
   if (o->algo < SS_ALGO_AUTO || o->algo > SS_ALGO_BALLOT) return fail(SS_EINVAL, "plan: algo must be auto, binary, bucket or ballot");
   if (o->tile < 0 || o->mlp_epochs < 0 || o->dir_cap < 0) return fail(SS_EINVAL, "plan: negative option");
   return SS_OK;

@@ -102,7 +102,7 @@ __global__ void k_window(WindowArgs a);
 const void* batched_1d_kernel(bool le, int family);   // family: 0 plain, 1 +spline/loghash, 2 +mlp
 const void* batched_1d_wide_kernel(bool le);          // tables searched through their wide section
 constexpr int kWideThreads = 1024;
-__global__ void k_batched_2d(BatchArgs2D a);
+const void* batched_2d_kernel(bool hunt);            // hunt: second pair of a thread starts from the first
 __global__ void k_grid_to_ff(const double* F, float2* G, int64_t count, unsigned* bad);
 __global__ void k_prep_cells(PrepArgs a);
 

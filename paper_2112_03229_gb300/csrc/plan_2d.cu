@@ -160,10 +160,11 @@ __device__ __forceinline__ void pair_2d(const StagedView& vr, const StagedView& 
 
 // Streams one tile's pairs: scalar head to an even pair, two pairs per
 // thread with 128-bit loads and stores, scalar tail.
-template <class CR, class CT>
+template <bool HUNT, class CR, class CT>
 __device__ __forceinline__ void stream_pairs(const BatchArgs2D& a, const StagedView& vr, const StagedView& vt,
                                              const float4* __restrict__ G, const double* __restrict__ G64,
-                                             const Tile& tile, int& nans, CR&& count_r, CT&& count_t) {
+                                             const Tile& tile, int& nans, int& fallbacks, CR&& count_r,
+                                             CT&& count_t) {
   const int64_t b = tile.begin;
   const int cnt = tile.count;
   auto scalar = [&](int i) {
@@ -186,13 +187,21 @@ __device__ __forceinline__ void stream_pairs(const BatchArgs2D& a, const StagedV
     int i0, j0, i1, j1;
     double v0, v1;
     pair_2d(vr, vt, G, G64, p0.x, p0.y, i0, j0, v0, nans, count_r, count_t, a.extrap, a.logspace);
-    pair_2d(vr, vt, G, G64, p1.x, p1.y, i1, j1, v1, nans, count_r, count_t, a.extrap, a.logspace);
+    if (HUNT) {
+      // consecutive pairs of a coherent sequence: start from the first pair's indices
+      pair_2d(vr, vt, G, G64, p1.x, p1.y, i1, j1, v1, nans,
+              [&](double, uint64_t q) { return hunt_count(vr, i0, q, fallbacks); },
+              [&](double, uint64_t q) { return hunt_count(vt, j0, q, fallbacks); }, a.extrap, a.logspace);
+    } else {
+      pair_2d(vr, vt, G, G64, p1.x, p1.y, i1, j1, v1, nans, count_r, count_t, a.extrap, a.logspace);
+    }
     st_stream(I4 + g, make_int4(i0, j0, i1, j1));
     st_stream(V2 + g, make_double2(v0, v1));
   }
   for (int i = head + 2 * np2 + threadIdx.x; i < cnt; i += blockDim.x) scalar(i);
 }
 
+template <bool HUNT>
 __global__ void __launch_bounds__(kNumThreads) k_batched_2d(BatchArgs2D a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
@@ -248,10 +257,12 @@ __global__ void __launch_bounds__(kNumThreads) k_batched_2d(BatchArgs2D a) {
     auto fast = [](const StagedView& v) {
       return v.h.algo == BL_BUCKET && v.h.stride == 1 && v.h.occ <= 2;
     };
-    if (fast(vr) && fast(vt))
-      stream_pairs(a, vr, vt, G, G64, tile, nans, scan2(vr), scan2(vt));
+    if (HUNT)
+      stream_pairs<true>(a, vr, vt, G, G64, tile, nans, fallbacks, generic(vr), generic(vt));
+    else if (fast(vr) && fast(vt))
+      stream_pairs<false>(a, vr, vt, G, G64, tile, nans, fallbacks, scan2(vr), scan2(vt));
     else
-      stream_pairs(a, vr, vt, G, G64, tile, nans, generic(vr), generic(vt));
+      stream_pairs<false>(a, vr, vt, G, G64, tile, nans, fallbacks, generic(vr), generic(vt));
   }
   nans = __reduce_add_sync(0xFFFFFFFFu, nans);
   fallbacks = __reduce_add_sync(0xFFFFFFFFu, fallbacks);
@@ -260,6 +271,11 @@ __global__ void __launch_bounds__(kNumThreads) k_batched_2d(BatchArgs2D a) {
     if (fallbacks) atomicAdd(&a.stat->fallbacks, (unsigned long long)fallbacks);
   }
   if (a.stat != nullptr && threadIdx.x == 0 && !ok) atomicOr(&a.stat->flags, SS_FLAG_STAGING_TIMEOUT);
+}
+
+// Kernel entry of the batched 2D lookup (template stubs stay local to this unit).
+const void* batched_2d_kernel(bool hunt) {
+  return hunt ? reinterpret_cast<const void*>(&k_batched_2d<true>) : reinterpret_cast<const void*>(&k_batched_2d<false>);
 }
 
 void plan_cell_offsets(PlanBase* p) {
@@ -395,7 +411,7 @@ extern "C" ss_status ss_plan_create_2d(ss_plan** out, int32_t ntables, const int
   if (o.side != SS_SIDE_LT) return fail(SS_EINVAL, "ss_plan_create_2d: the 2D lookup uses side SS_SIDE_LT");
   if ((o.extrap != 0 && o.extrap != 1) || (o.logspace != 0 && o.logspace != 1))
     return fail(SS_EINVAL, "ss_plan_create_2d: extrap and logspace must be 0 or 1");
-  if (o.model < SS_MODEL_NONE || o.model > SS_MODEL_LOGHASH || o.algo == SS_ALGO_BALLOT || o.algo == SS_ALGO_BRANCHY ||
+  if (o.model < SS_MODEL_NONE || o.model > SS_MODEL_HUNT || o.algo == SS_ALGO_BALLOT || o.algo == SS_ALGO_BRANCHY ||
       o.algo < 0 || o.algo > SS_ALGO_BALLOT)
     return fail(SS_EINVAL, "ss_plan_create_2d: algo must be auto, binary or bucket");
   auto* p = new ss_plan();

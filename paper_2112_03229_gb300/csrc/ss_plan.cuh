@@ -124,7 +124,12 @@ __host__ __device__ inline void staged_range(const BlobHdr& h, int& lo, int& hi)
     case BL_BALLOT8: case BL_BALLOT16: case BL_BALLOT32: lo = h.off_keys; hi = h.off_keys + (h.ns + kPad) * 8; break;
     default: lo = h.off_mlp; hi = h.off_keys + (h.ns + kPad) * 8; break;   // bucket, spline, mlp, loghash
   }
-  if (h.off_cells >= 0) hi = h.staged_end;   // 2D axes keep their cells right after
+  if (h.off_cells >= 0) {
+    // 2D axes keep their cells right after, and always their keys: the
+    // weights and the hunt read entries of the axis whatever its search
+    hi = h.staged_end;
+    lo = lo < h.off_keys ? lo : h.off_keys;
+  }
   lo &= ~15;
   hi = (hi + 15) & ~15;
 }
@@ -341,6 +346,26 @@ __device__ __forceinline__ int learned_count(const StagedView& v, int p, uint64_
   if (!ok) {
     ++fallbacks;
     return plain_bucket(v, q);
+  }
+  return c;
+}
+
+// Hunt: the answer for a target that follows one whose answer was p, checked
+// exactly in the window [p-1, p+1]; the plain search when it lies outside.
+__device__ __forceinline__ int hunt_count(const StagedView& v, int p, uint64_t q, int& fallbacks) {
+  const BlobHdr& h = v.h;
+  bool ok;
+  int c;
+  if (h.stride == 1) {
+    const uint64_t* keys = v.keys;
+    c = window_count([keys](int i) { return keys[i]; }, h.nk, 1, p, q, ok);
+  } else {
+    const uint64_t* full = v.full;
+    c = window_count([full](int i) { return __ldg(full + i); }, h.nk, 1, p, q, ok);
+  }
+  if (!ok) {
+    ++fallbacks;
+    return h.algo == BL_BINARY ? plain_binary(v, q) : plain_bucket(v, q);   // the axis' own search
   }
   return c;
 }

@@ -185,6 +185,71 @@ def test_plan_bound_to_page_locked_host_buffers(ss):
     assert (np.abs(hV.numpy() - wv) / np.abs(wv)).max() <= REL_TOL
 
 
+def test_hunt_is_2d_only_and_falls_back(ss):
+    """The hunt proposal applies to 2D plans; on a random order most of its
+    windows miss and the plain search answers them (indices stay exact)."""
+    b = small_batch(seed=17)
+    with pytest.raises(ss.SSError):
+        ss.Plan.create_1d(b.X_off, b.X.to(DEV), model="hunt")
+    b2 = wl.batched_2d(ntables=4, pairs_per_table=4001, seed=18)
+    wi, wv = oracle.search_interp_2d_batched(b2.R_off.numpy(), b2.R.numpy(), b2.T_off.numpy(), b2.T.numpy(),
+                                             b2.F_off.numpy(), b2.F.numpy(), b2.Y_off.numpy(), b2.Y2.numpy())
+    plan = ss.Plan.create_2d(b2.R_off, b2.R.to(DEV), b2.T_off, b2.T.to(DEV), b2.F_off, b2.F.to(DEV), model="hunt")
+    m = b2.Y2.shape[0]
+    idx = torch.empty((m, 2), dtype=torch.int32, device=DEV)
+    val = torch.empty(m, dtype=torch.float64, device=DEV)
+    stat = ss.new_stat()
+    plan.bind_2d(b2.Y_off, b2.Y2.to(DEV), idx, val, stat=stat)
+    plan.execute()
+    np.testing.assert_array_equal(idx.cpu().numpy(), wi)
+    assert (np.abs(val.cpu().numpy() - wv) / np.abs(wv)).max() <= REL_TOL
+    assert ss.read_stat(stat).fallbacks > m // 4
+    # axes searched by the breadth-first binary search still stage their
+    # keys: the hunt's window and its fallback read the axis
+    plan = ss.Plan.create_2d(b2.R_off, b2.R.to(DEV), b2.T_off, b2.T.to(DEV), b2.F_off, b2.F.to(DEV), model="hunt",
+                             algo="binary")
+    idx.fill_(-1)
+    plan.bind_2d(b2.Y_off, b2.Y2.to(DEV), idx, val)
+    plan.execute()
+    np.testing.assert_array_equal(idx.cpu().numpy(), wi)
+    assert (np.abs(val.cpu().numpy() - wv) / np.abs(wv)).max() <= REL_TOL
+
+
+def test_plan_2d_binary_axes_with_options(ss):
+    """Linear extrapolation reads axis entries on the fp64 path; with
+    binary-search axes those entries must be staged too."""
+    b = wl.batched_2d(ntables=5, pairs_per_table=3001, seed=19)
+    rng = np.random.default_rng(20)
+    Y2 = b.Y2.numpy() * np.exp(rng.uniform(-2.0, 2.0, size=b.Y2.shape))
+    wi, wv = oracle.search_interp_2d_batched(b.R_off.numpy(), b.R.numpy(), b.T_off.numpy(), b.T.numpy(),
+                                             b.F_off.numpy(), b.F.numpy(), b.Y_off.numpy(), Y2, extrap=1)
+    plan = ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), algo="binary",
+                             extrap=True)
+    m = Y2.shape[0]
+    idx = torch.empty((m, 2), dtype=torch.int32, device=DEV)
+    val = torch.empty(m, dtype=torch.float64, device=DEV)
+    plan.bind_2d(b.Y_off, torch.from_numpy(Y2).to(DEV), idx, val)
+    plan.execute()
+    np.testing.assert_array_equal(idx.cpu().numpy(), wi)
+    v = val.cpu().numpy()
+    outside = 0
+    for k in range(5):
+        y0, y1 = int(b.Y_off[k]), int(b.Y_off[k + 1])
+        R = b.R.numpy()[int(b.R_off[k]):int(b.R_off[k + 1])]
+        T = b.T.numpy()[int(b.T_off[k]):int(b.T_off[k + 1])]
+        F2 = b.F.numpy()[int(b.F_off[k]):int(b.F_off[k + 1])].reshape(len(R), len(T))
+        y = Y2[y0:y1]
+        outside += int((~((y[:, 0] >= R[0]) & (y[:, 0] <= R[-1]) & (y[:, 1] >= T[0]) & (y[:, 1] <= T[-1]))).sum())
+        cr = np.minimum(wi[y0:y1, 0], len(R) - 2)
+        ct = np.minimum(wi[y0:y1, 1], len(T) - 2)
+        wr = np.abs((y[:, 0] - R[cr]) / (R[cr + 1] - R[cr]))
+        wt = np.abs((y[:, 1] - T[ct]) / (T[ct + 1] - T[ct]))
+        lo = np.abs(1 - wt) * np.abs(F2[cr, ct]) + wt * np.abs(F2[cr, ct + 1])
+        hi = np.abs(1 - wt) * np.abs(F2[cr + 1, ct]) + wt * np.abs(F2[cr + 1, ct + 1])
+        assert (np.abs(v[y0:y1] - wv[y0:y1]) <= REL_TOL * (np.abs(1 - wr) * lo + wr * hi)).all()
+    assert outside > 500
+
+
 def test_plan_not_sorted_rejected(ss):
     X = torch.tensor([1.0, 2.0, 2.0, 3.0, 1.0, 5.0, 7.0], dtype=torch.float64, device=DEV)
     with pytest.raises(ss.SSError) as e:
@@ -305,7 +370,7 @@ def test_loghash_proposal(ss):
 # ---------------------------------------------------------------- 2D plans
 
 @pytest.mark.parametrize("coherent", [False, True])
-@pytest.mark.parametrize("model", ["none", "spline", "mlp", "loghash"])
+@pytest.mark.parametrize("model", ["none", "spline", "mlp", "loghash", "hunt"])
 def test_plan_2d_batched(ss, model, coherent):
     b = wl.batched_2d(ntables=12, pairs_per_table=4001, coherent=coherent, seed=9)
     wi, wv = oracle.search_interp_2d_batched(b.R_off.numpy(), b.R.numpy(), b.T_off.numpy(), b.T.numpy(),
