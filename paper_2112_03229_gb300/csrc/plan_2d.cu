@@ -127,9 +127,10 @@ __device__ __forceinline__ void pair_2d(const StagedView& vr, const StagedView& 
   const int nt = vt.h.n;
   const int cr = min(ir, vr.h.n - 2), ct = min(it, nt - 2);
   const int64_t cell = (int64_t)cr * (nt - 1) + ct;
-  const float4 q0 = __ldg(G + 2 * cell), q1 = __ldg(G + 2 * cell + 1);
-  const float2 g00 = make_float2(q0.x, q0.y), g01 = make_float2(q0.z, q0.w);
-  const float2 g10 = make_float2(q1.x, q1.y), g11 = make_float2(q1.z, q1.w);
+  float q[8];
+  ld_nc_v8(reinterpret_cast<const float*>(G + 2 * cell), q);     // records are 32-byte aligned
+  const float2 g00 = make_float2(q[0], q[1]), g01 = make_float2(q[2], q[3]);
+  const float2 g10 = make_float2(q[4], q[5]), g11 = make_float2(q[6], q[7]);
   if (logspace | extrap) {
     const bool outside = (ir >= vr.h.n - 1) | (ir == 0 && kr <= vr.h.k0) | (it >= nt - 1) | (it == 0 && kt <= vt.h.k0);
     if (logspace | outside) {
