@@ -73,7 +73,7 @@ struct BatchArgs1D {
   int* counter;
   const double* Y;
   int32_t* out;
-  int vec;               // Y and out 16-byte aligned: 128-bit path inside tiles
+  int vec;               // 1: Y and out 16-byte aligned (128-bit loads); 2: Y also 32-byte aligned (256-bit)
   ss_devstat* stat;
 };
 

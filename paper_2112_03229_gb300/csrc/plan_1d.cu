@@ -364,12 +364,14 @@ enum : int { FAM_PLAIN = 0, FAM_SPLINE = 1, FAM_MLP = 2 };
 constexpr uint64_t kKeyNegInf = 0x0010000000000000ull;   // image of -inf; NaNs map below it
 
 // Streams one tile's targets through count(y, q): a scalar head up to a
-// 4-target boundary, then 128-bit quads two at a time (both loads issue
-// before any search, and the eight searches are independent code, so their
+// 4-target boundary, then quads two at a time (both loads issue before any
+// search, and the eight searches are independent code, so their
 // shared-memory round trips overlap), one last quad, and a scalar tail.
+// vec: 0 scalar only, 1 quads as two 128-bit loads, 2 quads as one 256-bit
+// load (Y 32-byte aligned).
 template <class F>
 __device__ __forceinline__ void stream_tile(const double* __restrict__ Y, int32_t* __restrict__ out, int64_t b,
-                                            int cnt, bool vec, uint64_t le, int& nans, F&& count) {
+                                            int cnt, int vec, uint64_t le, int& nans, F&& count) {
   const int bs = blockDim.x;
   const int head = vec ? min(cnt, (int)((-b) & 3)) : cnt;
   const int nq = (cnt - head) >> 2;
@@ -383,9 +385,18 @@ __device__ __forceinline__ void stream_tile(const double* __restrict__ Y, int32_
   int4* O4 = reinterpret_cast<int4*>(out + b + head);
   int g = threadIdx.x;
   for (; g + bs < nq; g += 2 * bs) {
-    const double2 p0 = ld_stream(Y2 + 2 * g), p1 = ld_stream(Y2 + 2 * g + 1);
-    const double2 p2 = ld_stream(Y2 + 2 * (g + bs)), p3 = ld_stream(Y2 + 2 * (g + bs) + 1);
-    const double y[8] = {p0.x, p0.y, p1.x, p1.y, p2.x, p2.y, p3.x, p3.y};
+    double y[8];
+    if (vec == 2) {
+      double* lo = y;
+      double* hi = y + 4;
+      ld_stream4(reinterpret_cast<const double*>(Y2 + 2 * g), *reinterpret_cast<double(*)[4]>(lo));
+      ld_stream4(reinterpret_cast<const double*>(Y2 + 2 * (g + bs)), *reinterpret_cast<double(*)[4]>(hi));
+    } else {
+      const double2 p0 = ld_stream(Y2 + 2 * g), p1 = ld_stream(Y2 + 2 * g + 1);
+      const double2 p2 = ld_stream(Y2 + 2 * (g + bs)), p3 = ld_stream(Y2 + 2 * (g + bs) + 1);
+      y[0] = p0.x; y[1] = p0.y; y[2] = p1.x; y[3] = p1.y;
+      y[4] = p2.x; y[5] = p2.y; y[6] = p3.x; y[7] = p3.y;
+    }
     int r[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -482,7 +493,7 @@ __global__ void __launch_bounds__(kNumThreads, FAM == FAM_MLP ? 2 : 4) k_batched
     }
     // one uniform branch per tile picks the search; inside the tile the
     // searches are branch-free straight-line code where the table allows it
-    const bool vec = a.vec != 0;
+    const int vec = a.vec;
     if (FAM >= FAM_MLP && algo == BL_MLP) {
       stream_tile(a.Y, a.out, b, cnt, vec, le, nans, [&](double y, uint64_t q) { return mlp_count(v, y, q, fallbacks); });
     } else if (FAM >= FAM_SPLINE && algo == BL_SPLINE) {
@@ -554,10 +565,10 @@ __global__ void __launch_bounds__(kWideThreads, 1) k_batched_1d_wide(BatchArgs1D
     }
     const WideView wv = wide_view(smem + sizeof(BlobHdr), v);
     if (wv.w.occ <= 1)
-      stream_tile(a.Y, a.out, tile.begin, tile.count, a.vec != 0, le, nans,
+      stream_tile(a.Y, a.out, tile.begin, tile.count, a.vec, le, nans,
                   [&](double, uint64_t q) { return wide_count<true>(wv, q); });
     else
-      stream_tile(a.Y, a.out, tile.begin, tile.count, a.vec != 0, le, nans,
+      stream_tile(a.Y, a.out, tile.begin, tile.count, a.vec, le, nans,
                   [&](double, uint64_t q) { return wide_count<false>(wv, q); });
   }
   if (!ok && threadIdx.x == 0) s_err = 1;

@@ -278,7 +278,7 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
   cudaError_t e = cudaMemsetAsync(p->d_counter, 0, 2 * sizeof(int), p->cap_stream);
   if (e == cudaSuccess) {
     if (p->kind == 1) {
-      const int vec = (aligned(Y, 16) && aligned(out, 16)) ? 1 : 0;
+      const int vec = (aligned(Y, 16) && aligned(out, 16)) ? (aligned(Y, 32) ? 2 : 1) : 0;
       if (nreg > 0) {
         BatchArgs1D a{p->d_blobs, p->d_blob_off, p->d_tiles, (int)nreg, p->d_counter, Y, out, vec, stat};
         void* args[1] = {&a};

@@ -44,6 +44,11 @@ __device__ __forceinline__ double2 ld_stream(const double2* p) { return __ldcs(p
 __device__ __forceinline__ void st_stream(int4* p, int4 v) { __stcs(p, v); }
 __device__ __forceinline__ void st_stream(double2* p, double2 v) { __stcs(p, v); }
 
+// Streaming 256-bit load of four doubles (p must be 32-byte aligned).
+__device__ __forceinline__ void ld_stream4(const double* p, double (&r)[4]) {
+  asm("ld.global.cs.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(r[0]), "=d"(r[1]), "=d"(r[2]), "=d"(r[3]) : "l"(p));
+}
+
 // One 256-bit read-only load of 32 bytes (p must be 32-byte aligned): a
 // gathered record costs one L1 request instead of two 128-bit ones.
 __device__ __forceinline__ void ld_nc_v8(const float* p, float (&r)[8]) {
