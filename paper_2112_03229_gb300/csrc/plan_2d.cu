@@ -184,7 +184,16 @@ __device__ __forceinline__ void stream_pairs(const BatchArgs2D& a, const StagedV
   int4* I4 = reinterpret_cast<int4*>(a.idx + 2 * (b + head));
   double2* V2 = reinterpret_cast<double2*>(a.val + b + head);
   for (int g = threadIdx.x; g < np2; g += blockDim.x) {
-    const double2 p0 = ld_stream(Y + 2 * g), p1 = ld_stream(Y + 2 * g + 1);
+    double2 p0, p1;
+    if (a.vec == 2) {       // both pairs in one 256-bit load
+      double y[4];
+      ld_stream4(reinterpret_cast<const double*>(Y + 2 * g), y);
+      p0 = make_double2(y[0], y[1]);
+      p1 = make_double2(y[2], y[3]);
+    } else {
+      p0 = ld_stream(Y + 2 * g);
+      p1 = ld_stream(Y + 2 * g + 1);
+    }
     int i0, j0, i1, j1;
     double v0, v1;
     pair_2d(vr, vt, G, G64, p0.x, p0.y, i0, j0, v0, nans, count_r, count_t, a.extrap, a.logspace);

@@ -293,7 +293,7 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
       BatchArgs2D a{p->d_blobs, p->d_blob_off, reinterpret_cast<const float4*>(p->d_grid), p->d_grid64,
                     p->d_grid_off, p->d_cell_off, p->opts.extrap, p->opts.logspace, p->d_tiles, (int)p->ntiles,
                     p->d_counter, Y, out, val,
-                    (aligned(Y, 16) && aligned(out, 16) && aligned(val, 16)) ? 1 : 0, stat};
+                    (aligned(Y, 16) && aligned(out, 16) && aligned(val, 16)) ? (aligned(Y, 32) ? 2 : 1) : 0, stat};
       void* args[1] = {&a};
       e = cudaLaunchKernel(kern, dim3(p->grid_blocks), dim3(kNumThreads), args, (size_t)smem, p->cap_stream);
     }

@@ -20,7 +20,8 @@ struct Args1D {
   int64_t m;
   int32_t* out;
   int64_t head;       // targets [0, head) take the scalar path (alignment prologue)
-  int64_t nq;         // quads in the 128-bit body that follows
+  int64_t nq;         // quads in the vector body that follows
+  int w256;           // 1: Y + head is 32-byte aligned, quads load as one 256-bit access
   uint64_t le;        // 1 for side "<=", else 0 (added to the query key)
   Layout1D lay;
   ss_devstat* stat;
@@ -46,10 +47,18 @@ __device__ __forceinline__ int stream_targets(const Args1D& a, F&& idx_of) {
   int4* O4 = reinterpret_cast<int4*>(a.out + a.head);
   int64_t g = gtid;
   for (; g + gs < a.nq; g += 2 * gs) {
-    const double2 p0 = ld_stream(Y2 + 2 * g), p1 = ld_stream(Y2 + 2 * g + 1);
-    const double2 p2 = ld_stream(Y2 + 2 * (g + gs)), p3 = ld_stream(Y2 + 2 * (g + gs) + 1);
-    uint64_t k[8] = {order_key(p0.x), order_key(p0.y), order_key(p1.x), order_key(p1.y),
-                     order_key(p2.x), order_key(p2.y), order_key(p3.x), order_key(p3.y)};
+    double y[8];
+    if (a.w256) {
+      ld_stream4(reinterpret_cast<const double*>(Y2 + 2 * g), *reinterpret_cast<double(*)[4]>(y));
+      ld_stream4(reinterpret_cast<const double*>(Y2 + 2 * (g + gs)), *reinterpret_cast<double(*)[4]>(y + 4));
+    } else {
+      const double2 p0 = ld_stream(Y2 + 2 * g), p1 = ld_stream(Y2 + 2 * g + 1);
+      const double2 p2 = ld_stream(Y2 + 2 * (g + gs)), p3 = ld_stream(Y2 + 2 * (g + gs) + 1);
+      y[0] = p0.x; y[1] = p0.y; y[2] = p1.x; y[3] = p1.y;
+      y[4] = p2.x; y[5] = p2.y; y[6] = p3.x; y[7] = p3.y;
+    }
+    uint64_t k[8] = {order_key(y[0]), order_key(y[1]), order_key(y[2]), order_key(y[3]),
+                     order_key(y[4]), order_key(y[5]), order_key(y[6]), order_key(y[7])};
     int r[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -214,11 +223,23 @@ __global__ void __launch_bounds__(kNumThreads) k_search_1d_ballot(Args1D a, int 
 // Host launch
 // ---------------------------------------------------------------------------
 
-// Split [0, m) into a scalar prologue, a 128-bit body of quads and a tail.
-// The body needs Y+head 16-byte aligned and out+head 16-byte aligned.
-static void split_vector(const void* Y, const void* out, int64_t m, int64_t& head, int64_t& nq) {
+// Split [0, m) into a scalar prologue, a vector body of quads and a tail.
+// The body needs Y+head 16-byte aligned (32-byte for 256-bit loads) and
+// out+head 16-byte aligned.
+static void split_vector(const void* Y, const void* out, int64_t m, int64_t& head, int64_t& nq, int& w256) {
   head = m;
   nq = 0;
+  w256 = 0;
+  for (int h = 0; h < 4 && h <= m; ++h) {
+    const uintptr_t y = reinterpret_cast<uintptr_t>(Y) + 8u * h;
+    const uintptr_t o = reinterpret_cast<uintptr_t>(out) + 4u * h;
+    if ((y & 31) == 0 && (o & 15) == 0) {
+      head = h;
+      nq = (m - h) / 4;
+      w256 = 1;
+      return;
+    }
+  }
   for (int h = 0; h < 4 && h <= m; ++h) {
     const uintptr_t y = reinterpret_cast<uintptr_t>(Y) + 8u * h;
     const uintptr_t o = reinterpret_cast<uintptr_t>(out) + 4u * h;
@@ -278,7 +299,7 @@ ss_status search_1d(const double* X, int32_t n, const double* Y, int64_t m, int3
   if (m == 0) return SS_OK;
   Args1D a{};
   a.X = X; a.n = n; a.Y = Y; a.m = m; a.out = out; a.le = side == SS_SIDE_LE ? 1 : 0; a.stat = stat;
-  split_vector(Y, out, m, a.head, a.nq);
+  split_vector(Y, out, m, a.head, a.nq, a.w256);
   const int64_t items = a.nq > 0 ? a.head + a.nq + (m - a.head - 4 * a.nq) : m;
   const bool fits = (n - 1) <= kMaxSmemKeys;
   if (algo == SS_ALGO_AUTO) algo = fits ? SS_ALGO_BUCKET : SS_ALGO_BINARY;
