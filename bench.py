@@ -94,7 +94,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -105,6 +105,13 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def wait_first(self, timeout_s=3.0):
+        """Block until the sampler has produced a line (nvidia-smi takes a
+        moment to start), so that the timed region that follows is covered."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout_s:
+            time.sleep(0.01)
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -705,6 +712,11 @@ def main():
     torch.cuda.set_device(dev)
     wl_obj.setup(dev, rank)
     stream = torch.cuda.current_stream()
+    # clocks are sampled from the warm-up through the timed and end-to-end
+    # regions (nvidia-smi every 50 ms; a short timed region alone may fall
+    # between two samples)
+    clk = ClockSampler(dev.index).__enter__()
+    clk.wait_first()
     for _ in range(args.warmup):
         wl_obj.step()
     torch.cuda.synchronize()
@@ -715,16 +727,15 @@ def main():
     launches = 0
     barrier(world)
     torch.cuda.synchronize()
-    with ClockSampler(dev.index) as clk:
-        t_all0 = torch.cuda.Event(enable_timing=True)
-        t_all1 = torch.cuda.Event(enable_timing=True)
-        t_all0.record(stream)
-        for i in range(args.steps):
-            starts[i].record(stream)
-            launches += wl_obj.step()
-            ends[i].record(stream)
-        t_all1.record(stream)
-        torch.cuda.synchronize()
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    t_all0.record(stream)
+    for i in range(args.steps):
+        starts[i].record(stream)
+        launches += wl_obj.step()
+        ends[i].record(stream)
+    t_all1.record(stream)
+    torch.cuda.synchronize()
     barrier(world)
     elapsed_ms = t_all0.elapsed_time(t_all1)
     elapsed_ms = max_over_ranks(elapsed_ms, world)
@@ -744,6 +755,7 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, world)
     e2e_value = wl_obj.targets() * args.steps * world / (e2e_ms / 1e3) / 1e9
+    clk.__exit__(None, None, None)
     if hasattr(wl_obj, "e2e_finish"):
         wl_obj.e2e_finish()
 
