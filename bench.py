@@ -442,6 +442,7 @@ class Sweep1D(PlanWorkload):
     """Table-size sweep: clustered tables of 16, 256, 4096 and 65536 entries,
     256M log-uniform targets per table, learned (spline) proposals vs plain."""
     name = "sweep1d-16-65536-256M"
+    m = 0                  # --targets: total targets of a smaller case (profiling)
 
     def __init__(self, per_table=256 << 20, **kw):
         super().__init__(**kw)
@@ -450,7 +451,7 @@ class Sweep1D(PlanWorkload):
     def generate(self, dev, seed, max_targets=None):
         from paper_2112_03229_gb300 import workloads as wl
         tabs = [wl.sweep_table(n, seed=4 + 1000 * seed) for n in (16, 256, 4096, 65536)]
-        per = self.per_table if max_targets is None else max(1, max_targets // 4)
+        per = (self.m // 4 if self.m else self.per_table) if max_targets is None else max(1, max_targets // 4)
         Ys = [wl.log_uniform(per, 0.5 * t[0].item(), 2 * t[-1].item(), seed=7 + i + 1000 * seed,
                              device=dev) for i, t in enumerate(tabs)]
         X = torch.cat(tabs)
