@@ -35,7 +35,8 @@
  *    record `ss_devstat` (pass NULL to skip); zero it before the call.
  *  - Element pointers must be naturally aligned (8 bytes for double, 4 for
  *    int32).  16-byte alignment of the target and output arrays selects the
- *    128-bit load/store path; other alignments are handled, more slowly.
+ *    vector load/store path (32-byte aligned targets load as 256-bit
+ *    accesses); other alignments are handled, more slowly.
  *  - n >= 2 (each 2D axis >= 2), m >= 0; m == 0 launches nothing.
  *  - Results for a table that is not strictly increasing are unspecified
  *    (the table check sets SS_FLAG_NOT_SORTED) but every index stays in
