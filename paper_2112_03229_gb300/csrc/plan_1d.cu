@@ -141,11 +141,11 @@ __global__ void __launch_bounds__(256) k_prep_1d(PrepArgs a) {
     for (int s = tid; s < wg.L; s += nt) {
       const uint64_t b = s > 0 ? ws[s - 1] : kx0;
       const uint64_t d = ws[s] - b;                          // > 0 for a strictly increasing table
-      const int sh = max(0, 64 - __clzll((long long)d) - 16);
+      const int sh = max(0, 64 - __clzll((long long)d) - 15);   // offsets fit 15 bits
       wsh[s] = (uint8_t)sh;
       for (int j = 0; j < kLeaf; ++j) {
         const int i = s * kLeaf + j;
-        wl[i] = i < nk ? (uint16_t)((full[i] - b) >> sh) : (uint16_t)0xFFFF;
+        wl[i] = i < nk ? (uint16_t)((full[i] - b) >> sh) : (uint16_t)0x7FFF;
       }
     }
     if (tid == 0) {
@@ -427,6 +427,53 @@ __device__ __forceinline__ void stream_tile(const double* __restrict__ Y, int32_
   }
 }
 
+// stream_tile for the MLP proposal: the eight proposals of a thread's two
+// quads are evaluated together (mlp_propose_w), then each is checked.
+__device__ __forceinline__ void stream_tile_mlp(const StagedView& v, const double* __restrict__ Y,
+                                                int32_t* __restrict__ out, int64_t b, int cnt, int vec, uint64_t le,
+                                                int& nans, int& fallbacks) {
+  const int bs = blockDim.x;
+  const BlobHdr& h = v.h;
+  const MlpFeatScale sc{h.e_lo, h.e_scale};
+  auto one = [&](int64_t i) {
+    const double y = Y[i];
+    const uint64_t k = order_key(y);
+    nans += k < kKeyNegInf;
+    out[i] = mlp_count(v, y, k + le, fallbacks);
+  };
+  const int head = vec ? min(cnt, (int)((-b) & 3)) : cnt;
+  const int nq = (cnt - head) >> 2;
+  for (int i = threadIdx.x; i < head; i += bs) one(b + i);
+  const double2* Y2 = reinterpret_cast<const double2*>(Y + b + head);
+  int4* O4 = reinterpret_cast<int4*>(out + b + head);
+  int g = threadIdx.x;
+  for (; g + bs < nq; g += 2 * bs) {
+    double y[8];
+    if (vec == 2) {
+      ld_stream4(reinterpret_cast<const double*>(Y2 + 2 * g), *reinterpret_cast<double(*)[4]>(y));
+      ld_stream4(reinterpret_cast<const double*>(Y2 + 2 * (g + bs)), *reinterpret_cast<double(*)[4]>(y + 4));
+    } else {
+      const double2 p0 = ld_stream(Y2 + 2 * g), p1 = ld_stream(Y2 + 2 * g + 1);
+      const double2 p2 = ld_stream(Y2 + 2 * (g + bs)), p3 = ld_stream(Y2 + 2 * (g + bs) + 1);
+      y[0] = p0.x; y[1] = p0.y; y[2] = p1.x; y[3] = p1.y;
+      y[4] = p2.x; y[5] = p2.y; y[6] = p3.x; y[7] = p3.y;
+    }
+    int prop[8], r[8];
+    mlp_propose_w<8>(v.mlp, sc, h.n, y, prop);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint64_t k = order_key(y[j]);
+      nans += k < kKeyNegInf;
+      r[j] = learned_count(v, prop[j], k + le, fallbacks);
+    }
+    st_stream(O4 + g, make_int4(r[0], r[1], r[2], r[3]));
+    st_stream(O4 + g + bs, make_int4(r[4], r[5], r[6], r[7]));
+  }
+  for (; g < nq; g += bs)
+    for (int j = 0; j < 4; ++j) one(b + head + 4 * (int64_t)g + j);
+  for (int i = head + 4 * nq + threadIdx.x; i < cnt; i += bs) one(b + i);
+}
+
 template <int G>
 __device__ __forceinline__ void ballot_tile(const StagedView& v, const double* __restrict__ Y, int32_t* __restrict__ out,
                                             int64_t b, int cnt, uint64_t le, int& nans) {
@@ -453,7 +500,7 @@ __device__ __forceinline__ void ballot_tile(const StagedView& v, const double* _
 }
 
 template <bool LE, int FAM>
-__global__ void __launch_bounds__(kNumThreads, FAM == FAM_MLP ? 2 : 4) k_batched_1d(BatchArgs1D a) {
+__global__ void __launch_bounds__(kNumThreads, 4) k_batched_1d(BatchArgs1D a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
   __shared__ int s_tile;
@@ -495,7 +542,10 @@ __global__ void __launch_bounds__(kNumThreads, FAM == FAM_MLP ? 2 : 4) k_batched
     // searches are branch-free straight-line code where the table allows it
     const int vec = a.vec;
     if (FAM >= FAM_MLP && algo == BL_MLP) {
-      stream_tile(a.Y, a.out, b, cnt, vec, le, nans, [&](double y, uint64_t q) { return mlp_count(v, y, q, fallbacks); });
+      // staged tables: the eight proposals of a thread together; sampled
+      // tables (wide windows searched in global memory) one by one
+      if (h.stride == 1) stream_tile_mlp(v, a.Y, a.out, b, cnt, vec, le, nans, fallbacks);
+      else stream_tile(a.Y, a.out, b, cnt, vec, le, nans, [&](double y, uint64_t q) { return mlp_count(v, y, q, fallbacks); });
     } else if (FAM >= FAM_SPLINE && algo == BL_SPLINE) {
       stream_tile(a.Y, a.out, b, cnt, vec, le, nans, [&](double, uint64_t q) { return spline_count(v, q, fallbacks); });
     } else if (FAM >= FAM_SPLINE && algo == BL_LOGHASH) {

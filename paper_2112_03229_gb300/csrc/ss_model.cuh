@@ -105,6 +105,32 @@ __device__ __forceinline__ float spline_position(const int* __restrict__ dir, in
   return (float)lo + frac * (float)(hi - lo);
 }
 
+// The MLP's proposals for W targets at once, hidden unit by hidden unit:
+// each unit's four parameters are read once for all W targets, so only
+// they, and not all 65, are live at a time.  Same arithmetic, in the same
+// order, as mlp_propose for each target.
+template <int W>
+__device__ __forceinline__ void mlp_propose_w(const float* __restrict__ p, const MlpFeatScale& s, int n,
+                                              const double (&t)[W], int (&prop)[W]) {
+  float x0[W], x1[W], y[W];
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    mlp_features(t[j], s, x0[j], x1[j]);
+    y[j] = p[4 * kHidden];
+  }
+#pragma unroll 2
+  for (int k = 0; k < kHidden; ++k) {
+    const float w0 = p[2 * k], w1 = p[2 * k + 1], bk = p[2 * kHidden + k], vk = p[3 * kHidden + k];
+#pragma unroll
+    for (int j = 0; j < W; ++j) y[j] = fmaf(vk, fmaxf(fmaf(w0, x0[j], fmaf(w1, x1[j], bk)), 0.0f), y[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    const float pos = rintf(y[j] * (float)(n - 1));
+    prop[j] = (int)fminf(fmaxf(pos, 0.0f), (float)(n - 1));
+  }
+}
+
 // Logarithm hash of Sec. 3.4 as a position proposal (no training).  With the
 // base b fitted so that the table's range spans n-1 steps (Eq. 1) and the
 // offset of Eq. 2, hash(t) = floor(log_b t - log_b X[0]) is the count of

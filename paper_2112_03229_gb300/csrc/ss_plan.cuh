@@ -16,14 +16,15 @@
 // tables, see ss_table.cuh); full keys hold all of them.
 //
 // Wide section (a table too large for shared memory as 8-byte keys, but not
-// as 16-bit ones): the keys form leaves of 16; per leaf, its last key (the
+// as 16-bit offsets): the keys form leaves of 16; per leaf, its last key (the
 // sample), a shift, and the 16 keys as offsets from the previous leaf's
-// last key, shifted right until they fit 16 bits.  A target's leaf comes
-// from a bucket directory over the samples; inside the leaf a 16-bit
-// comparison decides every key except those whose offset equals the
-// target's, which are compared in full from global memory (rare: the
-// truncation would have to land on the same 16-bit step).  Everything else
-// is one shared-memory stage of about 2.5 bytes per key.
+// last key, shifted right until they fit 15 bits (stored in 16).  A target's
+// leaf comes from a bucket directory over the samples; inside the leaf a
+// packed comparison of the offsets, two per 32-bit word, decides every key
+// except those whose offset equals the target's, which are compared in full
+// from global memory (rare: the truncation would have to land on the same
+// step).  Everything else is one shared-memory stage of about 2.5 bytes per
+// key.
 #pragma once
 
 #include "ss_ff.cuh"
@@ -249,11 +250,23 @@ __device__ __forceinline__ WideView wide_view(const unsigned char* sec, const St
   return wv;
 }
 
+// Number of the eight 15-bit offsets packed two per word in a, b (uint4
+// each) that are at least t (t <= 0x8000): for an offset x, (0x8000 | x) - t
+// keeps bit 15 set exactly when x >= t, and never borrows into the other
+// half of the word.
+__device__ __forceinline__ int count_ge15(const uint4& a, const uint4& b, uint32_t t) {
+  const uint32_t t2 = t | (t << 16);
+  const uint32_t m = 0x80008000u;
+  return __popc(((a.x | m) - t2) & m) + __popc(((a.y | m) - t2) & m) + __popc(((a.z | m) - t2) & m) +
+         __popc(((a.w | m) - t2) & m) + __popc(((b.x | m) - t2) & m) + __popc(((b.y | m) - t2) & m) +
+         __popc(((b.z | m) - t2) & m) + __popc(((b.w | m) - t2) & m);
+}
+
 // Count of keys below q on a wide section: the leaf from the sample
-// directory (SCAN1: at most one sample per bucket), then a branchless lower
-// bound of the target's 16-bit offset among the leaf's 16 (offsets below it
-// belong to smaller keys, above it to larger ones), then the keys whose
-// offset equals the target's, compared in full.
+// directory (SCAN1: at most one sample per bucket); in the leaf, the 16
+// offsets (15 bits each) are compared with the target's, two per 32-bit
+// word: offsets below it belong to smaller keys, above it to larger ones;
+// the keys whose offset equals the target's are compared in full.
 template <bool SCAN1>
 __device__ __forceinline__ int wide_count(const WideView& wv, uint64_t q) {
   const int s = SCAN1 ? search_bucket<1>(wv.samples, wv.dir, wv.w.shift, wv.w.base, wv.w.nb, q)
@@ -262,16 +275,14 @@ __device__ __forceinline__ int wide_count(const WideView& wv, uint64_t q) {
   if (s >= wv.w.L) return wv.nk;
   const uint64_t base = s > 0 ? wv.samples[s - 1] : wv.k0;
   if (q <= base) return kLeaf * s;               // only below X[0] (leaf 0)
-  const uint32_t tq = (uint32_t)((q - base) >> wv.shifts[s]);   // < 2^16: q <= samples[s]
-  const uint16_t* t = wv.leaf + kLeaf * s;
-  int c = 0;
-#pragma unroll
-  for (int step = kLeaf / 2; step > 0; step >>= 1) c += t[c + step - 1] < tq ? step : 0;
-  c += t[c] < tq ? 1 : 0;
-  while (c < kLeaf && t[c] == tq) {
+  const uint32_t tq = (uint32_t)((q - base) >> wv.shifts[s]);   // < 2^15: q <= samples[s]
+  const uint4* t4 = reinterpret_cast<const uint4*>(wv.leaf + kLeaf * s);
+  const uint4 a = t4[0], b = t4[1];
+  int c = kLeaf - count_ge15(a, b, tq);                          // offsets below the target's
+  const int le = kLeaf - count_ge15(a, b, tq + 1);               // ... at most the target's
+  for (; c < le; ++c) {                                          // equal offsets: full keys
     const int j = kLeaf * s + c;
     if (j >= wv.nk || __ldg(wv.full + j) >= q) break;
-    ++c;
   }
   return kLeaf * s + c;
 }
