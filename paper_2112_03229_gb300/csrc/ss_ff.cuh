@@ -140,14 +140,29 @@ struct Weights {
   ff w, wbar;
 };
 
+// 1 - a for 0 <= a <= 1/2 (plus rounding): the result is at least 1/2, so
+// the float-float difference keeps its relative precision.
+__device__ __forceinline__ ff one_minus(ff a) {
+  const ff s = two_sum(1.0f, -a.hi);
+  return fast_two_sum(s.hi, s.lo - a.lo);
+}
+
+// Only the smaller weight needs its exact numerator: it is at most 1/2, and
+// the larger one, 1 minus it, is at least 1/2, where the float-float
+// subtraction loses nothing relative to its size.  Both weights so keep
+// their full relative precision (however small the smaller one is).
 __device__ __forceinline__ Weights cell_weights(uint64_t u, const CellW& c) {
   const int ex = (int)((u >> 52) & 0x7FF);
   const uint64_t MxS = ((u & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << (ex - c.ec);
   const ff g{c.ghi, c.glo};
   const uint64_t D = MxS - c.Mc, Dn = c.MnS - MxS;
+  const bool low = D <= Dn;                      // the target sits in the lower half of the cell
+  const uint64_t v = low ? D : Dn;
+  const ff small = v == 0 ? ff{0.0f, 0.0f} : ff_mul_u(numerator(v), g);
+  const ff large = one_minus(small);
   Weights r;
-  r.w = D == 0 ? ff{0.0f, 0.0f} : ff_mul_u(numerator(D), g);
-  r.wbar = Dn == 0 ? ff{0.0f, 0.0f} : ff_mul_u(numerator(Dn), g);
+  r.w = low ? small : large;
+  r.wbar = low ? large : small;
   return r;
 }
 
