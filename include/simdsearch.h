@@ -207,6 +207,9 @@ typedef struct ss_plan_info {
   int64_t ntiles;           /* tiles of the bound batch */
   int32_t tuned;            /* 1 if the autotuner (or its cache) set the choices */
   int32_t kernels;          /* kernels one ss_plan_execute launches for the bound batch (0, 1 or 2) */
+  int32_t block_threads;    /* threads per block of the bound batched kernel (256, or 512 for large staged tables) */
+  int32_t smem_bytes;       /* dynamic shared memory per block of that kernel */
+  int32_t max_occupancy;    /* most keys in one directory bucket over the tables staged whole */
 } ss_plan_info;
 
 /* Fill *opts with the defaults. */

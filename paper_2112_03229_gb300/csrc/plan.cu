@@ -224,6 +224,9 @@ extern "C" ss_status ss_plan_info_get(const ss_plan* p, ss_plan_info* out) {
   out->ntiles = p->ntiles;
   out->tuned = p->tuned;
   out->kernels = p->kernels;
+  out->block_threads = p->threads;
+  out->smem_bytes = p->smem_bytes;
+  out->max_occupancy = p->max_occupancy;
   return SS_OK;
 }
 

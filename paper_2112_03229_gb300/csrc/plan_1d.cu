@@ -499,8 +499,14 @@ __device__ __forceinline__ void ballot_tile(const StagedView& v, const double* _
   }
 }
 
+// Launched with 256 threads, or with 512 when a staged table leaves room for
+// fewer than four 256-thread blocks on an SM (the bound keeps 64 registers
+// per thread either way, so an SM holds 1024 threads in both shapes).
+constexpr int kPlanMaxThreads = 512;
+int batched_1d_max_threads() { return kPlanMaxThreads; }
+
 template <bool LE, int FAM>
-__global__ void __launch_bounds__(kNumThreads, 4) k_batched_1d(BatchArgs1D a) {
+__global__ void __launch_bounds__(kPlanMaxThreads, 2) k_batched_1d(BatchArgs1D a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
   __shared__ int s_tile;

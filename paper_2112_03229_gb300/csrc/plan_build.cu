@@ -16,6 +16,7 @@
 namespace ss {
 
 int default_dir_cap(int n);
+int batched_1d_max_threads();   // largest block of the batched 1D kernel
 
 // Algorithm field (and the ballot top-level stride) of every blob.
 __global__ void k_set_algo(unsigned char* blobs, const int64_t* blob_off, const int* algo, int nblobs) {
@@ -74,8 +75,9 @@ ss_status plan_window_stats(ss_plan* p) {
   for (int k = 0; k < nb; ++k)
     SS_CHECK_CUDA(cudaMemcpy(&hs[k], p->d_blobs + p->blob_off[k], sizeof(BlobHdr), cudaMemcpyDeviceToHost));
   double sw = 0, sl = 0;
-  int mw = 0, cnt = 0;
+  int mw = 0, cnt = 0, occ = 0;
   for (const auto& h : hs) {
+    if (h.stride == 1 && h.algo != BL_WIDE) occ = std::max(occ, h.occ);
     if (h.algo == BL_SPLINE || h.algo == BL_MLP || h.algo == BL_LOGHASH) {
       mw = std::max(mw, h.E);
       sw += h.E;
@@ -84,6 +86,7 @@ ss_status plan_window_stats(ss_plan* p) {
     }
   }
   p->max_window = mw;
+  p->max_occupancy = occ;
   p->mean_window = cnt ? (float)(sw / cnt) : 0.0f;
   p->train_loss = cnt ? (float)(sl / cnt) : 0.0f;
   return SS_OK;
@@ -97,6 +100,75 @@ int table_algo(int algo, int n) {
   return n - 1 > kMaxSmemKeys ? BL_BINARY : BL_BUCKET;
 }
 
+// Host image of a table entry under the order-preserving key map.
+static uint64_t host_key(double x) {
+  uint64_t u;
+  std::memcpy(&u, &x, 8);
+  const uint64_t neg = (u >> 63) ? ~0ull : 0ull;
+  return (u ^ (neg | 0x8000000000000000ull)) - neg;
+}
+
+// Shared-memory budgets of a staged 1D table: four 256-thread blocks per SM,
+// or two 512-thread blocks per SM (the kernel is launched with 512 threads
+// when a table needs more than the first).
+constexpr int kStageBudgetSmall = 56 * 1024;
+constexpr int kStageBudgetLarge = 110 * 1024;
+constexpr int kRefitBytes = 4096;   // directory growth allowed for a table with two keys per bucket
+
+// Bucket budget of a table staged whole, from its own keys.  The directory
+// is cut at a power-of-two key granularity (Sec. 3.5's bins, generalised);
+// the default budget of about 4 buckets per entry leaves clustered tables
+// with crowded buckets, each costing a dependent shared-memory round trip
+// of the bisection inside the bucket.  Finer cuts are tried in turn: the
+// coarsest that leaves at most one key per bucket within the small budget,
+// else the coarsest with at most two keys (a two-key scan) within the large
+// budget, else the finest within the large budget.  A table whose default
+// directory already holds at most two keys per bucket is refitted only when
+// that adds at most kRefitBytes of directory (measured on GB300: a lone
+// 256-entry clustered table searched 10 % faster with one key per bucket,
+// while refitting the 1241..2000-entry tables of a 10,000-table batch bound
+// by HBM bandwidth made the batch 1 % slower).  The budget returned is the
+// exact bucket count of the chosen cut, so the device preparation, which
+// picks the finest cut whose bucket count fits the budget, arrives at the
+// same one.  keys: images of X[1..n-1] in order.
+int fitted_dir_cap(const std::vector<uint64_t>& keys, int n) {
+  const int def = default_dir_cap(n);
+  const int nk = (int)keys.size();
+  if (nk < 2 || nk > kMaxSmemKeys) return def;
+  for (int i = 1; i < nk; ++i)
+    if (!(keys[i] > keys[i - 1])) return def;   // not strictly increasing: preparation rejects the table
+  const uint64_t k0 = keys.front(), k1 = keys.back();
+  auto buckets = [&](int s) { return (k1 >> s) - (k0 >> s) + 1; };
+  auto occupancy = [&](int s) {
+    int best = 1, run = 1;
+    for (int i = 1; i < nk; ++i) {
+      run = (keys[i] >> s) == (keys[i - 1] >> s) ? run + 1 : 1;
+      best = std::max(best, run);
+    }
+    return best;
+  };
+  int s0 = 0;
+  while (s0 < 63 && ((k1 >> s0) - (k0 >> s0)) >= (uint64_t)def) ++s0;
+  const int occ0 = occupancy(s0);
+  if (occ0 <= 1) return def;
+  int fit1 = -1, fit2 = -1, finest = -1;
+  for (int s = s0; s >= 1; --s) {
+    const uint64_t nb = buckets(s);
+    if (nb > 65535) break;
+    const int bytes = staged_bytes(n, (int)nb, false, BL_BUCKET);
+    if (bytes > kStageBudgetLarge) break;
+    const int occ = occupancy(s);
+    finest = s;
+    if (occ <= 1 && bytes <= kStageBudgetSmall && fit1 < 0) fit1 = s;
+    if (occ <= 2 && fit2 < 0) fit2 = s;
+    if (occ <= 1) break;
+  }
+  const int s = fit1 >= 0 ? fit1 : fit2 >= 0 ? fit2 : finest;
+  if (s < 0 || s == s0) return def;
+  if (occ0 <= 2 && (int64_t)(buckets(s) - buckets(s0)) * 4 > kRefitBytes) return def;
+  return (int)buckets(s);
+}
+
 ss_status plan_build_1d(ss_plan* p, const double* X, cudaStream_t stream) {
   const int nt = p->ntables;
   const ss_plan_opts& o = p->opts;
@@ -107,10 +179,26 @@ ss_status plan_build_1d(ss_plan* p, const double* X, cudaStream_t stream) {
     for (int k = 0; k < nt; ++k)
       if (wide_eligible(p->sizes[k] - 1)) p->algo[k] = BL_WIDE;
   p->blob_off.resize(nt);
+  // directory budgets fitted to the tables' keys (a host copy of the tables; set-up only)
+  std::vector<double> Xh;
+  if (o.dir_cap == 0 && p->X_off[nt] > 0) {
+    Xh.resize((size_t)p->X_off[nt]);
+    SS_CHECK_CUDA(cudaMemcpyAsync(Xh.data(), X, Xh.size() * sizeof(double), cudaMemcpyDefault, stream));
+    SS_CHECK_CUDA(cudaStreamSynchronize(stream));
+  }
   int64_t off = 0;
   for (int k = 0; k < nt; ++k) {
     const int n = p->sizes[k];
-    p->dir_cap[k] = o.dir_cap > 0 ? o.dir_cap : default_dir_cap(n);
+    if (o.dir_cap > 0) {
+      p->dir_cap[k] = o.dir_cap;
+    } else {
+      std::vector<uint64_t> keys;
+      if (n - 1 <= kMaxSmemKeys) {
+        keys.resize(n - 1);
+        for (int j = 1; j < n; ++j) keys[j - 1] = host_key(Xh[(size_t)p->X_off[k] + j]);
+      }
+      p->dir_cap[k] = keys.empty() ? default_dir_cap(n) : fitted_dir_cap(keys, n);
+    }
     p->blob_off[k] = off;
     off += (blob_geom_dev(n, p->dir_cap[k], false).bytes + 255) & ~(int64_t)255;
   }
@@ -230,7 +318,18 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
   else kern = batched_2d_kernel(p->opts.model == SS_MODEL_HUNT);
   SS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int per_sm = 0;
-  SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNumThreads, smem));
+  int threads = kNumThreads;
+  SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+  if (p->kind == 1 && per_sm * kNumThreads < 1024) {
+    // a large staged table: fewer, wider blocks share one staged copy
+    int per_sm_big = 0;
+    const int big = batched_1d_max_threads();
+    SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_big, kern, big, smem));
+    if (per_sm_big * big > per_sm * kNumThreads) {
+      per_sm = per_sm_big;
+      threads = big;
+    }
+  }
   if (per_sm < 1) return fail(SS_EUNSUPPORTED, "plan: kernel does not fit on an SM");
   const int resident = num_sms() * per_sm;
   const void* kern_w = nullptr;
@@ -266,6 +365,7 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
     SS_CHECK_CUDA(cudaMemcpy(p->d_tiles, reg.data(), reg.size() * sizeof(Tile), cudaMemcpyHostToDevice));
   }
   p->smem_bytes = smem;
+  p->threads = threads;
   p->kernels = p->kind == 2 ? (p->ntiles > 0 ? 1 : 0) : (nreg > 0 ? 1 : 0) + (nw > 0 ? 1 : 0);
   p->grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)resident, nreg));
   const int grid_w = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)resident_w, nw));
@@ -282,7 +382,7 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
       if (nreg > 0) {
         BatchArgs1D a{p->d_blobs, p->d_blob_off, p->d_tiles, (int)nreg, p->d_counter, Y, out, vec, stat};
         void* args[1] = {&a};
-        e = cudaLaunchKernel(kern, dim3(p->grid_blocks), dim3(kNumThreads), args, (size_t)smem, p->cap_stream);
+        e = cudaLaunchKernel(kern, dim3(p->grid_blocks), dim3(threads), args, (size_t)smem, p->cap_stream);
       }
       if (e == cudaSuccess && nw > 0) {
         BatchArgs1D a{p->d_blobs, p->d_blob_off, p->d_tiles + nreg, (int)nw, p->d_counter + 1, Y, out, vec, stat};

@@ -62,11 +62,13 @@ struct PlanBase {
   int grid_blocks = 0;
   int kernels = 0;                    // kernels in the bound graph
   int smem_bytes = 0;
+  int threads = 0;                    // threads per block of the bound batched kernel
   // diagnostics
   int64_t device_bytes = 0;
   int max_window = 0;
   float mean_window = 0.0f;
   float train_loss = 0.0f;
+  int max_occupancy = 0;              // most keys in one bucket over the tables staged whole
 };
 
 ss_status plan_build_1d(ss_plan* p, const double* X, cudaStream_t stream);

@@ -82,6 +82,46 @@ def test_plan_table_size_sweep(ss, model):
     np.testing.assert_array_equal(got, want)
 
 
+@pytest.mark.parametrize("side", [0, 1])
+@pytest.mark.parametrize("tile", [0, 1000])
+def test_plan_fitted_directory_and_wide_blocks(ss, side, tile):
+    """A clustered 4096-entry table crowds the default bucket budget (up to 9
+    keys in a bucket); the plan fits a finer directory to its keys (at most
+    2 per bucket) and, with that table staged, runs 512-thread blocks.
+    Smaller tables in the same batch, ragged tiles (tile=1000, not a multiple
+    of the vector width) and a misaligned target array keep exact indices."""
+    tabs = [wl.sweep_table(n) for n in (16, 256, 4096)]
+    X = torch.cat(tabs)
+    X_off = np.concatenate([[0], np.cumsum([len(t) for t in tabs])])
+    Ys = [wl.log_uniform(50_001 + 7 * i, 0.5 * t[0].item(), 2 * t[-1].item(), seed=30 + i) for i, t in enumerate(tabs)]
+    Ys[2][:4095] = tabs[2][1:]                               # exact hits on every searched key
+    Ys[2][4095:8190] = torch.from_numpy(np.nextafter(tabs[2][1:].numpy(), -np.inf))
+    Y = torch.cat(Ys)
+    Y_off = np.concatenate([[0], np.cumsum([len(y) for y in Ys])])
+    want = oracle.search_1d_batched(X_off, X.numpy(), Y_off, Y.numpy(), side)
+    plan = ss.Plan.create_1d(X_off, X.to(DEV), side=side, tile=tile)
+    inf = plan.info()
+    assert inf.max_occupancy <= 2
+    buf = torch.empty(Y.numel() + 1, dtype=torch.float64, device=DEV)
+    Yd = buf[1:]                                              # 8-byte aligned, not 16
+    Yd.copy_(Y)
+    out = torch.full((Y.numel(),), -1, dtype=torch.int32, device=DEV)
+    stat = ss.new_stat()
+    plan.bind_1d(Y_off, Yd, out, stat=stat)
+    assert plan.info().block_threads == 512
+    plan.execute()
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
+    assert ss.read_stat(stat).flags == 0
+    # the same batch with the default directory budget keeps 256-thread blocks
+    plan2 = ss.Plan.create_1d(X_off, X.to(DEV), side=side, tile=tile, dir_cap=4096)
+    assert plan2.info().max_occupancy > 2
+    out2 = torch.full_like(out, -1)
+    plan2.bind_1d(Y_off, Yd, out2)
+    assert plan2.info().block_threads == 256
+    plan2.execute()
+    np.testing.assert_array_equal(out2.cpu().numpy(), want)
+
+
 def test_plan_wide_section_with_ties(ss):
     """Tables of 8129..~76K entries search a wide section (16-bit offsets in
     shared memory).  Runs of consecutive doubles inside a leaf whose other
