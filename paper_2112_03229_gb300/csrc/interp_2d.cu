@@ -33,7 +33,7 @@ constexpr int kMaxAxis2D = 4096;   // largest axis staged whole with its per-cel
 
 struct Axis2D {                    // shared-memory offsets of one axis
   Layout1D lay;
-  int cells;                       // CellW[n-1]: exact weight numerators' data and scale
+  int cells;                       // cell table of n-1 cells (CellTable layout): exact weight numerators' data and scale
   int rg;                          // double[n-1]: 1 / (X[c+1] - X[c]) for the fp64 path (X[c] read from global);
                                    // in log coordinates 1 / (ln X[c+1] - ln X[c])
   int lx;                          // double[n]: ln X[j] (log coordinates only, else -1)
@@ -68,7 +68,6 @@ struct Args2D {
 
 // Per-cell data and the float-float eligibility of one axis.
 static __device__ void stage_cells(const double* __restrict__ X, int n, const Axis2D& ax, unsigned char* smem) {
-  CellW* cells = reinterpret_cast<CellW*>(smem + ax.cells);
   double* rg = reinterpret_cast<double*>(smem + ax.rg);
   double* lx = ax.lx >= 0 ? reinterpret_cast<double*>(smem + ax.lx) : nullptr;
   AxisAux& aux = *reinterpret_cast<AxisAux*>(smem + ax.aux);
@@ -85,7 +84,7 @@ static __device__ void stage_cells(const double* __restrict__ X, int n, const Ax
     }
     CellW w;
     ok &= make_cell(a, b, w);
-    cells[c] = w;
+    store_cell(smem + ax.cells, n - 1, c, w);
   }
   ok = __syncthreads_and(ok);
   if (threadIdx.x == 0) {
@@ -101,7 +100,7 @@ struct AxisView {
   const uint64_t* keys;
   const uint64_t* eyt;
   const int* dir;
-  const CellW* cells;
+  CellTable cells;
   const double* x;           // the axis in global memory
   const double* rg;
   const double* lx;          // ln X[j] (log coordinates), else nullptr
@@ -117,7 +116,7 @@ __device__ __forceinline__ AxisView view_of(const Axis2D& ax, const unsigned cha
   v.keys = ax.lay.keys >= 0 ? reinterpret_cast<const uint64_t*>(smem + ax.lay.keys) : nullptr;
   v.eyt = ax.lay.eyt >= 0 ? reinterpret_cast<const uint64_t*>(smem + ax.lay.eyt) : nullptr;
   v.dir = ax.lay.dir >= 0 ? reinterpret_cast<const int*>(smem + ax.lay.dir) : nullptr;
-  v.cells = reinterpret_cast<const CellW*>(smem + ax.cells);
+  v.cells = cell_table(smem + ax.cells, h.n - 1);
   v.rg = reinterpret_cast<const double*>(smem + ax.rg);
   v.lx = ax.lx >= 0 ? reinterpret_cast<const double*>(smem + ax.lx) : nullptr;
   v.extrap = 0;
@@ -143,7 +142,7 @@ __device__ __forceinline__ int axis_search(const AxisView& a, uint64_t k) {
 __device__ __forceinline__ Weights axis_weights_ff(const AxisView& a, int i, int c, uint64_t k, uint64_t u) {
   if (i >= a.n - 1) return {{1.0f, 0.0f}, {0.0f, 0.0f}};          // above the last entry
   if (i == 0 && k <= a.k0) return {{0.0f, 0.0f}, {1.0f, 0.0f}};   // at or below the first entry
-  return cell_weights(u, a.cells[c]);
+  return cell_weights(u, a.cells, c);
 }
 
 // fp64 weight of coordinate x in cell c: linear or log coordinates, clamped
@@ -324,7 +323,7 @@ static Axis2D make_axis(int n, int algo, int offset, bool logspace) {
   ax.lay = make_layout_1d(n, bucket, !bucket, bucket ? default_dir_cap(n) : 0, offset);
   int off = ax.lay.bytes;
   auto take = [&](int bytes) { int o = off; off += (bytes + 15) & ~15; return o; };
-  ax.cells = take((n - 1) * (int)sizeof(CellW));
+  ax.cells = take((n - 1) * kCellBytes);
   ax.rg = take((n - 1) * 8);
   ax.lx = logspace ? take(n * 8) : -1;
   ax.aux = take((int)sizeof(AxisAux));

@@ -19,7 +19,7 @@ __host__ __device__ inline BlobGeom blob_geom_dev(int n, int dir_cap, bool cells
   g.off_keys = off; off += (g.ns + kPad) * 8;
   g.off_eyt = off;  off += g.P * 8;
   g.off_cells = -1;
-  if (cells) { g.off_cells = off; off += (((n - 1) * (int)sizeof(CellW)) + 15) & ~15; }
+  if (cells) { off = (off + 15) & ~15; g.off_cells = off; off += (((n - 1) * kCellBytes) + 15) & ~15; }   // 16-byte aligned cell table
   g.staged_end = off;
   g.off_full = g.stride > 1 ? off : -1;
   g.bytes = g.stride > 1 ? wide_offset(off, nk) : ((off + 15) & ~15);
@@ -102,7 +102,7 @@ __global__ void k_window(WindowArgs a);
 const void* batched_1d_kernel(bool le, int family);   // family: 0 plain, 1 +spline/loghash, 2 +mlp
 const void* batched_1d_wide_kernel(bool le);          // tables searched through their wide section
 constexpr int kWideThreads = 1024;
-const void* batched_2d_kernel(bool hunt);            // hunt: second pair of a thread starts from the first
+const void* batched_2d_kernel(bool hunt, bool learned);   // hunt: second pair of a thread starts from the first; learned: position models compiled in
 __global__ void k_grid_to_ff(const double* F, float2* G, int64_t count, unsigned* bad);
 __global__ void k_prep_cells(PrepArgs a);
 

@@ -22,12 +22,12 @@ __global__ void __launch_bounds__(256) k_prep_cells(PrepArgs a) {
   const int n = (int)(a.X_off[k + 1] - a.X_off[k]);
   unsigned char* blob = a.blobs + a.blob_off[k];
   BlobHdr* h = reinterpret_cast<BlobHdr*>(blob);
-  CellW* cells = reinterpret_cast<CellW*>(blob + h->off_cells);
+  unsigned char* cells = blob + h->off_cells;
   bool ok = true;
   for (int c = threadIdx.x; c < n - 1; c += blockDim.x) {
     CellW w;
     ok &= make_cell(X[c], X[c + 1], w);
-    cells[c] = w;
+    store_cell(cells, n - 1, c, w);
   }
   ok = __syncthreads_and(ok);
   if (threadIdx.x == 0) h->ffok = ok ? 1 : 0;
@@ -66,8 +66,11 @@ __global__ void __launch_bounds__(256) k_grid_cells(const double* __restrict__ F
   if (!ok) atomicOr(bad, 1u);
 }
 
-// Exact count for one axis with the axis' algorithm.
+// Exact count for one axis with the axis' algorithm (LEARNED: the position
+// models are compiled in; a plan without them runs a kernel built without).
+template <bool LEARNED>
 __device__ __forceinline__ int axis_count(const StagedView& v, double t, uint64_t q, int& fallbacks) {
+  if (!LEARNED) return v.h.algo == BL_BINARY ? plain_binary(v, q) : plain_bucket(v, q);
   switch (v.h.algo) {
     case BL_BINARY: return plain_binary(v, q);
     case BL_SPLINE: return spline_count(v, q, fallbacks);
@@ -89,7 +92,7 @@ __device__ __forceinline__ Weights axis_weights(const StagedView& v, int i, int 
   const BlobHdr& h = v.h;
   if (i >= h.n - 1) return {{1.0f, 0.0f}, {0.0f, 0.0f}};
   if (i == 0 && k <= h.k0) return {{0.0f, 0.0f}, {1.0f, 0.0f}};
-  if (h.ffok) return cell_weights(static_cast<uint64_t>(__double_as_longlong(x)), v.cells[c]);
+  if (h.ffok) return cell_weights(static_cast<uint64_t>(__double_as_longlong(x)), v.cells, c);
   const double a = entry_value(v, c), b = entry_value(v, c + 1);
   double w = (x - a) / (b - a);
   w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
@@ -211,8 +214,11 @@ __device__ __forceinline__ void stream_pairs(const BatchArgs2D& a, const StagedV
   for (int i = head + 2 * np2 + threadIdx.x; i < cnt; i += blockDim.x) scalar(i);
 }
 
-template <bool HUNT>
-__global__ void __launch_bounds__(kNumThreads) k_batched_2d(BatchArgs2D a) {
+// Three blocks per SM (80 registers).  A plan without position models runs
+// the kernel built without them (LEARNED false), which fits that budget
+// without spilling.
+template <bool HUNT, bool LEARNED>
+__global__ void __launch_bounds__(kNumThreads, 3) k_batched_2d(BatchArgs2D a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
   __shared__ int s_tile;
@@ -255,7 +261,7 @@ __global__ void __launch_bounds__(kNumThreads) k_batched_2d(BatchArgs2D a) {
     // staged tables with at most two keys per bucket (the common case) take a
     // branch-free two-key scan; every other combination the generic dispatch
     auto generic = [&](const StagedView& v) {
-      return [&v, &fallbacks](double t, uint64_t q) { return axis_count(v, t, q, fallbacks); };
+      return [&v, &fallbacks](double t, uint64_t q) { return axis_count<LEARNED>(v, t, q, fallbacks); };
     };
     auto scan2 = [](const StagedView& v) {
       const uint64_t* keys = v.keys;
@@ -284,8 +290,10 @@ __global__ void __launch_bounds__(kNumThreads) k_batched_2d(BatchArgs2D a) {
 }
 
 // Kernel entry of the batched 2D lookup (template stubs stay local to this unit).
-const void* batched_2d_kernel(bool hunt) {
-  return hunt ? reinterpret_cast<const void*>(&k_batched_2d<true>) : reinterpret_cast<const void*>(&k_batched_2d<false>);
+const void* batched_2d_kernel(bool hunt, bool learned) {
+  if (learned)
+    return hunt ? reinterpret_cast<const void*>(&k_batched_2d<true, true>) : reinterpret_cast<const void*>(&k_batched_2d<false, true>);
+  return hunt ? reinterpret_cast<const void*>(&k_batched_2d<true, false>) : reinterpret_cast<const void*>(&k_batched_2d<false, false>);
 }
 
 void plan_cell_offsets(PlanBase* p) {

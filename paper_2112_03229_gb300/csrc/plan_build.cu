@@ -315,7 +315,7 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
   int family = 0;
   for (int a : p->algo) family = std::max(family, a == BL_MLP ? 2 : (a == BL_SPLINE || a == BL_LOGHASH) ? 1 : 0);
   if (p->kind == 1) kern = batched_1d_kernel(p->opts.side == SS_SIDE_LE, family);
-  else kern = batched_2d_kernel(p->opts.model == SS_MODEL_HUNT);
+  else kern = batched_2d_kernel(p->opts.model == SS_MODEL_HUNT, family > 0);
   SS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int per_sm = 0;
   int threads = kNumThreads;

@@ -97,7 +97,7 @@ __device__ __forceinline__ double widen(float f) {
 // Double nearest to hi + lo (one fp64 add rounds the exact sum).
 __device__ __forceinline__ double ff2d(ff a) { return widen(a.hi) + widen(a.lo); }
 
-// Per-cell data for the float-float weights (32 bytes).
+// Per-cell data for the float-float weights, as computed.
 struct CellW {
   uint64_t Mc;      // significand of X[c] (53 bits with the implicit one)
   uint64_t MnS;     // significand of X[c+1] shifted left by e(X[c+1]) - e(X[c])
@@ -105,6 +105,33 @@ struct CellW {
   int pad;
   float ghi, glo;   // 2^48 / (MnS - Mc) as float-float
 };
+
+// Cell data as stored in memory, 24 bytes per cell in a 16-byte aligned
+// region: an array of 16-byte records A[c] = {Mc | ec << 53, MnS} (the
+// exponent sits above the 53-bit significand), then an array of 8-byte
+// scales G[c] = {ghi, glo}.  Each array is read with one load per cell at its
+// own stride, which spreads a warp's random reads over all shared-memory
+// banks; 32-byte records read field by field put the same field of every
+// cell on one quarter of the banks and conflicted about twice as often.
+// The scale is only needed at the end of the weight computation, so it is
+// read there and the record's registers are free by then.
+constexpr int kCellBytes = 24;
+
+struct CellTable {
+  const ulonglong2* a;
+  const float2* g;
+};
+
+__device__ __forceinline__ CellTable cell_table(const void* region, int ncell) {
+  const ulonglong2* a = reinterpret_cast<const ulonglong2*>(region);
+  return {a, reinterpret_cast<const float2*>(a + ncell)};
+}
+
+__device__ __forceinline__ void store_cell(void* region, int ncell, int c, const CellW& w) {
+  ulonglong2* a = reinterpret_cast<ulonglong2*>(region);
+  a[c] = make_ulonglong2(w.Mc | ((uint64_t)w.ec << 53), w.MnS);
+  reinterpret_cast<float2*>(a + ncell)[c] = make_float2(w.ghi, w.glo);
+}
 
 // Cell data of [a, b]; false if the cell is outside the float-float preconditions.
 __device__ __forceinline__ bool make_cell(double a, double b, CellW& c) {
@@ -151,13 +178,17 @@ __device__ __forceinline__ ff one_minus(ff a) {
 // the larger one, 1 minus it, is at least 1/2, where the float-float
 // subtraction loses nothing relative to its size.  Both weights so keep
 // their full relative precision (however small the smaller one is).
-__device__ __forceinline__ Weights cell_weights(uint64_t u, const CellW& c) {
+__device__ __forceinline__ Weights cell_weights(uint64_t u, const CellTable& t, int c) {
+  const ulonglong2 rec = t.a[c];
+  const int ec = (int)(rec.x >> 53);
+  const uint64_t Mc = rec.x & ((1ull << 53) - 1), MnS = rec.y;
   const int ex = (int)((u >> 52) & 0x7FF);
-  const uint64_t MxS = ((u & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << (ex - c.ec);
-  const ff g{c.ghi, c.glo};
-  const uint64_t D = MxS - c.Mc, Dn = c.MnS - MxS;
+  const uint64_t MxS = ((u & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << (ex - ec);
+  const uint64_t D = MxS - Mc, Dn = MnS - MxS;
   const bool low = D <= Dn;                      // the target sits in the lower half of the cell
   const uint64_t v = low ? D : Dn;
+  const float2 gs = t.g[c];
+  const ff g{gs.x, gs.y};
   const ff small = v == 0 ? ff{0.0f, 0.0f} : ff_mul_u(numerator(v), g);
   const ff large = one_minus(small);
   Weights r;

@@ -54,7 +54,7 @@ struct __align__(16) BlobHdr {
   float loss;                // final training loss of the MLP (diagnostic)
   int gnb;                   // fine directory: bucket count (0: none)
   // 2D axes only: per-cell float-float data follows the staged part
-  int off_cells;             // CellW[n-1] (staged with the axis), -1 for 1D
+  int off_cells;             // cell table of n-1 cells (staged with the axis, 16-byte aligned), -1 for 1D
   int ffok;                  // cells usable by the float-float path
   uint64_t gbase;            // fine directory: bucket of the first key
 };
@@ -181,7 +181,7 @@ struct StagedView {
   const int* dir;
   const uint64_t* keys;
   const uint64_t* eyt;
-  const CellW* cells;
+  CellTable cells;           // 2D axes: per-cell weight data
   const uint64_t* full;      // global full keys (stride > 1)
   const int* gdir;           // global fine directory over all keys (stride > 1)
 };
@@ -219,7 +219,7 @@ __device__ __forceinline__ StagedView stage_blob(const unsigned char* __restrict
   v.dir = reinterpret_cast<const int*>(dst + hdr.off_dir + shift_off);
   v.keys = reinterpret_cast<const uint64_t*>(dst + hdr.off_keys + shift_off);
   v.eyt = reinterpret_cast<const uint64_t*>(dst + hdr.off_eyt + shift_off);
-  v.cells = hdr.off_cells >= 0 ? reinterpret_cast<const CellW*>(dst + hdr.off_cells + shift_off) : nullptr;
+  v.cells = hdr.off_cells >= 0 ? cell_table(dst + hdr.off_cells + shift_off, hdr.n - 1) : CellTable{nullptr, nullptr};
   v.full = hdr.off_full >= 0 ? reinterpret_cast<const uint64_t*>(src + hdr.off_full) : nullptr;
   v.gdir = hdr.gnb > 0 ? reinterpret_cast<const int*>(src + hdr.off_full + (int64_t)(hdr.nk + kPad) * 8) : nullptr;
   return v;
