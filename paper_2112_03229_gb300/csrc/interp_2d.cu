@@ -174,7 +174,7 @@ __device__ __forceinline__ double blend64w(double wr, double wrb, double wt, dou
 template <int MODE, bool FF, bool SG>
 __device__ __forceinline__ void lookup_pair(const AxisView& vr, const AxisView& vt, const double* __restrict__ F,
                                             const float2* __restrict__ Gs, int nt, double rho, double tem, int& ir,
-                                            int& it, double& v, int& nans) {
+                                            int& it, double& v, int& nans, bool gall) {
   const uint64_t ur = static_cast<uint64_t>(__double_as_longlong(rho));
   const uint64_t ut = static_cast<uint64_t>(__double_as_longlong(tem));
   const uint64_t kr = order_key(rho), kt = order_key(tem);
@@ -205,7 +205,7 @@ __device__ __forceinline__ void lookup_pair(const AxisView& vr, const AxisView& 
   if (SG) {
     const float2 g00 = Gs[o], g01 = Gs[o + 1], g10 = Gs[o + nt], g11 = Gs[o + nt + 1];
     a00 = {g00.x, g00.y}; a01 = {g01.x, g01.y}; a10 = {g10.x, g10.y}; a11 = {g11.x, g11.y};
-    ok = !(isnan(g00.x) | isnan(g01.x) | isnan(g10.x) | isnan(g11.x));
+    ok = gall || !(isnan(g00.x) | isnan(g01.x) | isnan(g10.x) | isnan(g11.x));   // gall: every value split
   } else {
     const double* f = F + o;
     ok = d2ff(__ldg(f), a00) & d2ff(__ldg(f + 1), a01) & d2ff(__ldg(f + nt), a10) & d2ff(__ldg(f + nt + 1), a11);
@@ -227,14 +227,14 @@ __device__ __forceinline__ void lookup_pair(const AxisView& vr, const AxisView& 
 
 template <int MODE, bool FF, bool SG>
 __device__ __forceinline__ int stream_pairs(const Args2D& a, const AxisView& vr, const AxisView& vt,
-                                            const float2* Gs) {
+                                            const float2* Gs, bool gall) {
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gs = (int64_t)gridDim.x * blockDim.x;
   int nans = 0;
   auto scalar = [&](int64_t i) {
     int ir, it;
     double v;
-    lookup_pair<MODE, FF, SG>(vr, vt, a.F, Gs, a.nt, a.Y2[2 * i], a.Y2[2 * i + 1], ir, it, v, nans);
+    lookup_pair<MODE, FF, SG>(vr, vt, a.F, Gs, a.nt, a.Y2[2 * i], a.Y2[2 * i + 1], ir, it, v, nans, gall);
     a.idx[2 * i] = ir;
     a.idx[2 * i + 1] = it;
     a.val[i] = v;
@@ -247,8 +247,8 @@ __device__ __forceinline__ int stream_pairs(const Args2D& a, const AxisView& vr,
     const double2 p0 = ld_stream(Y + 2 * g), p1 = ld_stream(Y + 2 * g + 1);
     int i0, j0, i1, j1;
     double v0, v1;
-    lookup_pair<MODE, FF, SG>(vr, vt, a.F, Gs, a.nt, p0.x, p0.y, i0, j0, v0, nans);
-    lookup_pair<MODE, FF, SG>(vr, vt, a.F, Gs, a.nt, p1.x, p1.y, i1, j1, v1, nans);
+    lookup_pair<MODE, FF, SG>(vr, vt, a.F, Gs, a.nt, p0.x, p0.y, i0, j0, v0, nans, gall);
+    lookup_pair<MODE, FF, SG>(vr, vt, a.F, Gs, a.nt, p1.x, p1.y, i1, j1, v1, nans, gall);
     st_stream(I4 + g, make_int4(i0, j0, i1, j1));
     st_stream(V2 + g, make_double2(v0, v1));
   }
@@ -263,16 +263,19 @@ __device__ __forceinline__ void interp_body(const Args2D& a, unsigned char* smem
   stage_cells(a.R, a.nr, a.ar, smem);
   stage_cells(a.T, a.nt, a.at, smem);
   float2* Gs = nullptr;
+  bool gok = true;
   if (SG) {
     // the value grid as float-float, once per block
     Gs = reinterpret_cast<float2*>(smem + a.grid_smem);
     const int64_t cnt = (int64_t)a.nr * a.nt;
     for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
       ff r;
-      Gs[i] = d2ff(__ldg(a.F + i), r) ? make_float2(r.hi, r.lo) : make_float2(__int_as_float(0x7FC00000), 0.0f);
+      const bool ok = d2ff(__ldg(a.F + i), r);
+      gok &= ok;
+      Gs[i] = ok ? make_float2(r.hi, r.lo) : make_float2(__int_as_float(0x7FC00000), 0.0f);
     }
   }
-  __syncthreads();
+  const bool gall = __syncthreads_and(gok);   // every grid value split exactly enough (no fp64 corners)
   AxisView vr = view_of(a.ar, smem), vt = view_of(a.at, smem);
   vr.x = a.R;
   vt.x = a.T;
@@ -284,12 +287,12 @@ __device__ __forceinline__ void interp_body(const Args2D& a, unsigned char* smem
   const int mode = a.algo == SS_ALGO_BINARY ? 2 : (hr.occ <= 1 && ht.occ <= 1) ? 0 : (hr.occ <= 2 && ht.occ <= 2) ? 3 : 1;
   int nans;
   if (ff) {
-    nans = mode == 0 ? stream_pairs<0, true, SG>(a, vr, vt, Gs)
-         : mode == 3 ? stream_pairs<3, true, SG>(a, vr, vt, Gs)
-         : mode == 1 ? stream_pairs<1, true, SG>(a, vr, vt, Gs) : stream_pairs<2, true, SG>(a, vr, vt, Gs);
+    nans = mode == 0 ? stream_pairs<0, true, SG>(a, vr, vt, Gs, gall)
+         : mode == 3 ? stream_pairs<3, true, SG>(a, vr, vt, Gs, gall)
+         : mode == 1 ? stream_pairs<1, true, SG>(a, vr, vt, Gs, gall) : stream_pairs<2, true, SG>(a, vr, vt, Gs, gall);
   } else {
-    nans = mode == 0 ? stream_pairs<0, false, false>(a, vr, vt, Gs)
-         : mode == 2 ? stream_pairs<2, false, false>(a, vr, vt, Gs) : stream_pairs<1, false, false>(a, vr, vt, Gs);
+    nans = mode == 0 ? stream_pairs<0, false, false>(a, vr, vt, Gs, gall)
+         : mode == 2 ? stream_pairs<2, false, false>(a, vr, vt, Gs, gall) : stream_pairs<1, false, false>(a, vr, vt, Gs, gall);
   }
   nans = __reduce_add_sync(0xFFFFFFFFu, nans);
   if (a.stat != nullptr) {

@@ -149,7 +149,8 @@ __device__ __forceinline__ void pair_2d(const StagedView& vr, const StagedView& 
   const Weights wt = axis_weights(vt, it, ct, kt, tem);
   if (nan) {
     v = __longlong_as_double(0x7FF8000000000000ll);
-  } else if (!(isnan(g00.x) | isnan(g01.x) | isnan(g10.x) | isnan(g11.x))) {
+  } else if (G64 == nullptr || !(isnan(g00.x) | isnan(g01.x) | isnan(g10.x) | isnan(g11.x))) {
+    // (a plan keeps the fp64 grid only when some value is outside the float-float range)
     const ff lo = ff_add_u(ff_mul_u(wt.wbar, ff{g00.x, g00.y}), ff_mul_u(wt.w, ff{g01.x, g01.y}));
     const ff hi = ff_add_u(ff_mul_u(wt.wbar, ff{g10.x, g10.y}), ff_mul_u(wt.w, ff{g11.x, g11.y}));
     v = ff2d(ff_add_u(ff_mul_u(wr.wbar, lo), ff_mul_u(wr.w, hi)));

@@ -351,6 +351,27 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
                                          : auto_tile(wb ? total_w : total_reg, wb ? resident_w : resident, smem_b[b],
                                                      p->bucket_mult[b]);
   }
+  if (p->kind == 2 && p->opts.tile <= 0) {
+    // 2D lookups gather corner records from the grids of the tables in
+    // flight.  Blocks take consecutive tiles, so about resident / (tiles per
+    // table) tables are in flight; tiles are capped so that their records
+    // fit in a quarter of L2 (a batch of 1,000 tables of 1.45 MB of records
+    // ran 4 % faster with 32K-pair tiles than with the tuned 91K).
+    int dev = 0, l2 = 0;
+    SS_CHECK_CUDA(cudaGetDevice(&dev));
+    SS_CHECK_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    double pairs[kNumBuckets] = {0}, rec[kNumBuckets] = {0};
+    for (int k = 0; k < p->ntables; ++k) {
+      pairs[bucket_of[k]] += (double)(Y_off[k + 1] - Y_off[k]);
+      rec[bucket_of[k]] += 32.0 * (double)(p->cell_off[k + 1] - p->cell_off[k]);
+    }
+    for (int b = 0; b < kNumBuckets; ++b) {
+      if (pairs[b] <= 0 || rec[b] <= 0) continue;
+      const double cap = pairs[b] / rec[b] * (0.25 * l2) / std::max(1, resident);
+      const int c = (int)std::max(8192.0, std::min(cap, (double)p->bucket_tile[b])) & ~255;
+      p->bucket_tile[b] = std::min(p->bucket_tile[b], c);
+    }
+  }
   int64_t total = 0;
   std::vector<Tile> tiles = make_tiles(Y_off, bucket_of, p->bucket_tile, total);
   std::vector<Tile> reg, wtiles;

@@ -7,7 +7,7 @@
 // 2^-47 per operation), built from the error-free transformations of Knuth
 // (two-sum), Dekker (fast two-sum) and the fma-based exact product.  Doubles
 // are split into hi + lo with integer bit operations, so the hot loop issues
-// no fp64 arithmetic except one final add per output value.
+// no fp64 arithmetic except the final widening and add per output value.
 //
 // The interpolation weights are formed from exact integers: for a target x in
 // cell [X_c, X_c+1] whose binary exponents differ by at most kMaxCellOctaves,
@@ -86,16 +86,10 @@ __device__ __forceinline__ bool d2ff(double d, ff& r) {
   return ok;
 }
 
-// Exact widening of a float (zero and subnormals give 0: below 2^-126).
-__device__ __forceinline__ double widen(float f) {
-  const uint32_t b = __float_as_uint(f);
-  if ((b & 0x7F800000u) == 0) return 0.0;
-  const uint64_t w = ((uint64_t)(b & 0x80000000u) << 32) | (((uint64_t)(b & 0x7FFFFFFFu) << 29) + (896ull << 52));
-  return __longlong_as_double((long long)w);
-}
-
-// Double nearest to hi + lo (one fp64 add rounds the exact sum).
-__device__ __forceinline__ double ff2d(ff a) { return widen(a.hi) + widen(a.lo); }
+// Double nearest to hi + lo: both floats widen exactly (the hardware
+// conversion, which measured faster than building the bit patterns with
+// integer operations), and one fp64 add rounds the exact sum.
+__device__ __forceinline__ double ff2d(ff a) { return (double)a.hi + (double)a.lo; }
 
 // Per-cell data for the float-float weights, as computed.
 struct CellW {
@@ -168,9 +162,10 @@ struct Weights {
 };
 
 // 1 - a for 0 <= a <= 1/2 (plus rounding): the result is at least 1/2, so
-// the float-float difference keeps its relative precision.
+// the float-float difference keeps its relative precision.  1 >= |a.hi|, so
+// the exact sum of the high parts needs only the ordered (fast) form.
 __device__ __forceinline__ ff one_minus(ff a) {
-  const ff s = two_sum(1.0f, -a.hi);
+  const ff s = fast_two_sum(1.0f, -a.hi);
   return fast_two_sum(s.hi, s.lo - a.lo);
 }
 
