@@ -143,9 +143,11 @@ __global__ void __launch_bounds__(256) k_prep_1d(PrepArgs a) {
       const uint64_t d = ws[s] - b;                          // > 0 for a strictly increasing table
       const int sh = max(0, 64 - __clzll((long long)d) - 15);   // offsets fit 15 bits
       wsh[s] = (uint8_t)sh;
+      // leaf s: offsets 0..7 at wl[8s..], offsets 8..15 in a second array after all leaves
       for (int j = 0; j < kLeaf; ++j) {
         const int i = s * kLeaf + j;
-        wl[i] = i < nk ? (uint16_t)((full[i] - b) >> sh) : (uint16_t)0x7FFF;
+        const int at = j < kLeaf / 2 ? s * (kLeaf / 2) + j : (wg.L + s) * (kLeaf / 2) + (j - kLeaf / 2);
+        wl[at] = i < nk ? (uint16_t)((full[i] - b) >> sh) : (uint16_t)0x7FFF;
       }
     }
     if (tid == 0) {

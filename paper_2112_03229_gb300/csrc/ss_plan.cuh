@@ -231,7 +231,7 @@ struct WideView {
   const int* dir;
   const uint64_t* samples;      // last key of each leaf, then kPad sentinels
   const uint8_t* shifts;
-  const uint16_t* leaf;         // 16 offsets per leaf
+  const uint16_t* leaf;         // offsets 0..7 of every leaf (16 bytes each), then offsets 8..15 of every leaf
   const uint64_t* full;         // all keys, global memory (ties)
   uint64_t k0;                  // key of X[0]: the base of leaf 0
   int nk;
@@ -276,8 +276,11 @@ __device__ __forceinline__ int wide_count(const WideView& wv, uint64_t q) {
   const uint64_t base = s > 0 ? wv.samples[s - 1] : wv.k0;
   if (q <= base) return kLeaf * s;               // only below X[0] (leaf 0)
   const uint32_t tq = (uint32_t)((q - base) >> wv.shifts[s]);   // < 2^15: q <= samples[s]
-  const uint4* t4 = reinterpret_cast<const uint4*>(wv.leaf + kLeaf * s);
-  const uint4 a = t4[0], b = t4[1];
+  // the two halves of a leaf sit in two arrays of 16-byte entries: read at a
+  // 16-byte stride, a warp's random leaves spread over all shared-memory banks
+  // (one 32-byte leaf read as two 16-byte halves used half of them)
+  const uint4* l4 = reinterpret_cast<const uint4*>(wv.leaf);
+  const uint4 a = l4[s], b = l4[wv.w.L + s];
   int c = kLeaf - count_ge15(a, b, tq);                          // offsets below the target's
   const int le = kLeaf - count_ge15(a, b, tq + 1);               // ... at most the target's
   for (; c < le; ++c) {                                          // equal offsets: full keys
