@@ -282,10 +282,16 @@ __device__ __forceinline__ int wide_count(const WideView& wv, uint64_t q) {
   const uint4* l4 = reinterpret_cast<const uint4*>(wv.leaf);
   const uint4 a = l4[s], b = l4[wv.w.L + s];
   int c = kLeaf - count_ge15(a, b, tq);                          // offsets below the target's
-  const int le = kLeaf - count_ge15(a, b, tq + 1);               // ... at most the target's
-  for (; c < le; ++c) {                                          // equal offsets: full keys
-    const int j = kLeaf * s + c;
-    if (j >= wv.nk || __ldg(wv.full + j) >= q) break;
+  // a leaf's offsets never decrease, so offsets equal to the target's (whose
+  // keys are compared in full) start at position c; one 16-bit read of that
+  // offset rules them out, and only a tie pays for the second packed count
+  const int h = kLeaf / 2;
+  if (c < kLeaf && wv.leaf[c < h ? s * h + c : (wv.w.L + s) * h + (c - h)] == tq) {
+    const int le = kLeaf - count_ge15(a, b, tq + 1);             // offsets at most the target's
+    for (; c < le; ++c) {
+      const int j = kLeaf * s + c;
+      if (j >= wv.nk || __ldg(wv.full + j) >= q) break;
+    }
   }
   return kLeaf * s + c;
 }
