@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(256) k_prep_1d(PrepArgs a) {
   if (g.off_wide >= 0) {
     const WideGeom wg = wide_geom(nk);
     unsigned char* sec = blob + g.off_wide;
-    int* wdir = reinterpret_cast<int*>(sec + wg.off_dir);
+    uint16_t* wdir = reinterpret_cast<uint16_t*>(sec + wg.off_dir);
     uint64_t* ws = reinterpret_cast<uint64_t*>(sec + wg.off_samples);
     uint8_t* wsh = sec + wg.off_shift;
     uint16_t* wl = reinterpret_cast<uint16_t*>(sec + wg.off_leaf);
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(256) k_prep_1d(PrepArgs a) {
     }
     __syncthreads();
     for (int b = tid; b <= s_wnb; b += nt)
-      wdir[b] = b == s_wnb ? wg.L : lower_count(ws, wg.L, (s_wbase + (uint64_t)b) << s_wshift);
+      wdir[b] = (uint16_t)(b == s_wnb ? wg.L : lower_count(ws, wg.L, (s_wbase + (uint64_t)b) << s_wshift));
     __syncthreads();
     int oc = 0;
     for (int b = tid; b < s_wnb; b += nt) oc = max(oc, wdir[b + 1] - wdir[b]);
@@ -624,10 +624,13 @@ __global__ void __launch_bounds__(kWideThreads, 1) k_batched_1d_wide(BatchArgs1D
     const WideView wv = wide_view(smem + sizeof(BlobHdr), v);
     if (wv.w.occ <= 1)
       stream_tile(a.Y, a.out, tile.begin, tile.count, a.vec, le, nans,
-                  [&](double, uint64_t q) { return wide_count<true>(wv, q); });
+                  [&](double, uint64_t q) { return wide_count<1>(wv, q); });
+    else if (wv.w.occ <= 2)
+      stream_tile(a.Y, a.out, tile.begin, tile.count, a.vec, le, nans,
+                  [&](double, uint64_t q) { return wide_count<2>(wv, q); });
     else
       stream_tile(a.Y, a.out, tile.begin, tile.count, a.vec, le, nans,
-                  [&](double, uint64_t q) { return wide_count<false>(wv, q); });
+                  [&](double, uint64_t q) { return wide_count<0>(wv, q); });
   }
   if (!ok && threadIdx.x == 0) s_err = 1;
   __syncthreads();

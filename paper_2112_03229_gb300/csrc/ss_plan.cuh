@@ -89,12 +89,23 @@ struct WideGeom {
   int L, dcap, off_dir, off_samples, off_shift, off_leaf, bytes;
 };
 
+// Bytes of a wide section besides its directory: header, samples (with
+// sentinels), shifts and leaves.
+__host__ __device__ inline int wide_rest_bytes(int L) {
+  return (int)sizeof(WideHdr) + ((((L + kPad) * 8) + 15) & ~15) + ((L + 15) & ~15) + L * kLeaf * 2;
+}
+
+// The sample directory holds 16-bit counts (at most L samples) and takes
+// the shared memory the rest of the section leaves within the budget, up to
+// six buckets per sample: on clustered tables a finer directory leaves
+// fewer samples per bucket to search.
 __host__ __device__ inline WideGeom wide_geom(int nk) {
   WideGeom w{};
   w.L = (nk + kLeaf - 1) / kLeaf;
-  w.dcap = w.L * 2 < 64 ? 64 : (w.L * 2 > 8192 ? 8192 : w.L * 2);
+  const int room = (kWideSmemBudget - (int)sizeof(BlobHdr) - wide_rest_bytes(w.L) - 16) / 2 - 1;
+  w.dcap = room < 64 ? 64 : (room > 6 * w.L ? 6 * w.L : room);
   int off = (int)sizeof(WideHdr);
-  w.off_dir = off;     off += (((w.dcap + 1) * 4) + 15) & ~15;
+  w.off_dir = off;     off += (((w.dcap + 1) * 2) + 15) & ~15;
   w.off_samples = off; off += (((w.L + kPad) * 8) + 15) & ~15;
   w.off_shift = off;   off += (w.L + 15) & ~15;
   w.off_leaf = off;    off += w.L * kLeaf * 2;
@@ -103,9 +114,13 @@ __host__ __device__ inline WideGeom wide_geom(int nk) {
 }
 
 // A table gets a wide section when its keys exceed shared memory as 8-byte
-// keys and the section (with the blob header) fits the budget.
+// keys and the section fits the budget with a directory of at least two
+// buckets per sample (at most 8192) in 32-bit entries.
 __host__ __device__ inline bool wide_eligible(int nk) {
-  return nk > kMaxSmemKeys && (int64_t)sizeof(BlobHdr) + wide_geom(nk).bytes <= kWideSmemBudget;
+  if (nk <= kMaxSmemKeys) return false;
+  const int L = (nk + kLeaf - 1) / kLeaf;
+  const int dmin = L * 2 > 8192 ? 8192 : L * 2;
+  return (int64_t)sizeof(BlobHdr) + wide_rest_bytes(L) + ((((dmin + 1) * 4) + 15) & ~15) <= kWideSmemBudget;
 }
 
 // Blob offset of the wide section: after the global-only keys and fine directory.
@@ -228,7 +243,7 @@ __device__ __forceinline__ StagedView stage_blob(const unsigned char* __restrict
 // Staged wide section (shared memory, right after the staged header).
 struct WideView {
   WideHdr w;                    // directory parameters, in registers
-  const int* dir;
+  const uint16_t* dir;          // bucket directory over the samples (16-bit counts)
   const uint64_t* samples;      // last key of each leaf, then kPad sentinels
   const uint8_t* shifts;
   const uint16_t* leaf;         // offsets 0..7 of every leaf (16 bytes each), then offsets 8..15 of every leaf
@@ -240,7 +255,7 @@ struct WideView {
 __device__ __forceinline__ WideView wide_view(const unsigned char* sec, const StagedView& v) {
   WideView wv;
   wv.w = *reinterpret_cast<const WideHdr*>(sec);
-  wv.dir = reinterpret_cast<const int*>(sec + wv.w.off_dir);
+  wv.dir = reinterpret_cast<const uint16_t*>(sec + wv.w.off_dir);
   wv.samples = reinterpret_cast<const uint64_t*>(sec + wv.w.off_samples);
   wv.shifts = sec + wv.w.off_shift;
   wv.leaf = reinterpret_cast<const uint16_t*>(sec + wv.w.off_leaf);
@@ -263,17 +278,36 @@ __device__ __forceinline__ int count_ge15(const uint4& a, const uint4& b, uint32
 }
 
 // Count of keys below q on a wide section: the leaf from the sample
-// directory (SCAN1: at most one sample per bucket); in the leaf, the 16
-// offsets (15 bits each) are compared with the target's, two per 32-bit
+// directory (SCAN 1 or 2: at most that many samples per bucket, compared
+// with independent reads; 0: bisection inside the bucket); in the leaf, the
+// 16 offsets (15 bits each) are compared with the target's, two per 32-bit
 // word: offsets below it belong to smaller keys, above it to larger ones;
 // the keys whose offset equals the target's are compared in full.
-template <bool SCAN1>
+template <int SCAN>
 __device__ __forceinline__ int wide_count(const WideView& wv, uint64_t q) {
-  const int s = SCAN1 ? search_bucket<1>(wv.samples, wv.dir, wv.w.shift, wv.w.base, wv.w.nb, q)
-                      : search_bucket_bisect(wv.samples, wv.dir, wv.w.shift, wv.w.base, wv.w.nb,
-                                             32 - __clz(wv.w.occ), q);
-  if (s >= wv.w.L) return wv.nk;
-  const uint64_t base = s > 0 ? wv.samples[s - 1] : wv.k0;
+  const int bk = bucket_index(q, wv.w.shift, wv.w.base, wv.w.nb);
+  const int lo = wv.dir[bk];
+  int s = lo;
+  uint64_t base;                                 // last key of the previous leaf
+  if (SCAN >= 1) {
+    // samples past the bucket are larger than q, or sentinels; the leaf's base
+    // is one of the samples just compared unless no sample is below q
+    const uint64_t k0 = wv.samples[lo], k1 = SCAN >= 2 ? wv.samples[lo + 1] : 0;
+    s += (k0 < q ? 1 : 0) + (SCAN >= 2 && k1 < q ? 1 : 0);
+    if (s >= wv.w.L) return wv.nk;
+    base = s == lo ? (lo > 0 ? wv.samples[lo - 1] : wv.k0) : (s == lo + 1 ? k0 : k1);
+  } else {
+    int len = wv.dir[bk + 1] - s;
+    const int T = 32 - __clz(wv.w.occ);
+    for (int it = 0; it < T; ++it) {
+      const int half = len >> 1;
+      const bool go = len > 0 && wv.samples[s + half] < q;
+      s = go ? s + half + 1 : s;
+      len = go ? len - half - 1 : half;
+    }
+    if (s >= wv.w.L) return wv.nk;
+    base = s > 0 ? wv.samples[s - 1] : wv.k0;
+  }
   if (q <= base) return kLeaf * s;               // only below X[0] (leaf 0)
   const uint32_t tq = (uint32_t)((q - base) >> wv.shifts[s]);   // < 2^15: q <= samples[s]
   // the two halves of a leaf sit in two arrays of 16-byte entries: read at a
@@ -283,10 +317,13 @@ __device__ __forceinline__ int wide_count(const WideView& wv, uint64_t q) {
   const uint4 a = l4[s], b = l4[wv.w.L + s];
   int c = kLeaf - count_ge15(a, b, tq);                          // offsets below the target's
   // a leaf's offsets never decrease, so offsets equal to the target's (whose
-  // keys are compared in full) start at position c; one 16-bit read of that
-  // offset rules them out, and only a tie pays for the second packed count
-  const int h = kLeaf / 2;
-  if (c < kLeaf && wv.leaf[c < h ? s * h + c : (wv.w.L + s) * h + (c - h)] == tq) {
+  // keys are compared in full) start at position c; offset c, picked from the
+  // words already in registers, rules them out, and only a tie pays for the
+  // second packed count
+  const int wi = c >> 1;
+  const uint32_t wc = wi < 4 ? (wi < 2 ? (wi == 0 ? a.x : a.y) : (wi == 2 ? a.z : a.w))
+                             : (wi < 6 ? (wi == 4 ? b.x : b.y) : (wi == 6 ? b.z : b.w));
+  if (c < kLeaf && ((c & 1) ? (wc >> 16) : (wc & 0xFFFFu)) == tq) {
     const int le = kLeaf - count_ge15(a, b, tq + 1);             // offsets at most the target's
     for (; c < le; ++c) {
       const int j = kLeaf * s + c;
