@@ -15,7 +15,7 @@ __host__ __device__ inline BlobGeom blob_geom_dev(int n, int dir_cap, bool cells
   g.D = ilog2(g.P);
   int off = (int)sizeof(BlobHdr);
   g.off_mlp = off;  off += kMlpBytes;
-  g.off_dir = off;  off += (((dir_cap + 1) * 4) + 15) & ~15;
+  g.off_dir = off;  off += (((dir_cap + 1) * 2) + 15) & ~15;   // 16-bit counts (staged keys <= 8128)
   g.off_keys = off; off += (g.ns + kPad) * 8;
   g.off_eyt = off;  off += g.P * 8;
   g.off_cells = -1;

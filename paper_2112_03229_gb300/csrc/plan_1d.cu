@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256) k_prep_1d(PrepArgs a) {
   BlobHdr* h = reinterpret_cast<BlobHdr*>(blob);
   uint64_t* keys = reinterpret_cast<uint64_t*>(blob + g.off_keys);
   uint64_t* eyt = reinterpret_cast<uint64_t*>(blob + g.off_eyt);
-  int* dir = reinterpret_cast<int*>(blob + g.off_dir);
+  uint16_t* dir = reinterpret_cast<uint16_t*>(blob + g.off_dir);
   float* mlp = reinterpret_cast<float*>(blob + g.off_mlp);
   uint64_t* full = g.off_full >= 0 ? reinterpret_cast<uint64_t*>(blob + g.off_full) : nullptr;
   const int nk = n - 1, tid = threadIdx.x, nt = blockDim.x;
@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(256) k_prep_1d(PrepArgs a) {
   __syncthreads();
   const int shift = s_shift, nb = s_nb;
   const uint64_t base = s_base;
-  for (int b = tid; b <= nb; b += nt) dir[b] = b == nb ? g.ns : lower_count(keys, g.ns, (base + (uint64_t)b) << shift);
+  for (int b = tid; b <= nb; b += nt)
+    dir[b] = (uint16_t)(b == nb ? g.ns : lower_count(keys, g.ns, (base + (uint64_t)b) << shift));
   __syncthreads();
   int occ = 0;
   for (int b = tid; b < nb; b += nt) occ = max(occ, dir[b + 1] - dir[b]);
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(kTrainThreads) k_train_mlp(TrainArgs a) {
   // global view of the blob for labelling (no staging needed: reads hit L2)
   StagedView v;
   v.h = h;
-  v.dir = reinterpret_cast<const int*>(blob + h.off_dir);
+  v.dir = reinterpret_cast<const uint16_t*>(blob + h.off_dir);
   v.keys = reinterpret_cast<const uint64_t*>(blob + h.off_keys);
   v.full = h.off_full >= 0 ? reinterpret_cast<const uint64_t*>(blob + h.off_full) : nullptr;
   v.gdir = h.gnb > 0 ? reinterpret_cast<const int*>(blob + h.off_full + (int64_t)(h.nk + kPad) * 8) : nullptr;
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(256) k_window(WindowArgs a) {
   StagedView v;
   v.h = h;
   v.mlp = reinterpret_cast<const float*>(blob + h.off_mlp);
-  v.dir = reinterpret_cast<const int*>(blob + h.off_dir);
+  v.dir = reinterpret_cast<const uint16_t*>(blob + h.off_dir);
   v.keys = reinterpret_cast<const uint64_t*>(blob + h.off_keys);
   v.full = h.off_full >= 0 ? reinterpret_cast<const uint64_t*>(blob + h.off_full) : nullptr;
   v.gdir = h.gnb > 0 ? reinterpret_cast<const int*>(blob + h.off_full + (int64_t)(h.nk + kPad) * 8) : nullptr;
@@ -565,7 +566,7 @@ __global__ void __launch_bounds__(kPlanMaxThreads, 2) k_batched_1d(BatchArgs1D a
       stream_tile(a.Y, a.out, b, cnt, vec, le, nans, [&](double, uint64_t q) { return plain_binary(v, q); });
     } else if (h.stride == 1 && h.occ <= 2) {
       const uint64_t* keys = v.keys;
-      const int* dir = v.dir;
+      const uint16_t* dir = v.dir;
       const int shift = h.shift, nb = h.nb;
       const uint64_t base = h.base;
       if (h.occ <= 1)

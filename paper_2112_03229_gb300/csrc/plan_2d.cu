@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kNumThreads, 3) k_batched_2d(BatchArgs2D a) {
     };
     auto scan2 = [](const StagedView& v) {
       const uint64_t* keys = v.keys;
-      const int* dir = v.dir;
+      const uint16_t* dir = v.dir;
       const int shift = v.h.shift, nb = v.h.nb;
       const uint64_t base = v.h.base;
       return [=](double, uint64_t q) { return search_bucket<2>(keys, dir, shift, base, nb, q); };

@@ -121,8 +121,9 @@ constexpr int kRefitBytes = 4096;   // directory growth allowed for a table with
 // with crowded buckets, each costing a dependent shared-memory round trip
 // of the bisection inside the bucket.  Finer cuts are tried in turn: the
 // coarsest that leaves at most one key per bucket within the small budget,
-// else the coarsest with at most two keys (a two-key scan) within the large
-// budget, else the finest within the large budget.  A table whose default
+// else within the large budget, else the coarsest with at most two keys (a
+// two-key scan) within the large budget, else the finest within the large
+// budget (directory entries are 16-bit counts).  A table whose default
 // directory already holds at most two keys per bucket is refitted only when
 // that adds at most kRefitBytes of directory (measured on GB300: a lone
 // 256-entry clustered table searched 10 % faster with one key per bucket,
@@ -151,7 +152,7 @@ int fitted_dir_cap(const std::vector<uint64_t>& keys, int n) {
   while (s0 < 63 && ((k1 >> s0) - (k0 >> s0)) >= (uint64_t)def) ++s0;
   const int occ0 = occupancy(s0);
   if (occ0 <= 1) return def;
-  int fit1 = -1, fit2 = -1, finest = -1;
+  int fit1 = -1, fit1l = -1, fit2 = -1, finest = -1;
   for (int s = s0; s >= 1; --s) {
     const uint64_t nb = buckets(s);
     if (nb > 65535) break;
@@ -160,12 +161,13 @@ int fitted_dir_cap(const std::vector<uint64_t>& keys, int n) {
     const int occ = occupancy(s);
     finest = s;
     if (occ <= 1 && bytes <= kStageBudgetSmall && fit1 < 0) fit1 = s;
+    if (occ <= 1 && fit1l < 0) fit1l = s;
     if (occ <= 2 && fit2 < 0) fit2 = s;
     if (occ <= 1) break;
   }
-  const int s = fit1 >= 0 ? fit1 : fit2 >= 0 ? fit2 : finest;
+  const int s = fit1 >= 0 ? fit1 : fit1l >= 0 ? fit1l : fit2 >= 0 ? fit2 : finest;
   if (s < 0 || s == s0) return def;
-  if (occ0 <= 2 && (int64_t)(buckets(s) - buckets(s0)) * 4 > kRefitBytes) return def;
+  if (occ0 <= 2 && (int64_t)(buckets(s) - buckets(s0)) * 2 > kRefitBytes) return def;
   return (int)buckets(s);
 }
 
@@ -320,12 +322,18 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
   int per_sm = 0;
   int threads = kNumThreads;
   SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
-  if (p->kind == 1 && per_sm * kNumThreads < 1024) {
+  // tables over 8128 entries without a wide section finish their searches in
+  // the full keys in global memory, which L1 caches: fewer staged copies per
+  // SM leave it more room
+  bool global_keys = false;
+  if (p->kind == 1)
+    for (int k = 0; k < p->ntables; ++k) global_keys |= !wide[k] && p->sizes[k] - 1 > kMaxSmemKeys;
+  if (p->kind == 1 && (per_sm * kNumThreads < 1024 || global_keys)) {
     // a large staged table: fewer, wider blocks share one staged copy
     int per_sm_big = 0;
     const int big = batched_1d_max_threads();
     SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_big, kern, big, smem));
-    if (per_sm_big * big > per_sm * kNumThreads) {
+    if (per_sm_big * big > per_sm * kNumThreads || (global_keys && per_sm_big * big == per_sm * kNumThreads)) {
       per_sm = per_sm_big;
       threads = big;
     }

@@ -88,14 +88,15 @@ __device__ __forceinline__ int mlp_propose(const float* __restrict__ p, const Ml
 // Position (in directory count units, fractional) proposed by the spline for
 // query key q over directory dir[0..nb] (counts of keys below each knot
 // (base + b) << shift): linear interpolation between the two knots around q.
-__device__ __forceinline__ float spline_position(const int* __restrict__ dir, int shift, uint64_t base, int nb,
+template <class D>   // D: directory entry type
+__device__ __forceinline__ float spline_position(const D* __restrict__ dir, int shift, uint64_t base, int nb,
                                                  uint64_t q) {
   const uint64_t hb = q >> shift;
   if (hb < base) return 0.0f;
   const uint64_t d = hb - base;
   if (d >= (uint64_t)nb) return (float)dir[nb];
   const int b = (int)d;
-  const int lo = dir[b], hi = dir[b + 1];
+  const int lo = (int)dir[b], hi = (int)dir[b + 1];
   // fraction of the way through the bucket, from the key bits below the shift
   // (the top 24 of those bits fit a 32-bit integer: int-to-float stays on the 32-bit path)
   const uint64_t below = shift > 0 ? (q & ((1ull << shift) - 1)) : 0ull;
@@ -152,7 +153,8 @@ __device__ __forceinline__ int loghash_propose(float a, float c, int nk, double 
   return (int)fminf(fmaxf(p, 0.0f), (float)nk);
 }
 
-__device__ __forceinline__ int spline_propose(const int* __restrict__ dir, int shift, uint64_t base, int nb,
+template <class D>
+__device__ __forceinline__ int spline_propose(const D* __restrict__ dir, int shift, uint64_t base, int nb,
                                               uint64_t q) {
   return (int)rintf(spline_position(dir, shift, base, nb, q));
 }

@@ -193,7 +193,7 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 struct StagedView {
   BlobHdr h;                 // header fields, held in registers
   const float* mlp;
-  const int* dir;
+  const uint16_t* dir;       // bucket directory: counts of staged keys (at most 8128) in 16 bits
   const uint64_t* keys;
   const uint64_t* eyt;
   CellTable cells;           // 2D axes: per-cell weight data
@@ -231,7 +231,7 @@ __device__ __forceinline__ StagedView stage_blob(const unsigned char* __restrict
   StagedView v;
   v.h = hdr;
   v.mlp = reinterpret_cast<const float*>(dst + hdr.off_mlp + shift_off);
-  v.dir = reinterpret_cast<const int*>(dst + hdr.off_dir + shift_off);
+  v.dir = reinterpret_cast<const uint16_t*>(dst + hdr.off_dir + shift_off);
   v.keys = reinterpret_cast<const uint64_t*>(dst + hdr.off_keys + shift_off);
   v.eyt = reinterpret_cast<const uint64_t*>(dst + hdr.off_eyt + shift_off);
   v.cells = hdr.off_cells >= 0 ? cell_table(dst + hdr.off_cells + shift_off, hdr.n - 1) : CellTable{nullptr, nullptr};

@@ -196,8 +196,8 @@ __device__ __forceinline__ int bucket_index(uint64_t q, int shift, uint64_t base
   return hb < base ? 0 : (int)min(hb - base, (uint64_t)(nb - 1));
 }
 
-template <int SCAN>
-__device__ __forceinline__ int search_bucket(const uint64_t* __restrict__ keys, const int* __restrict__ dir,
+template <int SCAN, class D>   // D: directory entry type (int in one-shot calls, uint16_t in plans)
+__device__ __forceinline__ int search_bucket(const uint64_t* __restrict__ keys, const D* __restrict__ dir,
                                              int shift, uint64_t base, int nb, uint64_t q) {
   const int b = bucket_index(q, shift, base, nb);
   const int lo = dir[b];
@@ -209,7 +209,8 @@ __device__ __forceinline__ int search_bucket(const uint64_t* __restrict__ keys, 
 
 // Bucket directory + bounded bisection inside the bucket (T = bit length of
 // the largest occupancy).
-__device__ __forceinline__ int search_bucket_bisect(const uint64_t* __restrict__ keys, const int* __restrict__ dir,
+template <class D>
+__device__ __forceinline__ int search_bucket_bisect(const uint64_t* __restrict__ keys, const D* __restrict__ dir,
                                                     int shift, uint64_t base, int nb, int T, uint64_t q) {
   const int b = bucket_index(q, shift, base, nb);
   int lo = dir[b], len = dir[b + 1] - lo;
