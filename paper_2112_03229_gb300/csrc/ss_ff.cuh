@@ -12,9 +12,9 @@
 // The interpolation weights are formed from exact integers: for a target x in
 // cell [X_c, X_c+1] whose binary exponents differ by at most kMaxCellOctaves,
 // x - X_c and X_c+1 - x are integer multiples of 2^(e_c - 1075) computed in
-// 64-bit integers, then scaled by the per-cell factor 1 / (X_c+1 - X_c) in the
-// same units.  Both weights keep full relative precision (none is formed as
-// 1 - w).
+// 64-bit integers; the smaller of the two is scaled by the per-cell factor
+// 1 / (X_c+1 - X_c) in the same units, and the other weight is 1 minus it.
+// That one is at least 1/2, so both weights keep full relative precision.
 #pragma once
 
 #include "ss_common.cuh"
