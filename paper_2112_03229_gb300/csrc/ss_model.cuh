@@ -91,6 +91,19 @@ __device__ __forceinline__ int mlp_propose(const float* __restrict__ p, const Ml
 template <class D>   // D: directory entry type
 __device__ __forceinline__ float spline_position(const D* __restrict__ dir, int shift, uint64_t base, int nb,
                                                  uint64_t q) {
+  if (shift >= 32) {
+    // cuts no finer than 2^-20 of an octave (the usual case, uniform per
+    // table): the bucket comes from the key's high word, and the fraction's
+    // 24 bits are the key bits just below the cut (the same bits and the same
+    // float arithmetic as the general form below)
+    const uint32_t hb = (uint32_t)(q >> 32) >> (shift - 32);
+    if (hb < (uint32_t)base) return 0.0f;
+    const uint32_t d = hb - (uint32_t)base;
+    if (d >= (uint32_t)nb) return (float)dir[nb];
+    const int lo = (int)dir[d], hi = (int)dir[d + 1];
+    const float frac = (float)((uint32_t)(q >> (shift - 24)) & 0xFFFFFFu) * __int_as_float((127 - 24) << 23);
+    return (float)lo + frac * (float)(hi - lo);
+  }
   const uint64_t hb = q >> shift;
   if (hb < base) return 0.0f;
   const uint64_t d = hb - base;

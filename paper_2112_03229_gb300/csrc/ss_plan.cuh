@@ -373,12 +373,24 @@ __device__ __forceinline__ int plain_binary(const StagedView& v, uint64_t q) {
 template <class KEYS>
 __device__ __forceinline__ int window_count(KEYS key, int nk, int E, int p, uint64_t q, bool& ok) {
   const int lo = max(p - E, 0), hi = min(p + E, nk);
-  ok = (lo == 0 || key(lo - 1) < q) && (hi == nk || key(hi) >= q);
+  // both key arrays end in sentinels above every key, so key(hi) exists for
+  // hi == nk and the check needs no branch
+  const uint64_t kb = key(lo > 0 ? lo - 1 : 0), ke = key(hi);
+  ok = ((lo == 0) | (kb < q)) & (ke >= q);
   if (E <= 3) {
+    // 2E keys from lo (the window's length at most): those from hi on are at
+    // least key(hi), so when the check holds they add nothing (and the answer
+    // is discarded when it fails); the branch on E is uniform per table
     int c = lo;
+    if (E <= 1) {
+      c += (key(lo) < q ? 1 : 0) + (key(lo + 1) < q ? 1 : 0);
+    } else if (E == 2) {
 #pragma unroll
-    for (int j = 0; j < 6; ++j)
-      if (lo + j < hi) c += key(lo + j) < q ? 1 : 0;
+      for (int j = 0; j < 4; ++j) c += key(lo + j) < q ? 1 : 0;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) c += key(lo + j) < q ? 1 : 0;
+    }
     return c;
   }
   int c = lo, len = hi - lo;
