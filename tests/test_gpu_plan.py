@@ -180,6 +180,34 @@ def test_plan_empty_tiny_tiles_and_misaligned(ss):
             assert np.all(o[:off] == -5) and np.all(o[off + len(Y):] == -5)
 
 
+@pytest.mark.parametrize("model", ["spline", "mlp", "loghash"])
+@pytest.mark.parametrize("side", [0, 1])
+def test_learned_windows_at_the_table_ends(ss, model, side):
+    """Learned proposals on tables of 2..9 entries put their checked windows
+    against both ends of the key array (window start 0, window end at the
+    last key, where the check reads the sentinels after it).  Every entry,
+    its neighbouring doubles, values between entries, far outside the range
+    and IEEE specials; indices bit-exact for both sides."""
+    sizes = list(range(2, 10))
+    tabs = [wl.log_spaced_table(n, 0.5, 2.0 ** n, 0.2, seed=100 + n) for n in sizes]
+    X = torch.cat(tabs)
+    X_off = np.concatenate([[0], np.cumsum(sizes)])
+    Ys = []
+    for t in tabs:
+        x = t.numpy()
+        mids = np.sqrt(x[1:] * x[:-1])
+        Ys.append(np.concatenate([x, np.nextafter(x, np.inf), np.nextafter(x, -np.inf), mids,
+                                  [x[0] / 4, x[-1] * 4, 0.0, -0.0, -1.0, np.inf, -np.inf, np.nan]]))
+    Y = torch.as_tensor(np.concatenate(Ys))
+    Y_off = np.concatenate([[0], np.cumsum([len(y) for y in Ys])])
+    want = oracle.search_1d_batched(X_off, X.numpy(), Y_off, Y.numpy(), side)
+    b = wl.Batched1D(torch.as_tensor(X_off), X, torch.as_tensor(Y_off), Y, None, None)
+    plan, got, st = run_plan_1d(ss, b, model=model, side=side, tile=1024,
+                                mlp_epochs=100 if model == "mlp" else None)
+    np.testing.assert_array_equal(got, want)
+    assert st.nan_targets == len(sizes)
+
+
 def test_plan_graph_replay_and_rebind(ss):
     b = small_batch(seed=6)
     plan = ss.Plan.create_1d(b.X_off, b.X.to(DEV), model="spline")
