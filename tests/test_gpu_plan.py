@@ -122,6 +122,34 @@ def test_plan_fitted_directory_and_wide_blocks(ss, side, tile):
     np.testing.assert_array_equal(out2.cpu().numpy(), want)
 
 
+@pytest.mark.parametrize("model", ["none", "spline", "mlp", "loghash"])
+@pytest.mark.parametrize("side", [0, 1])
+def test_plan_every_layout_regime(ss, model, side):
+    """One plan over tables of every layout regime: staged whole with fitted
+    16-bit directories (2 .. 8128 entries, jittered and clustered), wide
+    sections of different directory budgets (8129, 20000 and 65535
+    entries), and a two-level table (80000 entries, searched in global
+    memory); exact key hits and their neighbours in every table."""
+    rng = np.random.default_rng(77)
+    tabs = [wl.log_spaced_table(n, 1e-4, 1e6, 0.2, seed=200 + n) for n in (2, 3, 17, 255, 1025, 8128, 8129, 20000)]
+    tabs += [wl.sweep_table(4096, seed=9), wl.sweep_table(65535, seed=10), wl.log_spaced_table(80000, 1e-3, 1e7, 0.2, seed=11)]
+    Ys = []
+    for t in tabs:
+        x = t.numpy()
+        hits = x[rng.integers(0, len(x), 500)]
+        Ys.append(np.concatenate([10 ** rng.uniform(np.log10(x[0]) - 1, np.log10(x[-1]) + 1, 6000), hits,
+                                  np.nextafter(hits, np.inf), np.nextafter(hits, -np.inf)]))
+    X = torch.cat(tabs)
+    X_off = np.concatenate([[0], np.cumsum([len(t) for t in tabs])])
+    Y = torch.as_tensor(np.concatenate(Ys))
+    Y_off = np.concatenate([[0], np.cumsum([len(y) for y in Ys])])
+    want = oracle.search_1d_batched(X_off, X.numpy(), Y_off, Y.numpy(), side)
+    b = wl.Batched1D(torch.as_tensor(X_off), X, torch.as_tensor(Y_off), Y, None, None)
+    plan, got, st = run_plan_1d(ss, b, model=model, side=side, mlp_epochs=60 if model == "mlp" else None)
+    np.testing.assert_array_equal(got, want)
+    assert st.flags == 0
+
+
 def test_plan_wide_section_with_ties(ss):
     """Tables of 8129..~76K entries search a wide section (16-bit offsets in
     shared memory).  Runs of consecutive doubles inside a leaf whose other
