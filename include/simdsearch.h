@@ -186,7 +186,9 @@ typedef struct ss_plan_opts {
   int32_t tile;             /* targets per tile; 0: library default or tuned */
   int32_t mlp_epochs;       /* full-batch Adam steps of the MLP (default 400; 0 keeps the untrained initialisation) */
   float mlp_lr;             /* peak Adam learning rate, cosine-decayed (default 2e-3) */
-  int32_t dir_cap;          /* bucket-directory budget per table (0: 4 n clamped to [64, 4096]; 8192 above 8128 entries) */
+  int32_t dir_cap;          /* bucket-directory budget per table.  0: fitted to each table's keys at plan creation
+                               (4 n clamped to [64, 4096], refined where a bucket would hold two or more keys,
+                               see ss_plan_info.max_occupancy; 8192 above 8128 entries); > 0: that budget for every table */
   uint64_t seed;            /* seed of the counter-based sampler of training and probe targets */
   const char* tune_cache;   /* JSON file the autotuner reads and writes (NULL: none) */
   int32_t extrap;           /* 2D plans: interpolation options as in ss_interp_opts */
@@ -249,7 +251,9 @@ ss_status ss_plan_execute(ss_plan* plan, cudaStream_t stream);
 ss_status ss_plan_info_get(const ss_plan* plan, ss_plan_info* info);
 
 /* Write the prepared tables, models and tuning choices to a file, and read
- * them back (the loaded plan gives identical results; bind it again). */
+ * them back (the loaded plan gives identical results; bind it again).  The
+ * file records the layout version of the prepared tables; ss_plan_load
+ * returns SS_EINVAL for a file of another version (prepare the plan again). */
 ss_status ss_plan_save(const ss_plan* plan, const char* path);
 ss_status ss_plan_load(ss_plan** plan, const char* path, cudaStream_t stream);
 
