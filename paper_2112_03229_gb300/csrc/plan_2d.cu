@@ -274,12 +274,35 @@ __global__ void __launch_bounds__(kNumThreads, 3) k_batched_2d(BatchArgs2D a) {
     auto fast = [](const StagedView& v) {
       return v.h.algo == BL_BUCKET && v.h.stride == 1 && v.h.occ <= 2;
     };
-    if (HUNT)
+    if (HUNT) {
       stream_pairs<true>(a, vr, vt, G, G64, tile, nans, fallbacks, generic(vr), generic(vt));
-    else if (fast(vr) && fast(vt))
+    } else if (fast(vr) && fast(vt)) {
       stream_pairs<false>(a, vr, vt, G, G64, tile, nans, fallbacks, scan2(vr), scan2(vt));
-    else
-      stream_pairs<false>(a, vr, vt, G, G64, tile, nans, fallbacks, generic(vr), generic(vt));
+    } else {
+      // a plan's model is the same on both axes: one uniform branch per tile
+      // picks its proposal, so the pairs run it as straight-line code
+      bool done = false;
+      if constexpr (LEARNED) {
+        const int al = vr.h.algo;
+        if (al == vt.h.algo && al == BL_SPLINE) {
+          stream_pairs<false>(a, vr, vt, G, G64, tile, nans, fallbacks,
+                              [&](double, uint64_t q) { return spline_count(vr, q, fallbacks); },
+                              [&](double, uint64_t q) { return spline_count(vt, q, fallbacks); });
+          done = true;
+        } else if (al == vt.h.algo && al == BL_LOGHASH) {
+          stream_pairs<false>(a, vr, vt, G, G64, tile, nans, fallbacks,
+                              [&](double t, uint64_t q) { return loghash_count(vr, t, q, fallbacks); },
+                              [&](double t, uint64_t q) { return loghash_count(vt, t, q, fallbacks); });
+          done = true;
+        } else if (al == vt.h.algo && al == BL_MLP) {
+          stream_pairs<false>(a, vr, vt, G, G64, tile, nans, fallbacks,
+                              [&](double t, uint64_t q) { return mlp_count(vr, t, q, fallbacks); },
+                              [&](double t, uint64_t q) { return mlp_count(vt, t, q, fallbacks); });
+          done = true;
+        }
+      }
+      if (!done) stream_pairs<false>(a, vr, vt, G, G64, tile, nans, fallbacks, generic(vr), generic(vt));
+    }
   }
   nans = __reduce_add_sync(0xFFFFFFFFu, nans);
   fallbacks = __reduce_add_sync(0xFFFFFFFFu, fallbacks);
