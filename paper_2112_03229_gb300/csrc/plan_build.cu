@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <unistd.h>
+
 #include "plan.h"
 #include "plan_host.h"
 
@@ -481,21 +483,32 @@ static bool read_cache(ss_plan* p, const std::string& dev) {
   return found > 0;
 }
 
+// Written to a private file and renamed over the cache, so that processes
+// sharing one cache file (one per GPU of a node) never read a half-written one.
 static void write_cache(const ss_plan* p, const std::string& dev) {
   if (p->opts.tune_cache == nullptr) return;
-  std::ofstream f(p->opts.tune_cache);
-  if (!f) return;
-  f << "{\"device\": \"" << dev << "\", \"kind\": " << p->kind << ", \"model\": " << p->opts.model
-    << ", \"side\": " << p->opts.side << ", \"buckets\": [\n";
-  bool first = true;
-  for (int b = 0; b < kNumBuckets; ++b) {
-    if (p->bucket_tables[b] == 0) continue;
-    if (!first) f << ",\n";
-    first = false;
-    f << " {\"bucket\": " << b << ", \"algo\": \"" << algo_name(p->bucket_algo[b]) << "\", \"tile_multiple\": "
-      << p->bucket_mult[b] << "}";
+  const std::string tmp = std::string(p->opts.tune_cache) + ".tmp." + std::to_string((long)getpid());
+  {
+    std::ofstream f(tmp);
+    if (!f) return;
+    f << "{\"device\": \"" << dev << "\", \"kind\": " << p->kind << ", \"model\": " << p->opts.model
+      << ", \"side\": " << p->opts.side << ", \"buckets\": [\n";
+    bool first = true;
+    for (int b = 0; b < kNumBuckets; ++b) {
+      if (p->bucket_tables[b] == 0) continue;
+      if (!first) f << ",\n";
+      first = false;
+      f << " {\"bucket\": " << b << ", \"algo\": \"" << algo_name(p->bucket_algo[b]) << "\", \"tile_multiple\": "
+        << p->bucket_mult[b] << "}";
+    }
+    f << "\n]}\n";
+    if (!f) {
+      f.close();
+      std::remove(tmp.c_str());
+      return;
+    }
   }
-  f << "\n]}\n";
+  if (std::rename(tmp.c_str(), p->opts.tune_cache) != 0) std::remove(tmp.c_str());
 }
 
 // Apply the bucket choices to every table's algorithm (both axes for 2D).
