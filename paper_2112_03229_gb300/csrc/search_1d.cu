@@ -127,7 +127,10 @@ __global__ void __launch_bounds__(kNumThreads) k_search_1d_bucket(Args1D a) {
   const uint64_t base = h.base;
   int nans;
   // occupancy is the same for every block: a uniform branch picks the loop
-  if (occ <= 1) {
+  // (tables staged whole, the common case, also skip the two-level finish)
+  if (occ <= 1 && h.stride == 1) {
+    nans = stream_targets(a, [&](uint64_t q) { return search_bucket<1>(keys, dir, shift, base, nb, q); });
+  } else if (occ <= 1) {
     nans = stream_targets(a, [&](uint64_t q) { return finish_count(a, h, search_bucket<1>(keys, dir, shift, base, nb, q), q); });
   } else if (occ == 2) {
     nans = stream_targets(a, [&](uint64_t q) { return finish_count(a, h, search_bucket<2>(keys, dir, shift, base, nb, q), q); });
