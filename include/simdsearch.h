@@ -85,6 +85,9 @@ typedef struct ss_devstat {
   unsigned int max_window;          /* largest learned fix-up window used */
 } ss_devstat;
 
+/* Largest bucket-directory budget a caller may ask for (ss_plan_opts.dir_cap). */
+#define SS_MAX_DIR_CAP 65536
+
 #define SS_FLAG_NOT_SORTED 0x1u     /* a table was not strictly increasing (or held NaN) */
 #define SS_FLAG_BAD_VALUE 0x2u      /* a 2D value-path precondition failed; fp64 path used */
 #define SS_FLAG_STAGING_TIMEOUT 0x4u /* a shared-memory staging copy did not complete in time; outputs incomplete */
@@ -188,7 +191,9 @@ typedef struct ss_plan_opts {
   float mlp_lr;             /* peak Adam learning rate, cosine-decayed (default 2e-3) */
   int32_t dir_cap;          /* bucket-directory budget per table.  0: fitted to each table's keys at plan creation
                                (4 n clamped to [64, 4096], refined where a bucket would hold two or more keys,
-                               see ss_plan_info.max_occupancy; 8192 above 8128 entries); > 0: that budget for every table */
+                               see ss_plan_info.max_occupancy; 8192 above 8128 entries); 1 .. SS_MAX_DIR_CAP: that
+                               budget for every table (SS_EINVAL above it; SS_EUNSUPPORTED at bind when the
+                               directory does not fit shared memory) */
   uint64_t seed;            /* seed of the counter-based sampler of training and probe targets */
   const char* tune_cache;   /* JSON file the autotuner reads and writes (NULL: none) */
   int32_t extrap;           /* 2D plans: interpolation options as in ss_interp_opts */
@@ -253,7 +258,13 @@ ss_status ss_plan_info_get(const ss_plan* plan, ss_plan_info* info);
 /* Write the prepared tables, models and tuning choices to a file, and read
  * them back (the loaded plan gives identical results; bind it again).  The
  * file records the layout version of the prepared tables; ss_plan_load
- * returns SS_EINVAL for a file of another version (prepare the plan again). */
+ * returns SS_EINVAL for a file of another version (prepare the plan again)
+ * and for a file whose layout is inconsistent: before any kernel sees a
+ * loaded plan, its options, offsets and every prepared table's header,
+ * bucket directories, occupancies and strides are checked on the host
+ * against the sizes and budgets it records, so that no search reads outside
+ * the plan.  Model weights and learned windows are not checked beyond their
+ * sign: a wrong one costs fallbacks to the plain search, not exactness. */
 ss_status ss_plan_save(const ss_plan* plan, const char* path);
 ss_status ss_plan_load(ss_plan** plan, const char* path, cudaStream_t stream);
 

@@ -65,7 +65,9 @@ ss_status workspace(size_t bytes, Workspace** out) {
 size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Device address of page-locked, mapped host memory [p, p + bytes), or
-// nullptr if either end is not such memory (pageable, device, unregistered).
+// nullptr if either end is not such memory (pageable, device, unregistered)
+// or the two ends do not map to one contiguous device range (two separate
+// page-locked allocations that happen to sit side by side in host memory).
 template <class T>
 T* mapped(T* p, size_t bytes) {
   if (p == nullptr || bytes == 0) return nullptr;
@@ -76,7 +78,21 @@ T* mapped(T* p, size_t bytes) {
     return nullptr;
   }
   if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return nullptr;
+  if (static_cast<const unsigned char*>(b.devicePointer) != static_cast<const unsigned char*>(a.devicePointer) + bytes - 1)
+    return nullptr;
   return static_cast<T*>(a.devicePointer);
+}
+
+// Waits for everything queued on the workspace's two streams, so that no copy
+// into the caller's buffers is still in flight when a call returns, an error
+// part way through the chunks included.  The first failure is returned.
+ss_status drain(Workspace* w, ss_status st) {
+  const cudaError_t e0 = cudaStreamSynchronize(w->st[0]);
+  const cudaError_t e1 = cudaStreamSynchronize(w->st[1]);
+  if (st != SS_OK) return st;
+  if (e0 != cudaSuccess) return cuda_fail(e0, "cudaStreamSynchronize");
+  if (e1 != cudaSuccess) return cuda_fail(e1, "cudaStreamSynchronize");
+  return SS_OK;
 }
 
 }  // namespace
@@ -98,27 +114,24 @@ extern "C" ss_status ss_search_1d_host(const double* X, int32_t n, const double*
   Workspace* w = nullptr;
   if (ss_status st = workspace(direct ? tab : tab + 2 * (cin + cout), &w)) return st;
   double* dX = reinterpret_cast<double*>(w->buf);
-  SS_CHECK_CUDA(cudaMemcpyAsync(dX, X, (size_t)n * 8, cudaMemcpyHostToDevice, w->st[0]));
-  if (direct) {
+  auto queue = [&]() -> ss_status {
+    SS_CHECK_CUDA(cudaMemcpyAsync(dX, X, (size_t)n * 8, cudaMemcpyHostToDevice, w->st[0]));
     // page-locked buffers: one launch streams them over the link
-    if (ss_status st = search_1d(dX, n, mY, m, mO, side, algo, nullptr, w->st[0], 0, 0)) return st;
-    SS_CHECK_CUDA(cudaStreamSynchronize(w->st[0]));
+    if (direct) return search_1d(dX, n, mY, m, mO, side, algo, nullptr, w->st[0], 0, 0);
+    SS_CHECK_CUDA(cudaEventRecord(w->ready, w->st[0]));
+    SS_CHECK_CUDA(cudaStreamWaitEvent(w->st[1], w->ready, 0));
+    for (int64_t off = 0, c = 0; off < m; off += kChunk1D, ++c) {
+      const int64_t cnt = std::min(kChunk1D, m - off);
+      cudaStream_t s = w->st[c & 1];
+      double* dY = reinterpret_cast<double*>(w->buf + tab + (c & 1) * (cin + cout));
+      int32_t* dO = reinterpret_cast<int32_t*>(w->buf + tab + (c & 1) * (cin + cout) + cin);
+      SS_CHECK_CUDA(cudaMemcpyAsync(dY, Y + off, (size_t)cnt * 8, cudaMemcpyHostToDevice, s));
+      if (ss_status st = search_1d(dX, n, dY, cnt, dO, side, algo, nullptr, s, 0, 0)) return st;
+      SS_CHECK_CUDA(cudaMemcpyAsync(lowbounds + off, dO, (size_t)cnt * 4, cudaMemcpyDeviceToHost, s));
+    }
     return SS_OK;
-  }
-  SS_CHECK_CUDA(cudaEventRecord(w->ready, w->st[0]));
-  SS_CHECK_CUDA(cudaStreamWaitEvent(w->st[1], w->ready, 0));
-  for (int64_t off = 0, c = 0; off < m; off += kChunk1D, ++c) {
-    const int64_t cnt = std::min(kChunk1D, m - off);
-    cudaStream_t s = w->st[c & 1];
-    double* dY = reinterpret_cast<double*>(w->buf + tab + (c & 1) * (cin + cout));
-    int32_t* dO = reinterpret_cast<int32_t*>(w->buf + tab + (c & 1) * (cin + cout) + cin);
-    SS_CHECK_CUDA(cudaMemcpyAsync(dY, Y + off, (size_t)cnt * 8, cudaMemcpyHostToDevice, s));
-    if (ss_status st = search_1d(dX, n, dY, cnt, dO, side, algo, nullptr, s, 0, 0)) return st;
-    SS_CHECK_CUDA(cudaMemcpyAsync(lowbounds + off, dO, (size_t)cnt * 4, cudaMemcpyDeviceToHost, s));
-  }
-  SS_CHECK_CUDA(cudaStreamSynchronize(w->st[0]));
-  SS_CHECK_CUDA(cudaStreamSynchronize(w->st[1]));
-  return SS_OK;
+  };
+  return drain(w, queue());
 }
 
 extern "C" ss_status ss_search_interp_2d_host(const double* R, int32_t nr, const double* T, int32_t nt,
@@ -141,30 +154,27 @@ extern "C" ss_status ss_search_interp_2d_host(const double* R, int32_t nr, const
   double* dR = reinterpret_cast<double*>(w->buf);
   double* dT = reinterpret_cast<double*>(w->buf + tr);
   double* dF = reinterpret_cast<double*>(w->buf + tr + tt);
-  SS_CHECK_CUDA(cudaMemcpyAsync(dR, R, (size_t)nr * 8, cudaMemcpyHostToDevice, w->st[0]));
-  SS_CHECK_CUDA(cudaMemcpyAsync(dT, T, (size_t)nt * 8, cudaMemcpyHostToDevice, w->st[0]));
-  SS_CHECK_CUDA(cudaMemcpyAsync(dF, F, (size_t)nr * nt * 8, cudaMemcpyHostToDevice, w->st[0]));
-  if (direct) {
-    if (ss_status st = search_interp_2d(dR, nr, dT, nt, dF, mY, m, mI, mV, algo, 0, nullptr, w->st[0], 0, 0)) return st;
-    SS_CHECK_CUDA(cudaStreamSynchronize(w->st[0]));
+  auto queue = [&]() -> ss_status {
+    SS_CHECK_CUDA(cudaMemcpyAsync(dR, R, (size_t)nr * 8, cudaMemcpyHostToDevice, w->st[0]));
+    SS_CHECK_CUDA(cudaMemcpyAsync(dT, T, (size_t)nt * 8, cudaMemcpyHostToDevice, w->st[0]));
+    SS_CHECK_CUDA(cudaMemcpyAsync(dF, F, (size_t)nr * nt * 8, cudaMemcpyHostToDevice, w->st[0]));
+    if (direct) return search_interp_2d(dR, nr, dT, nt, dF, mY, m, mI, mV, algo, 0, nullptr, w->st[0], 0, 0);
+    SS_CHECK_CUDA(cudaEventRecord(w->ready, w->st[0]));
+    SS_CHECK_CUDA(cudaStreamWaitEvent(w->st[1], w->ready, 0));
+    unsigned char* base = w->buf + tr + tt + tf;
+    for (int64_t off = 0, c = 0; off < m; off += kChunk2D, ++c) {
+      const int64_t cnt = std::min(kChunk2D, m - off);
+      cudaStream_t s = w->st[c & 1];
+      unsigned char* b = base + (c & 1) * chunk;
+      double* dY = reinterpret_cast<double*>(b);
+      int32_t* dI = reinterpret_cast<int32_t*>(b + cin);
+      double* dV = reinterpret_cast<double*>(b + cin + cidx);
+      SS_CHECK_CUDA(cudaMemcpyAsync(dY, Y2 + 2 * off, (size_t)cnt * 16, cudaMemcpyHostToDevice, s));
+      if (ss_status st = search_interp_2d(dR, nr, dT, nt, dF, dY, cnt, dI, dV, algo, 0, nullptr, s, 0, 0)) return st;
+      SS_CHECK_CUDA(cudaMemcpyAsync(lowbounds2 + 2 * off, dI, (size_t)cnt * 8, cudaMemcpyDeviceToHost, s));
+      SS_CHECK_CUDA(cudaMemcpyAsync(values + off, dV, (size_t)cnt * 8, cudaMemcpyDeviceToHost, s));
+    }
     return SS_OK;
-  }
-  SS_CHECK_CUDA(cudaEventRecord(w->ready, w->st[0]));
-  SS_CHECK_CUDA(cudaStreamWaitEvent(w->st[1], w->ready, 0));
-  unsigned char* base = w->buf + tr + tt + tf;
-  for (int64_t off = 0, c = 0; off < m; off += kChunk2D, ++c) {
-    const int64_t cnt = std::min(kChunk2D, m - off);
-    cudaStream_t s = w->st[c & 1];
-    unsigned char* b = base + (c & 1) * chunk;
-    double* dY = reinterpret_cast<double*>(b);
-    int32_t* dI = reinterpret_cast<int32_t*>(b + cin);
-    double* dV = reinterpret_cast<double*>(b + cin + cidx);
-    SS_CHECK_CUDA(cudaMemcpyAsync(dY, Y2 + 2 * off, (size_t)cnt * 16, cudaMemcpyHostToDevice, s));
-    if (ss_status st = search_interp_2d(dR, nr, dT, nt, dF, dY, cnt, dI, dV, algo, 0, nullptr, s, 0, 0)) return st;
-    SS_CHECK_CUDA(cudaMemcpyAsync(lowbounds2 + 2 * off, dI, (size_t)cnt * 8, cudaMemcpyDeviceToHost, s));
-    SS_CHECK_CUDA(cudaMemcpyAsync(values + off, dV, (size_t)cnt * 8, cudaMemcpyDeviceToHost, s));
-  }
-  SS_CHECK_CUDA(cudaStreamSynchronize(w->st[0]));
-  SS_CHECK_CUDA(cudaStreamSynchronize(w->st[1]));
-  return SS_OK;
+  };
+  return drain(w, queue());
 }

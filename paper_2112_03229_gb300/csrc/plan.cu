@@ -132,12 +132,26 @@ extern "C" void ss_plan_opts_default(ss_plan_opts* o) {
   o->tune_cache = nullptr;
 }
 
-static ss_status check_opts(const ss_plan_opts* o) {
-  if (o->side != SS_SIDE_LT && o->side != SS_SIDE_LE) return fail(SS_EINVAL, "plan: bad side");
-  if (o->model < SS_MODEL_NONE || o->model > SS_MODEL_LOGHASH)
-    return fail(SS_EINVAL, o->model == SS_MODEL_HUNT ? "plan: the hunt applies to 2D plans only" : "plan: bad model");
-  if (o->algo < SS_ALGO_AUTO || o->algo > SS_ALGO_BALLOT) return fail(SS_EINVAL, "plan: algo must be auto, binary, bucket or ballot");
-  if (o->tile < 0 || o->mlp_epochs < 0 || o->dir_cap < 0) return fail(SS_EINVAL, "plan: negative option");
+// Options of a 1D (kind 1) or 2D (kind 2) plan: at creation and again when a
+// plan is read from a file.
+ss_status ss::check_plan_opts(const ss_plan_opts& o, int kind) {
+  if (o.tile < 0 || o.mlp_epochs < 0 || o.dir_cap < 0) return fail(SS_EINVAL, "plan: negative option");
+  if (o.dir_cap > SS_MAX_DIR_CAP) return fail(SS_EINVAL, "plan: dir_cap above SS_MAX_DIR_CAP");
+  if (!(o.mlp_lr >= 0.0f && o.mlp_lr < 1e30f)) return fail(SS_EINVAL, "plan: mlp_lr must be finite and >= 0");
+  if (kind == 1) {
+    if (o.side != SS_SIDE_LT && o.side != SS_SIDE_LE) return fail(SS_EINVAL, "plan: bad side");
+    if (o.model < SS_MODEL_NONE || o.model > SS_MODEL_LOGHASH)
+      return fail(SS_EINVAL, o.model == SS_MODEL_HUNT ? "plan: the hunt applies to 2D plans only" : "plan: bad model");
+    if (o.algo < SS_ALGO_AUTO || o.algo > SS_ALGO_BALLOT)
+      return fail(SS_EINVAL, "plan: algo must be auto, binary, bucket or ballot");
+    return SS_OK;
+  }
+  if (o.side != SS_SIDE_LT) return fail(SS_EINVAL, "ss_plan_create_2d: the 2D lookup uses side SS_SIDE_LT");
+  if ((o.extrap != 0 && o.extrap != 1) || (o.logspace != 0 && o.logspace != 1))
+    return fail(SS_EINVAL, "ss_plan_create_2d: extrap and logspace must be 0 or 1");
+  if (o.model < SS_MODEL_NONE || o.model > SS_MODEL_HUNT || o.algo == SS_ALGO_BALLOT || o.algo == SS_ALGO_BRANCHY ||
+      o.algo < 0 || o.algo > SS_ALGO_BALLOT)
+    return fail(SS_EINVAL, "ss_plan_create_2d: algo must be auto, binary or bucket");
   return SS_OK;
 }
 
@@ -163,7 +177,7 @@ extern "C" ss_status ss_plan_create_1d(ss_plan** out, int32_t ntables, const int
   ss_plan_opts o;
   ss_plan_opts_default(&o);
   if (opts_in) o = *opts_in;
-  if (ss_status st = check_opts(&o)) return st;
+  if (ss_status st = check_plan_opts(o, 1)) return st;
   auto* p = new ss_plan();
   p->kind = 1;
   p->ntables = ntables;

@@ -450,12 +450,7 @@ extern "C" ss_status ss_plan_create_2d(ss_plan** out, int32_t ntables, const int
   ss_plan_opts o;
   ss_plan_opts_default(&o);
   if (opts_in) o = *opts_in;
-  if (o.side != SS_SIDE_LT) return fail(SS_EINVAL, "ss_plan_create_2d: the 2D lookup uses side SS_SIDE_LT");
-  if ((o.extrap != 0 && o.extrap != 1) || (o.logspace != 0 && o.logspace != 1))
-    return fail(SS_EINVAL, "ss_plan_create_2d: extrap and logspace must be 0 or 1");
-  if (o.model < SS_MODEL_NONE || o.model > SS_MODEL_HUNT || o.algo == SS_ALGO_BALLOT || o.algo == SS_ALGO_BRANCHY ||
-      o.algo < 0 || o.algo > SS_ALGO_BALLOT)
-    return fail(SS_EINVAL, "ss_plan_create_2d: algo must be auto, binary or bucket");
+  if (ss_status st = check_plan_opts(o, 2)) return st;
   auto* p = new ss_plan();
   p->kind = 2;
   p->ntables = ntables;

@@ -17,6 +17,7 @@ const char* algo_name(int a);
 int algo_from_name(const std::string& s);
 int staged_bytes(int n, int dir_cap, bool cells, int algo);
 int initial_algo(const ss_plan_opts& o);
+ss_status check_plan_opts(const ss_plan_opts& o, int kind);   // kind 1: 1D plan, 2: 2D plan
 std::vector<Tile> make_tiles(const std::vector<int64_t>& Y_off, const std::vector<int>& bucket_of,
                              const int* bucket_tile, int64_t& total);
 int auto_tile(int64_t total, int blocks, int staged_bytes, float mult);

@@ -351,6 +351,7 @@ ss_status ss_search_1d(const double* X, int32_t n, const double* Y, int64_t m, i
 ss_status ss_search_1d_tuned(const double* X, int32_t n, const double* Y, int64_t m, int32_t* lowbounds,
                              int32_t side, int32_t algo, int32_t dir_cap, int32_t ballot_g, ss_devstat* stat,
                              cudaStream_t stream) {
+  if (dir_cap < 0 || dir_cap > SS_MAX_DIR_CAP) return ss::fail(SS_EINVAL, "ss_search_1d_tuned: dir_cap out of range");
   return ss::search_1d(X, n, Y, m, lowbounds, side, algo, stat, stream, dir_cap, ballot_g);
 }
 

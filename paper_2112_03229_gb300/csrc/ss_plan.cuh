@@ -8,7 +8,7 @@
 // the stream of targets.
 //
 // Blob layout (all offsets from the blob start, 16-byte aligned):
-//   [BlobHdr 128 B][mlp 65 floats, padded to 272 B][dir (cap+1) int32]
+//   [BlobHdr 128 B][mlp 65 floats, padded to 272 B][dir (cap+1) uint16]
 //   [keys (ns + kPad) uint64][eyt P uint64]           <- staged part
 //   [full keys nk + kPad uint64][fine dir]             <- global only (stride > 1)
 //   [wide section]                                    <- tables of 8129 .. ~76K keys

@@ -124,12 +124,14 @@ def test_plan_fitted_directory_and_wide_blocks(ss, side, tile):
 
 @pytest.mark.parametrize("model", ["none", "spline", "mlp", "loghash"])
 @pytest.mark.parametrize("side", [0, 1])
-def test_plan_every_layout_regime(ss, model, side):
+def test_plan_every_layout_regime(ss, model, side, tmp_path):
     """One plan over tables of every layout regime: staged whole with fitted
     16-bit directories (2 .. 8128 entries, jittered and clustered), wide
     sections of different directory budgets (8129, 20000 and 65535
     entries), and a two-level table (80000 entries, searched in global
-    memory); exact key hits and their neighbours in every table."""
+    memory); exact key hits and their neighbours in every table.  The plan
+    also goes through a file: the load's layout checks accept every regime
+    and the loaded plan gives the same answers."""
     rng = np.random.default_rng(77)
     tabs = [wl.log_spaced_table(n, 1e-4, 1e6, 0.2, seed=200 + n) for n in (2, 3, 17, 255, 1025, 8128, 8129, 20000)]
     tabs += [wl.sweep_table(4096, seed=9), wl.sweep_table(65535, seed=10), wl.log_spaced_table(80000, 1e-3, 1e7, 0.2, seed=11)]
@@ -148,6 +150,13 @@ def test_plan_every_layout_regime(ss, model, side):
     plan, got, st = run_plan_1d(ss, b, model=model, side=side, mlp_epochs=60 if model == "mlp" else None)
     np.testing.assert_array_equal(got, want)
     assert st.flags == 0
+    path = tmp_path / "regimes.bin"
+    plan.save(path)
+    re = ss.Plan.load(path)
+    out = torch.full((len(Y),), -1, dtype=torch.int32, device=DEV)
+    re.bind_1d(b.Y_off, Y.to(DEV), out)
+    re.execute()
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
 
 
 def test_plan_wide_section_with_ties(ss):
@@ -401,6 +410,57 @@ def test_plan_save_load_and_forced_fallback(ss, tmp_path):
     np.testing.assert_array_equal(out.cpu().numpy(), want)
     st = ss.read_stat(stat)
     assert st.fallbacks > len(b.Y) // 2
+
+
+# byte offsets of blob header fields (the 128-byte header of every prepared table)
+HDR_NB, HDR_OCC, HDR_E, HDR_S0, HDR_OFF_DIR, HDR_OFF_CELLS = 28, 32, 36, 40, 52, 112
+
+
+def test_plan_load_refuses_inconsistent_layouts(ss, tmp_path):
+    """A plan file whose layout does not hold together is refused by the
+    load's host-side checks (SS_EINVAL) before any kernel could read outside
+    it: a shifted blob offset, a bucket count above the budget, a directory
+    that does not start at 0, a wrong occupancy, a negative window, a wrong
+    ballot stride, a moved 2D cell table."""
+    b = small_batch(seed=12, ntables=20)
+    plan = ss.Plan.create_1d(b.X_off, b.X.to(DEV), model="spline")
+    path = tmp_path / "ok.bin"
+    plan.save(path)
+    raw = path.read_bytes()
+    offs, start = _blob_headers(raw)
+    h = start + offs[3]
+    blob_off_pos = raw.index(struct.pack("<q", len(offs)) + struct.pack("<%dq" % len(offs), *offs))
+
+    def corrupt(edit):
+        r = bytearray(raw)
+        edit(r)
+        bad = tmp_path / "bad.bin"
+        bad.write_bytes(bytes(r))
+        with pytest.raises(ss.SSError) as e:
+            ss.Plan.load(bad)
+        assert e.value.code == 1 and "corrupt plan file" in str(e.value)
+
+    dir_cap = struct.unpack_from("<i", raw, h + 44)[0]
+    off_dir = struct.unpack_from("<i", raw, h + HDR_OFF_DIR)[0]
+    occ = struct.unpack_from("<i", raw, h + HDR_OCC)[0]
+    corrupt(lambda r: struct.pack_into("<q", r, blob_off_pos + 8 + 8 * 2, offs[2] + 256))
+    corrupt(lambda r: struct.pack_into("<i", r, h + HDR_NB, dir_cap + 1))
+    corrupt(lambda r: struct.pack_into("<H", r, h + off_dir, 1))
+    corrupt(lambda r: struct.pack_into("<i", r, h + HDR_OCC, occ + 1))
+    corrupt(lambda r: struct.pack_into("<i", r, h + HDR_E, -1))
+    corrupt(lambda r: struct.pack_into("<i", r, h + HDR_S0, 7))
+    ss.Plan.load(path)   # the untouched file still loads
+
+    b2 = wl.batched_2d(ntables=3, pairs_per_table=100, seed=13)
+    plan2 = ss.Plan.create_2d(b2.R_off, b2.R.to(DEV), b2.T_off, b2.T.to(DEV), b2.F_off, b2.F.to(DEV))
+    path2 = tmp_path / "ok2.bin"
+    plan2.save(path2)
+    raw = path2.read_bytes()
+    offs, start = _blob_headers(raw)
+    h = start + offs[1]
+    cells = struct.unpack_from("<i", raw, h + HDR_OFF_CELLS)[0]
+    corrupt(lambda r: struct.pack_into("<i", r, h + HDR_OFF_CELLS, cells + 16))
+    ss.Plan.load(path2)
 
 
 def test_plan_autotune_and_cache(ss, tmp_path):

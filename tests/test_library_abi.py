@@ -50,3 +50,59 @@ def test_argument_errors_without_gpu(built):
     assert L.ss_search_1d(p, 4, p, 1, p, 7, 0, None, None) == 1                      # bad side
     assert L.ss_search_1d(p, 4, p, 0, p, 0, 0, None, None) == 0                      # m == 0: nothing to do
     assert L.ss_search_interp_2d(p, 1, p, 4, p, p, 1, p, p, 0, None, None) == 1      # axis < 2
+    # directory budgets above SS_MAX_DIR_CAP (65536) are refused
+    assert L.ss_search_1d_tuned(p, 4, p, 1, p, 0, 2, 65537, 0, None, None) == 1
+    assert L.ss_search_1d_tuned(p, 4, p, 1, p, 0, 2, -1, 0, None, None) == 1
+    for kind in (1, 2):
+        o = ss.plan_opts(dir_cap=65537)
+        h = ctypes.c_void_p()
+        off = (ctypes.c_int64 * 2)(0, 4)
+        if kind == 1:
+            st = L.ss_plan_create_1d(ctypes.byref(h), 1, off, p, ctypes.byref(o), None)
+        else:
+            st = L.ss_plan_create_2d(ctypes.byref(h), 1, off, p, off, p, off, p, ctypes.byref(o), None)
+        assert st == 1 and b"dir_cap" in L.ss_last_error() and not h.value
+
+
+def plan_file_version():
+    src = open(os.path.join(ROOT, "paper_2112_03229_gb300", "csrc", "plan_io.cu")).read()
+    return int(re.search(r"kVersion = (\d+);", src).group(1))
+
+
+def test_plan_load_checks_without_gpu(built, tmp_path):
+    # a plan file is checked on the host before anything reaches the device:
+    # unreadable, foreign, truncated and inconsistent files are refused
+    import struct
+    import paper_2112_03229_gb300 as ss
+    L = ss.lib()
+    h = ctypes.c_void_p()
+
+    def load(data):
+        path = tmp_path / "p.bin"
+        path.write_bytes(data)
+        return L.ss_plan_load(ctypes.byref(h), str(path).encode(), None)
+
+    assert L.ss_plan_load(ctypes.byref(h), str(tmp_path / "missing.bin").encode(), None) == 1
+    magic = b"SSPLAN\x00\x01"
+    head = magic + struct.pack("<iii", plan_file_version(), 1, 1)
+    assert load(b"not a plan") == 1
+    assert load(magic + struct.pack("<iii", plan_file_version() + 1, 1, 1)) == 1
+    assert b"version" in L.ss_last_error()
+    assert load(head) == 1                                          # truncated after the header
+
+    def vec(fmt, vals):
+        return struct.pack("<q", len(vals)) + struct.pack("<%d%s" % (len(vals), fmt), *vals)
+
+    def one_table(opts, blob_bytes, dir_cap=256):
+        body = bytes(opts) + vec("i", [64]) + vec("i", []) + vec("q", [0, 64]) + vec("i", [dir_cap]) + vec("i", [0])
+        body += vec("q", [0]) + vec("q", [])
+        body += struct.pack("<8i", *[0] * 8) + struct.pack("<8f", *[1.0] * 8) + struct.pack("<8i", 1, *[0] * 7)
+        body += struct.pack("<i", 0) + struct.pack("<q", blob_bytes)
+        return head + body + bytes(blob_bytes)
+
+    assert load(one_table(ss.plan_opts(dir_cap=65537), 4096)) == 1   # options out of range
+    assert b"dir_cap" in L.ss_last_error()
+    assert load(one_table(ss.plan_opts(), 256)) == 1                  # blob bytes off the layout
+    assert b"corrupt plan file" in L.ss_last_error()
+    assert load(one_table(ss.plan_opts(), 4096, dir_cap=0)) == 1      # no directory budget
+    assert not h.value
