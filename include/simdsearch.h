@@ -314,10 +314,14 @@ ss_status ss_search_interp_2d_batched(int32_t ntables, const int64_t* R_off, con
  * one 8 MiB array inside the library that every GPU loading the library
  * holds until the process exits.  A batch whose working set exceeds 8 MiB is
  * rejected with SS_EINVAL (about 250 tables of 2000 entries fit).  Every
- * call reuses that array and clears what must start at zero, so calls whose
- * work overlaps on the GPU (other streams or host threads) race: serialise
- * them.  The first call on each device looks up the array's device address;
- * make that first call before any stream capture.  A table that is not
+ * call reuses that array and clears what must start at zero, so calls are
+ * ordered on the GPU: each call's work waits for the previous call's (on
+ * any stream, from any host thread), and calls from different streams run
+ * one after another.  A stream being captured into a graph cannot wait on
+ * the previous call: calls captured into graphs must be ordered by the
+ * caller.  The first call on each device looks up the array's device
+ * address and creates its event; make that first call before any stream
+ * capture.  A table that is not
  * strictly increasing sets SS_FLAG_NOT_SORTED in *stat. */
 ss_status ss_search_1d_batched_static(int32_t ntables, const int64_t* X_off, const double* X,
                                       const int64_t* Y_off, const double* Y, int32_t* lowbounds,

@@ -45,6 +45,28 @@ def test_static_matches_plan_on_two_calls_in_a_row(ss):
         assert ss.read_stat(stat).flags == 0
 
 
+def test_static_calls_on_two_streams_are_ordered(ss):
+    # calls queued on two streams without synchronising in between share the
+    # one array: each call's work waits for the previous call's, so every
+    # result is still exact
+    bs = [wl.batched_1d(ntables=30 + 7 * i, count_scale=0.004, seed=31 + i) for i in range(4)]
+    wants = [reference(ss, b, i & 1) for i, b in enumerate(bs)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    ins = [b.Y.to(DEV) for b in bs]
+    Xs = [b.X.to(DEV) for b in bs]
+    outs = [torch.full((len(b.Y),), -1, dtype=torch.int32, device=DEV) for b in bs]
+    torch.cuda.synchronize()
+    for rep in range(3):
+        for i, b in enumerate(bs):
+            ss.search_1d_batched_static(b.X_off, Xs[i], b.Y_off, ins[i], out=outs[i], side=i & 1,
+                                        stream=streams[i & 1])
+        torch.cuda.synchronize()
+        for i in range(len(bs)):
+            np.testing.assert_array_equal(outs[i].cpu().numpy(), wants[i])
+            outs[i].fill_(-1)
+        torch.cuda.synchronize()
+
+
 def test_static_rejects_a_batch_over_its_limit(ss):
     b = wl.batched_1d(ntables=4000, count_scale=0.00005, seed=23)
     with pytest.raises(ss.SSError) as e:
