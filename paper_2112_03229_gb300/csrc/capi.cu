@@ -10,8 +10,6 @@ namespace ss {
 
 static thread_local std::string g_last_error;
 
-void set_error(const std::string& msg) { g_last_error = msg; }
-
 ss_status fail(ss_status code, const std::string& msg) {
   g_last_error = msg;
   return code;

@@ -1,6 +1,6 @@
 // ss_common.cuh -- device helpers shared by every kernel of the library:
-// the order-preserving integer image of a float64, 128-bit streaming
-// loads/stores, status reporting and host-side error plumbing.
+// the order-preserving integer image of a float64, streaming 128- and
+// 256-bit loads and stores, and host-side error plumbing.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -34,11 +34,6 @@ __device__ __forceinline__ uint64_t order_key(double x) {
   return k > kKeyPosInf ? 0ull : k;
 }
 
-__device__ __forceinline__ bool is_nan_key_input(double x) {
-  const uint64_t u = static_cast<uint64_t>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
-  return u > 0x7FF0000000000000ull;
-}
-
 // Streaming (evict-first) 128-bit global accesses for data touched once.
 __device__ __forceinline__ double2 ld_stream(const double2* p) { return __ldcs(p); }
 __device__ __forceinline__ void st_stream(int4* p, int4 v) { __stcs(p, v); }
@@ -57,16 +52,9 @@ __device__ __forceinline__ void ld_nc_v8(const float* p, float (&r)[8]) {
       : "l"(p));
 }
 
-// Warp-aggregated increment of a device counter (one atomic per warp).
-__device__ __forceinline__ void warp_count(unsigned long long* ctr, bool pred) {
-  const unsigned mask = __ballot_sync(0xFFFFFFFFu, pred);
-  if (ctr != nullptr && mask != 0u && (threadIdx.x & 31) == 0) atomicAdd(ctr, (unsigned long long)__popc(mask));
-}
-
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-void set_error(const std::string& msg);
 ss_status fail(ss_status code, const std::string& msg);
 ss_status cuda_fail(cudaError_t err, const char* what);
 int num_sms();

@@ -39,25 +39,13 @@ __device__ __forceinline__ ff fast_two_sum(float a, float b) {
   return {s, e};
 }
 
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-  const ff s = two_sum(a.hi, b.hi);
-  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
-}
-
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
-  const float p = a.hi * b.hi;
-  float e = fmaf(a.hi, b.hi, -p);
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
-  return fast_two_sum(p, e);
-}
-
 constexpr int kMaxCellOctaves = 10;   // exact integer weights when a cell spans at most 2^10
 constexpr int kFFMinExp = 1023 - 70;  // doubles split into float-float must lie in [2^-70, 2^101)
 constexpr int kFFMaxExp = 1023 + 100;
 
-// Products and sums that feed further float-float arithmetic are left
-// unnormalised (the pair still sums exactly to the represented value).
+// Product and sum of two float-float values, left unnormalised: the pair
+// still sums exactly to the represented value, and the final widening to
+// double adds hi and lo anyway, so no fast two-sum is spent on them.
 __device__ __forceinline__ ff ff_mul_u(ff a, ff b) {
   const float p = a.hi * b.hi;
   float e = fmaf(a.hi, b.hi, -p);

@@ -166,10 +166,4 @@ __device__ __forceinline__ int loghash_propose(float a, float c, int nk, double 
   return (int)fminf(fmaxf(p, 0.0f), (float)nk);
 }
 
-template <class D>
-__device__ __forceinline__ int spline_propose(const D* __restrict__ dir, int shift, uint64_t base, int nb,
-                                              uint64_t q) {
-  return (int)rintf(spline_position(dir, shift, base, nb, q));
-}
-
 }  // namespace ss
