@@ -86,6 +86,9 @@ def _stream(stream):
 def _dev(t, dtype, name):
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError("%s must be a CUDA tensor" % name)
+    if t.device.index is not None and t.device.index != torch.cuda.current_device():
+        raise ValueError("%s is on %s, but the library runs on the current device cuda:%d"
+                         % (name, t.device, torch.cuda.current_device()))
     if t.dtype != dtype:
         raise TypeError("%s must be %s" % (name, dtype))
     if not t.is_contiguous():
@@ -123,7 +126,19 @@ def read_stat(stat: torch.Tensor, stream=None, timeout_ms: int = 60_000) -> DevS
 
 
 def _statp(stat):
-    return C.c_void_p(stat.data_ptr()) if stat is not None else None
+    if stat is None:
+        return None
+    if not isinstance(stat, torch.Tensor) or not stat.is_cuda or not stat.is_contiguous():
+        raise TypeError("stat must be a contiguous CUDA tensor (see new_stat)")
+    if stat.numel() * stat.element_size() < C.sizeof(DevStat):
+        raise ValueError("stat must hold at least %d bytes" % C.sizeof(DevStat))
+    return _dev(stat, stat.dtype, "stat")
+
+
+def _need(t, count, name):
+    """The library reads or writes `count` elements of t."""
+    if t.numel() < count:
+        raise ValueError("%s holds %d elements, %d needed" % (name, t.numel(), count))
 
 
 def search_1d(X: torch.Tensor, Y: torch.Tensor, out: torch.Tensor | None = None, side: int = SIDE_LT,
@@ -131,6 +146,7 @@ def search_1d(X: torch.Tensor, Y: torch.Tensor, out: torch.Tensor | None = None,
     """ss_search_1d: int32 index of the largest entry of X below each target of Y."""
     if out is None:
         out = torch.empty(Y.shape, dtype=torch.int32, device=Y.device)
+    _need(out, Y.numel(), "out")
     args = (_dev(X, torch.float64, "X"), X.numel(), _dev(Y, torch.float64, "Y"), Y.numel(),
             _dev(out, torch.int32, "out"), side, _algo(algo))
     if dir_cap or ballot_g:
@@ -157,6 +173,8 @@ def search_interp_2d(R, T, F, Y2, idx=None, val=None, algo="auto", stat=None, st
         idx = torch.empty((m, 2), dtype=torch.int32, device=Y2.device)
     if val is None:
         val = torch.empty((m,), dtype=torch.float64, device=Y2.device)
+    _need(idx, 2 * m, "idx")
+    _need(val, m, "val")
     if extrap or logspace:
         L = lib()
         L.ss_search_interp_2d_ex.argtypes = [_vp, _i32, _vp, _i32, _vp, _vp, _i64, _vp, _vp,
@@ -181,6 +199,8 @@ def search_interp_2d(R, T, F, Y2, idx=None, val=None, algo="auto", stat=None, st
 # ---------------------------------------------------------------------------
 def mlp_loss_grad(params, x, y, stream=None):
     """Mean squared error of the MLP over (x, y) and its gradient (65 floats), on the GPU."""
+    _need(params, 65, "params")
+    _need(x, 2 * y.numel(), "x")
     grad = torch.empty(65, dtype=torch.float32, device=params.device)
     loss = torch.empty(1, dtype=torch.float32, device=params.device)
     _check(lib().ss_mlp_loss_grad(_dev(params, torch.float32, "params"), _dev(x, torch.float32, "x"),
@@ -190,6 +210,7 @@ def mlp_loss_grad(params, x, y, stream=None):
 
 
 def mlp_forward(params, x, stream=None):
+    _need(params, 65, "params")
     y = torch.empty(x.numel() // 2, dtype=torch.float32, device=x.device)
     _check(lib().ss_mlp_forward(_dev(params, torch.float32, "params"), _dev(x, torch.float32, "x"), y.numel(),
                                 _dev(y, torch.float32, "y"), _stream(stream)))
@@ -197,6 +218,8 @@ def mlp_forward(params, x, stream=None):
 
 
 def mlp_adam_step(params, grad, m1, m2, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    for t, name in ((params, "params"), (grad, "grad"), (m1, "m1"), (m2, "m2")):
+        _need(t, 65, name)
     _check(lib().ss_mlp_adam_step(_dev(params, torch.float32, "params"), _dev(grad, torch.float32, "grad"),
                                   _dev(m1, torch.float32, "m1"), _dev(m2, torch.float32, "m2"), step, lr, beta1,
                                   beta2, eps, _stream(stream)))
@@ -245,9 +268,20 @@ def _plan_sigs(L):
         getattr(L, n).restype = _i32
 
 
-def _offsets(off):
+def _offsets(off, name="offsets", length=None, data=None, per=1):
+    """CSR offsets as a host int64 array and its pointer.  The library reads
+    ntables + 1 of them (`length`, when the table count is already fixed), and
+    the last one, times `per` elements, must lie within `data`."""
     import numpy as np
     a = np.ascontiguousarray(off.cpu().numpy() if isinstance(off, torch.Tensor) else off, dtype=np.int64)
+    if a.ndim != 1 or len(a) < 2:
+        raise ValueError("%s must list ntables + 1 >= 2 offsets" % name)
+    if length is not None and len(a) != length:
+        raise ValueError("%s has %d entries, %d expected (ntables + 1)" % (name, len(a), length))
+    if a[0] < 0 or (np.diff(a) < 0).any():
+        raise ValueError("%s must be non-negative and non-decreasing" % name)
+    if data is not None and isinstance(data, torch.Tensor) and int(a[-1]) * per > data.numel():
+        raise ValueError("%s end past the data (%d elements needed, %d held)" % (name, int(a[-1]) * per, data.numel()))
     return a, a.ctypes.data_as(C.POINTER(C.c_int64))
 
 
@@ -288,7 +322,7 @@ class Plan:
     @classmethod
     def create_1d(cls, X_off, X, stream=None, **opts):
         o = plan_opts(**opts)
-        off, offp = _offsets(X_off)
+        off, offp = _offsets(X_off, "X_off", data=X)
         h = C.c_void_p()
         _check(lib().ss_plan_create_1d(C.byref(h), len(off) - 1, offp, _dev(X, torch.float64, "X"), C.byref(o),
                                        _stream(stream)))
@@ -297,9 +331,9 @@ class Plan:
     @classmethod
     def create_2d(cls, R_off, R, T_off, T, F_off, F, stream=None, **opts):
         o = plan_opts(**opts)
-        ro, rp = _offsets(R_off)
-        to, tp = _offsets(T_off)
-        fo, fp = _offsets(F_off)
+        ro, rp = _offsets(R_off, "R_off", data=R)
+        to, tp = _offsets(T_off, "T_off", length=len(ro), data=T)
+        fo, fp = _offsets(F_off, "F_off", length=len(ro), data=F)
         h = C.c_void_p()
         _check(lib().ss_plan_create_2d(C.byref(h), len(ro) - 1, rp, _dev(R, torch.float64, "R"), tp,
                                        _dev(T, torch.float64, "T"), fp, _dev(F, torch.float64, "F"), C.byref(o),
@@ -317,13 +351,16 @@ class Plan:
         return p
 
     def bind_1d(self, Y_off, Y, out, stat=None, stream=None):
-        off, offp = _offsets(Y_off)
+        off, offp = _offsets(Y_off, "Y_off", length=self.ntables + 1, data=Y)
+        _need(out, int(off[-1]), "out")
         self._keep = (Y, out, stat)
         _check(lib().ss_plan_bind_1d(self._h, offp, _dev_or_pinned(Y, torch.float64, "Y"),
                                      _dev_or_pinned(out, torch.int32, "out"), _statp(stat), _stream(stream)))
 
     def bind_2d(self, Y_off, Y2, idx, val, stat=None, stream=None):
-        off, offp = _offsets(Y_off)
+        off, offp = _offsets(Y_off, "Y_off", length=self.ntables + 1, data=Y2, per=2)
+        _need(idx, 2 * int(off[-1]), "idx")
+        _need(val, int(off[-1]), "val")
         self._keep = (Y2, idx, val, stat)
         _check(lib().ss_plan_bind_2d(self._h, offp, _dev_or_pinned(Y2, torch.float64, "Y2"),
                                      _dev_or_pinned(idx, torch.int32, "idx"), _dev_or_pinned(val, torch.float64, "val"),
@@ -373,10 +410,11 @@ def search_1d_batched(X_off, X, Y_off, Y, out=None, side=SIDE_LT, stat=None, str
     """ss_search_1d_batched: one call over many tables (table k = X[X_off[k]:X_off[k+1]],
     its targets Y[Y_off[k]:Y_off[k+1]]); synchronous."""
     L = _batched_lib()
-    xo, xp = _offsets(X_off)
-    yo, yp = _offsets(Y_off)
+    xo, xp = _offsets(X_off, "X_off", data=X)
+    yo, yp = _offsets(Y_off, "Y_off", length=len(xo), data=Y)
     if out is None:
         out = torch.empty(Y.shape, dtype=torch.int32, device=Y.device)
+    _need(out, int(yo[-1]), "out")
     _check(L.ss_search_1d_batched(len(xo) - 1, xp, _dev(X, torch.float64, "X"), yp, _dev(Y, torch.float64, "Y"),
                                   _dev(out, torch.int32, "out"), side, _statp(stat), _stream(stream)))
     return out
@@ -386,15 +424,17 @@ def search_interp_2d_batched(R_off, R, T_off, T, F_off, F, Y_off, Y2, idx=None, 
     """ss_search_interp_2d_batched: the 2D lookup over many tables in one call; synchronous.
     Returns (idx [m, 2] int32, val [m] float64)."""
     L = _batched_lib()
-    ro, rp = _offsets(R_off)
-    to, tp = _offsets(T_off)
-    fo, fp = _offsets(F_off)
-    yo, yp = _offsets(Y_off)
+    ro, rp = _offsets(R_off, "R_off", data=R)
+    to, tp = _offsets(T_off, "T_off", length=len(ro), data=T)
+    fo, fp = _offsets(F_off, "F_off", length=len(ro), data=F)
+    yo, yp = _offsets(Y_off, "Y_off", length=len(ro), data=Y2, per=2)
     m = Y2.numel() // 2
     if idx is None:
         idx = torch.empty((m, 2), dtype=torch.int32, device=Y2.device)
     if val is None:
         val = torch.empty((m,), dtype=torch.float64, device=Y2.device)
+    _need(idx, 2 * int(yo[-1]), "idx")
+    _need(val, int(yo[-1]), "val")
     _check(L.ss_search_interp_2d_batched(len(ro) - 1, rp, _dev(R, torch.float64, "R"), tp, _dev(T, torch.float64, "T"),
                                          fp, _dev(F, torch.float64, "F"), yp, _dev(Y2, torch.float64, "Y2"),
                                          _dev(idx, torch.int32, "idx"), _dev(val, torch.float64, "val"),
@@ -411,10 +451,11 @@ def search_1d_batched_static(X_off, X, Y_off, Y, out=None, side=SIDE_LT, stat=No
                                                   _i32, _vp, _vp]
         L.ss_search_1d_batched_static.restype = _i32
         L._static_sig = True
-    xo, xp = _offsets(X_off)
-    yo, yp = _offsets(Y_off)
+    xo, xp = _offsets(X_off, "X_off", data=X)
+    yo, yp = _offsets(Y_off, "Y_off", length=len(xo), data=Y)
     if out is None:
         out = torch.empty(Y.shape, dtype=torch.int32, device=Y.device)
+    _need(out, int(yo[-1]), "out")
     _check(L.ss_search_1d_batched_static(len(xo) - 1, xp, _dev(X, torch.float64, "X"), yp,
                                          _dev(Y, torch.float64, "Y"), _dev(out, torch.int32, "out"), side,
                                          _statp(stat), _stream(stream)))
@@ -450,6 +491,7 @@ def search_1d_host(X, Y, out=None, side=SIDE_LT, algo="auto"):
     L = _host_lib()
     if out is None:
         out = torch.empty(Y.shape, dtype=torch.int32)
+    _need(out, Y.numel(), "out")
     _check(L.ss_search_1d_host(_host(X, torch.float64, "X"), X.numel(), _host(Y, torch.float64, "Y"), Y.numel(),
                                _host(out, torch.int32, "out"), side, _algo(algo)))
     return out
@@ -459,10 +501,14 @@ def search_interp_2d_host(R, T, F, Y2, idx=None, val=None, algo="auto"):
     """ss_search_interp_2d_host: all arrays in host memory."""
     L = _host_lib()
     m = Y2.numel() // 2
+    if F.numel() != R.numel() * T.numel():
+        raise ValueError("F must hold len(R) * len(T) values")
     if idx is None:
         idx = torch.empty((m, 2), dtype=torch.int32)
     if val is None:
         val = torch.empty((m,), dtype=torch.float64)
+    _need(idx, 2 * m, "idx")
+    _need(val, m, "val")
     _check(L.ss_search_interp_2d_host(_host(R, torch.float64, "R"), R.numel(), _host(T, torch.float64, "T"), T.numel(),
                                       _host(F, torch.float64, "F"), _host(Y2, torch.float64, "Y2"), m,
                                       _host(idx, torch.int32, "idx"), _host(val, torch.float64, "val"), _algo(algo)))
