@@ -1,7 +1,8 @@
 // plan_io.cu -- plan checkpoint: the prepared tables (keys, directories,
 // trained models, learned windows), value grids and tuning choices written
 // to a versioned binary file and read back; a loaded plan gives the same
-// results as the one that was saved.
+// results as the one that was saved.  A file is read whole on the host and
+// its layout checked there before anything reaches the device.
 #include <cstdio>
 #include <cstring>
 #include <memory>
