@@ -1,8 +1,9 @@
 // plan_io.cu -- plan checkpoint: the prepared tables (keys, directories,
 // trained models, learned windows), value grids and tuning choices written
 // to a versioned binary file and read back; a loaded plan gives the same
-// results as the one that was saved.  A file is read whole on the host and
-// its layout checked there before anything reaches the device.
+// results as the one that was saved.  The prepared tables are read whole on
+// the host and their layout checked there before anything reaches the
+// device; value grids follow in chunks.
 #include <cstdio>
 #include <cstring>
 #include <memory>
