@@ -62,6 +62,39 @@ MUTATIONS = [
     ("Adam bias correction dropped",
      "double c1 = 1.0 - pow(beta1, (double)step);",
      "double c1 = 1.0;"),
+    ("side <= searched as <",
+     "int below = side ? (X[mid] <= t) : (X[mid] < t);",
+     "int below = side ? (X[mid] < t) : (X[mid] < t);"),
+    ("log-space weight measured from the upper entry",
+     "if (logspace) w = (log(x) - log(X[c])) / (log(X[c + 1]) - log(X[c]));",
+     "if (logspace) w = (log(X[c + 1]) - log(x)) / (log(X[c + 1]) - log(X[c]));"),
+    ("extrapolation flag ignored",
+     "return extrap ? w : clamp01(w);",
+     "return clamp01(w);"),
+    ("outer blend weighted by the T weight",
+     "*v_out = (1.0 - wr) * lo_row + wr * hi_row;",
+     "*v_out = (1.0 - wt) * lo_row + wt * hi_row;"),
+    ("mantissa feature scaled by 2^-53",
+     "/ 4503599627370496.0;",
+     "/ 9007199254740992.0;"),
+    ("output bias left out of the forward pass",
+     "double y = b2;",
+     "double y = 0.0;"),
+    ("ReLU gradient passed through inactive units",
+     "if (h[k] > 0.0) {",
+     "if (h[k] >= 0.0) {"),
+    ("loss summed instead of averaged",
+     "return loss / (double)B;",
+     "return loss;"),
+    ("second Adam moment from the raw gradient",
+     "(1.0 - beta2) * grad[k] * grad[k];",
+     "(1.0 - beta2) * grad[k];"),
+    ("bucket shift one step too coarse",
+     "if ((k1 >> s) - (k0 >> s) < (uint64_t)cap_buckets) return s;",
+     "if ((k1 >> s) - (k0 >> s) < (uint64_t)cap_buckets) return s + 1;"),
+    ("spline knot counts its own key",
+     "if (oracle_order_key(X[i]) < kappa) ++c;",
+     "if (oracle_order_key(X[i]) <= kappa) ++c;"),
 ]
 
 
