@@ -95,6 +95,18 @@ MUTATIONS = [
     ("spline knot counts its own key",
      "if (oracle_order_key(X[i]) < kappa) ++c;",
      "if (oracle_order_key(X[i]) <= kappa) ++c;"),
+    ("2D batch options dropped",
+     "Y2 + 2 * y0, Y_off[k + 1] - y0, extrap, logspace,",
+     "Y2 + 2 * y0, Y_off[k + 1] - y0, 0, 0,"),
+    ("2D batch pairs offset by one double per pair",
+     "Y2 + 2 * y0, Y_off[k + 1] - y0, extrap, logspace,",
+     "Y2 + y0, Y_off[k + 1] - y0, extrap, logspace,"),
+    ("sampled 1D form reads the k-th target",
+     "lowbounds[k] = lower_bound_index(X, n, Y[sample[k]], side);",
+     "lowbounds[k] = lower_bound_index(X, n, Y[k], side);"),
+    ("sampled 2D form reads the k-th pair",
+     "int64_t i = sample[k];",
+     "int64_t i = k;"),
 ]
 
 

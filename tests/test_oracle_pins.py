@@ -329,6 +329,34 @@ def test_batched_equals_per_table():
         np.testing.assert_array_equal(got[b.Y_off[k]:b.Y_off[k + 1]], brute(x, y, 0) if len(y) < 3000 else oracle.search_1d(x, y))
 
 
+def test_batched_2d_equals_per_table():
+    # every table of a 2D batch is looked up exactly as on its own (whose
+    # values the closed-form pins above fix), options included
+    b = wl.batched_2d(ntables=5, pairs_per_table=300, seed=4)
+    Ro, To, Fo, Yo = (o.numpy() for o in (b.R_off, b.T_off, b.F_off, b.Y_off))
+    R, T, F, Y2 = b.R.numpy(), b.T.numpy(), b.F.numpy(), b.Y2.numpy()
+    for extrap, logspace in ((0, 0), (1, 0), (0, 1)):
+        gi, gv = oracle.search_interp_2d_batched(Ro, R, To, T, Fo, F, Yo, Y2, extrap=extrap, logspace=logspace)
+        for k in range(5):
+            wi, wv = oracle.search_interp_2d(R[Ro[k]:Ro[k + 1]], T[To[k]:To[k + 1]], F[Fo[k]:Fo[k + 1]],
+                                             Y2[Yo[k]:Yo[k + 1]], extrap=extrap, logspace=logspace)
+            np.testing.assert_array_equal(gi[Yo[k]:Yo[k + 1]], wi)
+            np.testing.assert_array_equal(gv[Yo[k]:Yo[k + 1]], wv)
+
+
+def test_sampled_forms_equal_the_full_forms():
+    rng = np.random.default_rng(8)
+    X, Y = (t.numpy() for t in wl.plain_1d(m=5000, seed=6))
+    sample = rng.choice(len(Y), 300, replace=False).astype(np.int64)
+    for side in (0, 1):
+        np.testing.assert_array_equal(oracle.search_1d_sampled(X, Y, sample, side), oracle.search_1d(X, Y, side)[sample])
+    R, T, F, Y2 = (t.numpy() for t in wl.interp_2d(m=4000, seed=7))
+    si, sv = oracle.search_interp_2d_sampled(R, T, F, Y2, sample[sample < 4000])
+    fi, fv = oracle.search_interp_2d(R, T, F, Y2)
+    np.testing.assert_array_equal(si, fi[sample[sample < 4000]])
+    np.testing.assert_array_equal(sv, fv[sample[sample < 4000]])
+
+
 # ---------------------------------------------------------------- position model
 
 def test_mlp_features_closed_form():
