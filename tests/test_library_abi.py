@@ -62,6 +62,22 @@ def test_argument_errors_without_gpu(built):
         else:
             st = L.ss_plan_create_2d(ctypes.byref(h), 1, off, p, off, p, off, p, ctypes.byref(o), None)
         assert st == 1 and b"dir_cap" in L.ss_last_error() and not h.value
+    # the other option checks of plan creation, also before any CUDA call
+    off = (ctypes.c_int64 * 2)(0, 4)
+    h = ctypes.c_void_p()
+    for kind, kw, msg in ((1, dict(tile=-1), b"negative"), (1, dict(model="hunt"), b"2D plans only"),
+                          (1, dict(side=5), b"side"), (2, dict(side=1), b"SS_SIDE_LT"),
+                          (2, dict(algo="ballot"), b"auto, binary or bucket"), (1, dict(mlp_lr=float("nan")), b"mlp_lr")):
+        o = ss.plan_opts(**kw)
+        if kind == 1:
+            st = L.ss_plan_create_1d(ctypes.byref(h), 1, off, p, ctypes.byref(o), None)
+        else:
+            st = L.ss_plan_create_2d(ctypes.byref(h), 1, off, p, off, p, off, p, ctypes.byref(o), None)
+        assert st == 1 and msg in L.ss_last_error(), (kw, L.ss_last_error())
+    o = ss.plan_opts()
+    o.extrap = 2
+    assert L.ss_plan_create_2d(ctypes.byref(h), 1, off, p, off, p, off, p, ctypes.byref(o), None) == 1
+    assert b"extrap" in L.ss_last_error() and not h.value
 
 
 def plan_file_version():
