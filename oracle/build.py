@@ -10,16 +10,17 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
 
+# -ffp-contract=off: no fused multiply-add, so every product and sum is
+# rounded on its own exactly as written in the source.
+CFLAGS = ["-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
 
 def build(force: bool = False) -> str:
     """Build liboracle.so if it is missing or older than oracle.c; return its path."""
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
     tmp = LIB + ".tmp.%d" % os.getpid()
-    # -ffp-contract=off: no fused multiply-add, so every product and sum is
-    # rounded on its own exactly as written in the source.
-    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-o", tmp, SRC, "-lm"]
+    cmd = ["gcc"] + CFLAGS + ["-o", tmp, SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

@@ -146,8 +146,8 @@ def test_each_planted_mistake_fails_a_pin(tmp_path, monkeypatch, name, old, new)
     mutant_src = tmp_path / "oracle_mutant.c"
     mutant_src.write_text(src.replace(old, new))
     lib = tmp_path / "liboracle_mutant.so"
-    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-                    "-o", str(lib), str(mutant_src), "-lm"], check=True, capture_output=True)
+    subprocess.run(["gcc"] + oracle._build_mod.CFLAGS + ["-o", str(lib), str(mutant_src), "-lm"],
+                   check=True, capture_output=True)
     # the oracle module loads the mutant in place of the real library for this case
     monkeypatch.setattr(oracle, "_lib", None)
     monkeypatch.setattr(oracle._build_mod, "build", lambda force=False: str(lib))
