@@ -1,0 +1,64 @@
+"""CPU checks of bench.py's host-side helpers: the clock record taken during
+the timed region, the traffic records and their source hashes, and the
+slicing of batched samples that the CPU baseline times."""
+import importlib.util
+import json
+import os
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def load_bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_clock_summary_reads_median_max_and_reasons():
+    b = load_bench()
+    c = b.ClockSampler(0)
+    c.lines = ["2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+               "1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+               "2070, 2070, 1000.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+               "garbled line", "[N/A], 2070, 0, 0, Not Active, Not Active, Not Active, Not Active"]
+    s = c.summary()
+    assert s["sm_mhz"] == 2070 and s["sm_max_mhz"] == 2070 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    c.lines = ["1500, 2070, 1000, 0x40, Not Active, Active, Not Active, Not Active"]
+    assert c.summary()["reasons"] == ["hw_thermal_slowdown"]
+    c.lines = []
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_traffic_records_are_current_and_go_null_on_change(monkeypatch):
+    b = load_bench()
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        rec = json.load(f)
+    assert rec
+    for key, r in rec.items():
+        kernel, workload = key.split("@")
+        v = b.recorded_traffic(kernel, workload)
+        assert v is not None and v == float(r["dram_bytes_per_launch"]), key
+    # a changed source file (a different hash) makes every record unusable
+    monkeypatch.setattr(b, "sources_hash", lambda files: "0" * 16)
+    for key in rec:
+        assert b.recorded_traffic(*key.split("@")) is None
+    assert b.recorded_traffic("no_such_kernel", "no_such_workload") is None
+
+
+def test_batched_sample_slices_cover_the_range():
+    b = load_bench()
+    Y_off = np.array([0, 5, 5, 12, 20, 31], dtype=np.int64)
+    for lo, hi in ((0, 31), (3, 17), (5, 12), (12, 13), (30, 31)):
+        t0, t1, yo = b._batched_tables(Y_off, lo, hi)
+        # the clipped offsets cover exactly [lo, hi), table by table
+        assert yo[0] == 0 and yo[-1] == hi - lo and (np.diff(yo) >= 0).all()
+        for k in range(t0, t1):
+            a, c = max(Y_off[k], lo), min(Y_off[k + 1], hi)
+            assert yo[k - t0 + 1] - yo[k - t0] == max(c - a, 0)
+        # and no table whose targets lie outside is included at either end
+        assert Y_off[t0 + 1] > lo or Y_off[t0 + 1] == Y_off[t0]
+        assert Y_off[t1 - 1] < hi
