@@ -88,6 +88,10 @@ typedef struct ss_devstat {
 /* Largest bucket-directory budget a caller may ask for (ss_plan_opts.dir_cap). */
 #define SS_MAX_DIR_CAP 65536
 
+/* Longest axis of the one-shot 2D lookups, which stage both axes with their
+ * per-cell data in shared memory (plans take axes of up to 2^20 entries). */
+#define SS_MAX_AXIS_2D 4096
+
 #define SS_FLAG_NOT_SORTED 0x1u     /* a table was not strictly increasing (or held NaN) */
 #define SS_FLAG_BAD_VALUE 0x2u      /* a 2D value-path precondition failed; fp64 path used */
 #define SS_FLAG_STAGING_TIMEOUT 0x4u /* a shared-memory staging copy did not complete in time; outputs incomplete */
@@ -109,7 +113,8 @@ ss_status ss_search_1d(const double* X, int32_t n, const double* Y, int64_t m,
  * F (device) [nr*nt] float64 row-major values; Y2 (device) [2m] interleaved
  * (rho, T) pairs; lowbounds2 (device) [2m] int32 output, interleaved
  * (i_rho, i_T); values (device) [m] float64 output.  algo applies to both
- * axis searches. */
+ * axis searches.  Each axis holds 2 .. SS_MAX_AXIS_2D entries
+ * (SS_EUNSUPPORTED above). */
 ss_status ss_search_interp_2d(const double* R, int32_t nr, const double* T, int32_t nt,
                               const double* F, const double* Y2, int64_t m,
                               int32_t* lowbounds2, double* values, int32_t algo,

@@ -140,6 +140,8 @@ extern "C" ss_status ss_search_interp_2d_host(const double* R, int32_t nr, const
   if (R == nullptr || T == nullptr || F == nullptr || (m > 0 && (Y2 == nullptr || lowbounds2 == nullptr || values == nullptr)))
     return fail(SS_EINVAL, "ss_search_interp_2d_host: null pointer");
   if (nr < 2 || nt < 2 || m < 0) return fail(SS_EINVAL, "ss_search_interp_2d_host: need axes >= 2 and m >= 0");
+  if (nr > SS_MAX_AXIS_2D || nt > SS_MAX_AXIS_2D)
+    return fail(SS_EUNSUPPORTED, "ss_search_interp_2d_host: axis longer than SS_MAX_AXIS_2D");
   if (m == 0) return SS_OK;
   std::lock_guard<std::mutex> lock(g_mu);
   const size_t tr = up256((size_t)nr * 8), tt = up256((size_t)nt * 8), tf = up256((size_t)nr * nt * 8);

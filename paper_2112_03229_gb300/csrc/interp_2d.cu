@@ -29,7 +29,7 @@
 
 namespace ss {
 
-constexpr int kMaxAxis2D = 4096;   // largest axis staged whole with its per-cell data
+constexpr int kMaxAxis2D = SS_MAX_AXIS_2D;   // largest axis staged whole with its per-cell data
 
 struct Axis2D {                    // shared-memory offsets of one axis
   Layout1D lay;

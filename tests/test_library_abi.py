@@ -74,6 +74,10 @@ def test_argument_errors_without_gpu(built):
         else:
             st = L.ss_plan_create_2d(ctypes.byref(h), 1, off, p, off, p, off, p, ctypes.byref(o), None)
         assert st == 1 and msg in L.ss_last_error(), (kw, L.ss_last_error())
+    # host-array 2D lookup: axes above SS_MAX_AXIS_2D (4096) are refused before any allocation
+    H = ss._host_lib()                   # declares the host-array signatures
+    assert H.ss_search_interp_2d_host(p, 4097, p, 4, p, p, 1, p, p, 0) == 6
+    assert b"SS_MAX_AXIS_2D" in L.ss_last_error()
     o = ss.plan_opts()
     o.extrap = 2
     assert L.ss_plan_create_2d(ctypes.byref(h), 1, off, p, off, p, off, p, ctypes.byref(o), None) == 1
