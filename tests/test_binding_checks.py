@@ -1,7 +1,8 @@
 """CPU checks of the Python binding's argument marshalling: offsets that the
 library would read past, outputs too small for what the library writes,
 and status records that are not device memory are refused with a Python
-error before any call reaches the library or a kernel."""
+error before any call reaches the library or a kernel; without the built
+library every call raises (there is no CPU fallback)."""
 import numpy as np
 import pytest
 import torch
@@ -83,3 +84,13 @@ def test_status_record_must_be_device_memory():
     with pytest.raises(TypeError, match="stat"):
         ss._statp(torch.zeros(24, dtype=torch.uint8))
     assert ss._statp(None) is None
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no CPU fallback: without the built library every call raises
+    monkeypatch.setattr(ss, "_lib", None)
+    monkeypatch.setattr(ss, "LIB_PATH", str(tmp_path / "libsimdsearch.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        ss.lib()
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        ss.search_1d_host(torch.zeros(4, dtype=torch.float64), torch.zeros(3, dtype=torch.float64))
