@@ -322,12 +322,15 @@ ss_status ss_search_interp_2d_batched(int32_t ntables, const int64_t* R_off, con
  * call reuses that array and clears what must start at zero, so calls are
  * ordered on the GPU: each call's work waits for the previous call's (on
  * any stream, from any host thread), and calls from different streams run
- * one after another.  A stream being captured into a graph cannot wait on
- * the previous call: calls captured into graphs must be ordered by the
- * caller.  The first call on each device looks up the array's device
- * address and creates its event; make that first call before any stream
- * capture.  A table that is not
- * strictly increasing sets SS_FLAG_NOT_SORTED in *stat. */
+ * one after another.  The metadata of a call is copied from pageable host
+ * memory, so a call on a stream that is being captured is refused with
+ * SS_EUNSUPPORTED before anything is queued (the capture stays valid).  The
+ * first call on each device looks up the array's device address and creates
+ * its event.  Bad offsets (negative, decreasing, a table of fewer than 2 or
+ * more than 2^30 entries) are refused with SS_EINVAL naming the table.  A
+ * table that is not strictly increasing sets SS_FLAG_NOT_SORTED in *stat;
+ * its indices are then unspecified but stay in [0, n-1], and the other
+ * tables' indices are unaffected. */
 ss_status ss_search_1d_batched_static(int32_t ntables, const int64_t* X_off, const double* X,
                                       const int64_t* Y_off, const double* Y, int32_t* lowbounds,
                                       int32_t side, ss_devstat* stat, cudaStream_t stream);

@@ -1,8 +1,11 @@
 // capi.cu -- host-side plumbing of the C ABI: per-thread error messages,
 // device properties, the polling status read-back.
 #include <chrono>
+#include <map>
+#include <mutex>
 #include <string>
 #include <thread>
+#include <utility>
 
 #include "ss_common.cuh"
 
@@ -32,6 +35,24 @@ int max_smem_optin() {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   return v > 0 ? v : 48 * 1024;
+}
+
+// The dynamic shared-memory limit of a kernel is a process-wide attribute.
+// Lowering it while another host thread holds a launch (or a captured graph)
+// sized for a larger limit would make that launch fail, so the limit is only
+// ever raised: per device and kernel, the largest size asked for so far.
+ss_status raise_smem_limit(const void* kernel, int smem) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> set;
+  int dev = 0;
+  SS_CHECK_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  int& cur = set[std::make_pair(dev, kernel)];
+  if (smem > cur) {
+    SS_CHECK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    cur = smem;
+  }
+  return SS_OK;
 }
 
 }  // namespace ss

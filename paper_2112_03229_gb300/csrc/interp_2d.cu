@@ -371,7 +371,7 @@ ss_status search_interp_2d(const double* R, int32_t nr, const double* T, int32_t
   const int threads = sg ? kSgThreads : kNumThreads;
   const int smem_all = sg ? a.grid_smem + (int)gbytes : smem;
   const void* k = sg ? reinterpret_cast<const void*>(&k_search_interp_2d_sg) : reinterpret_cast<const void*>(&k_search_interp_2d);
-  SS_CHECK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_all));
+  if (ss_status st_ = raise_smem_limit(k, smem_all)) return st_;
   int per_sm = 0;
   SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem_all));
   if (per_sm < 1) return fail(SS_EUNSUPPORTED, "ss_search_interp_2d: kernel does not fit on an SM");

@@ -320,7 +320,7 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
   for (int a : p->algo) family = std::max(family, a == BL_MLP ? 2 : (a == BL_SPLINE || a == BL_LOGHASH) ? 1 : 0);
   if (p->kind == 1) kern = batched_1d_kernel(p->opts.side == SS_SIDE_LE, family);
   else kern = batched_2d_kernel(p->opts.model == SS_MODEL_HUNT, family > 0);
-  SS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  if (ss_status st_ = raise_smem_limit(kern, smem)) return st_;
   int per_sm = 0;
   int threads = kNumThreads;
   SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -346,7 +346,7 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
   int resident_w = 0;
   if (any_wide) {
     kern_w = batched_1d_wide_kernel(p->opts.side == SS_SIDE_LE);
-    SS_CHECK_CUDA(cudaFuncSetAttribute(kern_w, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_w));
+    if (ss_status st_ = raise_smem_limit(kern_w, smem_w)) return st_;
     int per_sm_w = 0;
     SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_w, kern_w, kWideThreads, smem_w));
     if (per_sm_w < 1) return fail(SS_EUNSUPPORTED, "plan: wide kernel does not fit on an SM");
@@ -465,7 +465,10 @@ static bool read_cache(ss_plan* p, const std::string& dev) {
   std::snprintf(want, sizeof(want), "\"device\": \"%s\", \"kind\": %d, \"model\": %d, \"side\": %d", dev.c_str(),
                 p->kind, p->opts.model, p->opts.side);
   if (s.find(want) == std::string::npos) return false;
-  int found = 0;
+  // the choices are taken only if the cache covers every size bucket that
+  // this plan's tables fall in; otherwise the plan is tuned afresh
+  int algo[kNumBuckets], seen[kNumBuckets] = {0};
+  float mults[kNumBuckets];
   size_t pos = 0;
   while ((pos = s.find("{\"bucket\": ", pos)) != std::string::npos) {
     int b = -1;
@@ -474,13 +477,20 @@ static bool read_cache(ss_plan* p, const std::string& dev) {
     if (std::sscanf(s.c_str() + pos, "{\"bucket\": %d, \"algo\": \"%31[^\"]\", \"tile_multiple\": %f}", &b, name,
                     &mult) == 3 &&
         b >= 0 && b < kNumBuckets && algo_from_name(name) >= 0 && mult > 0.0f) {
-      p->bucket_algo[b] = algo_from_name(name);
-      p->bucket_mult[b] = mult;
-      ++found;
+      algo[b] = algo_from_name(name);
+      mults[b] = mult;
+      seen[b] = 1;
     }
     pos += 10;
   }
-  return found > 0;
+  for (int b = 0; b < kNumBuckets; ++b)
+    if (p->bucket_tables[b] > 0 && !seen[b]) return false;
+  for (int b = 0; b < kNumBuckets; ++b)
+    if (seen[b]) {
+      p->bucket_algo[b] = algo[b];
+      p->bucket_mult[b] = mults[b];
+    }
+  return true;
 }
 
 // Written to a private file and renamed over the cache, so that processes
@@ -568,8 +578,11 @@ ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
     for (int r = 0; r <= nr; ++r) yoff_r[r] = r * kPerRep;
     std::vector<int> blob_of_rep(nr);
     for (int r = 0; r < nr; ++r) blob_of_rep[r] = p->kind == 1 ? reps[r] : 2 * reps[r];
-    cudaMemcpy(d_tab, blob_of_rep.data(), nr * sizeof(int), cudaMemcpyHostToDevice);
-    cudaMemcpy(d_yoff, yoff_r.data(), (nr + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (cudaMemcpy(d_tab, blob_of_rep.data(), nr * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_yoff, yoff_r.data(), (nr + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+      st = fail(SS_ECUDA, "autotune: copy of the representative tables");
+      break;
+    }
     if (p->kind == 1) {
       k_synth_1d<<<nr, 256, 0, stream>>>(p->d_blobs, p->d_blob_off, d_tab, d_yoff, d_Y, p->opts.seed ^ 0x7E57ull);
     } else {
@@ -578,16 +591,27 @@ ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
       for (int r = 0; r < nr; ++r) tab_t[r] = 2 * reps[r] + 1;
       int* d_tab_t = nullptr;
       double* d_tmp = nullptr;
-      cudaMalloc(&d_tab_t, nr * sizeof(int));
-      cudaMalloc(&d_tmp, kTuneTargets * 8);
-      cudaMemcpy(d_tab_t, tab_t.data(), nr * sizeof(int), cudaMemcpyHostToDevice);
-      k_synth_1d<<<nr, 256, 0, stream>>>(p->d_blobs, p->d_blob_off, d_tab, d_yoff, d_tmp, p->opts.seed ^ 0x7E57ull);
-      cudaMemcpy2DAsync(d_Y, 16, d_tmp, 8, 8, nr * kPerRep, cudaMemcpyDeviceToDevice, stream);
-      k_synth_1d<<<nr, 256, 0, stream>>>(p->d_blobs, p->d_blob_off, d_tab_t, d_yoff, d_tmp, p->opts.seed ^ 0x7E58ull);
-      cudaMemcpy2DAsync(d_Y + 1, 16, d_tmp, 8, 8, nr * kPerRep, cudaMemcpyDeviceToDevice, stream);
-      cudaStreamSynchronize(stream);
-      cudaFree(d_tab_t);
-      cudaFree(d_tmp);
+      cudaError_t e = cudaMalloc(&d_tab_t, nr * sizeof(int));
+      if (e == cudaSuccess) e = cudaMalloc(&d_tmp, kTuneTargets * 8);
+      if (e == cudaSuccess) e = cudaMemcpy(d_tab_t, tab_t.data(), nr * sizeof(int), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) {
+        k_synth_1d<<<nr, 256, 0, stream>>>(p->d_blobs, p->d_blob_off, d_tab, d_yoff, d_tmp, p->opts.seed ^ 0x7E57ull);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = cudaMemcpy2DAsync(d_Y, 16, d_tmp, 8, 8, nr * kPerRep, cudaMemcpyDeviceToDevice, stream);
+      if (e == cudaSuccess) {
+        k_synth_1d<<<nr, 256, 0, stream>>>(p->d_blobs, p->d_blob_off, d_tab_t, d_yoff, d_tmp, p->opts.seed ^ 0x7E58ull);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = cudaMemcpy2DAsync(d_Y + 1, 16, d_tmp, 8, 8, nr * kPerRep, cudaMemcpyDeviceToDevice, stream);
+      const cudaError_t es = cudaStreamSynchronize(stream);   // the copies read d_tmp: drain before freeing it
+      if (e == cudaSuccess) e = es;
+      free_dev(d_tab_t);
+      free_dev(d_tmp);
+      if (e != cudaSuccess) {
+        st = cuda_fail(e, "autotune: synthetic target pairs");
+        break;
+      }
     }
     if (cudaGetLastError() != cudaSuccess) { st = fail(SS_ECUDA, "autotune: synthetic targets"); break; }
     // batch offsets over all tables: only the representatives have targets

@@ -260,7 +260,7 @@ static ss_status launch(const void* kernel, const Layout1D& lay, int64_t work_it
                         const char* name, Args1D a, const int* extra = nullptr) {
   const int smem = lay.bytes;
   if (smem > max_smem_optin()) return fail(SS_EUNSUPPORTED, std::string(name) + ": table too large for shared memory");
-  SS_CHECK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  if (ss_status st_ = raise_smem_limit(kernel, smem)) return st_;
   int per_sm = 0;
   SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kNumThreads, smem));
   if (per_sm < 1) return fail(SS_EUNSUPPORTED, std::string(name) + ": kernel does not fit on an SM");

@@ -59,6 +59,7 @@ ss_status fail(ss_status code, const std::string& msg);
 ss_status cuda_fail(cudaError_t err, const char* what);
 int num_sms();
 int max_smem_optin();
+ss_status raise_smem_limit(const void* kernel, int smem);   // raise-only, thread-safe
 
 #define SS_CHECK_CUDA(call)                                   \
   do {                                                        \

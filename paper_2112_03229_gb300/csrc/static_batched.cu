@@ -110,7 +110,7 @@ static ss_status queue_static(const StaticLayout& l, unsigned char* base, int32_
   SS_CHECK_CUDA(cudaGetLastError());
   if (tiles.empty()) return SS_OK;
   const void* kern = batched_1d_kernel(side == SS_SIDE_LE, 0);
-  SS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  if (ss_status st_ = raise_smem_limit(kern, smem)) return st_;
   int per_sm = 0;
   SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNumThreads, smem));
   if (per_sm < 1) return fail(SS_EUNSUPPORTED, "ss_search_1d_batched_static: kernel does not fit on an SM");
@@ -143,9 +143,17 @@ extern "C" ss_status ss_search_1d_batched_static(int32_t ntables, const int64_t*
   int64_t blobs = 0;
   int smem = 0;
   for (int k = 0; k < ntables; ++k) {
+    const std::string tab = std::string(me) + ": table " + std::to_string(k);
+    if (X_off[k] < 0) return fail(SS_EINVAL, tab + ": negative table offset X_off[k] = " + std::to_string(X_off[k]));
     const int64_t n = X_off[k + 1] - X_off[k];
-    if (n < 2 || n > (1 << 30) || X_off[k] < 0) return fail(SS_EINVAL, std::string(me) + ": every table needs >= 2 entries");
-    if (Y_off[k + 1] < Y_off[k] || Y_off[k] < 0) return fail(SS_EINVAL, std::string(me) + ": target offsets must be non-decreasing");
+    if (n < 0)
+      return fail(SS_EINVAL, tab + ": table offsets decrease (X_off[k+1] - X_off[k] = " + std::to_string(n) + ")");
+    if (n < 2) return fail(SS_EINVAL, tab + " has " + std::to_string(n) + " entries; every table needs >= 2");
+    if (n > (1 << 30)) return fail(SS_EINVAL, tab + " has " + std::to_string(n) + " entries, more than 2^30");
+    if (Y_off[k] < 0) return fail(SS_EINVAL, tab + ": negative target offset Y_off[k] = " + std::to_string(Y_off[k]));
+    if (Y_off[k + 1] < Y_off[k])
+      return fail(SS_EINVAL, tab + ": target offsets decrease (Y_off[k+1] - Y_off[k] = " +
+                                 std::to_string(Y_off[k + 1] - Y_off[k]) + ")");
     caps[k] = std::min(default_dir_cap((int)n), kStaticDirCap);
     blob_off[k] = blobs;
     blobs += (blob_geom_dev((int)n, caps[k], false).bytes + 255) & ~(int64_t)255;
@@ -163,23 +171,24 @@ extern "C" ss_status ss_search_1d_batched_static(int32_t ntables, const int64_t*
   if (tiles.size() > (size_t)0x7FFFFFFF) return fail(SS_EUNSUPPORTED, std::string(me) + ": too many tiles");
   smem = (smem + 127) & ~127;
   if (smem > max_smem_optin()) return fail(SS_EUNSUPPORTED, std::string(me) + ": a table is too large for shared memory");
+  // the metadata goes to the array by copies from pageable host memory, which
+  // a stream being captured into a graph cannot take: such a call is refused
+  // before anything is queued (the checks above are host-only), so the caller's capture stays valid
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  SS_CHECK_CUDA(cudaStreamIsCapturing(stream, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(SS_EUNSUPPORTED, std::string(me) + ": the stream is capturing; this entry point copies its "
+                                               "metadata from pageable host memory and cannot be captured");
   StaticDevice* d = nullptr;
   if (ss_status st = static_device(&d)) return st;
   std::lock_guard<std::mutex> lock(d->mu);
-  // order this call after the previous one on the GPU (a stream being
-  // captured into a graph cannot wait on an event recorded outside it: there
-  // the caller orders the calls); the event is recorded after whatever this
-  // call queued, on its error paths too
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  SS_CHECK_CUDA(cudaStreamIsCapturing(stream, &cap));
-  const bool order = cap == cudaStreamCaptureStatusNone;
-  if (order && d->used) SS_CHECK_CUDA(cudaStreamWaitEvent(stream, d->done, 0));
+  // order this call after the previous one on the GPU; the event is
+  // recorded after whatever this call queued, on its error paths too
+  if (d->used) SS_CHECK_CUDA(cudaStreamWaitEvent(stream, d->done, 0));
   const ss_status st = queue_static(l, d->addr, ntables, X_off, X, Y, lowbounds, side, stat, blob_off, caps, algo,
                                     tiles, smem, stream);
-  if (order) {
-    const cudaError_t e = cudaEventRecord(d->done, stream);
-    if (e != cudaSuccess) return st != SS_OK ? st : cuda_fail(e, "cudaEventRecord");
-    d->used = true;
-  }
+  const cudaError_t e = cudaEventRecord(d->done, stream);
+  if (e != cudaSuccess) return st != SS_OK ? st : cuda_fail(e, "cudaEventRecord");
+  d->used = true;
   return st;
 }

@@ -478,6 +478,19 @@ def test_plan_autotune_and_cache(ss, tmp_path):
     plan2, got2, _ = run_plan_1d(ss, b, autotune=True, tune_cache=cache)
     np.testing.assert_array_equal(got2, want)
     assert {k: v[0] for k, v in plan2.choices().items()} == {k: v[0] for k, v in ch.items()}
+    # a cache that lacks one of the plan's size buckets is not taken: the plan
+    # is tuned afresh and the cache rewritten with every bucket
+    lines = text.splitlines()
+    entries = [i for i, ln in enumerate(lines) if '{"bucket": ' in ln]
+    assert len(entries) >= 2
+    partial = [ln for i, ln in enumerate(lines) if i != entries[-1]]
+    partial[entries[-2]] = partial[entries[-2]].rstrip(",")
+    open(cache, "w").write("\n".join(partial) + "\n")
+    assert open(cache).read().count('{"bucket": ') == len(entries) - 1
+    plan3, got3, _ = run_plan_1d(ss, b, autotune=True, tune_cache=cache)
+    np.testing.assert_array_equal(got3, want)
+    assert plan3.info().tuned == 1
+    assert open(cache).read().count('{"bucket": ') == len(entries)
 
 
 def test_learned_gain(ss):

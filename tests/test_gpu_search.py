@@ -225,7 +225,6 @@ def test_2d_affine_field_exact(ss):
 
 # ---------------------------------------------------------------- full sizes, sampled
 
-@pytest.mark.slow
 def option_scale(R, T, F, Y, idx, logspace):
     """Per pair, the sum of |weight x corner| terms of the blend (unclamped
     weights): the size of the numbers the value is formed from, against

@@ -84,6 +84,31 @@ def test_argument_errors_without_gpu(built):
     assert b"extrap" in L.ss_last_error() and not h.value
 
 
+def test_static_batched_offset_messages_without_gpu(built):
+    # the no-allocation batched search checks its host offsets before any
+    # CUDA call, each bad offset with its own message naming the table
+    import paper_2112_03229_gb300 as ss
+    L = ss.lib()
+    L.ss_search_1d_batched_static.restype = ctypes.c_int32
+    buf = ctypes.create_string_buffer(64)
+    p = ctypes.c_void_p(ctypes.addressof(buf))
+
+    def call(xo, yo, side=0):
+        n = len(xo) - 1
+        st = L.ss_search_1d_batched_static(ctypes.c_int32(n), (ctypes.c_int64 * len(xo))(*xo), p,
+                                           (ctypes.c_int64 * len(yo))(*yo), p, p, ctypes.c_int32(side), None, None)
+        return st, L.ss_last_error()
+
+    for xo, yo, msg in (([0, 4, 5], [0, 1, 2], b"table 1 has 1 entries"),
+                        ([-2, 4, 8], [0, 1, 2], b"negative table offset"),
+                        ([0, 4, 2], [0, 1, 2], b"table offsets decrease"),
+                        ([0, 4, 8], [-1, 1, 2], b"negative target offset"),
+                        ([0, 4, 8], [0, 3, 2], b"target offsets decrease")):
+        st, err = call(xo, yo)
+        assert st == 1 and msg in err, (xo, yo, err)
+    assert call([0, 4, 8], [0, 1, 2], side=3)[0] == 1
+
+
 def plan_file_version():
     src = open(os.path.join(ROOT, "paper_2112_03229_gb300", "csrc", "plan_io.cu")).read()
     return int(re.search(r"kVersion = (\d+);", src).group(1))
