@@ -2,23 +2,39 @@
 """Throughput benchmark of the sorted-table search on GB300.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+                [--scaling weak|strong]
 
 Prints ONE JSON line (rank 0).  A step is one pass of the hot path over one
 batch of synthetic input that is already resident in HBM; `value` is the
 whole-job throughput in Gtargets/s (a 2D (rho, T) pair counts as one
-target).  The default workload is the batched plain-vs-learned case: 10,000
+target).  The headline workload is the batched plain-vs-learned case: 10,000
 tables of 20..2000 entries, Zipf(1.1) target counts (about 1.1B targets),
 one graph launch of the persistent plan kernel per step; the timed form is
-the autotuned plain search, and the spline and MLP proposal forms are timed
-on the same batch beside it.  Inputs are larger than L2, so no flush is needed between steps.
+the autotuned plain search, and the spline, MLP and log-hash proposal forms
+and the '<=' side are timed on the same batch beside it.  Inputs are larger
+than L2, so no flush is needed between steps.
+
+After the headline, a default run (N=1) measures every other configuration
+of the suite the same way and adds one record per configuration under
+`configs`: the 64-entry table with 1M targets (L2 flushed between steps) and
+scaled to 1B targets, the 200 x 100 2D lookup over 64M pairs, the 16..65536
+table-size sweep, and the 1,000-table 2D batch in random and coherent order.
+Each record carries its own value, CUDA-event times, roofline fraction,
+end-to-end rate, the learned (and hunt) forms and the '<=' side beside the
+plain search, and a CPU baseline whose outputs are compared element by
+element with the GPU's at the same targets (the parity sample).
+
 `e2e` is the same metric with the inputs in pinned host memory and the
 outputs written back to pinned host memory inside the timed region: the
 library's kernels stream page-locked buffers over the host link themselves
 (the host-array entry points, or a plan bound to host buffers), so the
-host-to-device and device-to-host traffic of a step is in flight at once.  `--impl reference`
-times the plain CPU oracle on host cores on a bounded sample of the same
-workload (the oracle is test infrastructure; this arm is its only use here
-besides `cpu_baseline`).
+host-to-device and device-to-host traffic of a step is in flight at once.
+`--impl reference` times the plain CPU oracle on host cores on a bounded
+sample of the same workload (the oracle is test infrastructure; this arm and
+`cpu_baseline` are its only uses here).  `--scaling strong` splits one
+workload over the ranks (tables by longest processing time on their target
+counts, or contiguous slices of one table's targets) instead of giving every
+rank its own.
 """
 from __future__ import annotations
 
@@ -121,10 +137,11 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, lo=0, hi=None):
+        """Median and max SM clock and the throttle reasons seen in samples lo..hi."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[lo:hi]:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -143,8 +160,14 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# The CPU oracle, timed as it stands (cpu_baseline and the reference arm)
+# The CPU oracle, timed as it stands (cpu_baseline and the reference arm).
+# The outputs of the single-thread run are also compared, element by element,
+# with the GPU's outputs at the same positions (taken right after the timed
+# region): a sampled parity check of every benchmarked configuration.
 # ---------------------------------------------------------------------------
+REL_TOL = 1e-12                 # interpolated values against the fp64 oracle
+
+
 def _batched_tables(Y_off, lo, hi):
     """Tables t0..t1-1 whose target ranges meet [lo, hi), and their offsets clipped to it."""
     t0 = max(int(np.searchsorted(Y_off, lo, side="right")) - 1, 0)
@@ -153,27 +176,53 @@ def _batched_tables(Y_off, lo, hi):
 
 
 def _oracle_call(kind, a, lo, hi):
-    """One oracle call on units [lo, hi) of a sample (targets, or pairs for 2D)."""
+    """One oracle call on units [lo, hi) of a sample (targets, or pairs for 2D);
+    returns the oracle's indices (and values for 2D)."""
     import oracle
+    side = a.get("side", 0)
     if kind == "1d":
-        oracle.search_1d(a["X"], a["Y"][lo:hi])
-    elif kind == "2d":
-        oracle.search_interp_2d(a["R"], a["T"], a["F"], a["Y2"][lo:hi])
-    elif kind == "1d_batched":
+        return oracle.search_1d(a["X"], a["Y"][lo:hi], side)
+    if kind == "2d":
+        return oracle.search_interp_2d(a["R"], a["T"], a["F"], a["Y2"][lo:hi])
+    if kind == "1d_batched":
         t0, t1, yo = _batched_tables(a["Y_off"], lo, hi)
         xo = a["X_off"][t0:t1 + 1]
-        oracle.search_1d_batched(xo - xo[0], a["X"][xo[0]:xo[-1]], yo, a["Y"][lo:hi])
-    else:
-        t0, t1, yo = _batched_tables(a["Y_off"], lo, hi)
-        ro, to, fo = (a[k][t0:t1 + 1] for k in ("R_off", "T_off", "F_off"))
-        oracle.search_interp_2d_batched(ro - ro[0], a["R"][ro[0]:ro[-1]], to - to[0], a["T"][to[0]:to[-1]],
-                                        fo - fo[0], a["F"][fo[0]:fo[-1]], yo, a["Y2"][lo:hi])
+        return oracle.search_1d_batched(xo - xo[0], a["X"][xo[0]:xo[-1]], yo, a["Y"][lo:hi], side)
+    t0, t1, yo = _batched_tables(a["Y_off"], lo, hi)
+    ro, to, fo = (a[k][t0:t1 + 1] for k in ("R_off", "T_off", "F_off"))
+    return oracle.search_interp_2d_batched(ro - ro[0], a["R"][ro[0]:ro[-1]], to - to[0], a["T"][to[0]:to[-1]],
+                                           fo - fo[0], a["F"][fo[0]:fo[-1]], yo, a["Y2"][lo:hi])
 
 
 def oracle_rate_1thread(kind, a, n):
+    """(units per second, outputs) of one single-thread oracle call on units [0, n)."""
     t0 = time.perf_counter()
-    _oracle_call(kind, a, 0, n)
-    return n / max(time.perf_counter() - t0, 1e-9)
+    res = _oracle_call(kind, a, 0, n)
+    return n / max(time.perf_counter() - t0, 1e-9), res
+
+
+def sample_parity(kind, res, snap):
+    """Oracle outputs on units [0, n) against the GPU's outputs there:
+    indices bit-exact, values within REL_TOL relative."""
+    if snap is None:
+        return None
+    if kind in ("1d", "1d_batched"):
+        n = len(res)
+        bad = int(np.count_nonzero(np.asarray(snap[:n]) != res))
+        return {"units": n, "index_mismatches": bad, "ok": bad == 0}
+    idx, val = res
+    n = len(val)
+    gi, gv = np.asarray(snap[0][:n]), np.asarray(snap[1][:n])
+    bad = int(np.count_nonzero((gi != idx).any(axis=1)))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rel = np.abs(gv - val) / np.abs(val)
+    both_nan = np.isnan(gv) & np.isnan(val)
+    rel = np.where(both_nan, 0.0, rel)
+    worst = float(np.nanmax(rel)) if n else 0.0
+    if np.isnan(rel).any():
+        worst = float("inf")
+    return {"units": n, "index_mismatches": bad, "max_rel_err": worst, "rel_tol": REL_TOL,
+            "ok": bad == 0 and worst <= REL_TOL}
 
 
 class OracleTimer:
@@ -194,15 +243,16 @@ class OracleTimer:
         list(self.pool.map(lambda r: _oracle_call(kind, a, r[0], r[1]), parts))
         return n / max(time.perf_counter() - t0, 1e-9)
 
-    def baseline(self, wl_obj, budget_s, reps=3):
-        """cpu_baseline: all host cores (median of reps) on a sample of about
-        budget_s seconds of single-thread work, plus the single-thread rate."""
-        kind, a, n, desc = wl_obj.cpu_spec(budget_s)
-        one = oracle_rate_1thread(kind, a, n)
+    def baseline_on(self, kind, a, n, desc, snap, reps=3):
+        """cpu_baseline: all host cores (median of reps) on the sample, plus
+        the single-thread rate; the single-thread outputs are checked against
+        the GPU's outputs at the same units (snap)."""
+        one, res = oracle_rate_1thread(kind, a, n)
         par = statistics.median([self.parallel(kind, a, n) for _ in range(reps)])
         return {"value": par / 1e9, "unit": UNIT, "cores": self.cores, "kind": "oracle",
                 "sample": "%s, split over %d threads" % (desc, self.cores),
-                "single_thread": {"value": one / 1e9, "cores": 1}}
+                "single_thread": {"value": one / 1e9, "cores": 1},
+                "parity": sample_parity(kind, res, snap)}
 
     def close(self):
         self.pool.shutdown()
@@ -211,10 +261,17 @@ class OracleTimer:
 # ---------------------------------------------------------------------------
 # Workloads
 # ---------------------------------------------------------------------------
+SNAP_MAX = 1 << 28          # most units whose GPU outputs are copied back for the parity sample
+
+
 class Workload:
     name = ""
     kernel = ""               # dominant kernel (ncu name)
     bytes_per_target = 0      # algorithmic HBM bytes per target
+    side = 0                  # 0: largest entry < target (default), 1: <= (SS_SIDE_LE)
+    share = None              # (rank, world) under strong scaling: this rank's part of one workload
+    snap = None               # GPU outputs of the oracle sample, taken right after the timed region
+    flush = None              # buffer written between timed steps when the inputs fit in L2
 
     def setup(self, dev, seed):
         raise NotImplementedError
@@ -224,6 +281,16 @@ class Workload:
 
     def targets(self):
         raise NotImplementedError
+
+    def release(self):
+        """Drop every tensor and plan of this workload (the next one needs the memory)."""
+        for k in list(vars(self)):
+            if k not in ("name", "kernel", "m", "side", "share", "pairs", "coherent", "per_table", "model",
+                         "autotune", "tile", "algo", "g"):
+                setattr(self, k, None)
+        import gc
+        gc.collect()
+        torch.cuda.empty_cache()
 
 
 class Interp2D(Workload):
@@ -263,13 +330,15 @@ class Interp2D(Workload):
     def e2e_step(self):
         self.ss.search_interp_2d_host(self.hR, self.hT, self.hF, self.hY, idx=self.hI, val=self.hV)
 
-    def cpu_spec(self, budget_s):
+    def sample(self, ns):
+        """Oracle inputs for the first ns pairs (same table)."""
+        ns = int(min(ns, self.m))
         a = {"R": self.R.cpu().numpy(), "T": self.T.cpu().numpy(), "F": self.F.cpu().numpy(),
-             "Y2": self.Y2[: 1 << 18].cpu().numpy()}
-        rate = oracle_rate_1thread("2d", a, 1 << 18)
-        ns = int(min(self.m, max(1 << 18, rate * budget_s)))
-        a["Y2"] = self.Y2[:ns].cpu().numpy()
+             "Y2": self.Y2[:ns].cpu().numpy()}
         return "2d", a, ns, "first %d of the %d pairs (same tables)" % (ns, self.m)
+
+    def snapshot(self, ns):
+        return self.idx[:ns].cpu().numpy(), self.val[:ns].cpu().numpy()
 
 
 class Plain1D(Workload):
@@ -291,16 +360,26 @@ class Plain1D(Workload):
     def setup(self, dev, seed):
         from paper_2112_03229_gb300 import workloads as wl
         import paper_2112_03229_gb300 as ss
+        from paper_2112_03229_gb300 import partition
         self.ss = ss
-        self.X, self.Y = wl.plain_1d(m=self.m, seed=1 + 1000 * seed, device=dev)
-        self.out = torch.empty((self.m,), dtype=torch.int32, device=dev)
+        if self.share is None:
+            self.X, self.Y = wl.plain_1d(m=self.m, seed=1 + 1000 * seed, device=dev)
+        else:
+            # strong scaling: every rank draws the same targets and keeps its contiguous slice
+            rank, world = self.share
+            X, Y = wl.plain_1d(m=self.m, seed=1, device=dev)
+            a, b = partition.target_slice(self.m, world, rank)
+            self.X, self.Y = X, Y[a:b].clone()
+            del Y
+        self.out = torch.empty(self.Y.shape, dtype=torch.int32, device=dev)
 
-    def step(self):
-        self.ss.search_1d(self.X, self.Y, out=self.out, algo=self.algo, ballot_g=self.g)
+    def step(self, side=None):
+        self.ss.search_1d(self.X, self.Y, out=self.out, algo=self.algo, ballot_g=self.g,
+                          side=self.side if side is None else side)
         return 1
 
     def targets(self):
-        return self.m
+        return int(self.Y.numel())
 
     def e2e_setup(self):
         """Host arrays (page-locked) through ss_search_1d_host."""
@@ -313,12 +392,46 @@ class Plain1D(Workload):
     def e2e_step(self):
         self.ss.search_1d_host(self.hX, self.hY, out=self.hO, algo=self.algo)
 
-    def cpu_spec(self, budget_s):
-        a = {"X": self.X.cpu().numpy(), "Y": self.Y[: 1 << 20].cpu().numpy()}
-        rate = oracle_rate_1thread("1d", a, 1 << 20)
-        ns = int(min(self.m, max(1 << 20, rate * budget_s)))
-        a["Y"] = self.Y[:ns].cpu().numpy()
-        return "1d", a, ns, "first %d of the %d targets (same table)" % (ns, self.m)
+    def sample(self, ns):
+        ns = int(min(ns, self.targets()))
+        a = {"X": self.X.cpu().numpy(), "Y": self.Y[:ns].cpu().numpy(), "side": self.side}
+        return "1d", a, ns, "first %d of the %d targets (same table)" % (ns, self.targets())
+
+    def snapshot(self, ns):
+        return self.out[:ns].cpu().numpy()
+
+
+class Plain1DSmall(Plain1D):
+    """The 64-entry table with 1M targets as stated (the whole working set,
+    12 MB, fits in L2): a 256 MB buffer is written between timed steps so
+    that every step reads its targets from HBM."""
+    name = "plain1d-n64-1M"
+
+    def __init__(self):
+        super().__init__(m=1 << 20)
+
+    def setup(self, dev, seed):
+        super().setup(dev, seed)
+        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+
+def _per_table_sample(Y_off, ns):
+    """Per table k, the first q_k of its targets, q_k proportional to its
+    count (at least one for a table that has targets): a sample of about ns
+    units that reaches every table.  Returns (start_k, q_k) arrays."""
+    Y_off = np.asarray(Y_off, dtype=np.int64)
+    cnt = np.diff(Y_off)
+    total = int(cnt.sum())
+    if total == 0:
+        return Y_off[:-1], np.zeros_like(cnt)
+    q = np.where(cnt > 0, np.maximum(1, np.floor(cnt * (ns / total))), 0).astype(np.int64)
+    return Y_off[:-1], np.minimum(q, cnt)
+
+
+def _gather(t, starts, q):
+    """The rows [starts[k], starts[k] + q[k]) of t for every k, back to back."""
+    parts = [t[int(s):int(s) + int(c)] for s, c in zip(starts, q) if c > 0]
+    return torch.cat(parts) if parts else t[:0]
 
 
 class PlanWorkload(Workload):
@@ -337,15 +450,25 @@ class PlanWorkload(Workload):
 
     tile = 0
 
-    def make_plan(self, model):
+    def make_plan(self, model, side=None):
         import paper_2112_03229_gb300 as ss
+        side = self.side if side is None else side
         return ss.Plan.create_1d(self.b.X_off, self.b.X_dev, model=model, autotune=self.autotune, tile=self.tile,
-                                 tune_cache=os.path.join(ROOT, "_build", "tune_%s_%s.json" % (self.name, model)))
+                                 side=side, tune_cache=os.path.join(ROOT, "_build", "tune_%s_%s_%d.json"
+                                                                    % (self.name, model, side)))
 
     def setup(self, dev, seed):
         import paper_2112_03229_gb300 as ss
         self.ss = ss
-        self.b = self.generate(dev, seed)
+        if self.share is None:
+            self.b = self.generate(dev, seed)
+        else:
+            # strong scaling: every rank draws the same batch and keeps the
+            # tables that the longest-processing-time split gives it
+            rank, world = self.share
+            full = self.generate(dev, 0)
+            self.b, self.tables = share_of_batch(full, world, rank)
+            del full
         self.b.X_dev = self.b.X.to(dev)
         self.Y = self.b.Y.to(dev)
         self.out = torch.empty(self.Y.shape, dtype=torch.int32, device=dev)
@@ -377,25 +500,21 @@ class PlanWorkload(Workload):
         self.b = self.generate("cpu", 0, max_targets=max_targets)
         self.Y = self.b.Y
 
-    def compare(self, stream, steps, model):
-        """A plan with another position model (or none) on the same bound batch, timed the same way."""
-        other = self.make_plan(model)
+    def compare(self, stream, steps, model, side=None):
+        """A plan with another position model (or none, or the other side) on
+        the same bound batch, timed the same way."""
+        other = self.make_plan(model, side)
         self.bind(other)
         for _ in range(3):
             other.execute()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            other.execute()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
+        ms = time_loop(other.execute, stream, steps)[1]
         inf = other.info()
         res = {"model": model, "Gtargets_s": round(self.targets() / (ms / 1e3) / 1e9, 3),
                "ms_per_step": round(ms, 4), "choices": other.choices(), "max_window": inf.max_window,
                "mean_window": round(inf.mean_window, 2), "train_loss": inf.train_loss}
         self.bind(self.plan)
+        del other
         return res
 
     def e2e_setup(self):
@@ -412,21 +531,46 @@ class PlanWorkload(Workload):
 
     def e2e_finish(self):
         self.bind(self.plan)
+        self.hY = self.hO = None
 
-    def cpu_spec(self, budget_s):
-        X_off, Y_off = self.b.X_off.cpu().numpy(), self.b.Y_off.cpu().numpy()
-        probe = int(min(Y_off[-1], 1 << 20))
-        a = {"X_off": X_off, "X": self.b.X.cpu().numpy(), "Y_off": Y_off, "Y": self.Y[:probe].cpu().numpy()}
-        rate = oracle_rate_1thread("1d_batched", a, probe)
-        ns = int(min(Y_off[-1], max(probe, rate * budget_s)))
-        a["Y"] = self.Y[:ns].cpu().numpy()
-        ntab = int(np.searchsorted(Y_off, ns, side="left"))
-        return "1d_batched", a, ns, "first %d targets (first %d tables) of the batch" % (ns, ntab)
+    def _sel(self, ns):
+        if getattr(self, "_selection", None) is None or self._selection[0] != ns:
+            self._selection = (ns,) + _per_table_sample(self.b.Y_off.cpu().numpy(), ns)
+        return self._selection[1:]
+
+    def sample(self, ns):
+        """Oracle inputs: the first q_k targets of every table k (about ns in all)."""
+        starts, q = self._sel(ns)
+        yo = np.concatenate([[0], np.cumsum(q)]).astype(np.int64)
+        a = {"X_off": self.b.X_off.cpu().numpy(), "X": self.b.X.cpu().numpy(), "Y_off": yo,
+             "Y": _gather(self.Y, starts, q).cpu().numpy(), "side": self.side}
+        n = int(yo[-1])
+        return "1d_batched", a, n, "first %d targets of every table by its share (%d of %d targets, %d tables)" % (
+            int(q.max()) if len(q) else 0, n, self.targets(), int(np.count_nonzero(q)))
+
+    def snapshot(self, ns):
+        starts, q = self._sel(ns)
+        return _gather(self.out, starts, q).cpu().numpy()
+
+
+def share_of_batch(b, world, rank):
+    """Rank's tables of a 1D batch under the longest-processing-time split
+    (partition.lpt_tables on the target counts): (the sub-batch with rebased
+    offsets, the indices of its tables in the full batch)."""
+    from paper_2112_03229_gb300 import partition
+    from paper_2112_03229_gb300 import workloads as wl
+    X_off, Y_off = b.X_off.cpu().numpy(), b.Y_off.cpu().numpy()
+    tables = partition.lpt_tables(np.diff(Y_off), world)[rank]
+    xo = np.concatenate([[0], np.cumsum(np.diff(X_off)[tables])]).astype(np.int64)
+    yo = np.concatenate([[0], np.cumsum(np.diff(Y_off)[tables])]).astype(np.int64)
+    X = _gather(b.X, X_off[tables], np.diff(X_off)[tables])
+    Y = _gather(b.Y, Y_off[tables], np.diff(Y_off)[tables]).clone()
+    return wl.Batched1D(torch.as_tensor(xo), X.cpu(), torch.as_tensor(yo), Y, None, None), tables
 
 
 class Batched1D(PlanWorkload):
     """10,000 tables (sizes log-uniform 20..2000), Zipf(1.1) target counts on
-    [1e3, 1e6] (about 1.1B targets), learned (spline) proposals vs plain.
+    [1e3, 1e6] (about 1.1B targets), learned proposals vs plain.
     --targets scales the counts (profiling cases)."""
     name = "batched1d-10k-zipf"
     m = 0
@@ -440,7 +584,7 @@ class Batched1D(PlanWorkload):
 
 class Sweep1D(PlanWorkload):
     """Table-size sweep: clustered tables of 16, 256, 4096 and 65536 entries,
-    256M log-uniform targets per table, learned (spline) proposals vs plain."""
+    256M log-uniform targets per table, learned proposals vs plain."""
     name = "sweep1d-16-65536-256M"
     m = 0                  # --targets: total targets of a smaller case (profiling)
 
@@ -477,24 +621,19 @@ def sweep_per_table(wl_obj, stream, steps):
             for _ in range(3):
                 plan.execute()
             torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(steps):
-                plan.execute()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / steps
+            ms = time_loop(plan.execute, stream, steps)[1]
             inf = plan.info()
             row[model] = {"Gtargets_s": round(Y.numel() / (ms / 1e3) / 1e9, 2), "window": inf.max_window,
                           "algo": list(plan.choices().values())[0][0]}
+            del plan
         res[str(X.numel())] = row
-    wl_obj.plan.bind_1d(b.Y_off, wl_obj.Y, wl_obj.out)
+    wl_obj.bind(wl_obj.plan)
     return res
 
 
 class Batched2D(PlanWorkload):
     """1,000 2D tables (axes U{50..500} x U{30..300}), 1M (rho, T) pairs each
-    (1B pairs), learned (spline) proposals on both axes vs plain."""
+    (1B pairs), learned proposals on both axes and the coherent hunt vs plain."""
     name = "batched2d-1000-1B"
     kernel = "k_batched_2d"
     bytes_per_target = 16 + 8 + 8
@@ -507,7 +646,7 @@ class Batched2D(PlanWorkload):
         if coherent:
             self.name = "batched2d-1000-1B-coherent"
 
-    def make_plan(self, model):
+    def make_plan(self, model, side=None):
         import paper_2112_03229_gb300 as ss
         b = self.b
         return ss.Plan.create_2d(b.R_off, b.R_dev, b.T_off, b.T_dev, b.F_off, b.F_dev, model=model,
@@ -533,9 +672,6 @@ class Batched2D(PlanWorkload):
         torch.cuda.synchronize()
         self.setup_s = time.perf_counter() - t0
 
-    def targets(self):
-        return self.m
-
     def bind(self, plan):
         plan.bind_2d(self.b.Y_off, self.Y, self.idx, self.val)
 
@@ -554,36 +690,73 @@ class Batched2D(PlanWorkload):
         self.plan.bind_2d(self.b.Y_off, self.hY, self.hI, self.hV)
         return self.hY.numel() * 8, self.hI.numel() * 4 + self.hV.numel() * 8
 
-    def e2e_step(self):
-        self.plan.execute()
-
     def e2e_finish(self):
         self.bind(self.plan)
+        self.hY = self.hI = self.hV = None
 
-    def cpu_spec(self, budget_s):
+    def sample(self, ns):
+        """Oracle inputs: the first q_k pairs of every table k (about ns in all)."""
         b = self.b
+        starts, q = self._sel(ns)
+        yo = np.concatenate([[0], np.cumsum(q)]).astype(np.int64)
         a = {"R_off": b.R_off.cpu().numpy(), "R": b.R.cpu().numpy(), "T_off": b.T_off.cpu().numpy(),
-             "T": b.T.cpu().numpy(), "F_off": b.F_off.cpu().numpy(), "F": b.F.cpu().numpy(),
-             "Y_off": b.Y_off.cpu().numpy()}
-        total = int(a["Y_off"][-1])
-        probe = int(min(total, 1 << 18))
-        a["Y2"] = self.Y[:probe].cpu().numpy()
-        rate = oracle_rate_1thread("2d_batched", a, probe)
-        ns = int(min(total, max(probe, rate * budget_s)))
-        a["Y2"] = self.Y[:ns].cpu().numpy()
-        ntab = int(np.searchsorted(a["Y_off"], ns, side="left"))
-        return "2d_batched", a, ns, "first %d pairs (first %d tables) of the batch" % (ns, ntab)
+             "T": b.T.cpu().numpy(), "F_off": b.F_off.cpu().numpy(), "F": b.F.cpu().numpy(), "Y_off": yo,
+             "Y2": _gather(self.Y, starts, q).cpu().numpy()}
+        n = int(yo[-1])
+        return "2d_batched", a, n, "first %d pairs of every table (%d of %d pairs, %d tables)" % (
+            int(q.max()) if len(q) else 0, n, self.targets(), int(np.count_nonzero(q)))
+
+    def snapshot(self, ns):
+        starts, q = self._sel(ns)
+        return _gather(self.idx, starts, q).cpu().numpy(), _gather(self.val, starts, q).cpu().numpy()
 
 
 WORKLOADS = {
     "interp2d": Interp2D,
     "plain1d": Plain1D,
+    "plain1d-1m": Plain1DSmall,
     "batched1d": Batched1D,
     "sweep1d": Sweep1D,
     "batched2d": Batched2D,
     "batched2d-coherent": lambda: Batched2D(coherent=True),
 }
 DEFAULT_WORKLOAD = "batched1d"
+# every configuration of the benchmark suite, in the order the default run
+# measures them after the headline: (key, stated configuration)
+SUITE = (
+    ("plain1d-1m", "plain 1D search, 64-entry table, 1M targets (L2 flushed between steps)"),
+    ("plain1d", "plain 1D search, 64-entry table, scaled to 1B targets (the >= 70% roofline bar)"),
+    ("interp2d", "fused 2D search + bilinear, 200 x 100 axes, 64M pairs"),
+    ("sweep1d", "table-size sweep 16 / 256 / 4096 / 65536 entries, 256M targets each, learned vs plain"),
+    ("batched2d", "1,000 2D tables, 1B pairs, random order, learned and hunt vs plain"),
+    ("batched2d-coherent", "1,000 2D tables, 1B pairs, coherent order, learned and hunt vs plain"),
+)
+
+
+# ---------------------------------------------------------------------------
+# Timing
+# ---------------------------------------------------------------------------
+def time_loop(fn, stream, steps, flush=None):
+    """Runs fn `steps` times on `stream` with CUDA events around every call.
+    Returns (ms of the whole region, mean ms per call, calls' return values
+    summed).  With `flush`, that buffer is written before every call, outside
+    the per-call events; the region then counts the calls only."""
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    count = 0
+    t0.record(stream)
+    for i in range(steps):
+        if flush is not None:
+            flush.add_(1)
+        starts[i].record(stream)
+        count += fn() or 0
+        ends[i].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total = sum(per) if flush is not None else t0.elapsed_time(t1)
+    return total, statistics.mean(per), count
 
 
 # ---------------------------------------------------------------------------
@@ -604,13 +777,26 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def reduce_over_ranks(x, world, op="max"):
     if world == 1:
         return x
     import torch.distributed as dist
     t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return t.item()
+
+
+def max_over_ranks(x, world):
+    return reduce_over_ranks(x, world, "max")
+
+
+def sample_size(wl_obj, budget_s):
+    """Units of the oracle sample: about budget_s seconds of single-thread
+    oracle work, from the oracle's rate on a small probe sample."""
+    kind, a, n, _ = wl_obj.sample(1 << 18)
+    oracle_rate_1thread(kind, a, min(n, 1024))       # first call loads the oracle library
+    rate, _ = oracle_rate_1thread(kind, a, n)
+    return int(max(1 << 18, min(rate * budget_s, SNAP_MAX, wl_obj.targets())))
 
 
 def run_reference(args, wl_obj):
@@ -625,7 +811,7 @@ def run_reference(args, wl_obj):
         wl_obj.m = min(wl_obj.m, 1 << 23)
         wl_obj.setup("cpu", 0)
     timer = OracleTimer()
-    kind, a, n, desc = wl_obj.cpu_spec(budget_s=4.0)
+    kind, a, n, desc = wl_obj.sample(sample_size(wl_obj, 4.0))
     rates = [timer.parallel(kind, a, n) for _ in range(args.warmup + args.steps)][args.warmup:]
     timer.close()
     value = statistics.median(rates) / 1e9
@@ -672,29 +858,100 @@ def small_m_latency(args):
                       "config": {"workload": "latency-n64", "table": 64}, "latency": res}), flush=True)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["latency"])
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--targets", type=int, default=0, help="override the workload's target count (profiling cases)")
-    ap.add_argument("--model", default=None, choices=["none", "spline", "mlp", "loghash", "hunt"],
-                    help="position model of the timed plan (default none: plain search; the learned forms are "
-                         "timed beside it)")
-    ap.add_argument("--no-compare", action="store_true", help="skip the plain-plan comparison of plan workloads")
-    ap.add_argument("--tile", type=int, default=0, help="fixed targets per tile for plan workloads (0: tuned)")
-    ap.add_argument("--algo", default=None, choices=["auto", "bucket", "binary", "branchy", "ballot", "ballot8", "ballot16"],
-                    help="in-block search of the plain1d workload")
-    args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
-    if args.workload == "latency":
-        return small_m_latency(args)
-    wl_obj = WORKLOADS[args.workload]()
+def measure(wl_obj, args, stream, world, cpu_budget, e2e_steps):
+    """One configuration: W warm-up steps, K timed steps (per-step CUDA
+    events on the launching stream, barrier and synchronise on both sides,
+    max over ranks), the GPU outputs of the oracle sample copied back, then
+    the end-to-end rate through the public API with host buffers."""
+    ns = sample_size(wl_obj, cpu_budget) if cpu_budget else 0
+    for _ in range(args.warmup):
+        wl_obj.step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    total_ms, per_ms, launches = time_loop(wl_obj.step, stream, args.steps, flush=wl_obj.flush)
+    barrier(world)
+    total_ms = max_over_ranks(total_ms, world)
+    mine = wl_obj.targets()
+    units = reduce_over_ranks(float(mine), world, "sum") if wl_obj.share is not None else mine * world
+    value = units * args.steps / (total_ms / 1e3) / 1e9
+    if ns:
+        wl_obj.sample_n = ns
+        wl_obj.snap = wl_obj.snapshot(ns)
+    peak, peak_kind = hbm_peak()
+    achieved = mine * wl_obj.bytes_per_target / (per_ms / 1e3) / 1e9
+    rec = {"value": round(value, 3), "ms_per_step": round(total_ms / args.steps, 4),
+           "ms_per_launch": round(per_ms, 4), "targets_per_gpu": mine, "gpu_launches": launches,
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                        "traffic": recorded_traffic(wl_obj.kernel, wl_obj.name), "kernel": wl_obj.kernel,
+                        "algorithmic_bytes_per_target": wl_obj.bytes_per_target}}
+    if e2e_steps:
+        h2d, d2h = wl_obj.e2e_setup()
+        for _ in range(2):
+            wl_obj.e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            wl_obj.e2e_step()
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, world)
+        rec["e2e"] = {"value": round(units * e2e_steps / (e2e_ms / 1e3) / 1e9, 3), "unit": UNIT,
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+        if hasattr(wl_obj, "e2e_finish"):
+            wl_obj.e2e_finish()
+    return rec
+
+
+def frac_of(wl_obj, ms):
+    peak, _ = hbm_peak()
+    return round(wl_obj.targets() * wl_obj.bytes_per_target / (ms / 1e3) / 1e9 / peak, 4)
+
+
+def other_forms(wl_obj, stream, steps, value):
+    """Beside the timed plain search on the same inputs: the learned
+    proposals (and the hunt, for 2D plans) and the '<=' side."""
+    extra = {}
+    if isinstance(wl_obj, PlanWorkload):
+        inf = wl_obj.plan.info()
+        extra["plan"] = {"model": wl_obj.model, "setup_s": round(wl_obj.setup_s, 2), "choices": wl_obj.plan.choices(),
+                         "max_window": inf.max_window, "mean_window": round(inf.mean_window, 2),
+                         "train_loss": inf.train_loss, "ntiles": inf.ntiles}
+        if wl_obj.model == "none":
+            learned = {}
+            models = ("spline", "mlp", "loghash") + (("hunt",) if isinstance(wl_obj, Batched2D) else ())
+            for model in models:
+                r = wl_obj.compare(stream, steps, model)
+                r["frac"] = frac_of(wl_obj, r["ms_per_step"])
+                learned[model] = r
+            extra["learned"] = learned
+            extra["learned_over_plain"] = {k: round(v["Gtargets_s"] / value, 3) for k, v in learned.items()}
+        else:
+            r = wl_obj.compare(stream, steps, "none")
+            r["frac"] = frac_of(wl_obj, r["ms_per_step"])
+            extra["plain"] = r
+            extra["learned_over_plain"] = round(value / r["Gtargets_s"], 3)
+        if isinstance(wl_obj, Sweep1D):
+            extra["per_table"] = sweep_per_table(wl_obj, stream, steps)
+        if not isinstance(wl_obj, Batched2D) and wl_obj.model == "none":
+            r = wl_obj.compare(stream, steps, "none", side=1)
+            extra["side_le"] = {"Gtargets_s": r["Gtargets_s"], "ms_per_step": r["ms_per_step"],
+                                "frac": frac_of(wl_obj, r["ms_per_step"]),
+                                "le_over_lt": round(r["Gtargets_s"] / value, 3), "choices": r["choices"]}
+    elif isinstance(wl_obj, Plain1D):
+        for _ in range(3):
+            wl_obj.step(side=1)
+        torch.cuda.synchronize()
+        ms = time_loop(lambda: wl_obj.step(side=1), stream, steps, flush=wl_obj.flush)[1]
+        g = wl_obj.targets() / (ms / 1e3) / 1e9
+        extra["side_le"] = {"Gtargets_s": round(g, 3), "ms_per_step": round(ms, 4), "frac": frac_of(wl_obj, ms),
+                            "le_over_lt": round(g / value, 3)}
+    return extra
+
+
+def make_workload(key, args):
+    wl_obj = WORKLOADS[key]()
     if args.targets:
         wl_obj.m = args.targets
     if args.model is not None and isinstance(wl_obj, PlanWorkload):
@@ -703,117 +960,111 @@ def main():
         wl_obj.tile = args.tile
     if args.algo is not None and isinstance(wl_obj, Plain1D):
         wl_obj.set_algo(args.algo)
+    return wl_obj
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["latency"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="weak: every rank runs the whole workload; strong: the ranks split one workload "
+                         "(tables by longest processing time, or slices of one table's targets)")
+    ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--config-cpu-budget", type=float, default=1.5,
+                    help="seconds of oracle work for each further configuration's baseline and parity sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-suite", action="store_true", help="time the chosen workload only (no configs records)")
+    ap.add_argument("--targets", type=int, default=0, help="override the workload's target count (profiling cases)")
+    ap.add_argument("--model", default=None, choices=["none", "spline", "mlp", "loghash", "hunt"],
+                    help="position model of the timed plan (default none: plain search; the learned forms are "
+                         "timed beside it)")
+    ap.add_argument("--no-compare", action="store_true", help="skip the learned and '<=' forms beside the timed one")
+    ap.add_argument("--tile", type=int, default=0, help="fixed targets per tile for plan workloads (0: tuned)")
+    ap.add_argument("--algo", default=None, choices=["auto", "bucket", "binary", "branchy", "ballot", "ballot8", "ballot16"],
+                    help="in-block search of the plain1d workload")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.workload == "latency":
+        return small_m_latency(args)
+    wl_obj = make_workload(args.workload, args)
     if args.impl == "reference":
         return run_reference(args, wl_obj)
 
     rank, world, local = dist_setup(args.gpus)
+    if args.scaling == "strong":
+        if not isinstance(wl_obj, (Batched1D, Plain1D)):
+            raise SystemExit("--scaling strong splits the batched1d and plain1d workloads only")
+        wl_obj.share = (rank, world)
     import __graft_entry__
     __graft_entry__.build()
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
     wl_obj.setup(dev, rank)
     stream = torch.cuda.current_stream()
-    # clocks are sampled from the warm-up through the timed and end-to-end
-    # regions (nvidia-smi every 50 ms; a short timed region alone may fall
-    # between two samples)
+    # clocks are sampled from the warm-up through the last configuration
+    # (nvidia-smi every 50 ms; a short timed region alone may fall between
+    # two samples); each record carries the samples taken while it ran
     clk = ClockSampler(dev.index).__enter__()
     clk.wait_first()
-    for _ in range(args.warmup):
-        wl_obj.step()
-    torch.cuda.synchronize()
-
-    # timed region: per-launch events on the launching stream, K steps
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    launches = 0
-    barrier(world)
-    torch.cuda.synchronize()
-    t_all0 = torch.cuda.Event(enable_timing=True)
-    t_all1 = torch.cuda.Event(enable_timing=True)
-    t_all0.record(stream)
-    for i in range(args.steps):
-        starts[i].record(stream)
-        launches += wl_obj.step()
-        ends[i].record(stream)
-    t_all1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    elapsed_ms = t_all0.elapsed_time(t_all1)
-    elapsed_ms = max_over_ranks(elapsed_ms, world)
-    per_launch_ms = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
-    units = wl_obj.targets() * args.steps * world
-    value = units / (elapsed_ms / 1e3) / 1e9
-
-    # end to end through the public API with host buffers
-    h2d, d2h = wl_obj.e2e_setup()
-    for _ in range(2):
-        wl_obj.e2e_step()
-    torch.cuda.synchronize()
-    barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        wl_obj.e2e_step()
-    torch.cuda.synchronize()
-    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, world)
-    e2e_value = wl_obj.targets() * args.steps * world / (e2e_ms / 1e3) / 1e9
-    clk.__exit__(None, None, None)
-    if hasattr(wl_obj, "e2e_finish"):
-        wl_obj.e2e_finish()
-
-    peak, peak_kind = hbm_peak()
-    achieved = wl_obj.targets() * wl_obj.bytes_per_target / (per_launch_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                "traffic": recorded_traffic(wl_obj.kernel, wl_obj.name), "kernel": wl_obj.kernel,
-                "algorithmic_bytes_per_target": wl_obj.bytes_per_target}
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        timer = OracleTimer()
-        cpu = timer.baseline(wl_obj, args.cpu_budget)
-        timer.close()
-
+    solo = rank == 0 and world == 1
+    cpu_budget = args.cpu_budget if solo and not args.no_cpu_baseline else 0
+    rec = measure(wl_obj, args, stream, world, cpu_budget, args.steps)
     extra = {}
-    if isinstance(wl_obj, PlanWorkload):
-        inf = wl_obj.plan.info()
-        extra["plan"] = {"model": wl_obj.model, "setup_s": round(wl_obj.setup_s, 2), "choices": wl_obj.plan.choices(),
-                         "max_window": inf.max_window, "mean_window": round(inf.mean_window, 2),
-                         "train_loss": inf.train_loss, "ntiles": inf.ntiles}
-        if world == 1 and not args.no_compare:
-            def frac_of(r):
-                return round(wl_obj.targets() * wl_obj.bytes_per_target / (r["ms_per_step"] / 1e3) / 1e9 / peak, 4)
-            if wl_obj.model == "none":
-                # the timed form is the plain search; the learned forms on the same batch
-                learned = {}
-                models = ("spline", "mlp", "loghash") + (("hunt",) if isinstance(wl_obj, Batched2D) else ())
-                for model in models:
-                    r = wl_obj.compare(stream, args.steps, model)
-                    r["frac"] = frac_of(r)
-                    learned[model] = r
-                extra["learned"] = learned
-                extra["learned_over_plain"] = {k: round(v["Gtargets_s"] / value, 3) for k, v in learned.items()}
-            else:
-                r = wl_obj.compare(stream, args.steps, "none")
-                r["frac"] = frac_of(r)
-                extra["plain"] = r
-                extra["learned_over_plain"] = round(value / r["Gtargets_s"], 3)
-        if isinstance(wl_obj, Sweep1D) and world == 1 and not args.no_compare:
-            extra["per_table"] = sweep_per_table(wl_obj, stream, args.steps)
+    if world == 1 and not args.no_compare:
+        extra = other_forms(wl_obj, stream, args.steps, rec["value"])
+    cpu = None
+    if cpu_budget:
+        timer = OracleTimer()
+        cpu = timer.baseline_on(*wl_obj.sample(wl_obj.sample_n), wl_obj.snap)
+        timer.close()
+    head_clocks = clk.summary()
+    name, targets, flushed = wl_obj.name, wl_obj.targets(), wl_obj.flush is not None
+    model = getattr(wl_obj, "model", None)
+    wl_obj.release()
+
+    # the other configurations of the suite, one after another on this GPU
+    configs = {}
+    if solo and not args.no_suite and args.workload == DEFAULT_WORKLOAD and not args.targets:
+        for key, what in SUITE:
+            other = make_workload(key, args)
+            lo = len(clk.lines)
+            other.setup(dev, 0)
+            budget = args.config_cpu_budget if not args.no_cpu_baseline else 0
+            r = measure(other, args, stream, 1, budget, min(args.steps, 3))
+            r["config"] = what
+            if not args.no_compare:
+                r.update(other_forms(other, stream, args.steps, r["value"]))
+            if budget:
+                timer = OracleTimer()
+                r["cpu_baseline"] = timer.baseline_on(*other.sample(other.sample_n), other.snap, reps=1)
+                timer.close()
+            r["clocks"] = clk.summary(lo, len(clk.lines))
+            configs[other.name] = r
+            other.release()
+    clk.__exit__(None, None, None)
 
     if rank == 0:
-        line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": wl_obj.name, "targets_per_gpu": wl_obj.targets(),
-                           "l2": "inputs larger than L2 (no flush needed)", "parallelism": "dp%d" % world},
-                "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
-                "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": d2h},
-                "clocks": clk.summary()}
-        if isinstance(wl_obj, PlanWorkload):
-            line["config"]["model"] = wl_obj.model
+        line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
+                "scaling": args.scaling, "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": name, "targets_per_gpu": targets,
+                           "l2": "256 MB buffer written between timed steps" if flushed
+                           else "inputs larger than L2 (no flush needed)",
+                           "parallelism": "dp%d" % world},
+                "gpu_launches": rec["gpu_launches"], "roofline": rec["roofline"], "cpu_baseline": cpu,
+                "e2e": rec["e2e"], "clocks": head_clocks}
+        if model is not None:
+            line["config"]["model"] = model
             line["config"]["setup"] = "tables prepared once before timing (plan creation, Sec. 5.3)"
         line.update(extra)
+        if configs:
+            line["configs"] = configs
+            line["clocks_all"] = clk.summary()
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

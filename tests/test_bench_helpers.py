@@ -65,3 +65,30 @@ def test_batched_sample_slices_cover_the_range():
         # and no table whose targets lie outside is included at either end
         assert Y_off[t0 + 1] > lo or Y_off[t0 + 1] == Y_off[t0]
         assert Y_off[t1 - 1] < hi
+
+
+def test_per_table_sample_reaches_every_table():
+    b = load_bench()
+    Y_off = np.array([0, 1000, 1000, 1003, 50_000, 50_001], dtype=np.int64)
+    starts, q = b._per_table_sample(Y_off, 5000)
+    cnt = np.diff(Y_off)
+    assert (q <= cnt).all() and ((q >= 1) == (cnt >= 1)).all()
+    assert abs(int(q.sum()) - 5000) <= len(cnt)
+    np.testing.assert_array_equal(starts, Y_off[:-1])
+
+
+def test_sample_parity_counts_mismatches_and_value_errors():
+    b = load_bench()
+    r = b.sample_parity("1d", np.array([0, 1, 2], np.int32), np.array([0, 1, 2, 9], np.int32))
+    assert r["ok"] and r["units"] == 3
+    r = b.sample_parity("1d_batched", np.array([0, 1, 2], np.int32), np.array([0, 5, 2], np.int32))
+    assert not r["ok"] and r["index_mismatches"] == 1
+    idx = np.array([[0, 1], [2, 3]], np.int32)
+    val = np.array([1.0, 2.0])
+    r = b.sample_parity("2d", (idx, val), (idx.copy(), val * (1 + 1e-13)))
+    assert r["ok"] and r["max_rel_err"] <= 1e-12
+    r = b.sample_parity("2d", (idx, val), (idx.copy(), val * (1 + 1e-11)))
+    assert not r["ok"]
+    r = b.sample_parity("2d_batched", (idx, np.array([1.0, np.nan])), (idx.copy(), np.array([1.0, np.nan])))
+    assert r["ok"]
+    assert b.sample_parity("1d", np.zeros(1, np.int32), None) is None

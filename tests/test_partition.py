@@ -93,3 +93,36 @@ def test_two_rank_gloo_partition_matches_single_rank(tmp_path):
     mp.start_processes(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, start_method="spawn", join=True)
     assert bool(np.load(tmp_path / "ok.npy")[0])
     assert bool(np.load(tmp_path / "ok1.npy")[0])
+
+
+def _bench_share_main(rank, world, port, outdir):
+    # the split that `bench.py --scaling strong` gives each rank of the
+    # batched workload: every table on exactly one rank, its data intact
+    import importlib.util
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    b = wl.batched_1d(ntables=57, count_scale=0.002, seed=12)
+    sub, tables = bench.share_of_batch(b, world, rank)
+    X_off, Y_off = b.X_off.numpy(), b.Y_off.numpy()
+    ok = len(sub.X_off) == len(tables) + 1 and len(sub.Y_off) == len(tables) + 1
+    for i, k in enumerate(tables):
+        xs, ys = sub.X[sub.X_off[i]:sub.X_off[i + 1]], sub.Y[sub.Y_off[i]:sub.Y_off[i + 1]]
+        ok &= torch.equal(xs, b.X[X_off[k]:X_off[k + 1]]) and torch.equal(ys, b.Y[Y_off[k]:Y_off[k + 1]])
+    got = [None] * world
+    dist.all_gather_object(got, (list(map(int, tables)), bool(ok), int(sub.Y_off[-1])))
+    if rank == 0:
+        every = sorted(k for t, _, _ in got for k in t)
+        total = sum(n for _, _, n in got)
+        np.save(os.path.join(outdir, "share.npy"),
+                np.array([every == list(range(57)), all(o for _, o, _ in got), total == int(Y_off[-1])]))
+    dist.destroy_process_group()
+
+
+def test_two_rank_gloo_bench_strong_split_covers_every_table_once(tmp_path):
+    port = _free_port()
+    mp.start_processes(_bench_share_main, args=(2, port, str(tmp_path)), nprocs=2, start_method="spawn", join=True)
+    assert np.load(tmp_path / "share.npy").all()
