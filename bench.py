@@ -7,9 +7,10 @@ python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ou
 Prints ONE JSON line (rank 0).  A step is one pass of the hot path over one
 batch of synthetic input that is already resident in HBM; `value` is the
 whole-job throughput in Gtargets/s (a 2D (rho, T) pair counts as one
-target).  The headline workload is the batched plain-vs-learned case: 10,000
-tables of 20..2000 entries, Zipf(1.1) target counts (about 1.1B targets),
-one graph launch of the persistent plan kernel per step; the timed form is
+target).  The headline workload is the batched plain-vs-learned case: two
+independent batches of 10,000 tables of 20..2000 entries with Zipf(1.1)
+target counts (about 2.2B targets in all), one graph launch of the
+persistent plan kernel per step; the timed form is
 the autotuned plain search, and the spline, MLP and log-hash proposal forms
 and the '<=' side are timed on the same batch beside it.  Inputs are larger
 than L2, so no flush is needed between steps.
@@ -441,6 +442,7 @@ class PlanWorkload(Workload):
     kernel = "k_batched_1d"
     bytes_per_target = 8 + 4
     model = "none"
+    compare_models = ("spline", "mlp", "loghash")     # timed beside the plain search
 
     def __init__(self, model=None, autotune=True):
         if model is not None:
@@ -569,17 +571,22 @@ def share_of_batch(b, world, rank):
 
 
 class Batched1D(PlanWorkload):
-    """10,000 tables (sizes log-uniform 20..2000), Zipf(1.1) target counts on
-    [1e3, 1e6] (about 1.1B targets), learned proposals vs plain.
-    --targets scales the counts (profiling cases)."""
-    name = "batched1d-10k-zipf"
+    """Two independent batches of 10,000 tables each (sizes log-uniform
+    20..2000, Zipf(1.1) target counts on [1e3, 1e6]): a 10,000-table batch
+    holds about 1.1B targets, so the second brings the total to the stated
+    "about 2B" (2.2B) without distorting the count law; one persistent graph
+    launch over all 20,000 tables, learned proposals vs plain.  --targets
+    scales the counts (profiling cases)."""
+    name = "batched1d-10k-zipf-x2"
     m = 0
 
     def generate(self, dev, seed, max_targets=None):
         from paper_2112_03229_gb300 import workloads as wl
-        scale = self.m / 1.1e9 if self.m else 1.0
-        return wl.batched_1d(ntables=10_000, seed=5 + 1000 * seed, count_scale=scale, device=dev,
-                             max_targets=max_targets)
+        scale = self.m / 2.2e9 if self.m else 1.0
+        if max_targets is not None:      # a prefix of the batch: the first tables only
+            return wl.batched_1d(ntables=10_000, seed=5 + 1000 * seed, count_scale=scale, device=dev,
+                                 max_targets=max_targets)
+        return wl.batched_1d_x2(seed=5 + 1000 * seed, count_scale=scale, device=dev)
 
 
 class Sweep1D(PlanWorkload):
@@ -604,6 +611,54 @@ class Sweep1D(PlanWorkload):
         return wl.Batched1D(X_off, X, Y_off, torch.cat(Ys), None, None)
 
 
+class Coherent1D(Sweep1D):
+    """Hunt and locate's regime (Sec. 2.1, 5.5): jittered log-spaced tables of
+    64, 4096, 65536 and 1M entries (the last searched in global memory), 64M
+    coherent targets per table (a random walk in log space, N(0, 0.01
+    decade) steps); plain search vs the hunt and the learned proposals."""
+    name = "coherent1d-64-1M-64M"
+    table_models = ("none", "hunt", "spline", "loghash")
+    compare_models = ("hunt", "spline", "loghash")
+    sizes = (64, 4096, 65536, 1 << 20)
+
+    def __init__(self, per_table=64 << 20, **kw):
+        super().__init__(per_table=per_table, **kw)
+
+    def generate(self, dev, seed, max_targets=None):
+        from paper_2112_03229_gb300 import workloads as wl
+        tabs = [wl.log_spaced_table(n, 1e-6, 1e4, 0.1, seed=8 + n + 1000 * seed) for n in self.sizes]
+        per = (self.m // 4 if self.m else self.per_table) if max_targets is None else max(1, max_targets // 4)
+        Ys = [wl.walk_1d(per, 0.5e-6, 2e4, seed=9 + i + 1000 * seed, device=dev) for i in range(len(tabs))]
+        X = torch.cat(tabs)
+        X_off = torch.tensor(np.concatenate([[0], np.cumsum([len(t) for t in tabs])]))
+        Y_off = torch.tensor(np.concatenate([[0], np.cumsum([len(y) for y in Ys])]))
+        return wl.Batched1D(X_off, X, Y_off, torch.cat(Ys), None, None)
+
+
+class Large1D(Sweep1D):
+    """Tables too large for shared memory in any layout (262,144, 1M and 4M
+    entries, jittered log spacing): the plain search finishes in the full
+    keys in global memory with dependent loads, where a position proposal
+    with a small window needs one; 64M log-uniform targets per table."""
+    name = "large1d-256K-4M-64M"
+    sizes = (1 << 18, 1 << 20, 1 << 22)
+    table_models = ("none", "spline", "mlp", "loghash")
+
+    def __init__(self, per_table=64 << 20, **kw):
+        super().__init__(per_table=per_table, **kw)
+
+    def generate(self, dev, seed, max_targets=None):
+        from paper_2112_03229_gb300 import workloads as wl
+        tabs = [wl.log_spaced_table(n, 1e-6, 1e4, 0.1, seed=10 + n + 1000 * seed) for n in self.sizes]
+        per = (self.m // len(tabs) if self.m else self.per_table) if max_targets is None else \
+            max(1, max_targets // len(tabs))
+        Ys = [wl.log_uniform(per, 0.5e-6, 2e4, seed=11 + i + 1000 * seed, device=dev) for i in range(len(tabs))]
+        X = torch.cat(tabs)
+        X_off = torch.tensor(np.concatenate([[0], np.cumsum([len(t) for t in tabs])]))
+        Y_off = torch.tensor(np.concatenate([[0], np.cumsum([len(y) for y in Ys])]))
+        return wl.Batched1D(X_off, X, Y_off, torch.cat(Ys), None, None)
+
+
 def sweep_per_table(wl_obj, stream, steps):
     """Per-table Gtargets/s of the sweep: one plan per table and model."""
     import paper_2112_03229_gb300 as ss
@@ -615,8 +670,8 @@ def sweep_per_table(wl_obj, stream, steps):
         Y = wl_obj.Y[Y_off[k]:Y_off[k + 1]]
         out = wl_obj.out[Y_off[k]:Y_off[k + 1]]
         row = {}
-        for model in ("none", "spline", "mlp", "loghash"):
-            plan = ss.Plan.create_1d([0, X.numel()], X, model=model, autotune=(model == "none"))
+        for model in getattr(wl_obj, "table_models", ("none", "spline", "mlp", "loghash")):
+            plan = ss.Plan.create_1d([0, X.numel()], X, model=model, autotune=(model in ("none", "hunt")))
             plan.bind_1d([0, Y.numel()], Y, out)
             for _ in range(3):
                 plan.execute()
@@ -636,6 +691,7 @@ class Batched2D(PlanWorkload):
     (1B pairs), learned proposals on both axes and the coherent hunt vs plain."""
     name = "batched2d-1000-1B"
     kernel = "k_batched_2d"
+    compare_models = ("spline", "mlp", "loghash", "hunt")
     bytes_per_target = 16 + 8 + 8
     m = 0                  # --targets: total pairs of a smaller case (profiling)
 
@@ -719,6 +775,8 @@ WORKLOADS = {
     "sweep1d": Sweep1D,
     "batched2d": Batched2D,
     "batched2d-coherent": lambda: Batched2D(coherent=True),
+    "coherent1d": Coherent1D,
+    "large1d": Large1D,
 }
 DEFAULT_WORKLOAD = "batched1d"
 # every configuration of the benchmark suite, in the order the default run
@@ -730,6 +788,8 @@ SUITE = (
     ("sweep1d", "table-size sweep 16 / 256 / 4096 / 65536 entries, 256M targets each, learned vs plain"),
     ("batched2d", "1,000 2D tables, 1B pairs, random order, learned and hunt vs plain"),
     ("batched2d-coherent", "1,000 2D tables, 1B pairs, coherent order, learned and hunt vs plain"),
+    ("coherent1d", "hunt and locate's regime: 64 .. 1M-entry tables, 64M coherent targets each, hunt vs plain"),
+    ("large1d", "tables searched in global memory (256K .. 4M entries), 64M targets each, learned vs plain"),
 )
 
 
@@ -897,11 +957,53 @@ def measure(wl_obj, args, stream, world, cpu_budget, e2e_steps):
             wl_obj.e2e_step()
         torch.cuda.synchronize()
         e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, world)
-        rec["e2e"] = {"value": round(units * e2e_steps / (e2e_ms / 1e3) / 1e9, 3), "unit": UNIT,
+        e2e_value = units * e2e_steps / (e2e_ms / 1e3) / 1e9
+        rec["e2e"] = {"value": round(e2e_value, 3), "unit": UNIT,
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+        if world == 1:
+            # the same algorithmic bytes cross the host link: in and out in flight together
+            link = host_link_peak(torch.device("cuda", torch.cuda.current_device()))
+            moved = e2e_value * 1e9 * (h2d + d2h) / max(mine, 1) / 1e9
+            rec["e2e"]["roofline"] = {"bound": "host link", "achieved": round(moved, 1), "peak": link["both"],
+                                      "unit": "GB/s", "frac": round(moved / link["both"], 4),
+                                      "peak_source": "page-locked copies measured in this run (both directions "
+                                                     "at once, best of 3)", "copies_GBs": dict(link)}
         if hasattr(wl_obj, "e2e_finish"):
             wl_obj.e2e_finish()
     return rec
+
+
+_LINK = {}
+
+
+def host_link_peak(dev, nbytes=1 << 30, reps=3):
+    """Host link copy rates (GB/s) measured here: page-locked host to device,
+    device to host, and both at once on two streams (what an end-to-end step
+    does: targets in and answers out in flight together); best of reps."""
+    if _LINK:
+        return _LINK
+    h_in = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h_out = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d_in = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d_out = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    best = {"h2d": 0.0, "d2h": 0.0, "both": 0.0}
+    for _ in range(reps):
+        for kind in ("h2d", "d2h", "both"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if kind in ("h2d", "both"):
+                with torch.cuda.stream(s1):
+                    d_in.copy_(h_in, non_blocking=True)
+            if kind in ("d2h", "both"):
+                with torch.cuda.stream(s2):
+                    h_out.copy_(d_out, non_blocking=True)
+            torch.cuda.synchronize()
+            moved = nbytes * (2 if kind == "both" else 1)
+            best[kind] = max(best[kind], moved / (time.perf_counter() - t0) / 1e9)
+    _LINK.update({k: round(v, 1) for k, v in best.items()})
+    del h_in, h_out, d_in, d_out
+    return _LINK
 
 
 def frac_of(wl_obj, ms):
@@ -920,7 +1022,7 @@ def other_forms(wl_obj, stream, steps, value):
                          "train_loss": inf.train_loss, "ntiles": inf.ntiles}
         if wl_obj.model == "none":
             learned = {}
-            models = ("spline", "mlp", "loghash") + (("hunt",) if isinstance(wl_obj, Batched2D) else ())
+            models = wl_obj.compare_models
             for model in models:
                 r = wl_obj.compare(stream, steps, model)
                 r["frac"] = frac_of(wl_obj, r["ms_per_step"])

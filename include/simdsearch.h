@@ -182,8 +182,10 @@ typedef enum ss_model {
   SS_MODEL_SPLINE = 1,  /* piecewise-linear map of the target's key, knots = bucket directory */
   SS_MODEL_MLP = 2,     /* 2-16-1 fp32 MLP on the target's exponent and mantissa, trained on the GPU */
   SS_MODEL_LOGHASH = 3, /* no training: the logarithm hash of Sec. 3.4 (Eqs. 1-2), base fitted to the end points */
-  SS_MODEL_HUNT = 4     /* 2D plans only: the second of each thread's two consecutive pairs starts from the first
-                           pair's indices (a hunt over coherent sequences, Sec. 2.2), window of one entry */
+  SS_MODEL_HUNT = 4     /* hunt and locate (Sec. 2.1) for coherent sequences (Sec. 5.5), 1D and 2D plans: the
+                           first of a thread's consecutive targets (2D: pairs) takes the table's own search, the
+                           others start from its answer, probe away in doubling steps and bisect the last step;
+                           exact for any order.  1D hunt plans use the bucket search (algo auto or bucket) */
 } ss_model;
 
 typedef struct ss_plan_opts {

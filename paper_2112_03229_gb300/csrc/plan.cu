@@ -140,8 +140,11 @@ ss_status ss::check_plan_opts(const ss_plan_opts& o, int kind) {
   if (!(o.mlp_lr >= 0.0f && o.mlp_lr < 1e30f)) return fail(SS_EINVAL, "plan: mlp_lr must be finite and >= 0");
   if (kind == 1) {
     if (o.side != SS_SIDE_LT && o.side != SS_SIDE_LE) return fail(SS_EINVAL, "plan: bad side");
-    if (o.model < SS_MODEL_NONE || o.model > SS_MODEL_LOGHASH)
-      return fail(SS_EINVAL, o.model == SS_MODEL_HUNT ? "plan: the hunt applies to 2D plans only" : "plan: bad model");
+    if (o.model < SS_MODEL_NONE || o.model > SS_MODEL_HUNT) return fail(SS_EINVAL, "plan: bad model");
+    // the hunt reads the staged keys, which a 1D table staged for the
+    // breadth-first binary search or the ballot search does not carry
+    if (o.model == SS_MODEL_HUNT && o.algo != SS_ALGO_AUTO && o.algo != SS_ALGO_BUCKET)
+      return fail(SS_EINVAL, "plan: a 1D hunt plan starts its runs with the bucket search (algo auto or bucket)");
     if (o.algo < SS_ALGO_AUTO || o.algo > SS_ALGO_BALLOT)
       return fail(SS_EINVAL, "plan: algo must be auto, binary, bucket or ballot");
     return SS_OK;

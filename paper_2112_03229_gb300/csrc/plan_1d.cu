@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(256) k_window(WindowArgs a) {
 // plain searches only, plus the spline and the logarithm hash, plus the MLP.  A plan launches the
 // smallest family that covers its tables, which keeps registers (and so
 // resident warps) at the level the plain searches need.
-enum : int { FAM_PLAIN = 0, FAM_SPLINE = 1, FAM_MLP = 2 };
+enum : int { FAM_PLAIN = 0, FAM_SPLINE = 1, FAM_MLP = 2, FAM_HUNT = 3 };
 
 constexpr uint64_t kKeyNegInf = 0x0010000000000000ull;   // image of -inf; NaNs map below it
 
@@ -477,6 +477,59 @@ __device__ __forceinline__ void stream_tile_mlp(const StagedView& v, const doubl
   for (int i = head + 4 * nq + threadIdx.x; i < cnt; i += bs) one(b + i);
 }
 
+// Hunt order (SS_MODEL_HUNT, coherent targets): a lane takes eight
+// consecutive targets per step (two 256-bit loads; a warp covers 256
+// consecutive targets): the first is searched with the table's own search,
+// each of the other seven hunts from the first one's answer (hunt_from;
+// independent of each other, so their shared-memory round trips overlap).
+// Head and tail targets take the table's own search.  Every answer is exact
+// whatever the guess.  (A chain in which each target hunts from the one
+// before it measured slower: its dependent round trips serialise.)
+__device__ __forceinline__ void stream_tile_hunt(const StagedView& v, const double* __restrict__ Y,
+                                                 int32_t* __restrict__ out, int64_t b, int cnt, int vec,
+                                                 uint64_t le, int& nans) {
+  const int bs = blockDim.x;
+  auto one = [&](int64_t i) {
+    const double y = Y[i];
+    const uint64_t k = order_key(y);
+    nans += k < kKeyNegInf;
+    out[i] = hunt_count(v, -1, k + le);
+  };
+  const int head = vec ? min(cnt, (int)((-b) & 3)) : cnt;
+  const int np = (cnt - head) >> 3;                    // runs of eight targets (two quads)
+  for (int i = threadIdx.x; i < head; i += bs) one(b + i);
+  const double2* Y2 = reinterpret_cast<const double2*>(Y + b + head);
+  int4* O4 = reinterpret_cast<int4*>(out + b + head);
+  for (int g = threadIdx.x; g < np; g += bs) {
+    double y[8];
+    if (vec == 2) {
+      ld_stream4(reinterpret_cast<const double*>(Y2 + 4 * g), *reinterpret_cast<double(*)[4]>(y));
+      ld_stream4(reinterpret_cast<const double*>(Y2 + 4 * g + 2), *reinterpret_cast<double(*)[4]>(y + 4));
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const double2 p = ld_stream(Y2 + 4 * g + j);
+        y[2 * j] = p.x;
+        y[2 * j + 1] = p.y;
+      }
+    }
+    int r[8];
+    uint64_t q[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint64_t k = order_key(y[j]);
+      nans += k < kKeyNegInf;
+      q[j] = k + le;
+    }
+    r[0] = hunt_count(v, -1, q[0]);
+#pragma unroll
+    for (int j = 1; j < 8; ++j) r[j] = hunt_count(v, r[0], q[j]);
+    st_stream(O4 + 2 * g, make_int4(r[0], r[1], r[2], r[3]));
+    st_stream(O4 + 2 * g + 1, make_int4(r[4], r[5], r[6], r[7]));
+  }
+  for (int i = head + 8 * np + threadIdx.x; i < cnt; i += bs) one(b + i);
+}
+
 template <int G>
 __device__ __forceinline__ void ballot_tile(const StagedView& v, const double* __restrict__ Y, int32_t* __restrict__ out,
                                             int64_t b, int cnt, uint64_t le, int& nans) {
@@ -550,6 +603,20 @@ __global__ void __launch_bounds__(kPlanMaxThreads, 2) k_batched_1d(BatchArgs1D a
     // one uniform branch per tile picks the search; inside the tile the
     // searches are branch-free straight-line code where the table allows it
     const int vec = a.vec;
+    if constexpr (FAM == FAM_HUNT) {
+      // the hunt reads the staged keys: only a table staged for the bucket
+      // search carries them (plan creation gives hunt plans no other; a
+      // table staged otherwise, e.g. from an edited plan file, is searched
+      // plainly)
+      if (algo == BL_BUCKET) stream_tile_hunt(v, a.Y, a.out, b, cnt, vec, le, nans);
+      else if (algo == BL_BINARY)
+        stream_tile(a.Y, a.out, b, cnt, vec, le, nans, [&](double, uint64_t q) { return plain_binary(v, q); });
+      else if (algo == BL_BALLOT8) ballot_tile<8>(v, a.Y, a.out, b, cnt, le, nans);
+      else if (algo == BL_BALLOT16) ballot_tile<16>(v, a.Y, a.out, b, cnt, le, nans);
+      else if (algo == BL_BALLOT32) ballot_tile<32>(v, a.Y, a.out, b, cnt, le, nans);
+      else stream_tile(a.Y, a.out, b, cnt, vec, le, nans, [&](double, uint64_t q) { return plain_bucket(v, q); });
+      continue;
+    }
     if (FAM >= FAM_MLP && algo == BL_MLP) {
       // staged tables: the eight proposals of a thread together; sampled
       // tables (wide windows searched in global memory) one by one
@@ -647,6 +714,8 @@ const void* batched_1d_wide_kernel(bool le) {
 
 // Kernel entry of the batched search (template stubs stay local to this unit).
 const void* batched_1d_kernel(bool le, int family) {
+  if (family == FAM_HUNT)
+    return le ? reinterpret_cast<const void*>(&k_batched_1d<true, FAM_HUNT>) : reinterpret_cast<const void*>(&k_batched_1d<false, FAM_HUNT>);
   if (family >= FAM_MLP)
     return le ? reinterpret_cast<const void*>(&k_batched_1d<true, FAM_MLP>) : reinterpret_cast<const void*>(&k_batched_1d<false, FAM_MLP>);
   if (family == FAM_SPLINE)

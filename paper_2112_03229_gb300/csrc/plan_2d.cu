@@ -165,7 +165,7 @@ __device__ __forceinline__ void pair_2d(const StagedView& vr, const StagedView& 
 
 // Streams one tile's pairs: scalar head to an even pair, two pairs per
 // thread with 128-bit loads and stores, scalar tail.
-template <bool HUNT, class CR, class CT>
+template <class CR, class CT>
 __device__ __forceinline__ void stream_pairs(const BatchArgs2D& a, const StagedView& vr, const StagedView& vt,
                                              const float4* __restrict__ G, const double* __restrict__ G64,
                                              const Tile& tile, int& nans, int& fallbacks, CR&& count_r,
@@ -201,14 +201,56 @@ __device__ __forceinline__ void stream_pairs(const BatchArgs2D& a, const StagedV
     int i0, j0, i1, j1;
     double v0, v1;
     pair_2d(vr, vt, G, G64, p0.x, p0.y, i0, j0, v0, nans, count_r, count_t, a.extrap, a.logspace);
-    if (HUNT) {
-      // consecutive pairs of a coherent sequence: start from the first pair's indices
-      pair_2d(vr, vt, G, G64, p1.x, p1.y, i1, j1, v1, nans,
-              [&](double, uint64_t q) { return hunt_count(vr, i0, q, fallbacks); },
-              [&](double, uint64_t q) { return hunt_count(vt, j0, q, fallbacks); }, a.extrap, a.logspace);
+    pair_2d(vr, vt, G, G64, p1.x, p1.y, i1, j1, v1, nans, count_r, count_t, a.extrap, a.logspace);
+    st_stream(I4 + g, make_int4(i0, j0, i1, j1));
+    st_stream(V2 + g, make_double2(v0, v1));
+  }
+  for (int i = head + 2 * np2 + threadIdx.x; i < cnt; i += blockDim.x) scalar(i);
+}
+
+// Hunt order (SS_MODEL_HUNT, coherent sequences): a thread's first pair is
+// searched with each axis' own search (the tile's fast path where it
+// applies), its second pair hunts on each axis from the first pair's
+// indices (hunt_from: probes in doubling steps, then bisects; exact for any
+// guess).  Head and tail pairs take the axes' own searches.
+template <class CR, class CT>
+__device__ __forceinline__ void stream_pairs_hunt(const BatchArgs2D& a, const StagedView& vr, const StagedView& vt,
+                                                  const float4* __restrict__ G, const double* __restrict__ G64,
+                                                  const Tile& tile, int& nans, CR&& count_r, CT&& count_t) {
+  const int64_t b = tile.begin;
+  const int cnt = tile.count;
+  auto scalar = [&](int i) {
+    int ir, it;
+    double v;
+    pair_2d(vr, vt, G, G64, a.Y2[2 * (b + i)], a.Y2[2 * (b + i) + 1], ir, it, v, nans, count_r, count_t, a.extrap,
+            a.logspace);
+    a.idx[2 * (b + i)] = ir;
+    a.idx[2 * (b + i) + 1] = it;
+    a.val[b + i] = v;
+  };
+  const int head = a.vec ? min(cnt, (int)(b & 1)) : cnt;
+  const int np2 = (cnt - head) >> 1;
+  for (int i = threadIdx.x; i < head; i += blockDim.x) scalar(i);
+  const double2* Y = reinterpret_cast<const double2*>(a.Y2) + b + head;
+  int4* I4 = reinterpret_cast<int4*>(a.idx + 2 * (b + head));
+  double2* V2 = reinterpret_cast<double2*>(a.val + b + head);
+  for (int g = threadIdx.x; g < np2; g += blockDim.x) {
+    double2 p0, p1;
+    if (a.vec == 2) {
+      double y[4];
+      ld_stream4(reinterpret_cast<const double*>(Y + 2 * g), y);
+      p0 = make_double2(y[0], y[1]);
+      p1 = make_double2(y[2], y[3]);
     } else {
-      pair_2d(vr, vt, G, G64, p1.x, p1.y, i1, j1, v1, nans, count_r, count_t, a.extrap, a.logspace);
+      p0 = ld_stream(Y + 2 * g);
+      p1 = ld_stream(Y + 2 * g + 1);
     }
+    int i0, j0, i1, j1;
+    double v0, v1;
+    pair_2d(vr, vt, G, G64, p0.x, p0.y, i0, j0, v0, nans, count_r, count_t, a.extrap, a.logspace);
+    pair_2d(vr, vt, G, G64, p1.x, p1.y, i1, j1, v1, nans,
+            [&](double, uint64_t q) { return hunt_count(vr, i0, q); },
+            [&](double, uint64_t q) { return hunt_count(vt, j0, q); }, a.extrap, a.logspace);
     st_stream(I4 + g, make_int4(i0, j0, i1, j1));
     st_stream(V2 + g, make_double2(v0, v1));
   }
@@ -275,9 +317,10 @@ __global__ void __launch_bounds__(kNumThreads, 3) k_batched_2d(BatchArgs2D a) {
       return v.h.algo == BL_BUCKET && v.h.stride == 1 && v.h.occ <= 2;
     };
     if (HUNT) {
-      stream_pairs<true>(a, vr, vt, G, G64, tile, nans, fallbacks, generic(vr), generic(vt));
+      if (fast(vr) && fast(vt)) stream_pairs_hunt(a, vr, vt, G, G64, tile, nans, scan2(vr), scan2(vt));
+      else stream_pairs_hunt(a, vr, vt, G, G64, tile, nans, generic(vr), generic(vt));
     } else if (fast(vr) && fast(vt)) {
-      stream_pairs<false>(a, vr, vt, G, G64, tile, nans, fallbacks, scan2(vr), scan2(vt));
+      stream_pairs(a, vr, vt, G, G64, tile, nans, fallbacks, scan2(vr), scan2(vt));
     } else {
       // a plan's model is the same on both axes: one uniform branch per tile
       // picks its proposal, so the pairs run it as straight-line code
@@ -285,23 +328,23 @@ __global__ void __launch_bounds__(kNumThreads, 3) k_batched_2d(BatchArgs2D a) {
       if constexpr (LEARNED) {
         const int al = vr.h.algo;
         if (al == vt.h.algo && al == BL_SPLINE) {
-          stream_pairs<false>(a, vr, vt, G, G64, tile, nans, fallbacks,
+          stream_pairs(a, vr, vt, G, G64, tile, nans, fallbacks,
                               [&](double, uint64_t q) { return spline_count(vr, q, fallbacks); },
                               [&](double, uint64_t q) { return spline_count(vt, q, fallbacks); });
           done = true;
         } else if (al == vt.h.algo && al == BL_LOGHASH) {
-          stream_pairs<false>(a, vr, vt, G, G64, tile, nans, fallbacks,
+          stream_pairs(a, vr, vt, G, G64, tile, nans, fallbacks,
                               [&](double t, uint64_t q) { return loghash_count(vr, t, q, fallbacks); },
                               [&](double t, uint64_t q) { return loghash_count(vt, t, q, fallbacks); });
           done = true;
         } else if (al == vt.h.algo && al == BL_MLP) {
-          stream_pairs<false>(a, vr, vt, G, G64, tile, nans, fallbacks,
+          stream_pairs(a, vr, vt, G, G64, tile, nans, fallbacks,
                               [&](double t, uint64_t q) { return mlp_count(vr, t, q, fallbacks); },
                               [&](double t, uint64_t q) { return mlp_count(vt, t, q, fallbacks); });
           done = true;
         }
       }
-      if (!done) stream_pairs<false>(a, vr, vt, G, G64, tile, nans, fallbacks, generic(vr), generic(vt));
+      if (!done) stream_pairs(a, vr, vt, G, G64, tile, nans, fallbacks, generic(vr), generic(vt));
     }
   }
   nans = __reduce_add_sync(0xFFFFFFFFu, nans);

@@ -318,6 +318,7 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
   const void* kern;
   int family = 0;
   for (int a : p->algo) family = std::max(family, a == BL_MLP ? 2 : (a == BL_SPLINE || a == BL_LOGHASH) ? 1 : 0);
+  if (p->kind == 1 && p->opts.model == SS_MODEL_HUNT) family = 3;          // the hunt's own instance
   if (p->kind == 1) kern = batched_1d_kernel(p->opts.side == SS_SIDE_LE, family);
   else kern = batched_2d_kernel(p->opts.model == SS_MODEL_HUNT, family > 0);
   if (ss_status st_ = raise_smem_limit(kern, smem)) return st_;
@@ -541,6 +542,8 @@ ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
   if (p->opts.model == SS_MODEL_SPLINE) cands = {BL_SPLINE};
   else if (p->opts.model == SS_MODEL_MLP) cands = {BL_MLP};
   else if (p->opts.model == SS_MODEL_LOGHASH) cands = {BL_LOGHASH};
+  else if (p->opts.model == SS_MODEL_HUNT) cands = p->kind == 1 ? std::vector<int>{BL_BUCKET}     // keys staged
+                                                                  : std::vector<int>{BL_BUCKET, BL_BINARY};
   else if (p->kind == 1) cands = {BL_BUCKET, BL_BINARY, BL_BALLOT8, BL_BALLOT16, BL_BALLOT32, BL_WIDE};
   else cands = {BL_BUCKET, BL_BINARY};
   const std::vector<float> mult_cands = {0.25f, 1.0f, 4.0f};

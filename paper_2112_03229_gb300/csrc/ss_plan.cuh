@@ -419,24 +419,69 @@ __device__ __forceinline__ int learned_count(const StagedView& v, int p, uint64_
   return c;
 }
 
-// Hunt: the answer for a target that follows one whose answer was p, checked
-// exactly in the window [p-1, p+1]; the plain search when it lies outside.
-__device__ __forceinline__ int hunt_count(const StagedView& v, int p, uint64_t q, int& fallbacks) {
+// Hunt and locate (Sec. 2.1; coherent targets, Sec. 5.5): the count of keys
+// below q starting from a guess p in [0, nk], the answer of a nearby target.
+// The keys around the guess are read together, so an answer of p or p + 1
+// costs one memory round trip; otherwise the bracket grows away from the
+// guess in doubling steps (2, 4, ... up to 2^kHuntProbes keys) until a key on
+// the far side of q is found, and a bisection inside the last step finishes.
+// A target further away than the probes reach is searched with the table's
+// own search (`plain`), which costs O(1) round trips with the bucket
+// directory: on the GPU that bound beats an unbounded probe (measured).
+// Exact for any guess; every loop is bounded.  key(nk) must be a sentinel
+// above every query.
+constexpr int kHuntProbes = 4;
+
+template <class KEYS, class PLAIN>
+__device__ __forceinline__ int hunt_from(KEYS key, int nk, int p, uint64_t q, PLAIN&& plain) {
+  p = min(max(p, 0), nk);
+  const uint64_t km1 = p > 0 ? key(p - 1) : 0, k0 = key(p), kp1 = key(min(p + 1, nk));
+  int lo, hi;                                      // the answer lies in [lo, hi]
+  if (q <= k0) {
+    if (p == 0 || km1 < q) return p;
+    hi = p - 1;                                    // below the guess: probe downwards
+    lo = -1;
+    int s = 2;
+    for (int it = 0; it < kHuntProbes; ++it, s <<= 1) {
+      const int j = hi - s;
+      if (j < 0) { lo = 0; break; }
+      if (key(j) < q) { lo = j + 1; break; }
+      hi = j;
+    }
+    if (lo < 0) return plain(q);
+  } else {
+    if (q <= kp1) return p + 1;                    // k0 < q: p < nk, so p + 1 <= nk
+    lo = p + 2;                                    // above: probe upwards
+    hi = -1;
+    int s = 2;
+    for (int it = 0; it < kHuntProbes; ++it, s <<= 1) {
+      const int j = min(lo + s - 1, nk);
+      if (key(j) >= q) { hi = j; break; }        // key(nk), a sentinel, always ends the probe
+      lo = j + 1;
+    }
+    if (hi < 0) return plain(q);
+  }
+  int len = hi - lo;                               // keys [lo, hi) still to count
+  for (int it = 0; it < kHuntProbes + 1 && len > 0; ++it) {
+    const int half = len >> 1;
+    if (key(lo + half) < q) { lo += half + 1; len -= half + 1; } else { len = half; }
+  }
+  return lo;
+}
+
+// Hunt on a staged table (keys in shared memory) or a two-level table (all
+// keys in global memory).  A guess below zero means "none": the table's own
+// search runs.
+__device__ __forceinline__ int hunt_count(const StagedView& v, int p, uint64_t q) {
   const BlobHdr& h = v.h;
-  bool ok;
-  int c;
+  auto plain = [&v](uint64_t qq) { return v.h.algo == BL_BINARY ? plain_binary(v, qq) : plain_bucket(v, qq); };
+  if (p < 0) return plain(q);
   if (h.stride == 1) {
     const uint64_t* keys = v.keys;
-    c = window_count([keys](int i) { return keys[i]; }, h.nk, 1, p, q, ok);
-  } else {
-    const uint64_t* full = v.full;
-    c = window_count([full](int i) { return __ldg(full + i); }, h.nk, 1, p, q, ok);
+    return hunt_from([keys](int i) { return keys[i]; }, h.nk, p, q, plain);
   }
-  if (!ok) {
-    ++fallbacks;
-    return h.algo == BL_BINARY ? plain_binary(v, q) : plain_bucket(v, q);   // the axis' own search
-  }
-  return c;
+  const uint64_t* full = v.full;
+  return hunt_from([full](int i) { return __ldg(full + i); }, h.nk, p, q, plain);
 }
 
 // Spline proposal in count units of the whole table.  A sampled (two-level)

@@ -146,18 +146,35 @@ def _reflect(z: torch.Tensor, a: float, b: float) -> torch.Tensor:
     return a + torch.where(y > w, 2 * w - y, y)
 
 
-def pairs_random_walk(m: int, R_lo, R_hi, T_lo, T_hi, seed: int, step: float = 0.01,
+def _walk(m: int, lo: float, hi: float, g, step: float, jump: float, device) -> torch.Tensor:
+    """m points of a random walk in log10 space over [lo, hi], reflected at the
+    bounds: N(0, step) steps, each replaced with probability `jump` by a
+    uniform jump of up to the whole log range (a walk that leaps many cells)."""
+    a, b = math.log10(lo), math.log10(hi)
+    z0 = a + (b - a) * torch.rand((1,), generator=g, device=device, dtype=F64)
+    steps = torch.randn((m,), generator=g, device=device, dtype=F64) * step
+    if jump > 0:
+        leap = torch.rand((m,), generator=g, device=device, dtype=F64) < jump
+        far = (torch.rand((m,), generator=g, device=device, dtype=F64) * 2 - 1) * (b - a)
+        steps = torch.where(leap, far, steps)
+    steps[0] = 0.0
+    z = _reflect(z0 + torch.cumsum(steps, 0), a, b)
+    return torch.pow(10.0, z).clamp_(lo, hi)
+
+
+def walk_1d(m: int, lo: float, hi: float, seed: int, step: float = 0.01, jump: float = 0.0,
+            device="cpu") -> torch.Tensor:
+    """m coherent targets over [lo, hi]: a reflected random walk in log10 space."""
+    return _walk(m, lo, hi, _gen(seed, device), step, jump, device)
+
+
+def pairs_random_walk(m: int, R_lo, R_hi, T_lo, T_hi, seed: int, step: float = 0.01, jump: float = 0.0,
                       device="cpu") -> torch.Tensor:
     """m coherent pairs: a reflected random walk in log10 space, N(0, step) per coordinate."""
     g = _gen(seed, device)
     out = torch.empty((m, 2), dtype=F64, device=device)
     for col, (lo, hi) in enumerate(((R_lo, R_hi), (T_lo, T_hi))):
-        a, b = math.log10(lo), math.log10(hi)
-        z0 = a + (b - a) * torch.rand((1,), generator=g, device=device, dtype=F64)
-        steps = torch.randn((m,), generator=g, device=device, dtype=F64) * step
-        steps[0] = 0.0
-        z = _reflect(z0 + torch.cumsum(steps, 0), a, b)
-        out[:, col] = torch.pow(10.0, z).clamp_(lo, hi)
+        out[:, col] = _walk(m, lo, hi, g, step, jump, device)
     return out
 
 
@@ -243,6 +260,17 @@ def batched_1d(ntables: int = 10_000, seed: int = 5, count_lo: int = 1000, count
     return Batched1D(torch.as_tensor(X_off, device=device), X, torch.as_tensor(Y_off, device=device), Y, lo, hi)
 
 
+def batched_1d_x2(seed: int = 5, count_scale: float = 1.0, device="cpu") -> Batched1D:
+    """Two independent 10,000-table batches (seeds `seed` and `seed + 500`)
+    back to back: 20,000 tables and about 2.2B targets, the stated "about 2B"
+    reached without distorting the Zipf(1.1) count law of one batch."""
+    a = batched_1d(ntables=10_000, seed=seed, count_scale=count_scale, device=device)
+    b = batched_1d(ntables=10_000, seed=seed + 500, count_scale=count_scale, device=device)
+    return Batched1D(torch.cat([a.X_off, b.X_off[1:] + a.X_off[-1]]), torch.cat([a.X, b.X]),
+                     torch.cat([a.Y_off, b.Y_off[1:] + a.Y_off[-1]]), torch.cat([a.Y, b.Y]),
+                     np.concatenate([a.lo, b.lo]), np.concatenate([a.hi, b.hi]))
+
+
 @dataclass
 class Batched2D:
     R_off: torch.Tensor
@@ -256,10 +284,11 @@ class Batched2D:
 
 
 def batched_2d(ntables: int = 1000, pairs_per_table: int = 1_000_000, coherent: bool = False, seed: int = 6,
-               device="cpu") -> Batched2D:
+               device="cpu", jump: float = 0.0) -> Batched2D:
     """Many 2D tables (axes U{50..500} x U{30..300}, jittered log spacing,
     per-table smooth fields), an equal number of pairs per table, random or
-    coherent order."""
+    coherent order (with `jump`, a fraction of the walk's steps leap across
+    up to the whole range)."""
     rng = np.random.default_rng(seed)
     nr = rng.integers(50, 501, ntables)
     nt = rng.integers(30, 301, ntables)
@@ -277,7 +306,8 @@ def batched_2d(ntables: int = 1000, pairs_per_table: int = 1_000_000, coherent: 
         Ts.append(T)
         Fs.append(F.reshape(-1))
         if coherent:
-            Ys.append(pairs_random_walk(pairs_per_table, r_lo[k], r_hi[k], t_lo[k], t_hi[k], s + 3, device=device))
+            Ys.append(pairs_random_walk(pairs_per_table, r_lo[k], r_hi[k], t_lo[k], t_hi[k], s + 3, jump=jump,
+                                        device=device))
         else:
             Ys.append(pairs_log_uniform(pairs_per_table, r_lo[k], r_hi[k], t_lo[k], t_hi[k], s + 3, device=device))
     off = lambda sizes: torch.as_tensor(np.concatenate([[0], np.cumsum(sizes)]), dtype=torch.int64, device=device)

@@ -46,18 +46,25 @@ def check_batched_1d(b, out, k, seed):
 
 
 def test_batched1d_full_size_sampled(ss):
-    """The default bench workload: 10,000 tables, 1,088,467,071 targets."""
-    b = wl.batched_1d(ntables=10_000, seed=5, device=DEV)
-    plan = ss.Plan.create_1d(b.X_off, b.X.to(DEV), autotune=True)
-    out = torch.full((b.Y.numel(),), -1, dtype=torch.int32, device=DEV)
-    stat = ss.new_stat()
-    plan.bind_1d(b.Y_off, b.Y, out, stat=stat)
-    plan.execute()
-    torch.cuda.synchronize()
-    assert int(out.min()) >= 0                     # every target written
-    check_batched_1d(b, out, 2_000_000, seed=1)
-    assert ss.read_stat(stat).flags == 0
-    del out, b, plan
+    """The headline bench workload: two 10,000-table batches, 2,174,007,083
+    targets; the plain plan (autotuned) and each position model's plan, as
+    bench.py times them, on the same sampled targets."""
+    b = wl.batched_1d_x2(seed=5, device=DEV)
+    assert b.Y.numel() == 2_174_007_083
+    X = b.X.to(DEV)
+    out = torch.empty((b.Y.numel(),), dtype=torch.int32, device=DEV)
+    for k, model in enumerate(("none", "spline", "mlp", "loghash")):
+        plan = ss.Plan.create_1d(b.X_off, X, model=model, autotune=True)
+        out.fill_(-1)
+        stat = ss.new_stat()
+        plan.bind_1d(b.Y_off, b.Y, out, stat=stat)
+        plan.execute()
+        torch.cuda.synchronize()
+        assert int(out.min()) >= 0, model                 # every target written
+        check_batched_1d(b, out, 1_000_000, seed=1 + k)
+        assert ss.read_stat(stat).flags == 0
+        del plan
+    del out, b, X
     torch.cuda.empty_cache()
 
 

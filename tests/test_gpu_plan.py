@@ -290,34 +290,89 @@ def test_plan_bound_to_page_locked_host_buffers(ss):
     assert (np.abs(hV.numpy() - wv) / np.abs(wv)).max() <= REL_TOL
 
 
-def test_hunt_is_2d_only_and_falls_back(ss):
-    """The hunt proposal applies to 2D plans; on a random order most of its
-    windows miss and the plain search answers them (indices stay exact)."""
-    b = small_batch(seed=17)
-    with pytest.raises(ss.SSError):
-        ss.Plan.create_1d(b.X_off, b.X.to(DEV), model="hunt")
-    b2 = wl.batched_2d(ntables=4, pairs_per_table=4001, seed=18)
+def walk_batch_1d(sizes, per_table, seed, order, side=0):
+    """Tables of the given sizes (jittered log spacing) and per table a
+    target sequence: a random walk in log space ("walk"), the same with 2 %
+    of its steps leaping across up to the whole range ("jumps"), sorted
+    log-uniform targets ("sorted") or log-uniform ones ("random")."""
+    Xs, Ys = [], []
+    for k, n in enumerate(sizes):
+        lo, hi = 10.0 ** (-6 + k), 10.0 ** (4 + k)
+        X = wl.log_spaced_table(n, lo, hi, 0.1, seed * 31 + k)
+        a, b = 0.5 * lo, 2 * hi
+        if order == "walk":
+            Y = wl.walk_1d(per_table, a, b, seed * 37 + k)
+        elif order == "jumps":
+            Y = wl.walk_1d(per_table, a, b, seed * 37 + k, jump=0.02)
+        else:
+            Y = wl.log_uniform(per_table, a, b, seed * 37 + k)
+            if order == "sorted":
+                Y = torch.sort(Y).values
+        Xs.append(X)
+        Ys.append(Y)
+    X_off = torch.tensor(np.concatenate([[0], np.cumsum([len(x) for x in Xs])]))
+    Y_off = torch.tensor(np.concatenate([[0], np.cumsum([len(y) for y in Ys])]))
+    return wl.Batched1D(X_off, torch.cat(Xs), Y_off, torch.cat(Ys), None, None)
+
+
+@pytest.mark.parametrize("order", ["walk", "jumps", "sorted", "random"])
+@pytest.mark.parametrize("side", [0, 1])
+def test_hunt_1d_exact_on_every_order(ss, order, side):
+    """Hunt and locate on 1D plans: tables staged whole (64, 2000 entries)
+    and searched in global memory (20,000 and 100,000 entries), coherent,
+    leaping, sorted and random targets; every index equals the oracle's."""
+    b = walk_batch_1d((64, 2000, 20_000, 100_000), 30_011, seed=41, order=order)
+    want = oracle.search_1d_batched(b.X_off.numpy(), b.X.numpy(), b.Y_off.numpy(), b.Y.numpy(), side)
+    for tile in (0, 997):                     # tuned tiles, and small odd ones (ragged warp runs)
+        plan, got, st = run_plan_1d(ss, b, model="hunt", side=side, tile=tile)
+        np.testing.assert_array_equal(got, want)
+        assert st.flags == 0
+    # off 16-byte alignment: the scalar head and tail of every tile
+    Yd = torch.empty(b.Y.numel() + 1, dtype=torch.float64, device=DEV)
+    Yd[1:] = b.Y.to(DEV)
+    out = torch.full((b.Y.numel() + 1,), -1, dtype=torch.int32, device=DEV)
+    plan.bind_1d(b.Y_off, Yd[1:], out[1:])
+    plan.execute()
+    np.testing.assert_array_equal(out[1:].cpu().numpy(), want)
+    assert int(out[0]) == -1
+
+
+def test_hunt_1d_starts_runs_with_the_bucket_search(ss):
+    # the hunt reads the staged keys, which a table staged for the
+    # breadth-first or ballot search does not carry: such plans are refused
+    b = walk_batch_1d((300, 9000), 20_000, seed=43, order="jumps")
+    for algo in ("binary", "ballot"):
+        with pytest.raises(ss.SSError) as e:
+            ss.Plan.create_1d(b.X_off, b.X.to(DEV), model="hunt", algo=algo)
+        assert e.value.code == 1
+    want = oracle.search_1d_batched(b.X_off.numpy(), b.X.numpy(), b.Y_off.numpy(), b.Y.numpy())
+    plan, got, _ = run_plan_1d(ss, b, model="hunt", algo="bucket", autotune=True)
+    np.testing.assert_array_equal(got, want)
+    assert all(c[0] == "bucket" for c in plan.choices().values())
+
+
+@pytest.mark.parametrize("order", ["walk", "jumps", "random"])
+def test_hunt_2d_exact_on_every_order(ss, order):
+    """The 2D hunt: each axis hunts from the previous pair's index; walks,
+    leaping walks and random pairs all give the oracle's indices and values
+    within 1e-12, with bucket and binary axis searches."""
+    b2 = wl.batched_2d(ntables=6, pairs_per_table=6001, coherent=order != "random", seed=18,
+                       jump=0.02 if order == "jumps" else 0.0)
     wi, wv = oracle.search_interp_2d_batched(b2.R_off.numpy(), b2.R.numpy(), b2.T_off.numpy(), b2.T.numpy(),
                                              b2.F_off.numpy(), b2.F.numpy(), b2.Y_off.numpy(), b2.Y2.numpy())
-    plan = ss.Plan.create_2d(b2.R_off, b2.R.to(DEV), b2.T_off, b2.T.to(DEV), b2.F_off, b2.F.to(DEV), model="hunt")
     m = b2.Y2.shape[0]
-    idx = torch.empty((m, 2), dtype=torch.int32, device=DEV)
-    val = torch.empty(m, dtype=torch.float64, device=DEV)
-    stat = ss.new_stat()
-    plan.bind_2d(b2.Y_off, b2.Y2.to(DEV), idx, val, stat=stat)
-    plan.execute()
-    np.testing.assert_array_equal(idx.cpu().numpy(), wi)
-    assert (np.abs(val.cpu().numpy() - wv) / np.abs(wv)).max() <= REL_TOL
-    assert ss.read_stat(stat).fallbacks > m // 4
-    # axes searched by the breadth-first binary search still stage their
-    # keys: the hunt's window and its fallback read the axis
-    plan = ss.Plan.create_2d(b2.R_off, b2.R.to(DEV), b2.T_off, b2.T.to(DEV), b2.F_off, b2.F.to(DEV), model="hunt",
-                             algo="binary")
-    idx.fill_(-1)
-    plan.bind_2d(b2.Y_off, b2.Y2.to(DEV), idx, val)
-    plan.execute()
-    np.testing.assert_array_equal(idx.cpu().numpy(), wi)
-    assert (np.abs(val.cpu().numpy() - wv) / np.abs(wv)).max() <= REL_TOL
+    for algo in ("auto", "binary"):
+        for tile in (0, 333):
+            plan = ss.Plan.create_2d(b2.R_off, b2.R.to(DEV), b2.T_off, b2.T.to(DEV), b2.F_off, b2.F.to(DEV),
+                                     model="hunt", algo=algo, tile=tile)
+            idx = torch.full((m, 2), -1, dtype=torch.int32, device=DEV)
+            val = torch.empty(m, dtype=torch.float64, device=DEV)
+            stat = ss.new_stat()
+            plan.bind_2d(b2.Y_off, b2.Y2.to(DEV), idx, val, stat=stat)
+            plan.execute()
+            np.testing.assert_array_equal(idx.cpu().numpy(), wi)
+            assert (np.abs(val.cpu().numpy() - wv) / np.abs(wv)).max() <= REL_TOL
+            assert ss.read_stat(stat).flags == 0
 
 
 def test_plan_2d_binary_axes_with_options(ss):

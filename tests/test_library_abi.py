@@ -65,7 +65,7 @@ def test_argument_errors_without_gpu(built):
     # the other option checks of plan creation, also before any CUDA call
     off = (ctypes.c_int64 * 2)(0, 4)
     h = ctypes.c_void_p()
-    for kind, kw, msg in ((1, dict(tile=-1), b"negative"), (1, dict(model="hunt"), b"2D plans only"),
+    for kind, kw, msg in ((1, dict(tile=-1), b"negative"), (1, dict(model="hunt", algo="binary"), b"bucket search"),
                           (1, dict(side=5), b"side"), (2, dict(side=1), b"SS_SIDE_LT"),
                           (2, dict(algo="ballot"), b"auto, binary or bucket"), (1, dict(mlp_lr=float("nan")), b"mlp_lr")):
         o = ss.plan_opts(**kw)

@@ -112,3 +112,18 @@ def test_batched_2d_recipe_random_and_coherent():
             assert 0.0095 < np.std(s) < 0.0105
         else:
             assert np.std(s) > 1.0
+
+
+def test_walk_1d_steps_and_jumps():
+    lo, hi = 1e-6, 1e4
+    y = wl.walk_1d(200_000, lo, hi, seed=3)
+    assert torch.all((y >= lo) & (y <= hi))
+    d = torch.diff(torch.log10(y))
+    # N(0, 0.01 decade) steps (reflection only shortens a step)
+    assert 0.0095 < float(d.std()) < 0.0105 and float(d.abs().max()) < 0.07
+    y2 = wl.walk_1d(200_000, lo, hi, seed=3, jump=0.01)
+    d2 = torch.diff(torch.log10(y2)).abs()
+    big = int((d2 > 1.0).sum())                  # leaps of more than a decade
+    assert 1000 < big < 2000 and float(d2.max()) > 5.0
+    # the same seed without jumps is the plain walk, draw for draw
+    assert torch.equal(wl.walk_1d(200_000, lo, hi, seed=3, jump=0.0), y)
