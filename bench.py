@@ -81,18 +81,50 @@ def sources_hash(files):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel, workload):
-    """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel's source files changed since the counters were taken."""
+def recorded(kernel, workload, field="dram_bytes_per_launch"):
+    """A per-launch (or per-unit) figure from the committed ncu summaries, or
+    None when the kernel's source files changed since the counters were taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             rec = json.load(f)[f"{kernel}@{workload}"]
         if rec.get("sources") != sources_hash(rec["files"]):
             return None
-        return float(rec["dram_bytes_per_launch"])
+        return float(rec[field])
     except Exception:
         return None
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary (None once stale)."""
+    return recorded(kernel, workload, "dram_bytes_per_launch")
+
+
+FP64_NOMINAL_GOPS = 1250.0     # GB300 fp64: 1.25 TFLOP/s nominal (no measured figure in this pool's peaks)
+
+
+def co_bound(wl_obj, value, sm_mhz):
+    """Beside the HBM roofline, the instruction-issue bound of a kernel that
+    computes per unit (the 2D lookups): warp instructions per unit from the
+    committed ncu capture times the measured rate, against four issue slots
+    per SM per clock at the sampled SM clock; and the fp64 instructions per
+    unit against the nominal fp64 rate.  None when no current record exists."""
+    w = recorded(wl_obj.kernel, wl_obj.name, "warp_inst_per_unit")
+    if w is None:
+        return None
+    f64 = recorded(wl_obj.kernel, wl_obj.name, "fp64_thread_inst_per_unit")
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = sm_mhz or 2070.0
+    achieved = value * 1e9 * w / 1e12
+    peak = sms * 4 * mhz * 1e6 / 1e12
+    out = {"bound": "issue", "warp_inst_per_unit": w, "achieved": round(achieved, 4), "peak": round(peak, 4),
+           "unit": "T warp instructions/s", "frac": round(achieved / peak, 4),
+           "peak_source": "%d SMs x 4 issue slots x %.0f MHz (median SM clock sampled during this record)" % (sms, mhz)}
+    if f64 is not None:
+        g = value * f64
+        out["fp64"] = {"thread_inst_per_unit": f64, "achieved_Gops": round(g, 1), "peak_Gops": FP64_NOMINAL_GOPS,
+                       "frac": round(g / FP64_NOMINAL_GOPS, 4), "peak_source": "nominal"}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -690,7 +722,7 @@ class Batched2D(PlanWorkload):
     """1,000 2D tables (axes U{50..500} x U{30..300}), 1M (rho, T) pairs each
     (1B pairs), learned proposals on both axes and the coherent hunt vs plain."""
     name = "batched2d-1000-1B"
-    kernel = "k_batched_2d"
+    kernel = "k_batched_2d_fast"     # every axis of this batch takes the lean kernel's path
     compare_models = ("spline", "mlp", "loghash", "hunt")
     bytes_per_target = 16 + 8 + 8
     m = 0                  # --targets: total pairs of a smaller case (profiling)
@@ -1125,6 +1157,7 @@ def main():
         cpu = timer.baseline_on(*wl_obj.sample(wl_obj.sample_n), wl_obj.snap)
         timer.close()
     head_clocks = clk.summary()
+    head_co = co_bound(wl_obj, rec["value"], head_clocks["sm_mhz"])
     name, targets, flushed = wl_obj.name, wl_obj.targets(), wl_obj.flush is not None
     model = getattr(wl_obj, "model", None)
     wl_obj.release()
@@ -1146,6 +1179,9 @@ def main():
                 r["cpu_baseline"] = timer.baseline_on(*other.sample(other.sample_n), other.snap, reps=1)
                 timer.close()
             r["clocks"] = clk.summary(lo, len(clk.lines))
+            cb = co_bound(other, r["value"], r["clocks"]["sm_mhz"])
+            if cb is not None:
+                r["co_bound"] = cb
             configs[other.name] = r
             other.release()
     clk.__exit__(None, None, None)
@@ -1163,6 +1199,8 @@ def main():
         if model is not None:
             line["config"]["model"] = model
             line["config"]["setup"] = "tables prepared once before timing (plan creation, Sec. 5.3)"
+        if head_co is not None:
+            line["co_bound"] = head_co
         line.update(extra)
         if configs:
             line["configs"] = configs

@@ -245,7 +245,7 @@ class PlanInfo(C.Structure):
                 ("nbuckets", C.c_int32), ("bucket_algo", C.c_int32 * 8), ("bucket_tile", C.c_int32 * 8),
                 ("bucket_tables", C.c_int32 * 8), ("ntiles", C.c_int64), ("tuned", C.c_int32),
                 ("kernels", C.c_int32), ("block_threads", C.c_int32), ("smem_bytes", C.c_int32),
-                ("max_occupancy", C.c_int32)]
+                ("max_occupancy", C.c_int32), ("lean_kernel", C.c_int32)]
 
 
 def _plan_sigs(L):

@@ -244,6 +244,7 @@ extern "C" ss_status ss_plan_info_get(const ss_plan* p, ss_plan_info* out) {
   out->block_threads = p->threads;
   out->smem_bytes = p->smem_bytes;
   out->max_occupancy = p->max_occupancy;
+  out->lean_kernel = p->lean != 0 ? 1 : 0;
   return SS_OK;
 }
 

@@ -356,6 +356,167 @@ __global__ void __launch_bounds__(kNumThreads, 3) k_batched_2d(BatchArgs2D a) {
   if (a.stat != nullptr && threadIdx.x == 0 && !ok) atomicOr(&a.stat->flags, SS_FLAG_STAGING_TIMEOUT);
 }
 
+// ---------------------------------------------------------------------------
+// Lean kernel for the common case, launched when every axis of the plan is
+// searched by the bucket directory over a whole staged table with at most
+// two keys per bucket, every cell is in the float-float range and no
+// interpolation option is set (checked on the device when a batch is bound,
+// k_fast_2d_check): per axis it keeps only the handful of fields that case
+// reads, as shared-memory offsets, so fewer registers stay live and more
+// warps fit on an SM than in the general kernel.
+// ---------------------------------------------------------------------------
+struct FastAxis {
+  int keys, dir, ca, cg;     // shared-memory byte offsets: keys, directory, cell records, cell scales
+  int shift, nb, n;
+  uint64_t base, k0;
+};
+
+__device__ __forceinline__ FastAxis fast_axis(const StagedView& v, const unsigned char* smem) {
+  FastAxis f;
+  f.keys = (int)(reinterpret_cast<const unsigned char*>(v.keys) - smem);
+  f.dir = (int)(reinterpret_cast<const unsigned char*>(v.dir) - smem);
+  f.ca = (int)(reinterpret_cast<const unsigned char*>(v.cells.a) - smem);
+  f.cg = (int)(reinterpret_cast<const unsigned char*>(v.cells.g) - smem);
+  f.shift = v.h.shift;
+  f.nb = v.h.nb;
+  f.n = v.h.n;
+  f.base = v.h.base;
+  f.k0 = v.h.k0;
+  return f;
+}
+
+// Weights of coordinate bits u (key k, index i, cell c) on a fast axis.
+__device__ __forceinline__ Weights fast_weights(const unsigned char* smem, const FastAxis& f, int i, int c, uint64_t k,
+                                                uint64_t u) {
+  if (i >= f.n - 1) return {{1.0f, 0.0f}, {0.0f, 0.0f}};
+  if (i == 0 && k <= f.k0) return {{0.0f, 0.0f}, {1.0f, 0.0f}};
+  const CellTable t{reinterpret_cast<const ulonglong2*>(smem + f.ca), reinterpret_cast<const float2*>(smem + f.cg)};
+  return cell_weights(u, t, c);
+}
+
+__device__ __forceinline__ void pair_fast(const unsigned char* smem, const FastAxis& fr, const FastAxis& ft,
+                                          const float4* __restrict__ G, double rho, double tem, int& ir, int& it,
+                                          double& v, int& nans) {
+  const uint64_t ur = static_cast<uint64_t>(__double_as_longlong(rho));
+  const uint64_t ut = static_cast<uint64_t>(__double_as_longlong(tem));
+  const uint64_t kr = order_key(rho), kt = order_key(tem);
+  const bool nan = (kr < kKeyNegInf) | (kt < kKeyNegInf);
+  nans += (kr < kKeyNegInf) + (kt < kKeyNegInf);
+  ir = search_bucket<2>(reinterpret_cast<const uint64_t*>(smem + fr.keys),
+                        reinterpret_cast<const uint16_t*>(smem + fr.dir), fr.shift, fr.base, fr.nb, kr);
+  it = search_bucket<2>(reinterpret_cast<const uint64_t*>(smem + ft.keys),
+                        reinterpret_cast<const uint16_t*>(smem + ft.dir), ft.shift, ft.base, ft.nb, kt);
+  const int cr = min(ir, fr.n - 2), ct = min(it, ft.n - 2);
+  const int64_t cell = (int64_t)cr * (ft.n - 1) + ct;
+  float q[8];
+  ld_nc_v8(reinterpret_cast<const float*>(G + 2 * cell), q);
+  const Weights wr = fast_weights(smem, fr, ir, cr, kr, ur);
+  const Weights wt = fast_weights(smem, ft, it, ct, kt, ut);
+  const ff lo = ff_add_u(ff_mul_u(wt.wbar, ff{q[0], q[1]}), ff_mul_u(wt.w, ff{q[2], q[3]}));
+  const ff hi = ff_add_u(ff_mul_u(wt.wbar, ff{q[4], q[5]}), ff_mul_u(wt.w, ff{q[6], q[7]}));
+  v = nan ? __longlong_as_double(0x7FF8000000000000ll) : ff2d(ff_add_u(ff_mul_u(wr.wbar, lo), ff_mul_u(wr.w, hi)));
+}
+
+// Four blocks of 256 threads per SM (61 registers, no spills; the general
+// kernel's 80 registers allow three).  Two pairs per thread and step, as in
+// the general kernel: one pair per step measured 6 % slower.
+__global__ void __launch_bounds__(kNumThreads, 4) k_batched_2d_fast(BatchArgs2D a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bar;
+  __shared__ int s_tile;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  int cur = -1;
+  FastAxis fr{}, ft{};
+  bool ok = true;
+  int nans = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int t = s_tile;
+    __syncthreads();
+    if (t >= a.ntiles) break;
+    const Tile tile = a.tiles[t];
+    if (tile.table != cur) {
+      const unsigned char* br = a.blobs + a.blob_off[2 * tile.table];
+      const unsigned char* bt = a.blobs + a.blob_off[2 * tile.table + 1];
+      BlobHdr hcopy;
+      const int4* g4 = reinterpret_cast<const int4*>(br);
+      int4* c4 = reinterpret_cast<int4*>(&hcopy);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) c4[i] = __ldg(g4 + i);
+      int lo, hi;
+      staged_range(hcopy, lo, hi);
+      const int t_off = (((int)sizeof(BlobHdr) + hi - lo) + 127) & ~127;
+      const StagedView vr = stage_blob(br, smem, &bar, phase, ok);
+      if (!ok) break;
+      const StagedView vt = stage_blob(bt, smem + t_off, &bar, phase, ok);
+      if (!ok) break;
+      fr = fast_axis(vr, smem);
+      ft = fast_axis(vt, smem);
+      cur = tile.table;
+    }
+    const float4* G = a.cells + 2 * a.cell_off[tile.table];
+    const int64_t b = tile.begin;
+    const int cnt = tile.count;
+    auto scalar = [&](int i) {
+      int ir, it;
+      double v;
+      pair_fast(smem, fr, ft, G, a.Y2[2 * (b + i)], a.Y2[2 * (b + i) + 1], ir, it, v, nans);
+      a.idx[2 * (b + i)] = ir;
+      a.idx[2 * (b + i) + 1] = it;
+      a.val[b + i] = v;
+    };
+    if (!a.vec) {            // arrays off 16-byte alignment: scalar accesses
+      for (int i = threadIdx.x; i < cnt; i += blockDim.x) scalar(i);
+      continue;
+    }
+    const int head = min(cnt, (int)(b & 1));
+    const int np2 = (cnt - head) >> 1;
+    for (int i = threadIdx.x; i < head; i += blockDim.x) scalar(i);
+    const double2* Y = reinterpret_cast<const double2*>(a.Y2) + b + head;
+    int4* I4 = reinterpret_cast<int4*>(a.idx + 2 * (b + head));
+    double2* V2 = reinterpret_cast<double2*>(a.val + b + head);
+    for (int g = threadIdx.x; g < np2; g += blockDim.x) {
+      double2 p0, p1;
+      if (a.vec == 2) {
+        double y[4];
+        ld_stream4(reinterpret_cast<const double*>(Y + 2 * g), y);
+        p0 = make_double2(y[0], y[1]);
+        p1 = make_double2(y[2], y[3]);
+      } else {
+        p0 = ld_stream(Y + 2 * g);
+        p1 = ld_stream(Y + 2 * g + 1);
+      }
+      int i0, j0, i1, j1;
+      double v0, v1;
+      pair_fast(smem, fr, ft, G, p0.x, p0.y, i0, j0, v0, nans);
+      pair_fast(smem, fr, ft, G, p1.x, p1.y, i1, j1, v1, nans);
+      st_stream(I4 + g, make_int4(i0, j0, i1, j1));
+      st_stream(V2 + g, make_double2(v0, v1));
+    }
+    for (int i = head + 2 * np2 + threadIdx.x; i < cnt; i += blockDim.x) scalar(i);
+  }
+  nans = __reduce_add_sync(0xFFFFFFFFu, nans);
+  if (a.stat != nullptr && (threadIdx.x & 31) == 0 && nans) atomicAdd(&a.stat->nan_targets, (unsigned long long)nans);
+  if (a.stat != nullptr && threadIdx.x == 0 && !ok) atomicOr(&a.stat->flags, SS_FLAG_STAGING_TIMEOUT);
+}
+
+// Eligibility of a plan for the lean kernel: *not_fast stays 0 when every
+// axis is a bucket search over a whole staged table with at most two keys
+// per bucket and float-float cell data.
+__global__ void k_fast_2d_check(const unsigned char* __restrict__ blobs, const int64_t* __restrict__ blob_off,
+                                int naxes, unsigned* not_fast) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < naxes; j += gridDim.x * blockDim.x) {
+    const BlobHdr* h = reinterpret_cast<const BlobHdr*>(blobs + blob_off[j]);
+    if (!(h->algo == BL_BUCKET && h->stride == 1 && h->occ <= 2 && h->ffok == 1 && h->off_cells >= 0))
+      atomicOr(not_fast, 1u);
+  }
+}
+
+const void* batched_2d_fast_kernel() { return reinterpret_cast<const void*>(&k_batched_2d_fast); }
+
 // Kernel entry of the batched 2D lookup (template stubs stay local to this unit).
 const void* batched_2d_kernel(bool hunt, bool learned) {
   if (learned)

@@ -319,7 +319,26 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
   int family = 0;
   for (int a : p->algo) family = std::max(family, a == BL_MLP ? 2 : (a == BL_SPLINE || a == BL_LOGHASH) ? 1 : 0);
   if (p->kind == 1 && p->opts.model == SS_MODEL_HUNT) family = 3;          // the hunt's own instance
+  // 2D plans whose every axis takes the common path (bucket search over a
+  // whole staged axis, at most two keys per bucket, float-float cells) and
+  // no interpolation option run the lean kernel: fewer live registers, four
+  // blocks per SM instead of three
+  p->lean = 0;
+  if (p->kind == 2 && p->opts.model == SS_MODEL_NONE && !p->opts.extrap && !p->opts.logspace &&
+      p->d_grid64 == nullptr) {
+    if (p->d_counter == nullptr) SS_CHECK_CUDA(cudaMalloc(&p->d_counter, 2 * sizeof(int)));
+    SS_CHECK_CUDA(cudaMemsetAsync(p->d_counter, 0, sizeof(int), stream));
+    const int naxes = 2 * p->ntables;
+    k_fast_2d_check<<<std::max(1, std::min(1024, (naxes + 255) / 256)), 256, 0, stream>>>(
+        p->d_blobs, p->d_blob_off, naxes, reinterpret_cast<unsigned*>(p->d_counter));
+    SS_CHECK_CUDA(cudaGetLastError());
+    unsigned not_fast = 1;
+    SS_CHECK_CUDA(cudaMemcpyAsync(&not_fast, p->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
+    SS_CHECK_CUDA(cudaStreamSynchronize(stream));
+    p->lean = not_fast == 0 ? 1 : 0;
+  }
   if (p->kind == 1) kern = batched_1d_kernel(p->opts.side == SS_SIDE_LE, family);
+  else if (p->lean) kern = batched_2d_fast_kernel();
   else kern = batched_2d_kernel(p->opts.model == SS_MODEL_HUNT, family > 0);
   if (ss_status st_ = raise_smem_limit(kern, smem)) return st_;
   int per_sm = 0;

@@ -64,6 +64,7 @@ struct PlanBase {
   int kernels = 0;                    // kernels in the bound graph
   int smem_bytes = 0;
   int threads = 0;                    // threads per block of the bound batched kernel
+  int lean = 0;                       // 2D: the bound batch runs the lean kernel (every axis on the common path)
   // diagnostics
   int64_t device_bytes = 0;
   int max_window = 0;

@@ -613,6 +613,54 @@ def test_plan_2d_batched(ss, model, coherent):
     assert ss.read_stat(stat).flags == 0
 
 
+def test_plan_2d_lean_kernel(ss):
+    """The lean kernel runs when every axis is a bucket search over a whole
+    staged axis with at most two keys per bucket and float-float cells (the
+    standard batch); it gives the oracle's indices and values, on aligned
+    and misaligned arrays, with NaN pairs; plans outside its case (an
+    interpolation option, a position model, a binary-search axis) run the
+    general kernel."""
+    b = wl.batched_2d(ntables=20, pairs_per_table=5003, seed=27)
+    Y2 = b.Y2.clone()
+    Y2[7, 0] = float("nan")                 # a NaN coordinate: value NaN, indices exact
+    Y2[5000, 1] = float("nan")
+    wi, wv = oracle.search_interp_2d_batched(b.R_off.numpy(), b.R.numpy(), b.T_off.numpy(), b.T.numpy(),
+                                             b.F_off.numpy(), b.F.numpy(), b.Y_off.numpy(), Y2.numpy())
+    m = Y2.shape[0]
+
+    def run(plan, offset):
+        Yd = torch.empty((m + offset, 2), dtype=torch.float64, device=DEV)
+        Yd[offset:] = Y2.to(DEV)
+        idx = torch.full((m + offset, 2), -1, dtype=torch.int32, device=DEV)
+        val = torch.empty(m + offset, dtype=torch.float64, device=DEV)
+        stat = ss.new_stat()
+        plan.bind_2d(b.Y_off, Yd[offset:], idx[offset:], val[offset:], stat=stat)
+        plan.execute()
+        np.testing.assert_array_equal(idx[offset:].cpu().numpy(), wi)
+        if offset:
+            assert (idx[0].cpu().numpy() == -1).all()
+        got = val[offset:].cpu().numpy()
+        assert np.array_equal(np.isnan(got), np.isnan(wv))
+        ok = ~np.isnan(wv)
+        assert (np.abs(got[ok] - wv[ok]) / np.abs(wv[ok])).max() <= REL_TOL
+        st = ss.read_stat(stat)
+        assert st.flags == 0 and st.nan_targets == 2
+
+    plan = ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV))
+    for offset in (0, 1):
+        run(plan, offset)
+        assert plan.info().lean_kernel == 1 and plan.info().max_occupancy <= 2
+    run(ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), autotune=True), 0)
+    for kw in (dict(model="spline"), dict(algo="binary"), dict(extrap=True)):
+        other = ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), **kw)
+        if "extrap" not in kw:
+            run(other, 0)
+        else:
+            other.bind_2d(b.Y_off, Y2.to(DEV), torch.empty((m, 2), dtype=torch.int32, device=DEV),
+                          torch.empty(m, dtype=torch.float64, device=DEV))
+        assert other.info().lean_kernel == 0, kw
+
+
 @pytest.mark.parametrize("extrap,logspace", [(1, 0), (0, 1), (1, 1)])
 def test_plan_2d_interpolation_options(ss, extrap, logspace):
     """2D plans with linear extrapolation / log-coordinate weights: pairs
