@@ -95,6 +95,8 @@ typedef struct ss_devstat {
 #define SS_FLAG_NOT_SORTED 0x1u     /* a table was not strictly increasing (or held NaN) */
 #define SS_FLAG_BAD_VALUE 0x2u      /* a 2D value-path precondition failed; fp64 path used */
 #define SS_FLAG_STAGING_TIMEOUT 0x4u /* a shared-memory staging copy did not complete in time; outputs incomplete */
+#define SS_FLAG_BOUNDS 0x8u          /* bounds-checked build only: an index outside its array was caught (the
+                                        read was skipped); see ss_checked_hits */
 
 /* ---------------------------------------------------------------------- */
 /* One-shot calls: no set-up kept between calls ("zero set-up cost",       */
@@ -349,6 +351,20 @@ ss_status ss_search_1d_batched_static(int32_t ntables, const int64_t* X_off, con
  * stream is still busy at the deadline; *out is then left untouched. */
 ss_status ss_sync_status(cudaStream_t stream, const ss_devstat* stat, ss_devstat* out,
                          int32_t timeout_ms);
+
+/* Bounds-checked build (the library compiled with -DSS_CHECKED; the paper
+ * has no counterpart: a debugging aid).  In that build the staging of a
+ * table, the wide-section search, the learned windows, the hunt and the
+ * searches in global memory check every index against its array; an index
+ * outside is not used (the read is skipped), the kernel sets SS_FLAG_BOUNDS
+ * in the caller's status record, and the count of such indices is kept on
+ * each device.  ss_checked_hits waits for the device, adds the counts of
+ * every part of the library into *hits and, if reset is nonzero, clears
+ * them.  ss_checked_selftest launches one check of an index that is out of
+ * range (no memory is read) so that a test can see the count move.  Both
+ * return SS_EUNSUPPORTED in the ordinary build. */
+ss_status ss_checked_hits(uint64_t* hits, int32_t reset);
+ss_status ss_checked_selftest(void);
 
 /* Message of the last failing call on this host thread ("" if none). */
 const char* ss_last_error(void);

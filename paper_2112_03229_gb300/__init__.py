@@ -46,14 +46,23 @@ _lib = None
 _vp, _i32, _i64 = C.c_void_p, C.c_int32, C.c_int64
 
 
+def lib_path():
+    """Path of the library this process loads: libsimdsearch.so, or the
+    bounds-checked build when SS_CHECKED_LIBRARY=1 is set in the environment."""
+    if os.environ.get("SS_CHECKED_LIBRARY") == "1":
+        return os.path.join(os.path.dirname(LIB_PATH), "libsimdsearch_checked.so")
+    return LIB_PATH
+
+
 def lib():
     """The loaded CUDA library (raises if it has not been built)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libsimdsearch.so is not built (run __graft_entry__.build()); "
-                               "this package has no CPU fallback")
-        L = C.CDLL(LIB_PATH)
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError("%s is not built (run __graft_entry__.build()); "
+                               "this package has no CPU fallback" % os.path.basename(path))
+        L = C.CDLL(path)
         L.ss_last_error.restype = C.c_char_p
         L.ss_version.restype = _i32
         L.ss_search_1d.argtypes = [_vp, _i32, _vp, _i64, _vp, _i32, _i32, _vp, _vp]
@@ -64,12 +73,24 @@ def lib():
         L.ss_mlp_loss_grad.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp, _vp]
         L.ss_mlp_forward.argtypes = [_vp, _vp, _i64, _vp, _vp]
         L.ss_mlp_adam_step.argtypes = [_vp, _vp, _vp, _vp, _i32, C.c_float, C.c_float, C.c_float, C.c_float, _vp]
+        L.ss_checked_hits.argtypes = [C.POINTER(C.c_uint64), _i32]
+        L.ss_checked_hits.restype = _i32
+        L.ss_checked_selftest.argtypes = []
+        L.ss_checked_selftest.restype = _i32
         for name in ("ss_search_1d", "ss_search_1d_tuned", "ss_search_interp_2d", "ss_search_interp_2d_fp64",
                      "ss_sync_status",
                      "ss_mlp_loss_grad", "ss_mlp_forward", "ss_mlp_adam_step"):
             getattr(L, name).restype = _i32
         _lib = L
     return _lib
+
+
+def checked_hits(reset=False) -> int:
+    """ss_checked_hits: indices caught out of range since the last reset
+    (bounds-checked build only; raises SSError otherwise)."""
+    v = C.c_uint64(0)
+    _check(lib().ss_checked_hits(C.byref(v), 1 if reset else 0))
+    return int(v.value)
 
 
 def _check(code):

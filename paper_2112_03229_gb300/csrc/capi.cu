@@ -6,6 +6,7 @@
 #include <string>
 #include <thread>
 #include <utility>
+#include <vector>
 
 #include "ss_common.cuh"
 
@@ -55,9 +56,51 @@ ss_status raise_smem_limit(const void* kernel, int smem) {
   return SS_OK;
 }
 
+#ifdef SS_CHECKED
+static std::vector<ss_status (*)(unsigned long long*, bool)>& bounds_counters() {
+  static std::vector<ss_status (*)(unsigned long long*, bool)> v;
+  return v;
+}
+
+void register_bounds_counter(ss_status (*read)(unsigned long long*, bool)) { bounds_counters().push_back(read); }
+
+// One check of an index past the end of a 3-entry array: counted, never read.
+__global__ void k_checked_selftest(int i) { (void)SS_IX(i, 3); }
+#endif
+
 }  // namespace ss
 
 extern "C" {
+
+ss_status ss_checked_hits(uint64_t* hits, int32_t reset) {
+#ifdef SS_CHECKED
+  if (hits == nullptr) return ss::fail(SS_EINVAL, "ss_checked_hits: null pointer");
+  SS_CHECK_CUDA(cudaDeviceSynchronize());
+  uint64_t sum = 0;
+  for (auto read : ss::bounds_counters()) {
+    unsigned long long v = 0;
+    if (ss_status st = read(&v, reset != 0)) return st;
+    sum += v;
+  }
+  *hits = sum;
+  return SS_OK;
+#else
+  (void)hits;
+  (void)reset;
+  return ss::fail(SS_EUNSUPPORTED, "ss_checked_hits: the library was built without -DSS_CHECKED");
+#endif
+}
+
+ss_status ss_checked_selftest(void) {
+#ifdef SS_CHECKED
+  ss::k_checked_selftest<<<1, 1>>>(5);
+  SS_CHECK_CUDA(cudaGetLastError());
+  SS_CHECK_CUDA(cudaDeviceSynchronize());
+  return SS_OK;
+#else
+  return ss::fail(SS_EUNSUPPORTED, "ss_checked_selftest: the library was built without -DSS_CHECKED");
+#endif
+}
 
 const char* ss_last_error(void) { return ss::g_last_error.c_str(); }
 

@@ -655,6 +655,7 @@ __global__ void __launch_bounds__(kPlanMaxThreads, 2) k_batched_1d(BatchArgs1D a
     if (fallbacks) atomicAdd(&a.stat->fallbacks, (unsigned long long)fallbacks);
   }
   if (a.stat != nullptr && threadIdx.x == 0 && s_err) atomicOr(&a.stat->flags, SS_FLAG_STAGING_TIMEOUT);
+  SS_BOUNDS_FOLD(a.stat);
 }
 
 // Persistent batched search over tables with a wide section: one block of
@@ -705,6 +706,7 @@ __global__ void __launch_bounds__(kWideThreads, 1) k_batched_1d_wide(BatchArgs1D
   nans = __reduce_add_sync(0xFFFFFFFFu, nans);
   if (a.stat != nullptr && (threadIdx.x & 31) == 0 && nans) atomicAdd(&a.stat->nan_targets, (unsigned long long)nans);
   if (a.stat != nullptr && threadIdx.x == 0 && s_err) atomicOr(&a.stat->flags, SS_FLAG_STAGING_TIMEOUT);
+  SS_BOUNDS_FOLD(a.stat);
 }
 
 const void* batched_1d_wide_kernel(bool le) {

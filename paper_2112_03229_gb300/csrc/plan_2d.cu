@@ -354,6 +354,7 @@ __global__ void __launch_bounds__(kNumThreads, 3) k_batched_2d(BatchArgs2D a) {
     if (fallbacks) atomicAdd(&a.stat->fallbacks, (unsigned long long)fallbacks);
   }
   if (a.stat != nullptr && threadIdx.x == 0 && !ok) atomicOr(&a.stat->flags, SS_FLAG_STAGING_TIMEOUT);
+  SS_BOUNDS_FOLD(a.stat);
 }
 
 // ---------------------------------------------------------------------------
@@ -390,7 +391,12 @@ __device__ __forceinline__ Weights fast_weights(const unsigned char* smem, const
                                                 uint64_t u) {
   if (i >= f.n - 1) return {{1.0f, 0.0f}, {0.0f, 0.0f}};
   if (i == 0 && k <= f.k0) return {{0.0f, 0.0f}, {1.0f, 0.0f}};
+#ifdef SS_CHECKED
+  const CellTable t{reinterpret_cast<const ulonglong2*>(smem + f.ca), reinterpret_cast<const float2*>(smem + f.cg),
+                    f.n - 1};
+#else
   const CellTable t{reinterpret_cast<const ulonglong2*>(smem + f.ca), reinterpret_cast<const float2*>(smem + f.cg)};
+#endif
   return cell_weights(u, t, c);
 }
 
@@ -501,6 +507,7 @@ __global__ void __launch_bounds__(kNumThreads, 4) k_batched_2d_fast(BatchArgs2D 
   nans = __reduce_add_sync(0xFFFFFFFFu, nans);
   if (a.stat != nullptr && (threadIdx.x & 31) == 0 && nans) atomicAdd(&a.stat->nan_targets, (unsigned long long)nans);
   if (a.stat != nullptr && threadIdx.x == 0 && !ok) atomicOr(&a.stat->flags, SS_FLAG_STAGING_TIMEOUT);
+  SS_BOUNDS_FOLD(a.stat);
 }
 
 // Eligibility of a plan for the lean kernel: *not_fast stays 0 when every

@@ -69,4 +69,58 @@ ss_status raise_smem_limit(const void* kernel, int smem);   // raise-only, threa
 
 inline bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
+// ---------------------------------------------------------------------------
+// Bounds-checked build (-DSS_CHECKED).  SS_IX(i, n) is index i of an array
+// of n entries: in the ordinary build it is i itself; in the checked build
+// an index outside [0, n) is counted (per translation unit, in device
+// memory) and replaced by 0, so the read that follows stays inside the
+// array instead of faulting.  SS_BOUNDS_FOLD(stat) at the end of a kernel
+// sets SS_FLAG_BOUNDS in the caller's status record when the count of this
+// unit is not zero.  ss_checked_hits (C ABI) adds up the counts of every
+// unit: each unit registers a reader of its own counter at load time.
+// ---------------------------------------------------------------------------
+#ifdef SS_CHECKED
+static __device__ unsigned long long g_ss_bounds_hits;
+
+__device__ __forceinline__ int ss_checked_index(int i, int n) {
+  if ((unsigned)i < (unsigned)n) return i;
+  atomicAdd(&g_ss_bounds_hits, 1ull);
+  return 0;
+}
+
+__device__ __forceinline__ void ss_checked_flag(bool bad) {
+  if (bad) atomicAdd(&g_ss_bounds_hits, 1ull);
+}
+
+void register_bounds_counter(ss_status (*read)(unsigned long long*, bool));
+
+static ss_status read_bounds_counter(unsigned long long* v, bool reset) {
+  SS_CHECK_CUDA(cudaMemcpyFromSymbol(v, g_ss_bounds_hits, sizeof(*v)));
+  if (reset) {
+    const unsigned long long zero = 0;
+    SS_CHECK_CUDA(cudaMemcpyToSymbol(g_ss_bounds_hits, &zero, sizeof(zero)));
+  }
+  return SS_OK;
+}
+
+namespace {
+struct BoundsCounterRegistration {
+  BoundsCounterRegistration() { register_bounds_counter(&read_bounds_counter); }
+};
+static BoundsCounterRegistration g_bounds_registration;
+}  // namespace
+
+#define SS_IX(i, n) ::ss::ss_checked_index((i), (n))
+#define SS_CHECK(bad) ::ss::ss_checked_flag(bad)
+#define SS_BOUNDS_FOLD(stat)                                                              \
+  do {                                                                                    \
+    if ((stat) != nullptr && threadIdx.x == 0 && ::ss::g_ss_bounds_hits != 0)            \
+      atomicOr(&(stat)->flags, SS_FLAG_BOUNDS);                                           \
+  } while (0)
+#else
+#define SS_IX(i, n) (i)
+#define SS_CHECK(bad) ((void)0)
+#define SS_BOUNDS_FOLD(stat) ((void)0)
+#endif
+
 }  // namespace ss

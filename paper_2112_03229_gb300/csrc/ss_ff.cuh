@@ -102,11 +102,18 @@ constexpr int kCellBytes = 24;
 struct CellTable {
   const ulonglong2* a;
   const float2* g;
+#ifdef SS_CHECKED
+  int n;                // cells (checked build)
+#endif
 };
 
 __device__ __forceinline__ CellTable cell_table(const void* region, int ncell) {
   const ulonglong2* a = reinterpret_cast<const ulonglong2*>(region);
+#ifdef SS_CHECKED
+  return {a, reinterpret_cast<const float2*>(a + ncell), ncell};
+#else
   return {a, reinterpret_cast<const float2*>(a + ncell)};
+#endif
 }
 
 __device__ __forceinline__ void store_cell(void* region, int ncell, int c, const CellW& w) {
@@ -162,6 +169,9 @@ __device__ __forceinline__ ff one_minus(ff a) {
 // subtraction loses nothing relative to its size.  Both weights so keep
 // their full relative precision (however small the smaller one is).
 __device__ __forceinline__ Weights cell_weights(uint64_t u, const CellTable& t, int c) {
+#ifdef SS_CHECKED
+  c = SS_IX(c, t.n);
+#endif
   const ulonglong2 rec = t.a[c];
   const int ec = (int)(rec.x >> 53);
   const uint64_t Mc = rec.x & ((1ull << 53) - 1), MnS = rec.y;

@@ -164,6 +164,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
@@ -216,15 +220,48 @@ __device__ __forceinline__ StagedView stage_blob(const unsigned char* __restrict
   for (int i = 0; i < 8; ++i) hp[i] = __ldg(gh4 + i);
   int lo, hi;
   staged_range(hdr, lo, hi);
+#ifdef SS_CHECKED
+  // the staged bytes must fit the block's dynamic shared memory from dst on,
+  // and every array the table's search reads must lie inside the staged range
+  bool fits;
+  {
+    extern __shared__ unsigned char ss_dynamic_smem[];
+    uint32_t dyn;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    fits = dst >= ss_dynamic_smem && dst + sizeof(BlobHdr) + (hi - lo) <= ss_dynamic_smem + dyn && hi >= lo;
+    auto inside = [&](int off, int64_t bytes) { return off >= lo && (int64_t)off + bytes <= (int64_t)hi; };
+    const int a = hdr.algo;
+    const bool keys = a == BL_BUCKET || a == BL_SPLINE || a == BL_MLP || a == BL_LOGHASH ||
+                      (a >= BL_BALLOT8 && a <= BL_BALLOT32) || hdr.off_cells >= 0;
+    const bool dir = a == BL_BUCKET || a == BL_SPLINE || a == BL_MLP || a == BL_LOGHASH;
+    bool ok_arrays = true;
+    if (keys) ok_arrays &= inside(hdr.off_keys, (int64_t)(hdr.ns + kPad) * 8);
+    if (dir) ok_arrays &= inside(hdr.off_dir, (int64_t)(hdr.nb + 1) * 2) && hdr.nb <= hdr.dir_cap;
+    if (a == BL_MLP || a == BL_LOGHASH) ok_arrays &= inside(hdr.off_mlp, kMlpBytes);
+    if (a == BL_BINARY) ok_arrays &= inside(hdr.off_eyt, (int64_t)8 << hdr.D);
+    if (hdr.off_cells >= 0) ok_arrays &= inside(hdr.off_cells, (int64_t)(hdr.n - 1) * kCellBytes);
+    if (threadIdx.x == 0) SS_CHECK(!fits || !ok_arrays);
+  }
+#endif
   __syncthreads();          // previous users of dst are done
   if (threadIdx.x == 0) {
     fence_proxy_async();
     const uint32_t bytes = (uint32_t)(sizeof(BlobHdr) + (hi - lo));
-    mbar_expect_tx(bar, bytes);
-    tma_load_1d(dst, src, (uint32_t)sizeof(BlobHdr), bar);
-    if (hi > lo) tma_load_1d(dst + sizeof(BlobHdr), src + lo, (uint32_t)(hi - lo), bar);
+#ifdef SS_CHECKED
+    if (!fits) {
+      mbar_arrive(bar);     // nothing copied: the phase completes, the block gives up below
+    } else
+#endif
+    {
+      mbar_expect_tx(bar, bytes);
+      tma_load_1d(dst, src, (uint32_t)sizeof(BlobHdr), bar);
+      if (hi > lo) tma_load_1d(dst + sizeof(BlobHdr), src + lo, (uint32_t)(hi - lo), bar);
+    }
   }
   ok &= mbar_wait(bar, phase);
+#ifdef SS_CHECKED
+  ok &= fits;
+#endif
   ok = __syncthreads_and(ok);          // uniform outcome for the whole block
   phase ^= 1u;
   const int shift_off = (int)sizeof(BlobHdr) - lo;     // smem position of blob offset o is o + shift_off
@@ -285,36 +322,39 @@ __device__ __forceinline__ int count_ge15(const uint4& a, const uint4& b, uint32
 // the keys whose offset equals the target's are compared in full.
 template <int SCAN>
 __device__ __forceinline__ int wide_count(const WideView& wv, uint64_t q) {
+  const int nsamp = wv.w.L + kPad, ndir = wv.w.dcap + 1;   // array sizes (checked build)
+  (void)nsamp;
+  (void)ndir;
   const int bk = bucket_index(q, wv.w.shift, wv.w.base, wv.w.nb);
-  const int lo = wv.dir[bk];
+  const int lo = wv.dir[SS_IX(bk, ndir)];
   int s = lo;
   uint64_t base;                                 // last key of the previous leaf
   if (SCAN >= 1) {
     // samples past the bucket are larger than q, or sentinels; the leaf's base
     // is one of the samples just compared unless no sample is below q
-    const uint64_t k0 = wv.samples[lo], k1 = SCAN >= 2 ? wv.samples[lo + 1] : 0;
+    const uint64_t k0 = wv.samples[SS_IX(lo, nsamp)], k1 = SCAN >= 2 ? wv.samples[SS_IX(lo + 1, nsamp)] : 0;
     s += (k0 < q ? 1 : 0) + (SCAN >= 2 && k1 < q ? 1 : 0);
     if (s >= wv.w.L) return wv.nk;
-    base = s == lo ? (lo > 0 ? wv.samples[lo - 1] : wv.k0) : (s == lo + 1 ? k0 : k1);
+    base = s == lo ? (lo > 0 ? wv.samples[SS_IX(lo - 1, nsamp)] : wv.k0) : (s == lo + 1 ? k0 : k1);
   } else {
-    int len = wv.dir[bk + 1] - s;
+    int len = wv.dir[SS_IX(bk + 1, ndir)] - s;
     const int T = 32 - __clz(wv.w.occ);
     for (int it = 0; it < T; ++it) {
       const int half = len >> 1;
-      const bool go = len > 0 && wv.samples[s + half] < q;
+      const bool go = len > 0 && wv.samples[SS_IX(s + half, nsamp)] < q;
       s = go ? s + half + 1 : s;
       len = go ? len - half - 1 : half;
     }
     if (s >= wv.w.L) return wv.nk;
-    base = s > 0 ? wv.samples[s - 1] : wv.k0;
+    base = s > 0 ? wv.samples[SS_IX(s - 1, nsamp)] : wv.k0;
   }
   if (q <= base) return kLeaf * s;               // only below X[0] (leaf 0)
-  const uint32_t tq = (uint32_t)((q - base) >> wv.shifts[s]);   // < 2^15: q <= samples[s]
+  const uint32_t tq = (uint32_t)((q - base) >> wv.shifts[SS_IX(s, wv.w.L)]);   // < 2^15: q <= samples[s]
   // the two halves of a leaf sit in two arrays of 16-byte entries: read at a
   // 16-byte stride, a warp's random leaves spread over all shared-memory banks
   // (one 32-byte leaf read as two 16-byte halves used half of them)
   const uint4* l4 = reinterpret_cast<const uint4*>(wv.leaf);
-  const uint4 a = l4[s], b = l4[wv.w.L + s];
+  const uint4 a = l4[SS_IX(s, wv.w.L)], b = l4[SS_IX(wv.w.L + s, 2 * wv.w.L)];
   int c = kLeaf - count_ge15(a, b, tq);                          // offsets below the target's
   // a leaf's offsets never decrease, so offsets equal to the target's (whose
   // keys are compared in full) start at position c; offset c, picked from the
@@ -327,7 +367,7 @@ __device__ __forceinline__ int wide_count(const WideView& wv, uint64_t q) {
     const int le = kLeaf - count_ge15(a, b, tq + 1);             // offsets at most the target's
     for (; c < le; ++c) {
       const int j = kLeaf * s + c;
-      if (j >= wv.nk || __ldg(wv.full + j) >= q) break;
+      if (j >= wv.nk || __ldg(wv.full + SS_IX(j, wv.nk + kPad)) >= q) break;
     }
   }
   return kLeaf * s + c;
@@ -341,7 +381,7 @@ __device__ __forceinline__ int finish_full(const StagedView& v, int c, uint64_t 
   int len = min(h.stride, h.nk - lo);
   while (len > 0) {
     const int half = len >> 1;
-    if (__ldg(v.full + lo + half) < q) { lo += half + 1; len -= half + 1; } else { len = half; }
+    if (__ldg(v.full + SS_IX(lo + half, h.nk + kPad)) < q) { lo += half + 1; len -= half + 1; } else { len = half; }
   }
   return lo;
 }
@@ -349,7 +389,7 @@ __device__ __forceinline__ int finish_full(const StagedView& v, int c, uint64_t 
 // Key i (0-based among X[1..n-1]) of the table, from shared memory when the
 // whole table is staged, else from the global full keys.
 __device__ __forceinline__ uint64_t key_at(const StagedView& v, int i) {
-  return v.h.stride == 1 ? v.keys[i] : __ldg(v.full + i);
+  return v.h.stride == 1 ? v.keys[SS_IX(i, v.h.ns + kPad)] : __ldg(v.full + SS_IX(i, v.h.nk + kPad));
 }
 
 // Plain count of keys below q with the bucket directory (any occupancy).
@@ -407,10 +447,12 @@ __device__ __forceinline__ int learned_count(const StagedView& v, int p, uint64_
   int c;
   if (h.stride == 1) {
     const uint64_t* keys = v.keys;
-    c = window_count([keys](int i) { return keys[i]; }, h.nk, h.E, p, q, ok);
+    const int lim = h.ns + kPad;
+    c = window_count([keys, lim](int i) { return keys[SS_IX(i, lim)]; }, h.nk, h.E, p, q, ok);
   } else {
     const uint64_t* full = v.full;
-    c = window_count([full](int i) { return __ldg(full + i); }, h.nk, h.E, p, q, ok);
+    const int lim = h.nk + kPad;
+    c = window_count([full, lim](int i) { return __ldg(full + SS_IX(i, lim)); }, h.nk, h.E, p, q, ok);
   }
   if (!ok) {
     ++fallbacks;
@@ -478,10 +520,12 @@ __device__ __forceinline__ int hunt_count(const StagedView& v, int p, uint64_t q
   if (p < 0) return plain(q);
   if (h.stride == 1) {
     const uint64_t* keys = v.keys;
-    return hunt_from([keys](int i) { return keys[i]; }, h.nk, p, q, plain);
+    const int lim = h.ns + kPad;
+    return hunt_from([keys, lim](int i) { return keys[SS_IX(i, lim)]; }, h.nk, p, q, plain);
   }
   const uint64_t* full = v.full;
-  return hunt_from([full](int i) { return __ldg(full + i); }, h.nk, p, q, plain);
+  const int lim = h.nk + kPad;
+  return hunt_from([full, lim](int i) { return __ldg(full + SS_IX(i, lim)); }, h.nk, p, q, plain);
 }
 
 // Spline proposal in count units of the whole table.  A sampled (two-level)

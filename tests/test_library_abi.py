@@ -109,6 +109,16 @@ def test_static_batched_offset_messages_without_gpu(built):
     assert call([0, 4, 8], [0, 1, 2], side=3)[0] == 1
 
 
+def test_checked_entry_points_in_the_ordinary_build(built):
+    # the bounds-checked build's counters exist only with -DSS_CHECKED
+    import paper_2112_03229_gb300 as ss
+    L = ss.lib()
+    v = ctypes.c_uint64(7)
+    assert L.ss_checked_hits(ctypes.byref(v), 0) == 6 and v.value == 7
+    assert b"SS_CHECKED" in L.ss_last_error()
+    assert L.ss_checked_selftest() == 6
+
+
 def plan_file_version():
     src = open(os.path.join(ROOT, "paper_2112_03229_gb300", "csrc", "plan_io.cu")).read()
     return int(re.search(r"kVersion = (\d+);", src).group(1))
