@@ -288,11 +288,17 @@ void ss_plan_destroy(ss_plan* plan);
  * Y[Y_off[k] .. Y_off[k+1]); X_off and Y_off are host arrays of ntables+1
  * entries (Y_off non-decreasing, empty tables allowed), X, Y and lowbounds
  * device arrays; table k's answers go to the same positions of lowbounds.
- * The call prepares the tables, runs the batch as one persistent launch on
- * `stream`, waits for it and releases the device memory it allocated, so the
- * results are written when it returns.  SS_ENOTSORTED if a table is not
- * strictly increasing (nothing is written then).  Callers that search the
- * same tables again should keep a plan: its preparation is paid once. */
+ * The 1D call is asynchronous on `stream`: it lays the batch out on the
+ * host from the offsets, takes its working memory (prepared tables, tiles)
+ * from the stream-ordered allocator, and queues the preparation, one
+ * persistent launch of the bucket search and the release of that memory;
+ * X, Y and lowbounds must stay valid until the stream reaches that point.
+ * A table that is not strictly increasing sets SS_FLAG_NOT_SORTED in *stat
+ * (its indices are then unspecified but in [0, n-1]; the other tables' are
+ * exact).  Bad offsets are refused with SS_EINVAL naming the table; a
+ * stream being captured is refused with SS_EUNSUPPORTED (the metadata is
+ * copied from pageable host memory).  Callers that search the same tables
+ * again should keep a plan: its preparation is paid once. */
 ss_status ss_search_1d_batched(int32_t ntables, const int64_t* X_off, const double* X,
                                const int64_t* Y_off, const double* Y, int32_t* lowbounds,
                                int32_t side, ss_devstat* stat, cudaStream_t stream);
@@ -301,7 +307,12 @@ ss_status ss_search_1d_batched(int32_t ntables, const int64_t* X_off, const doub
  * nr_k x nt_k grid F[F_off[k] ..]; its pairs are Y2[2 Y_off[k] ..
  * 2 Y_off[k+1]) interleaved (rho, T); lowbounds2 receives interleaved index
  * pairs and values one double per pair.  Offsets are host arrays, the rest
- * device arrays; synchronous like the 1D form. */
+ * device arrays.  The call prepares a plan without a model, runs the batch
+ * as one persistent launch on `stream`, waits for it and releases the
+ * plan, so the results are written when it returns.  SS_ENOTSORTED if an
+ * axis is not strictly increasing (nothing is written then).  The 2D lookup
+ * uses side SS_SIDE_LT (the cell of a target equal to an axis entry is the
+ * one above it either way, and so is the interpolated value). */
 ss_status ss_search_interp_2d_batched(int32_t ntables, const int64_t* R_off, const double* R,
                                       const int64_t* T_off, const double* T, const int64_t* F_off,
                                       const double* F, const int64_t* Y_off, const double* Y2,

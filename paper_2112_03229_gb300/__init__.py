@@ -429,7 +429,8 @@ def _batched_lib():
 
 def search_1d_batched(X_off, X, Y_off, Y, out=None, side=SIDE_LT, stat=None, stream=None):
     """ss_search_1d_batched: one call over many tables (table k = X[X_off[k]:X_off[k+1]],
-    its targets Y[Y_off[k]:Y_off[k+1]]); synchronous."""
+    its targets Y[Y_off[k]:Y_off[k+1]]); asynchronous on `stream` (default: the
+    current stream); an unsorted table sets FLAG_NOT_SORTED in `stat`."""
     L = _batched_lib()
     xo, xp = _offsets(X_off, "X_off", data=X)
     yo, yp = _offsets(Y_off, "Y_off", length=len(xo), data=Y)

@@ -1,8 +1,18 @@
 // batched_oneshot.cu -- the batched searches (Sec. 1 and 2.2 applied to many
-// tables at once) as single calls: a plan without a model is prepared, bound
-// to the caller's batch, executed once and released.  The call waits for the
-// launch before releasing the plan's memory, so it is synchronous; callers
-// that search the same tables again keep a plan instead and pay the
+// tables at once) as single calls.
+//
+// 1D: asynchronous on the caller's stream.  The host lays the batch out from
+// the offsets alone; a stream-ordered allocation holds the prepared tables
+// and tiles; the preparation, the persistent bucket search and the release
+// of that memory are queued behind each other, and the call returns without
+// waiting.  A table that is not strictly increasing is flagged in the
+// caller's status record (SS_FLAG_NOT_SORTED) by the preparation on the GPU.
+//
+// 2D: a plan without a model is prepared, bound to the caller's batch,
+// executed once and released; the call waits for the launch before
+// releasing the plan's memory, so it is synchronous.
+//
+// Callers that search the same tables again keep a plan instead and pay the
 // preparation once (Sec. 5.3).
 #include <string>
 
@@ -38,12 +48,27 @@ ss_status run_and_release(ss_plan* p, Bind&& bind, cudaStream_t stream) {
 extern "C" ss_status ss_search_1d_batched(int32_t ntables, const int64_t* X_off, const double* X,
                                           const int64_t* Y_off, const double* Y, int32_t* lowbounds, int32_t side,
                                           ss_devstat* stat, cudaStream_t stream) {
-  if (Y_off == nullptr) return ss::fail(SS_EINVAL, "ss_search_1d_batched: null pointer");
-  const ss_plan_opts o = oneshot_opts(side);
-  ss_plan* p = nullptr;
-  if (ss_status st = ss_plan_create_1d(&p, ntables, X_off, X, &o, stream)) return st;
-  return run_and_release(
-      p, [&](ss_plan* q) { return ss_plan_bind_1d(q, Y_off, Y, lowbounds, stat, stream); }, stream);
+  using namespace ss;
+  const char* me = "ss_search_1d_batched";
+  if (X_off == nullptr || Y_off == nullptr || X == nullptr) return fail(SS_EINVAL, std::string(me) + ": null pointer");
+  if (ntables < 1) return fail(SS_EINVAL, std::string(me) + ": ntables must be >= 1");
+  if (side != SS_SIDE_LT && side != SS_SIDE_LE) return fail(SS_EINVAL, std::string(me) + ": bad side");
+  if (Y_off[ntables] > 0 && (Y == nullptr || lowbounds == nullptr)) return fail(SS_EINVAL, std::string(me) + ": null pointer");
+  if (!aligned(X, 8) || !aligned(Y, 8) || !aligned(lowbounds, 4)) return fail(SS_EINVAL, std::string(me) + ": misaligned pointer");
+  BatchWork1D w;
+  if (ss_status st = batch_work_1d(me, ntables, X_off, Y_off, SS_MAX_DIR_CAP, w)) return st;
+  // the metadata is copied from pageable host memory, which a stream being
+  // captured into a graph cannot take: refused before anything is queued
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  SS_CHECK_CUDA(cudaStreamIsCapturing(stream, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(SS_EUNSUPPORTED, std::string(me) + ": the stream is capturing; keep a plan to replay in a graph");
+  unsigned char* base = nullptr;
+  SS_CHECK_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&base), (size_t)w.end, stream));
+  const ss_status st = queue_work_1d(w, base, ntables, X_off, X, Y, lowbounds, side, stat, stream);
+  const cudaError_t e = cudaFreeAsync(base, stream);        // after the queued work, on every path
+  if (st != SS_OK) return st;
+  return e == cudaSuccess ? SS_OK : cuda_fail(e, "cudaFreeAsync");
 }
 
 extern "C" ss_status ss_search_interp_2d_batched(int32_t ntables, const int64_t* R_off, const double* R,

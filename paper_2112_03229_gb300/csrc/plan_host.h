@@ -73,6 +73,25 @@ struct PlanBase {
   int max_occupancy = 0;              // most keys in one bucket over the tables staged whole
 };
 
+// A batched 1D search in one caller-provided device buffer (batched_work.cu):
+// per table its directory budget, algorithm (the bucket search) and blob
+// offset, the tiles, and the byte offsets of each part inside the buffer.
+struct BatchWork1D {
+  std::vector<int> caps, algo;
+  std::vector<int64_t> blob_off;
+  std::vector<Tile> tiles;
+  int smem = 0;
+  int64_t counter = 0, flag = 0, xoff = 0, boff = 0, caps_off = 0, algo_off = 0, tiles_off = 0, blobs_off = 0, end = 0;
+};
+// Host checks of the offsets (each bad one refused with a message naming the
+// table) and the layout; nothing is queued.
+ss_status batch_work_1d(const char* me, int32_t ntables, const int64_t* X_off, const int64_t* Y_off,
+                        int dir_cap_max, BatchWork1D& w);
+// Metadata copies, table preparation and the persistent search, queued on stream.
+ss_status queue_work_1d(const BatchWork1D& w, unsigned char* base, int32_t ntables, const int64_t* X_off,
+                        const double* X, const double* Y, int32_t* lowbounds, int32_t side, ss_devstat* stat,
+                        cudaStream_t stream);
+
 ss_status plan_build_1d(ss_plan* p, const double* X, cudaStream_t stream);
 ss_status plan_build_2d(ss_plan* p, const double* R, const double* T, const double* F, cudaStream_t stream);
 ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double* Y, int32_t* out, double* val,

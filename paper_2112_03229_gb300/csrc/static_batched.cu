@@ -28,8 +28,6 @@
 
 namespace ss {
 
-int default_dir_cap(int n);
-
 constexpr size_t kStaticScratchBytes = size_t(8) << 20;   // 8 MiB per GPU
 constexpr int kStaticDirCap = 2048;                        // bucket budget per table here
 
@@ -63,67 +61,6 @@ static ss_status static_device(StaticDevice** out) {
   return SS_OK;
 }
 
-// Byte offsets inside the array: tile counter, table-check flag, table
-// offsets, blob offsets, directory budgets, algorithms, tiles, then the
-// prepared tables.
-struct StaticLayout {
-  int64_t counter, flag, xoff, boff, caps, algo, tiles, blobs, end;
-};
-
-static StaticLayout static_layout(int ntables, size_t ntiles, int64_t blob_bytes) {
-  auto up = [](int64_t b) { return (b + 255) & ~(int64_t)255; };
-  StaticLayout l;
-  l.counter = 0;
-  l.flag = 256;
-  l.xoff = 512;
-  l.boff = l.xoff + up((int64_t)(ntables + 1) * 8);
-  l.caps = l.boff + up((int64_t)ntables * 8);
-  l.algo = l.caps + up((int64_t)ntables * 4);
-  l.tiles = l.algo + up((int64_t)ntables * 4);
-  l.blobs = l.tiles + up((int64_t)ntiles * (int64_t)sizeof(Tile));
-  l.end = l.blobs + blob_bytes;
-  return l;
-}
-
-// The work of one call, queued on `stream`: metadata into the array,
-// preparation of the tables there, and the persistent search over the tiles.
-static ss_status queue_static(const StaticLayout& l, unsigned char* base, int32_t ntables, const int64_t* X_off,
-                              const double* X, const double* Y, int32_t* lowbounds, int32_t side, ss_devstat* stat,
-                              const std::vector<int64_t>& blob_off, const std::vector<int>& caps,
-                              const std::vector<int>& algo, const std::vector<Tile>& tiles, int smem,
-                              cudaStream_t stream) {
-  // the copies read pageable host memory, which the runtime stages before
-  // returning, so the host vectors may go out of scope
-  SS_CHECK_CUDA(cudaMemsetAsync(base + l.counter, 0, 512, stream));   // tile counter and table-check flag
-  SS_CHECK_CUDA(cudaMemcpyAsync(base + l.xoff, X_off, (ntables + 1) * 8, cudaMemcpyHostToDevice, stream));
-  SS_CHECK_CUDA(cudaMemcpyAsync(base + l.boff, blob_off.data(), ntables * 8, cudaMemcpyHostToDevice, stream));
-  SS_CHECK_CUDA(cudaMemcpyAsync(base + l.caps, caps.data(), ntables * 4, cudaMemcpyHostToDevice, stream));
-  SS_CHECK_CUDA(cudaMemcpyAsync(base + l.algo, algo.data(), ntables * 4, cudaMemcpyHostToDevice, stream));
-  if (!tiles.empty())
-    SS_CHECK_CUDA(cudaMemcpyAsync(base + l.tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice, stream));
-  // prepare the tables into the array; an unsorted table sets SS_FLAG_NOT_SORTED
-  unsigned* flag = stat != nullptr ? &stat->flags : reinterpret_cast<unsigned*>(base + l.flag);
-  PrepArgs pa{ntables, reinterpret_cast<const int64_t*>(base + l.xoff), X, base + l.blobs,
-              reinterpret_cast<const int64_t*>(base + l.boff), reinterpret_cast<const int*>(base + l.caps),
-              reinterpret_cast<const int*>(base + l.algo), 0, flag};
-  k_prep_1d<<<ntables, 256, 0, stream>>>(pa);
-  SS_CHECK_CUDA(cudaGetLastError());
-  if (tiles.empty()) return SS_OK;
-  const void* kern = batched_1d_kernel(side == SS_SIDE_LE, 0);
-  if (ss_status st_ = raise_smem_limit(kern, smem)) return st_;
-  int per_sm = 0;
-  SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNumThreads, smem));
-  if (per_sm < 1) return fail(SS_EUNSUPPORTED, "ss_search_1d_batched_static: kernel does not fit on an SM");
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms() * per_sm, (int64_t)tiles.size()));
-  BatchArgs1D a{base + l.blobs, reinterpret_cast<const int64_t*>(base + l.boff),
-                reinterpret_cast<const Tile*>(base + l.tiles), (int)tiles.size(),
-                reinterpret_cast<int*>(base + l.counter), Y, lowbounds,
-                (aligned(Y, 16) && aligned(lowbounds, 16)) ? 1 : 0, stat};
-  void* args[1] = {&a};
-  SS_CHECK_CUDA(cudaLaunchKernel(kern, dim3(grid), dim3(kNumThreads), args, (size_t)smem, stream));
-  return SS_OK;
-}
-
 }  // namespace ss
 
 using namespace ss;
@@ -138,39 +75,12 @@ extern "C" ss_status ss_search_1d_batched_static(int32_t ntables, const int64_t*
   if (Y_off[ntables] > 0 && (Y == nullptr || lowbounds == nullptr)) return fail(SS_EINVAL, std::string(me) + ": null pointer");
   if (!aligned(X, 8) || !aligned(Y, 8) || !aligned(lowbounds, 4)) return fail(SS_EINVAL, std::string(me) + ": misaligned pointer");
   // host-side layout of the array
-  std::vector<int> caps(ntables), algo(ntables, BL_BUCKET), bucket_of(ntables, 0);
-  std::vector<int64_t> blob_off(ntables);
-  int64_t blobs = 0;
-  int smem = 0;
-  for (int k = 0; k < ntables; ++k) {
-    const std::string tab = std::string(me) + ": table " + std::to_string(k);
-    if (X_off[k] < 0) return fail(SS_EINVAL, tab + ": negative table offset X_off[k] = " + std::to_string(X_off[k]));
-    const int64_t n = X_off[k + 1] - X_off[k];
-    if (n < 0)
-      return fail(SS_EINVAL, tab + ": table offsets decrease (X_off[k+1] - X_off[k] = " + std::to_string(n) + ")");
-    if (n < 2) return fail(SS_EINVAL, tab + " has " + std::to_string(n) + " entries; every table needs >= 2");
-    if (n > (1 << 30)) return fail(SS_EINVAL, tab + " has " + std::to_string(n) + " entries, more than 2^30");
-    if (Y_off[k] < 0) return fail(SS_EINVAL, tab + ": negative target offset Y_off[k] = " + std::to_string(Y_off[k]));
-    if (Y_off[k + 1] < Y_off[k])
-      return fail(SS_EINVAL, tab + ": target offsets decrease (Y_off[k+1] - Y_off[k] = " +
-                                 std::to_string(Y_off[k + 1] - Y_off[k]) + ")");
-    caps[k] = std::min(default_dir_cap((int)n), kStaticDirCap);
-    blob_off[k] = blobs;
-    blobs += (blob_geom_dev((int)n, caps[k], false).bytes + 255) & ~(int64_t)255;
-    smem = std::max(smem, staged_bytes((int)n, caps[k], false, BL_BUCKET));
-  }
-  int tile_size[kNumBuckets];
-  for (int b = 0; b < kNumBuckets; ++b) tile_size[b] = kDefaultTile;
-  int64_t total = 0;
-  const std::vector<Tile> tiles = make_tiles(std::vector<int64_t>(Y_off, Y_off + ntables + 1), bucket_of, tile_size, total);
-  const StaticLayout l = static_layout(ntables, tiles.size(), blobs);
-  if (l.end > (int64_t)kStaticScratchBytes)
-    return fail(SS_EINVAL, std::string(me) + ": the batch needs " + std::to_string(l.end) +
+  BatchWork1D w;
+  if (ss_status st = batch_work_1d(me, ntables, X_off, Y_off, kStaticDirCap, w)) return st;
+  if (w.end > (int64_t)kStaticScratchBytes)
+    return fail(SS_EINVAL, std::string(me) + ": the batch needs " + std::to_string(w.end) +
                                " bytes of working memory, more than the fixed " +
                                std::to_string(kStaticScratchBytes) + " bytes of this entry point");
-  if (tiles.size() > (size_t)0x7FFFFFFF) return fail(SS_EUNSUPPORTED, std::string(me) + ": too many tiles");
-  smem = (smem + 127) & ~127;
-  if (smem > max_smem_optin()) return fail(SS_EUNSUPPORTED, std::string(me) + ": a table is too large for shared memory");
   // the metadata goes to the array by copies from pageable host memory, which
   // a stream being captured into a graph cannot take: such a call is refused
   // before anything is queued (the checks above are host-only), so the caller's capture stays valid
@@ -185,8 +95,7 @@ extern "C" ss_status ss_search_1d_batched_static(int32_t ntables, const int64_t*
   // order this call after the previous one on the GPU; the event is
   // recorded after whatever this call queued, on its error paths too
   if (d->used) SS_CHECK_CUDA(cudaStreamWaitEvent(stream, d->done, 0));
-  const ss_status st = queue_static(l, d->addr, ntables, X_off, X, Y, lowbounds, side, stat, blob_off, caps, algo,
-                                    tiles, smem, stream);
+  const ss_status st = queue_work_1d(w, d->addr, ntables, X_off, X, Y, lowbounds, side, stat, stream);
   const cudaError_t e = cudaEventRecord(d->done, stream);
   if (e != cudaSuccess) return st != SS_OK ? st : cuda_fail(e, "cudaEventRecord");
   d->used = true;

@@ -742,10 +742,52 @@ def test_oneshot_batched_1d_empty_tables_and_unsorted(ss):
     got = ss.search_1d_batched([0, 3, 7], X.to(DEV), [0, 0, 4], Y.to(DEV))   # table 0 has no targets
     want = oracle.search_1d_batched(np.array([0, 3, 7]), X.numpy(), np.array([0, 0, 4]), Y.numpy())
     np.testing.assert_array_equal(got.cpu().numpy(), want)
-    bad = torch.tensor([1.0, 2.0, 2.0, 3.0, 1.0, 5.0, 7.0], dtype=torch.float64, device=DEV)
-    with pytest.raises(ss.SSError) as e:
-        ss.search_1d_batched([0, 4, 7], bad, [0, 2, 4], Y.to(DEV))
-    assert e.value.code == 2
+    # a table that is not strictly increasing is flagged on the GPU; the
+    # other table's indices stay exact and every index stays in range
+    bad = torch.tensor([1.0, 2.0, 2.0, 3.0, 1.0, 5.0, 7.0], dtype=torch.float64)
+    stat = ss.new_stat()
+    got = ss.search_1d_batched([0, 4, 7], bad.to(DEV), [0, 2, 4], Y.to(DEV), stat=stat).cpu().numpy()
+    assert ss.read_stat(stat).flags & ss.FLAG_NOT_SORTED
+    want = oracle.search_1d(bad.numpy()[4:], Y.numpy()[2:])
+    np.testing.assert_array_equal(got[2:], want)
+    assert got[:2].min() >= 0 and got[:2].max() <= 3
+
+
+def test_oneshot_batched_1d_is_stream_ordered(ss):
+    """The one-call batched search queues its work on the caller's stream and
+    returns: several calls on a side stream, tables staged whole and searched
+    in global memory (20,000 and 100,000 entries), read after one
+    synchronisation; a capturing stream is refused before anything is queued."""
+    bs = [wl.batched_1d(ntables=25 + 10 * i, count_scale=0.003, seed=40 + i) for i in range(3)]
+    big = wl.Batched1D(torch.tensor([0, 20_000, 120_000]),
+                       torch.cat([wl.log_spaced_table(20_000, 1e-5, 1e5, 0.1, 44),
+                                  wl.log_spaced_table(100_000, 1e-3, 1e9, 0.1, 45)]),
+                       torch.tensor([0, 50_000, 130_001]),
+                       torch.cat([wl.log_uniform(50_000, 5e-6, 2e5, 46), wl.log_uniform(80_001, 5e-4, 2e9, 47)]),
+                       None, None)
+    bs.append(big)
+    s = torch.cuda.Stream()
+    ins = [(b.X.to(DEV), b.Y.to(DEV)) for b in bs]
+    outs = [torch.full((len(b.Y),), -1, dtype=torch.int32, device=DEV) for b in bs]
+    torch.cuda.synchronize()
+    for k, b in enumerate(bs):
+        ss.search_1d_batched(b.X_off, ins[k][0], b.Y_off, ins[k][1], out=outs[k], side=k & 1, stream=s)
+    s.synchronize()
+    for k, b in enumerate(bs):
+        want = oracle.search_1d_batched(b.X_off.numpy(), b.X.numpy(), b.Y_off.numpy(), b.Y.numpy(), k & 1)
+        np.testing.assert_array_equal(outs[k].cpu().numpy(), want)
+    g = torch.cuda.CUDAGraph()
+    x = torch.zeros(4, device=DEV)
+    codes = []
+    with torch.cuda.graph(g):
+        try:
+            ss.search_1d_batched(bs[0].X_off, ins[0][0], bs[0].Y_off, ins[0][1], out=outs[0])
+        except ss.SSError as e:
+            codes.append(e.code)
+        x.add_(1.0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert codes == [6] and float(x.sum()) == 4.0
 
 
 def test_oneshot_batched_2d(ss):
