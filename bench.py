@@ -851,6 +851,7 @@ SUITE = (
     ("plain1d-1m", "plain 1D search, 64-entry table, 1M targets (L2 flushed between steps)"),
     ("plain1d", "plain 1D search, 64-entry table, scaled to 1B targets (the >= 70% roofline bar)"),
     ("interp2d", "fused 2D search + bilinear, 200 x 100 axes, 64M pairs"),
+    ("interp2d-plan", "the same 200 x 100 table and 64M pairs through a plan (corner records, persistent launch)"),
     ("sweep1d", "table-size sweep 16 / 256 / 4096 / 65536 entries, 256M targets each, learned vs plain"),
     ("batched2d", "1,000 2D tables, 1B pairs, random order, learned and hunt vs plain"),
     ("batched2d-coherent", "1,000 2D tables, 1B pairs, coherent order, learned and hunt vs plain"),
@@ -951,15 +952,13 @@ def run_reference(args, wl_obj):
     print(json.dumps(line), flush=True)
 
 
-def small_m_latency(args):
+def latency_table(dev):
     """Per-call latency for small batches (the set-up-dominated regime of
     Sec. 5.1 / 5.3): one-shot call (no set-up kept) vs a prepared plan
-    replayed as a CUDA graph, on the 64-entry table; medians of 50 calls."""
-    import __graft_entry__
-    __graft_entry__.build()
+    replayed as a CUDA graph, on the 64-entry table; medians of 50 calls,
+    each timed on the host including its synchronisation."""
     import paper_2112_03229_gb300 as ss
     from paper_2112_03229_gb300 import workloads as wl
-    dev = torch.device("cuda", 0)
     X, Y = wl.plain_1d(m=1 << 20, seed=1, device=dev)
     res = {}
     for m in (1, 100, 10_000, 1_000_000):
@@ -980,6 +979,14 @@ def small_m_latency(args):
                 ts.append((time.perf_counter() - t0) * 1e6)
             row[name + "_us"] = round(statistics.median(ts), 2)
         res[str(m)] = row
+        del plan
+    return res
+
+
+def small_m_latency(args):
+    import __graft_entry__
+    __graft_entry__.build()
+    res = latency_table(torch.device("cuda", 0))
     print(json.dumps({"metric": "per-call latency (us), small target batches", "unit": "us", "n_gpus": 1,
                       "config": {"workload": "latency-n64", "table": 64}, "latency": res}), flush=True)
 
@@ -1230,6 +1237,11 @@ def main():
                 r["co_bound"] = cb
             configs[other.name] = r
             other.release()
+        # small batches (next row f4): per-call latency of one-shot calls and graph-replayed plans
+        lo = len(clk.lines)
+        configs["latency-n64"] = {"config": "64-entry table, 1 .. 1M targets per call: per-call latency (us)",
+                                  "unit": "us", "latency": latency_table(dev),
+                                  "clocks": clk.summary(lo, len(clk.lines))}
     clk.__exit__(None, None, None)
 
     if rank == 0:
