@@ -102,7 +102,10 @@ std::vector<Tile> make_tiles(const std::vector<int64_t>& Y_off, const std::vecto
 // table costs under ~6% of streaming its tile; scaled by the tuned multiple.
 int auto_tile(int64_t total, int blocks, int staged_bytes, float mult) {
   int64_t t = total / std::max<int64_t>(1, (int64_t)blocks * 6);
-  t = std::max<int64_t>(t, 8192);
+  // at least 8192 targets per tile, so that a tile's queue step and staging
+  // stay small against its stream; a small batch (under about 5M targets)
+  // takes smaller tiles so that every block still gets one
+  t = std::max<int64_t>(t, std::min<int64_t>(8192, std::max<int64_t>(1024, total / std::max(1, blocks))));
   t = std::max<int64_t>(t, (int64_t)staged_bytes * 16 / 12);
   t = std::min<int64_t>(t, 1 << 20);
   t = (int64_t)((double)t * mult);

@@ -397,6 +397,7 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
     }
     for (int b = 0; b < kNumBuckets; ++b) {
       if (pairs[b] <= 0 || rec[b] <= 0) continue;
+      if (rec[b] <= 0.25 * l2) continue;        // all of the bucket's records fit: no cap needed
       const double cap = pairs[b] / rec[b] * (0.25 * l2) / std::max(1, resident);
       const int c = (int)std::max(8192.0, std::min(cap, (double)p->bucket_tile[b])) & ~255;
       p->bucket_tile[b] = std::min(p->bucket_tile[b], c);
