@@ -256,6 +256,125 @@ __device__ __forceinline__ int stream_pairs(const Args2D& a, const AxisView& vr,
   return nans;
 }
 
+// ---------------------------------------------------------------------------
+// Lean path of the staged-grid kernel for the common case: both axes bucket
+// searches with at most two keys per bucket, float-float cells, every grid
+// value split, no interpolation option.  Each axis keeps only the fields that
+// case reads, as shared-memory offsets, so the loop runs without spilling in
+// the 64 registers a 1024-thread block allows (the general path, which keeps
+// every axis field live, spilled there).  The other paths of the kernel are
+// separate (non-inlined) functions, so their registers do not weigh on this
+// loop.
+// ---------------------------------------------------------------------------
+struct LeanAxis {
+  int keys, dir, ca, cg;       // shared-memory byte offsets: keys, directory, cell records, cell scales
+  int shift, nb, n;
+  uint64_t base, k0;
+};
+
+__device__ __forceinline__ LeanAxis lean_axis(const Axis2D& ax, const unsigned char* smem) {
+  const TableHdr& h = *reinterpret_cast<const TableHdr*>(smem + ax.lay.hdr);
+  const AxisAux& aux = *reinterpret_cast<const AxisAux*>(smem + ax.aux);
+  LeanAxis f;
+  f.keys = ax.lay.keys;
+  f.dir = ax.lay.dir;
+  f.ca = ax.cells;
+  f.cg = ax.cells + (h.n - 1) * (int)sizeof(ulonglong2);   // the scales follow the n-1 records (cell_table)
+  f.shift = h.shift;
+  f.nb = h.nb;
+  f.n = h.n;
+  f.base = h.base;
+  f.k0 = aux.k0;
+  return f;
+}
+
+__device__ __forceinline__ Weights lean_weights(const unsigned char* smem, const LeanAxis& f, int i, int c, uint64_t k,
+                                                uint64_t u) {
+  if (i >= f.n - 1) return {{1.0f, 0.0f}, {0.0f, 0.0f}};          // above the last entry
+  if (i == 0 && k <= f.k0) return {{0.0f, 0.0f}, {1.0f, 0.0f}};   // at or below the first entry
+#ifdef SS_CHECKED
+  const CellTable t{reinterpret_cast<const ulonglong2*>(smem + f.ca), reinterpret_cast<const float2*>(smem + f.cg),
+                    f.n - 1};
+#else
+  const CellTable t{reinterpret_cast<const ulonglong2*>(smem + f.ca), reinterpret_cast<const float2*>(smem + f.cg)};
+#endif
+  return cell_weights(u, t, c);
+}
+
+// One pair on the lean path (SCAN keys per bucket); the grid is the
+// float-float copy at byte offset gsm of shared memory.
+template <int SCAN>
+__device__ __forceinline__ void lean_pair(const unsigned char* smem, const LeanAxis& fr, const LeanAxis& ft, int gsm,
+                                          double rho, double tem, int& ir, int& it, double& v, int& nans) {
+  const uint64_t ur = static_cast<uint64_t>(__double_as_longlong(rho));
+  const uint64_t ut = static_cast<uint64_t>(__double_as_longlong(tem));
+  const uint64_t kr = order_key(rho), kt = order_key(tem);
+  // a NaN maps below the image of -inf (0x0010000000000000): its high word decides
+  const bool nr = (uint32_t)(kr >> 32) < 0x00100000u, nt_ = (uint32_t)(kt >> 32) < 0x00100000u;
+  nans += (int)nr + (int)nt_;
+  ir = search_bucket<SCAN>(reinterpret_cast<const uint64_t*>(smem + fr.keys),
+                           reinterpret_cast<const int*>(smem + fr.dir), fr.shift, fr.base, fr.nb, kr);
+  it = search_bucket<SCAN>(reinterpret_cast<const uint64_t*>(smem + ft.keys),
+                           reinterpret_cast<const int*>(smem + ft.dir), ft.shift, ft.base, ft.nb, kt);
+  const int nt = ft.n;
+  const int cr = min(ir, fr.n - 2), ct = min(it, nt - 2);
+  const int o = cr * nt + ct;                    // axes of at most 4096 entries: fits 32 bits
+#ifdef SS_CHECKED
+  const int ng = fr.n * nt;
+  const float2* Gs = reinterpret_cast<const float2*>(smem + gsm);
+  const float2 g00 = Gs[SS_IX(o, ng)], g01 = Gs[SS_IX(o + 1, ng)], g10 = Gs[SS_IX(o + nt, ng)],
+               g11 = Gs[SS_IX(o + nt + 1, ng)];
+#else
+  const float2* Gs = reinterpret_cast<const float2*>(smem + gsm);
+  const float2 g00 = Gs[o], g01 = Gs[o + 1], g10 = Gs[o + nt], g11 = Gs[o + nt + 1];
+#endif
+  const Weights wr = lean_weights(smem, fr, ir, cr, kr, ur);
+  const Weights wt = lean_weights(smem, ft, it, ct, kt, ut);
+  const ff lo = ff_add_u(ff_mul_u(wt.wbar, ff{g00.x, g00.y}), ff_mul_u(wt.w, ff{g01.x, g01.y}));
+  const ff hi = ff_add_u(ff_mul_u(wt.wbar, ff{g10.x, g10.y}), ff_mul_u(wt.w, ff{g11.x, g11.y}));
+  v = (nr | nt_) ? __longlong_as_double(0x7FF8000000000000ll)
+                 : ff2d(ff_add_u(ff_mul_u(wr.wbar, lo), ff_mul_u(wr.w, hi)));
+}
+
+template <int SCAN>
+__device__ __forceinline__ int lean_pairs(const Args2D& a, const unsigned char* smem) {
+  const LeanAxis fr = lean_axis(a.ar, smem), ft = lean_axis(a.at, smem);
+  const int gsm = a.grid_smem;
+  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+  int nans = 0;
+  auto scalar = [&](int64_t i) {
+    int ir, it;
+    double v;
+    lean_pair<SCAN>(smem, fr, ft, gsm, a.Y2[2 * i], a.Y2[2 * i + 1], ir, it, v, nans);
+    a.idx[2 * i] = ir;
+    a.idx[2 * i + 1] = it;
+    a.val[i] = v;
+  };
+  for (int64_t i = gtid; i < a.head; i += gs) scalar(i);
+  const double2* Y = reinterpret_cast<const double2*>(a.Y2) + a.head;
+  int4* I4 = reinterpret_cast<int4*>(a.idx + 2 * a.head);
+  double2* V2 = reinterpret_cast<double2*>(a.val + a.head);
+  for (int64_t g = gtid; g < a.np2; g += gs) {
+    const double2 p0 = ld_stream(Y + 2 * g), p1 = ld_stream(Y + 2 * g + 1);
+    int i0, j0, i1, j1;
+    double v0, v1;
+    lean_pair<SCAN>(smem, fr, ft, gsm, p0.x, p0.y, i0, j0, v0, nans);
+    lean_pair<SCAN>(smem, fr, ft, gsm, p1.x, p1.y, i1, j1, v1, nans);
+    st_stream(I4 + g, make_int4(i0, j0, i1, j1));
+    st_stream(V2 + g, make_double2(v0, v1));
+  }
+  for (int64_t i = a.head + 2 * a.np2 + gtid; i < a.m; i += gs) scalar(i);
+  return nans;
+}
+
+// The staged-grid kernel's other float-float paths, kept out of line.
+template <int MODE>
+__device__ __noinline__ int stream_pairs_sg(const Args2D& a, const AxisView& vr, const AxisView& vt, const float2* Gs,
+                                            bool gall) {
+  return stream_pairs<MODE, true, true>(a, vr, vt, Gs, gall);
+}
+
 template <bool SG>
 __device__ __forceinline__ void interp_body(const Args2D& a, unsigned char* smem) {
   stage_table_1d(a.R, a.nr, a.ar.lay, smem);
@@ -286,7 +405,18 @@ __device__ __forceinline__ void interp_body(const Args2D& a, unsigned char* smem
                   reinterpret_cast<const AxisAux*>(smem + a.at.aux)->ffok;
   const int mode = a.algo == SS_ALGO_BINARY ? 2 : (hr.occ <= 1 && ht.occ <= 1) ? 0 : (hr.occ <= 2 && ht.occ <= 2) ? 3 : 1;
   int nans;
-  if (ff) {
+  if constexpr (SG) {
+    if (ff && gall && !a.extrap && (mode == 0 || mode == 3)) {
+      nans = mode == 0 ? lean_pairs<1>(a, smem) : lean_pairs<2>(a, smem);
+    } else if (ff) {
+      nans = mode == 0 ? stream_pairs_sg<0>(a, vr, vt, Gs, gall)
+           : mode == 3 ? stream_pairs_sg<3>(a, vr, vt, Gs, gall)
+           : mode == 1 ? stream_pairs_sg<1>(a, vr, vt, Gs, gall) : stream_pairs_sg<2>(a, vr, vt, Gs, gall);
+    } else {
+      nans = mode == 0 ? stream_pairs<0, false, false>(a, vr, vt, Gs, gall)
+           : mode == 2 ? stream_pairs<2, false, false>(a, vr, vt, Gs, gall) : stream_pairs<1, false, false>(a, vr, vt, Gs, gall);
+    }
+  } else if (ff) {
     nans = mode == 0 ? stream_pairs<0, true, SG>(a, vr, vt, Gs, gall)
          : mode == 3 ? stream_pairs<3, true, SG>(a, vr, vt, Gs, gall)
          : mode == 1 ? stream_pairs<1, true, SG>(a, vr, vt, Gs, gall) : stream_pairs<2, true, SG>(a, vr, vt, Gs, gall);

@@ -137,16 +137,24 @@ __device__ __forceinline__ bool make_cell(double a, double b, CellW& c) {
   return true;
 }
 
-// Integer 0 < v < 2^63 as a float pair scaled by 2^-48: v is normalised so
-// that its leading one sits at bit 47 (shift k, either way), the 48 bits are
-// split into two 24-bit halves, and 2^(k-48) is folded into them.  The low
-// half is then below one unit of the high half's last place, so products
-// with it stay accurate to 2^-47 whatever the magnitude of v.
+// Integer 0 < v < 2^63 as a float pair scaled by 2^-48, from 32-bit
+// operations only: v is normalised so that its leading one sits at bit 63
+// (shift s = clz(v), taken on the nonzero word), and its top 48 bits are
+// split into two 24-bit halves.  The high half becomes a float by placing
+// its 24 bits under the exponent 2^(15-s) (no conversion); the low half is
+// converted (exact: under 2^24) and scaled by 2^(-32-s).  The low half is
+// below one unit of the high half's last place, so products with it stay
+// accurate to 2^-47 whatever the magnitude of v.
 __device__ __forceinline__ ff numerator(uint64_t v) {
-  const int k = 16 - __clzll((long long)v);                  // position of bit 47 relative to the leading one
-  const uint64_t t = k >= 0 ? v >> k : v << -k;              // in [2^47, 2^48)
-  const float sc = __int_as_float((127 + k - 48) << 23);      // 2^(k - 48)
-  return {(float)(uint32_t)(t >> 24) * (16777216.0f * sc), (float)((uint32_t)t & 0xFFFFFFu) * sc};
+  const uint32_t vh = (uint32_t)(v >> 32), vl = (uint32_t)v;
+  const bool z = vh == 0;
+  const uint32_t a = z ? vl : vh, b = z ? 0u : vl;      // the nonzero leading word and the one after it
+  const int c = __clz((int)a);
+  const uint32_t th = __funnelshift_l(b, a, c), tl = b << c;   // bits 63..32 and 31..0 of v << s
+  const int s = c + (z ? 32 : 0);
+  const float hi = __uint_as_float(((uint32_t)(141 - s) << 23) + (th >> 8));
+  const float lo = (float)(__funnelshift_r(tl, th, 16) & 0xFFFFFFu) * __uint_as_float((uint32_t)(95 - s) << 23);
+  return {hi, lo};
 }
 
 // Both weights of target x (bit pattern u, X[c] < x <= X[c+1]) in cell c:

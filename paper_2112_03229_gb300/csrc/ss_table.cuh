@@ -138,8 +138,14 @@ __device__ __forceinline__ void stage_table_1d(const double* __restrict__ X, int
   if (dir != nullptr) {
     if (tid == 0) {
       const uint64_t k0 = keys[0], k1 = keys[ns - 1];
-      int s = 0;
-      // the span is unsigned: a table may cover more than half of the key range
+      // smallest shift s with (k1 >> s) - (k0 >> s) < dir_cap.  That
+      // difference never grows with s, and exceeds span / 2^s - 1, so every
+      // s below bitlen(span) - bitlen(dir_cap + 1) still leaves it at least
+      // dir_cap: the scan starts there (a step or two instead of up to 63).
+      // The span is unsigned: a table may cover more than half of the key range.
+      const uint64_t span = k1 - k0;
+      const int bl = 64 - __clzll((long long)span), bc = 32 - __clz(lay.dir_cap + 1);
+      int s = max(0, bl - bc - 1);
       while (s < 63 && ((k1 >> s) - (k0 >> s)) >= (uint64_t)lay.dir_cap) ++s;
       h.shift = s;
       h.base = k0 >> s;

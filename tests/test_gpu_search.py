@@ -191,6 +191,27 @@ def test_2d_float_float_preconditions(ss):
                                                         wv[worst], v[worst]))
 
 
+def test_2d_crowded_bucket_takes_bisection(ss):
+    """Twenty entries packed inside one cell of the density axis leave a
+    bucket with many keys: the staged-grid kernel leaves its lean two-key scan
+    for the bounded bisection (and the binary layout), exact either way."""
+    rng = np.random.default_rng(12)
+    base = np.geomspace(1e-6, 1e4, 100)
+    R = np.sort(np.concatenate([base, base[50] * (1 + 1e-9 * np.arange(1, 21))]))
+    T = wl.log_spaced_table(90, 1e-4, 1e4, 0.1, seed=13).numpy()
+    F = wl.field_grid(torch.as_tensor(R), torch.as_tensor(T), wl.smooth_field(1e-6, 1e4, 1e-4, 1e4, seed=14)).numpy()
+    m = 300_001
+    rho = np.exp(rng.uniform(np.log(0.5e-6), np.log(2e4), m))
+    rho[::3] = base[50] * (1 + rng.uniform(0.0, 2.2e-8, len(rho[::3])))          # inside the crowded cell
+    rho[1::7] = R[rng.integers(0, len(R), len(rho[1::7]))]                       # on entries
+    tem = np.exp(rng.uniform(np.log(0.5e-4), np.log(2e4), m))
+    Y2 = np.stack([rho, tem], 1)
+    wi, wv = oracle.search_interp_2d(R, T, F, Y2)
+    for algo in ("bucket", "binary"):
+        idx, val = ss.search_interp_2d(*(torch.as_tensor(a).to(DEV) for a in (R, T, F.reshape(-1), Y2)), algo=algo)
+        check_2d(idx.cpu().numpy(), val.cpu().numpy(), wi, wv)
+
+
 def test_2d_ragged_misaligned_and_sizes(ss):
     for nr, nt in ((2, 2), (2, 3), (3, 2), (33, 65), (500, 300), (4096, 17)):
         R = wl.log_spaced_table(nr, 1e-6, 1e4, 0.1, seed=nr)
