@@ -131,7 +131,7 @@ __device__ __forceinline__ void pair_2d(const StagedView& vr, const StagedView& 
   const int cr = min(ir, vr.h.n - 2), ct = min(it, nt - 2);
   const int64_t cell = (int64_t)cr * (nt - 1) + ct;
   float q[8];
-  ld_nc_v8(reinterpret_cast<const float*>(G + 2 * cell), q);     // records are 32-byte aligned
+  ld_nc_v8_policy(reinterpret_cast<const float*>(G + 2 * cell), q, l2_policy_evict_last());   // 32-byte aligned
   const float2 g00 = make_float2(q[0], q[1]), g01 = make_float2(q[2], q[3]);
   const float2 g10 = make_float2(q[4], q[5]), g11 = make_float2(q[6], q[7]);
   if (logspace | extrap) {
@@ -401,8 +401,8 @@ __device__ __forceinline__ Weights fast_weights(const unsigned char* smem, const
 }
 
 __device__ __forceinline__ void pair_fast(const unsigned char* smem, const FastAxis& fr, const FastAxis& ft,
-                                          const float4* __restrict__ G, double rho, double tem, int& ir, int& it,
-                                          double& v, int& nans) {
+                                          const float4* __restrict__ G, uint64_t keep, double rho, double tem,
+                                          int& ir, int& it, double& v, int& nans) {
   const uint64_t ur = static_cast<uint64_t>(__double_as_longlong(rho));
   const uint64_t ut = static_cast<uint64_t>(__double_as_longlong(tem));
   const uint64_t kr = order_key(rho), kt = order_key(tem);
@@ -415,7 +415,7 @@ __device__ __forceinline__ void pair_fast(const unsigned char* smem, const FastA
   const int cr = min(ir, fr.n - 2), ct = min(it, ft.n - 2);
   const int64_t cell = (int64_t)cr * (ft.n - 1) + ct;
   float q[8];
-  ld_nc_v8(reinterpret_cast<const float*>(G + 2 * cell), q);
+  ld_nc_v8_policy(reinterpret_cast<const float*>(G + 2 * cell), q, keep);
   const Weights wr = fast_weights(smem, fr, ir, cr, kr, ur);
   const Weights wt = fast_weights(smem, ft, it, ct, kt, ut);
   const ff lo = ff_add_u(ff_mul_u(wt.wbar, ff{q[0], q[1]}), ff_mul_u(wt.w, ff{q[2], q[3]}));
@@ -425,9 +425,12 @@ __device__ __forceinline__ void pair_fast(const unsigned char* smem, const FastA
 
 // Four blocks of 256 threads per SM (61 registers, no spills; the general
 // kernel's 80 registers allow three).  Two pairs per thread and step, as in
-// the general kernel: one pair per step measured 6 % slower.
+// the general kernel: one pair per step measured 6 % slower.  Corner
+// gathers carry an evict-last L2 policy and the 256-bit target loads an
+// evict-first one (1-2 % measured).
 __global__ void __launch_bounds__(kNumThreads, 4) k_batched_2d_fast(BatchArgs2D a) {
   extern __shared__ __align__(128) unsigned char smem[];
+  const uint64_t keep = l2_policy_evict_last(), pass = l2_policy_evict_first();
   __shared__ uint64_t bar;
   __shared__ int s_tile;
   if (threadIdx.x == 0) mbar_init(&bar, 1);
@@ -469,7 +472,7 @@ __global__ void __launch_bounds__(kNumThreads, 4) k_batched_2d_fast(BatchArgs2D 
     auto scalar = [&](int i) {
       int ir, it;
       double v;
-      pair_fast(smem, fr, ft, G, a.Y2[2 * (b + i)], a.Y2[2 * (b + i) + 1], ir, it, v, nans);
+      pair_fast(smem, fr, ft, G, keep, a.Y2[2 * (b + i)], a.Y2[2 * (b + i) + 1], ir, it, v, nans);
       a.idx[2 * (b + i)] = ir;
       a.idx[2 * (b + i) + 1] = it;
       a.val[b + i] = v;
@@ -488,7 +491,7 @@ __global__ void __launch_bounds__(kNumThreads, 4) k_batched_2d_fast(BatchArgs2D 
       double2 p0, p1;
       if (a.vec == 2) {
         double y[4];
-        ld_stream4(reinterpret_cast<const double*>(Y + 2 * g), y);
+        ld_stream4_policy(reinterpret_cast<const double*>(Y + 2 * g), y, pass);
         p0 = make_double2(y[0], y[1]);
         p1 = make_double2(y[2], y[3]);
       } else {
@@ -497,8 +500,8 @@ __global__ void __launch_bounds__(kNumThreads, 4) k_batched_2d_fast(BatchArgs2D 
       }
       int i0, j0, i1, j1;
       double v0, v1;
-      pair_fast(smem, fr, ft, G, p0.x, p0.y, i0, j0, v0, nans);
-      pair_fast(smem, fr, ft, G, p1.x, p1.y, i1, j1, v1, nans);
+      pair_fast(smem, fr, ft, G, keep, p0.x, p0.y, i0, j0, v0, nans);
+      pair_fast(smem, fr, ft, G, keep, p1.x, p1.y, i1, j1, v1, nans);
       st_stream(I4 + g, make_int4(i0, j0, i1, j1));
       st_stream(V2 + g, make_double2(v0, v1));
     }

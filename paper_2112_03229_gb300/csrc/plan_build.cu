@@ -383,24 +383,27 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
   }
   if (p->kind == 2 && p->opts.tile <= 0) {
     // 2D lookups gather corner records from the grids of the tables in
-    // flight.  Blocks take consecutive tiles, so about resident / (tiles per
-    // table) tables are in flight; tiles are capped so that their records
-    // fit in a quarter of L2 (a batch of 1,000 tables of 1.45 MB of records
-    // ran 4 % faster with 32K-pair tiles than with the tuned 91K).
+    // flight.  Blocks take consecutive tiles, so about resident x tile /
+    // (pairs per table) tables are in flight, whose records take resident x
+    // tile x (record bytes per pair).  When the batch's records exceed a
+    // sixth of L2, every tile is capped so that those in flight fit there,
+    // at the batch's ratio of record bytes to pairs (the 1,000-table batch,
+    // 1.45 GB of records for 1B pairs: 23.8K-pair tiles, 92-93 G pairs/s,
+    // against 85.5 with the earlier cap per size bucket at a quarter of L2
+    // and 81.9 with 64K-pair tiles; 16K and 24K measured within 1 %).
     int dev = 0, l2 = 0;
     SS_CHECK_CUDA(cudaGetDevice(&dev));
     SS_CHECK_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
-    double pairs[kNumBuckets] = {0}, rec[kNumBuckets] = {0};
+    double pairs = 0, rec = 0;
     for (int k = 0; k < p->ntables; ++k) {
-      pairs[bucket_of[k]] += (double)(Y_off[k + 1] - Y_off[k]);
-      rec[bucket_of[k]] += 32.0 * (double)(p->cell_off[k + 1] - p->cell_off[k]);
+      pairs += (double)(Y_off[k + 1] - Y_off[k]);
+      rec += 32.0 * (double)(p->cell_off[k + 1] - p->cell_off[k]);
     }
-    for (int b = 0; b < kNumBuckets; ++b) {
-      if (pairs[b] <= 0 || rec[b] <= 0) continue;
-      if (rec[b] <= 0.25 * l2) continue;        // all of the bucket's records fit: no cap needed
-      const double cap = pairs[b] / rec[b] * (0.25 * l2) / std::max(1, resident);
-      const int c = (int)std::max(8192.0, std::min(cap, (double)p->bucket_tile[b])) & ~255;
-      p->bucket_tile[b] = std::min(p->bucket_tile[b], c);
+    const double room = (double)l2 / 6.0;
+    if (pairs > 0 && rec > room) {
+      const double cap = pairs / rec * room / std::max(1, resident);
+      const int c = (int)std::max(8192.0, cap) & ~255;
+      for (int b = 0; b < kNumBuckets; ++b) p->bucket_tile[b] = std::min(p->bucket_tile[b], c);
     }
   }
   int64_t total = 0;

@@ -52,6 +52,37 @@ __device__ __forceinline__ void ld_nc_v8(const float* p, float (&r)[8]) {
       : "l"(p));
 }
 
+// L2 eviction priorities (createpolicy descriptors) for the 2D plans: the
+// corner records a batch gathers are reused by every pair that falls in their
+// cell, while the targets stream past once, so the gathers are marked
+// evict-last and the target loads evict-first, and the stream of targets does
+// not push the records of the tables in flight out of L2.
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// ld_nc_v8 with an L2 policy.
+__device__ __forceinline__ void ld_nc_v8_policy(const float* p, float (&r)[8], uint64_t pol) {
+  asm("ld.global.nc.L2::cache_hint.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
+      : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7])
+      : "l"(p), "l"(pol));
+}
+
+// 256-bit load of four doubles read once (no L1 allocation) with an L2 policy.
+__device__ __forceinline__ void ld_stream4_policy(const double* p, double (&r)[4], uint64_t pol) {
+  asm("ld.global.L1::no_allocate.L2::cache_hint.v4.f64 {%0, %1, %2, %3}, [%4], %5;"
+      : "=d"(r[0]), "=d"(r[1]), "=d"(r[2]), "=d"(r[3])
+      : "l"(p), "l"(pol));
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
