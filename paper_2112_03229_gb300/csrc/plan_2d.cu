@@ -5,6 +5,7 @@
 // of (table, pair range) work items.
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "plan.h"
@@ -400,6 +401,7 @@ __device__ __forceinline__ Weights fast_weights(const unsigned char* smem, const
   return cell_weights(u, t, c);
 }
 
+template <int HI>   // 1: both bucket shifts are 32 or more; -1: decided per call
 __device__ __forceinline__ void pair_fast(const unsigned char* smem, const FastAxis& fr, const FastAxis& ft,
                                           const float4* __restrict__ G, uint64_t keep, double rho, double tem,
                                           int& ir, int& it, double& v, int& nans) {
@@ -408,10 +410,10 @@ __device__ __forceinline__ void pair_fast(const unsigned char* smem, const FastA
   const uint64_t kr = order_key(rho), kt = order_key(tem);
   const bool nan = (kr < kKeyNegInf) | (kt < kKeyNegInf);
   nans += (kr < kKeyNegInf) + (kt < kKeyNegInf);
-  ir = search_bucket<2>(reinterpret_cast<const uint64_t*>(smem + fr.keys),
-                        reinterpret_cast<const uint16_t*>(smem + fr.dir), fr.shift, fr.base, fr.nb, kr);
-  it = search_bucket<2>(reinterpret_cast<const uint64_t*>(smem + ft.keys),
-                        reinterpret_cast<const uint16_t*>(smem + ft.dir), ft.shift, ft.base, ft.nb, kt);
+  ir = search_bucket<2, HI>(reinterpret_cast<const uint64_t*>(smem + fr.keys),
+                            reinterpret_cast<const uint16_t*>(smem + fr.dir), fr.shift, fr.base, fr.nb, kr);
+  it = search_bucket<2, HI>(reinterpret_cast<const uint64_t*>(smem + ft.keys),
+                            reinterpret_cast<const uint16_t*>(smem + ft.dir), ft.shift, ft.base, ft.nb, kt);
   const int cr = min(ir, fr.n - 2), ct = min(it, ft.n - 2);
   const int64_t cell = (int64_t)cr * (ft.n - 1) + ct;
   float q[8];
@@ -472,7 +474,7 @@ __global__ void __launch_bounds__(kNumThreads, 4) k_batched_2d_fast(BatchArgs2D 
     auto scalar = [&](int i) {
       int ir, it;
       double v;
-      pair_fast(smem, fr, ft, G, keep, a.Y2[2 * (b + i)], a.Y2[2 * (b + i) + 1], ir, it, v, nans);
+      pair_fast<-1>(smem, fr, ft, G, keep, a.Y2[2 * (b + i)], a.Y2[2 * (b + i) + 1], ir, it, v, nans);
       a.idx[2 * (b + i)] = ir;
       a.idx[2 * (b + i) + 1] = it;
       a.val[b + i] = v;
@@ -487,24 +489,31 @@ __global__ void __launch_bounds__(kNumThreads, 4) k_batched_2d_fast(BatchArgs2D 
     const double2* Y = reinterpret_cast<const double2*>(a.Y2) + b + head;
     int4* I4 = reinterpret_cast<int4*>(a.idx + 2 * (b + head));
     double2* V2 = reinterpret_cast<double2*>(a.val + b + head);
-    for (int g = threadIdx.x; g < np2; g += blockDim.x) {
-      double2 p0, p1;
-      if (a.vec == 2) {
-        double y[4];
-        ld_stream4_policy(reinterpret_cast<const double*>(Y + 2 * g), y, pass);
-        p0 = make_double2(y[0], y[1]);
-        p1 = make_double2(y[2], y[3]);
-      } else {
-        p0 = ld_stream(Y + 2 * g);
-        p1 = ld_stream(Y + 2 * g + 1);
+    // the bucket index from the keys' high words when both shifts allow
+    // (straight-line pairs; 2 % measured), else decided per call
+    auto pairs = [&](auto hi) {
+      constexpr int HI = decltype(hi)::value;
+      for (int g = threadIdx.x; g < np2; g += blockDim.x) {
+        double2 p0, p1;
+        if (a.vec == 2) {
+          double y[4];
+          ld_stream4_policy(reinterpret_cast<const double*>(Y + 2 * g), y, pass);
+          p0 = make_double2(y[0], y[1]);
+          p1 = make_double2(y[2], y[3]);
+        } else {
+          p0 = ld_stream(Y + 2 * g);
+          p1 = ld_stream(Y + 2 * g + 1);
+        }
+        int i0, j0, i1, j1;
+        double v0, v1;
+        pair_fast<HI>(smem, fr, ft, G, keep, p0.x, p0.y, i0, j0, v0, nans);
+        pair_fast<HI>(smem, fr, ft, G, keep, p1.x, p1.y, i1, j1, v1, nans);
+        st_stream(I4 + g, make_int4(i0, j0, i1, j1));
+        st_stream(V2 + g, make_double2(v0, v1));
       }
-      int i0, j0, i1, j1;
-      double v0, v1;
-      pair_fast(smem, fr, ft, G, keep, p0.x, p0.y, i0, j0, v0, nans);
-      pair_fast(smem, fr, ft, G, keep, p1.x, p1.y, i1, j1, v1, nans);
-      st_stream(I4 + g, make_int4(i0, j0, i1, j1));
-      st_stream(V2 + g, make_double2(v0, v1));
-    }
+    };
+    if (fr.shift >= 32 && ft.shift >= 32) pairs(std::integral_constant<int, 1>{});
+    else pairs(std::integral_constant<int, -1>{});
     for (int i = head + 2 * np2 + threadIdx.x; i < cnt; i += blockDim.x) scalar(i);
   }
   nans = __reduce_add_sync(0xFFFFFFFFu, nans);

@@ -176,6 +176,11 @@ __device__ __forceinline__ ff one_minus(ff a) {
 // the larger one, 1 minus it, is at least 1/2, where the float-float
 // subtraction loses nothing relative to its size.  Both weights so keep
 // their full relative precision (however small the smaller one is).
+// ANY: the target may lie outside the cell (a caller that computes the
+// weights of every target and then picks the end weights of clamped ones
+// without a branch); the exponent difference is then taken modulo 64 so
+// every step stays defined, and the result is meaningless but unused.
+template <bool ANY = false>
 __device__ __forceinline__ Weights cell_weights(uint64_t u, const CellTable& t, int c) {
 #ifdef SS_CHECKED
   c = SS_IX(c, t.n);
@@ -184,7 +189,7 @@ __device__ __forceinline__ Weights cell_weights(uint64_t u, const CellTable& t, 
   const int ec = (int)(rec.x >> 53);
   const uint64_t Mc = rec.x & ((1ull << 53) - 1), MnS = rec.y;
   const int ex = (int)((u >> 52) & 0x7FF);
-  const uint64_t MxS = ((u & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << (ex - ec);
+  const uint64_t MxS = ((u & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << (ANY ? ((ex - ec) & 63) : (ex - ec));
   const uint64_t D = MxS - Mc, Dn = MnS - MxS;
   const bool low = D <= Dn;                      // the target sits in the lower half of the cell
   const uint64_t v = low ? D : Dn;

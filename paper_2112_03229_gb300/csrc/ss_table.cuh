@@ -186,14 +186,13 @@ __device__ __forceinline__ int search_eyt_rt(const uint64_t* __restrict__ eyt, i
   return i - (1 << D);
 }
 
-// Bucket directory + fixed-length scan (occupancy <= SCAN, Sec. 3.5's
-// linear search inside a bin).  Keys past the bucket are larger than q (they
-// sit in later buckets) or are sentinels, so scanning them adds nothing.
 // Bucket of query key q, clamped to [0, nb-1].  Shifts of 32 or more (the
 // common case: buckets no finer than 2^-20 of an octave) need only the key's
-// high word; the branch is uniform across the block.
-__device__ __forceinline__ int bucket_index(uint64_t q, int shift, uint64_t base, int nb) {
-  if (shift >= 32) {
+// high word.  HI fixes that case at compile time, so a caller that has
+// checked the shift once per table runs the search as straight-line code.
+template <bool HI>
+__device__ __forceinline__ int bucket_index_t(uint64_t q, int shift, uint64_t base, int nb) {
+  if (HI) {
     const uint32_t hb = (uint32_t)(q >> 32) >> (shift - 32);
     const uint32_t d = hb - (uint32_t)base;                 // base < 2^32 here
     return hb < (uint32_t)base ? 0 : (int)min(d, (uint32_t)(nb - 1));
@@ -202,10 +201,21 @@ __device__ __forceinline__ int bucket_index(uint64_t q, int shift, uint64_t base
   return hb < base ? 0 : (int)min(hb - base, (uint64_t)(nb - 1));
 }
 
-template <int SCAN, class D>   // D: directory entry type (int in one-shot calls, uint16_t in plans)
+// The same with the case taken per call (the branch is uniform across a block).
+__device__ __forceinline__ int bucket_index(uint64_t q, int shift, uint64_t base, int nb) {
+  return shift >= 32 ? bucket_index_t<true>(q, shift, base, nb) : bucket_index_t<false>(q, shift, base, nb);
+}
+
+// Bucket directory + fixed-length scan (occupancy <= SCAN, Sec. 3.5's
+// linear search inside a bin).  Keys past the bucket are larger than q (they
+// sit in later buckets) or are sentinels, so scanning them adds nothing.
+// D: directory entry type (int in one-shot calls, uint16_t in plans); HI:
+// 1 when the shift is known to be 32 or more, 0 when it is known not to be,
+// -1 to decide per call.
+template <int SCAN, int HI = -1, class D>
 __device__ __forceinline__ int search_bucket(const uint64_t* __restrict__ keys, const D* __restrict__ dir,
                                              int shift, uint64_t base, int nb, uint64_t q) {
-  const int b = bucket_index(q, shift, base, nb);
+  const int b = HI < 0 ? bucket_index(q, shift, base, nb) : bucket_index_t<(HI > 0)>(q, shift, base, nb);
   const int lo = dir[b];
   int c = lo;
 #pragma unroll
