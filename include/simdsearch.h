@@ -303,16 +303,24 @@ ss_status ss_search_1d_batched(int32_t ntables, const int64_t* X_off, const doub
                                const int64_t* Y_off, const double* Y, int32_t* lowbounds,
                                int32_t side, ss_devstat* stat, cudaStream_t stream);
 
-/* 2D: table k has axes R[R_off[k] ..], T[T_off[k] ..] and the row-major
- * nr_k x nt_k grid F[F_off[k] ..]; its pairs are Y2[2 Y_off[k] ..
- * 2 Y_off[k+1]) interleaved (rho, T); lowbounds2 receives interleaved index
- * pairs and values one double per pair.  Offsets are host arrays, the rest
- * device arrays.  The call prepares a plan without a model, runs the batch
- * as one persistent launch on `stream`, waits for it and releases the
- * plan, so the results are written when it returns.  SS_ENOTSORTED if an
- * axis is not strictly increasing (nothing is written then).  The 2D lookup
- * uses side SS_SIDE_LT (the cell of a target equal to an axis entry is the
- * one above it either way, and so is the interpolated value). */
+/* 2D: table k has axes R[R_off[k] ..], T[T_off[k] ..] (each of 2 ..
+ * SS_MAX_AXIS_2D entries) and the row-major nr_k x nt_k grid
+ * F[F_off[k] ..]; its pairs are Y2[2 Y_off[k] .. 2 Y_off[k+1]) interleaved
+ * (rho, T); lowbounds2 receives interleaved index pairs and values one
+ * double per pair.  Offsets are host arrays, the rest device arrays.
+ * Asynchronous on `stream` like the 1D call: the host lays the batch out
+ * from the offsets, the working memory (prepared axes, corner records,
+ * tiles) comes from the stream-ordered allocator, and the preparation, the
+ * choice between the lean and the general persistent kernel (made on the
+ * GPU: values outside the float-float range or crowded buckets take the
+ * general one), the lookup and the release of that memory are queued;
+ * R, T, F, Y2, lowbounds2 and values must stay valid until the stream
+ * reaches that point.  An axis that is not strictly increasing sets
+ * SS_FLAG_NOT_SORTED in *stat (the other tables' results are exact).  Bad
+ * offsets are refused with SS_EINVAL naming the table, a stream being
+ * captured with SS_EUNSUPPORTED.  The 2D lookup uses side SS_SIDE_LT (the
+ * cell of a target equal to an axis entry is the one above it either way,
+ * and so is the interpolated value). */
 ss_status ss_search_interp_2d_batched(int32_t ntables, const int64_t* R_off, const double* R,
                                       const int64_t* T_off, const double* T, const int64_t* F_off,
                                       const double* F, const int64_t* Y_off, const double* Y2,

@@ -443,8 +443,9 @@ def search_1d_batched(X_off, X, Y_off, Y, out=None, side=SIDE_LT, stat=None, str
 
 
 def search_interp_2d_batched(R_off, R, T_off, T, F_off, F, Y_off, Y2, idx=None, val=None, stat=None, stream=None):
-    """ss_search_interp_2d_batched: the 2D lookup over many tables in one call; synchronous.
-    Returns (idx [m, 2] int32, val [m] float64)."""
+    """ss_search_interp_2d_batched: the 2D lookup over many tables in one call,
+    queued on the stream (the current one by default).  Returns (idx [m, 2]
+    int32, val [m] float64)."""
     L = _batched_lib()
     ro, rp = _offsets(R_off, "R_off", data=R)
     to, tp = _offsets(T_off, "T_off", length=len(ro), data=T)

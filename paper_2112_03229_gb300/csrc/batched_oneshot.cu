@@ -8,9 +8,9 @@
 // waiting.  A table that is not strictly increasing is flagged in the
 // caller's status record (SS_FLAG_NOT_SORTED) by the preparation on the GPU.
 //
-// 2D: a plan without a model is prepared, bound to the caller's batch,
-// executed once and released; the call waits for the launch before
-// releasing the plan's memory, so it is synchronous.
+// 2D: the same, with both axes of every table prepared, the corner records
+// built and the lean or the general persistent kernel picked on the GPU
+// (batched_work_2d.cu).
 //
 // Callers that search the same tables again keep a plan instead and pay the
 // preparation once (Sec. 5.3).
@@ -18,32 +18,6 @@
 
 #include "plan.h"
 #include "plan_host.h"
-
-namespace {
-
-ss_plan_opts oneshot_opts(int32_t side) {
-  ss_plan_opts o;
-  ss_plan_opts_default(&o);
-  o.side = side;
-  o.model = SS_MODEL_NONE;
-  o.autotune = 0;
-  return o;
-}
-
-// Bind, execute, wait, release; the first failure's status is returned.
-template <class Bind>
-ss_status run_and_release(ss_plan* p, Bind&& bind, cudaStream_t stream) {
-  ss_status st = bind(p);
-  if (st == SS_OK) st = ss_plan_execute(p, stream);
-  if (st == SS_OK) {
-    const cudaError_t e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) st = ss::cuda_fail(e, "cudaStreamSynchronize");
-  }
-  ss_plan_destroy(p);
-  return st;
-}
-
-}  // namespace
 
 extern "C" ss_status ss_search_1d_batched(int32_t ntables, const int64_t* X_off, const double* X,
                                           const int64_t* Y_off, const double* Y, int32_t* lowbounds, int32_t side,
@@ -76,10 +50,28 @@ extern "C" ss_status ss_search_interp_2d_batched(int32_t ntables, const int64_t*
                                                  const double* F, const int64_t* Y_off, const double* Y2,
                                                  int32_t* lowbounds2, double* values, ss_devstat* stat,
                                                  cudaStream_t stream) {
-  if (Y_off == nullptr) return ss::fail(SS_EINVAL, "ss_search_interp_2d_batched: null pointer");
-  const ss_plan_opts o = oneshot_opts(SS_SIDE_LT);
-  ss_plan* p = nullptr;
-  if (ss_status st = ss_plan_create_2d(&p, ntables, R_off, R, T_off, T, F_off, F, &o, stream)) return st;
-  return run_and_release(
-      p, [&](ss_plan* q) { return ss_plan_bind_2d(q, Y_off, Y2, lowbounds2, values, stat, stream); }, stream);
+  using namespace ss;
+  const char* me = "ss_search_interp_2d_batched";
+  if (R_off == nullptr || T_off == nullptr || F_off == nullptr || Y_off == nullptr || R == nullptr || T == nullptr ||
+      F == nullptr)
+    return fail(SS_EINVAL, std::string(me) + ": null pointer");
+  if (ntables < 1) return fail(SS_EINVAL, std::string(me) + ": ntables must be >= 1");
+  if (Y_off[ntables] > 0 && (Y2 == nullptr || lowbounds2 == nullptr || values == nullptr))
+    return fail(SS_EINVAL, std::string(me) + ": null pointer");
+  if (!aligned(R, 8) || !aligned(T, 8) || !aligned(F, 8) || !aligned(Y2, 8) || !aligned(lowbounds2, 4) ||
+      !aligned(values, 8))
+    return fail(SS_EINVAL, std::string(me) + ": misaligned pointer");
+  BatchWork2D w;
+  if (ss_status st = batch_work_2d(me, ntables, R_off, T_off, F_off, Y_off, w)) return st;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  SS_CHECK_CUDA(cudaStreamIsCapturing(stream, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(SS_EUNSUPPORTED, std::string(me) + ": the stream is capturing; keep a plan to replay in a graph");
+  unsigned char* base = nullptr;
+  SS_CHECK_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&base), (size_t)w.end, stream));
+  const ss_status st = queue_work_2d(w, base, ntables, R_off, R, T_off, T, F_off, F, Y2, lowbounds2, values, stat,
+                                     stream);
+  const cudaError_t e = cudaFreeAsync(base, stream);        // after the queued work, on every path
+  if (st != SS_OK) return st;
+  return e == cudaSuccess ? SS_OK : cuda_fail(e, "cudaFreeAsync");
 }

@@ -286,6 +286,13 @@ static void unbind(ss_plan* p) {
   p->bound = false;
 }
 
+int tile_cap_2d(double pairs, double rec, int resident, int l2) {
+  const double room = (double)l2 / 6.0;
+  if (pairs <= 0 || rec <= room) return 0;
+  const double cap = pairs / rec * room / std::max(1, resident);
+  return (int)std::max(8192.0, cap) & ~255;
+}
+
 ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double* Y, int32_t* out, double* val,
                     ss_devstat* stat, cudaStream_t stream) {
   unbind(p);
@@ -399,12 +406,8 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
       pairs += (double)(Y_off[k + 1] - Y_off[k]);
       rec += 32.0 * (double)(p->cell_off[k + 1] - p->cell_off[k]);
     }
-    const double room = (double)l2 / 6.0;
-    if (pairs > 0 && rec > room) {
-      const double cap = pairs / rec * room / std::max(1, resident);
-      const int c = (int)std::max(8192.0, cap) & ~255;
+    if (const int c = tile_cap_2d(pairs, rec, resident, l2))
       for (int b = 0; b < kNumBuckets; ++b) p->bucket_tile[b] = std::min(p->bucket_tile[b], c);
-    }
   }
   int64_t total = 0;
   std::vector<Tile> tiles = make_tiles(Y_off, bucket_of, p->bucket_tile, total);

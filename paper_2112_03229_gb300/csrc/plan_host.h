@@ -92,6 +92,28 @@ ss_status queue_work_1d(const BatchWork1D& w, unsigned char* base, int32_t ntabl
                         const double* X, const double* Y, int32_t* lowbounds, int32_t side, ss_devstat* stat,
                         cudaStream_t stream);
 
+// The batched 2D lookup in one call, laid out and queued like the 1D one;
+// both persistent kernels are queued and the GPU picks the one that applies.
+struct BatchWork2D {
+  std::vector<int> caps_r, caps_t, algo;
+  std::vector<int64_t> blob_off, off_r, off_t, cell_off;
+  std::vector<Tile> tiles;
+  int smem = 0;
+  int64_t counters = 0, gate = 0, flag = 0, xr = 0, xt = 0, fo = 0, bo = 0, ro = 0, to = 0, cr = 0, ct = 0,
+          al = 0, co = 0, tiles_off = 0, blobs_off = 0, cells_off = 0, end = 0;
+};
+ss_status batch_work_2d(const char* me, int32_t ntables, const int64_t* R_off, const int64_t* T_off,
+                        const int64_t* F_off, const int64_t* Y_off, BatchWork2D& w);
+ss_status queue_work_2d(const BatchWork2D& w, unsigned char* base, int32_t ntables, const int64_t* R_off,
+                        const double* R, const int64_t* T_off, const double* T, const int64_t* F_off, const double* F,
+                        const double* Y2, int32_t* lowbounds2, double* values, ss_devstat* stat, cudaStream_t stream);
+// Tile cap of a 2D batch so that the corner records in flight fit a sixth
+// of L2 (0: the batch's records fit there, no cap).
+int tile_cap_2d(double pairs, double rec, int resident, int l2);
+__global__ void k_grid_cells(const double* __restrict__ F, const int64_t* __restrict__ F_off,
+                             const int64_t* __restrict__ R_off, const int64_t* __restrict__ T_off,
+                             const int64_t* __restrict__ cell_off, float4* __restrict__ cells, unsigned* bad);
+
 ss_status plan_build_1d(ss_plan* p, const double* X, cudaStream_t stream);
 ss_status plan_build_2d(ss_plan* p, const double* R, const double* T, const double* F, cudaStream_t stream);
 ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double* Y, int32_t* out, double* val,

@@ -800,3 +800,94 @@ def test_oneshot_batched_2d(ss):
     np.testing.assert_array_equal(idx.cpu().numpy(), wi)
     assert (np.abs(val.cpu().numpy() - wv) / np.abs(wv)).max() <= REL_TOL
     assert ss.read_stat(stat).flags == 0
+
+
+def _oracle_2d(b):
+    return oracle.search_interp_2d_batched(b.R_off.numpy(), b.R.numpy(), b.T_off.numpy(), b.T.numpy(),
+                                           b.F_off.numpy(), b.F.numpy(), b.Y_off.numpy(), b.Y2.numpy())
+
+
+def test_oneshot_batched_2d_is_stream_ordered(ss):
+    """The one-call batched 2D lookup queues its work on the caller's stream
+    and returns: batches on a side stream -- the common case (lean kernel),
+    grid values outside the float-float range and an axis with a crowded
+    bucket (both handed to the general kernel on the GPU), empty tables and
+    arrays off 16-byte alignment -- read after one synchronisation, exact
+    against the oracle; an axis that is not increasing is flagged on the GPU;
+    a capturing stream is refused before anything is queued."""
+    b1 = wl.batched_2d(ntables=7, pairs_per_table=2501, seed=21)
+    b2 = wl.batched_2d(ntables=5, pairs_per_table=2003, seed=22)
+    F = b2.F.clone()
+    nt0 = int(b2.T_off[1] - b2.T_off[0])
+    F[3 * nt0:5 * nt0] = 1e-200                      # table 0, rows 3 and 4: below the float-float range
+    F[int(b2.F_off[2]) + 7] = 1e250                  # table 2: one value above it
+    b2 = wl.Batched2D(b2.R_off, b2.R, b2.T_off, b2.T, b2.F_off, F, b2.Y_off, b2.Y2)
+    base = np.geomspace(1e-6, 1e4, 60)
+    Rc = np.sort(np.concatenate([base, base[30] * (1 + 1e-9 * np.arange(1, 13))]))
+    Tc = wl.log_spaced_table(40, 1e-4, 1e4, 0.1, seed=23).numpy()
+    Fc = wl.field_grid(torch.as_tensor(Rc), torch.as_tensor(Tc), wl.smooth_field(1e-6, 1e4, 1e-4, 1e4, seed=24))
+    rng = np.random.default_rng(25)
+    rho = np.exp(rng.uniform(np.log(0.5e-6), np.log(2e4), 3001))
+    rho[::2] = base[30] * (1 + rng.uniform(0, 1.4e-8, len(rho[::2])))
+    tem = np.exp(rng.uniform(np.log(0.5e-4), np.log(2e4), 3001))
+    b3 = wl.Batched2D(torch.tensor([0, len(Rc)]), torch.as_tensor(Rc), torch.tensor([0, len(Tc)]), torch.as_tensor(Tc),
+                      torch.tensor([0, len(Rc) * len(Tc)]), Fc.reshape(-1),
+                      torch.tensor([0, 3001]), torch.as_tensor(np.stack([rho, tem], 1)))
+    b4 = wl.batched_2d(ntables=4, pairs_per_table=777, seed=26)
+    b4 = wl.Batched2D(b4.R_off, b4.R, b4.T_off, b4.T, b4.F_off, b4.F, torch.tensor([0, 0, 777, 777, 1554]),
+                      b4.Y2[:1554])                  # tables 0 and 2 without pairs
+    bs = [b1, b2, b3, b4]
+    s = torch.cuda.Stream()
+    ins, outs = [], []
+    for k, b in enumerate(bs):
+        m = len(b.Y2)
+        off = k & 1                                  # odd batches: pairs, indices and values off 16-byte alignment
+        y = torch.empty(2 * m + 2, dtype=torch.float64, device=DEV)
+        y[off:off + 2 * m] = b.Y2.reshape(-1).to(DEV)
+        ib = torch.full((2 * m + 4,), -7, dtype=torch.int32, device=DEV)
+        vb = torch.full((m + 2,), -7.0, dtype=torch.float64, device=DEV)
+        ins.append((b.R.to(DEV), b.T.to(DEV), b.F.to(DEV), y[off:off + 2 * m]))
+        outs.append((ib, vb, off, m))
+    stats = [ss.new_stat() for _ in bs]
+    torch.cuda.synchronize()
+    for k, b in enumerate(bs):
+        R, T, F, y = ins[k]
+        ib, vb, off, m = outs[k]
+        ss.search_interp_2d_batched(b.R_off, R, b.T_off, T, b.F_off, F, b.Y_off, y, idx=ib[2 * off:2 * off + 2 * m],
+                                    val=vb[off:off + m], stat=stats[k], stream=s)
+    s.synchronize()
+    for k, b in enumerate(bs):
+        wi, wv = _oracle_2d(b)
+        ib, vb, off, m = outs[k]
+        np.testing.assert_array_equal(ib[2 * off:2 * off + 2 * m].cpu().numpy().reshape(-1, 2), wi)
+        v = vb[off:off + m].cpu().numpy()
+        assert (np.abs(v - wv) / np.abs(wv)).max(initial=0.0) <= REL_TOL
+        assert torch.all(vb[:off] == -7.0) and torch.all(vb[off + m:] == -7.0)
+        assert torch.all(ib[:2 * off] == -7) and torch.all(ib[2 * off + 2 * m:] == -7)
+        assert ss.read_stat(stats[k]).flags == 0
+    # an axis that is not strictly increasing: flagged, the other table exact
+    bad = wl.batched_2d(ntables=2, pairs_per_table=1000, seed=27)
+    R = bad.R.clone()
+    R[5] = R[4]
+    stat = ss.new_stat()
+    idx, val = ss.search_interp_2d_batched(bad.R_off, R.to(DEV), bad.T_off, bad.T.to(DEV), bad.F_off, bad.F.to(DEV),
+                                           bad.Y_off, bad.Y2.to(DEV), stat=stat)
+    assert ss.read_stat(stat).flags & ss.FLAG_NOT_SORTED
+    wi, wv = _oracle_2d(bad)
+    np.testing.assert_array_equal(idx[1000:].cpu().numpy(), wi[1000:])
+    assert (np.abs(val[1000:].cpu().numpy() - wv[1000:]) / np.abs(wv[1000:])).max() <= REL_TOL
+    # a capturing stream is refused and the capture stays valid
+    g = torch.cuda.CUDAGraph()
+    x = torch.zeros(4, device=DEV)
+    codes = []
+    R, T, F, y = ins[0]
+    with torch.cuda.graph(g):
+        try:
+            ss.search_interp_2d_batched(b1.R_off, R, b1.T_off, T, b1.F_off, F, b1.Y_off, y)
+        except ss.SSError as e:
+            codes.append(e.code)
+        x.add_(1.0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert codes == [6] and float(x.sum()) == 4.0
+
