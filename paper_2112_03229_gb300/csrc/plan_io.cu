@@ -17,7 +17,7 @@ using namespace ss;
 namespace {
 
 constexpr char kMagic[8] = {'S', 'S', 'P', 'L', 'A', 'N', 0, 1};
-constexpr int32_t kVersion = 9;
+constexpr int32_t kVersion = 10;
 
 struct Writer {
   FILE* f;

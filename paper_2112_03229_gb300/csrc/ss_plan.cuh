@@ -18,7 +18,8 @@
 // Wide section (a table too large for shared memory as 8-byte keys, but not
 // as 16-bit offsets): the keys form leaves of 16; per leaf, its last key (the
 // sample), a shift, and the 16 keys as offsets from the previous leaf's
-// last key, shifted right until they fit 15 bits (stored in 16).  A target's
+// last key, shifted right until they fit 15 bits (stored in 16, with bit 15
+// set so that the packed comparison needs no mask of its own).  A target's
 // leaf comes from a bucket directory over the samples; inside the leaf a
 // packed comparison of the offsets, two per 32-bit word, decides every key
 // except those whose offset equals the target's, which are compared in full
@@ -303,15 +304,16 @@ __device__ __forceinline__ WideView wide_view(const unsigned char* sec, const St
 }
 
 // Number of the eight 15-bit offsets packed two per word in a, b (uint4
-// each) that are at least t (t <= 0x8000): for an offset x, (0x8000 | x) - t
-// keeps bit 15 set exactly when x >= t, and never borrows into the other
-// half of the word.
+// each, every offset stored with bit 15 set) that are at least t
+// (t <= 0x8000): (0x8000 | x) - t keeps bit 15 set exactly when x >= t, and
+// never borrows into the other half of the word.  The flags of four words
+// are gathered at distinct bit positions (shifts 0..3) for one popc.
 __device__ __forceinline__ int count_ge15(const uint4& a, const uint4& b, uint32_t t) {
   const uint32_t t2 = t | (t << 16);
   const uint32_t m = 0x80008000u;
-  return __popc(((a.x | m) - t2) & m) + __popc(((a.y | m) - t2) & m) + __popc(((a.z | m) - t2) & m) +
-         __popc(((a.w | m) - t2) & m) + __popc(((b.x | m) - t2) & m) + __popc(((b.y | m) - t2) & m) +
-         __popc(((b.z | m) - t2) & m) + __popc(((b.w | m) - t2) & m);
+  const uint32_t pa = ((a.x - t2) & m) | (((a.y - t2) & m) >> 1) | (((a.z - t2) & m) >> 2) | (((a.w - t2) & m) >> 3);
+  const uint32_t pb = ((b.x - t2) & m) | (((b.y - t2) & m) >> 1) | (((b.z - t2) & m) >> 2) | (((b.w - t2) & m) >> 3);
+  return __popc(pa) + __popc(pb);
 }
 
 // Count of keys below q on a wide section: the leaf from the sample
@@ -363,7 +365,7 @@ __device__ __forceinline__ int wide_count(const WideView& wv, uint64_t q) {
   const int wi = c >> 1;
   const uint32_t wc = wi < 4 ? (wi < 2 ? (wi == 0 ? a.x : a.y) : (wi == 2 ? a.z : a.w))
                              : (wi < 6 ? (wi == 4 ? b.x : b.y) : (wi == 6 ? b.z : b.w));
-  if (c < kLeaf && ((c & 1) ? (wc >> 16) : (wc & 0xFFFFu)) == tq) {
+  if (c < kLeaf && ((c & 1) ? (wc >> 16) : (wc & 0xFFFFu)) == (tq | 0x8000u)) {
     const int le = kLeaf - count_ge15(a, b, tq + 1);             // offsets at most the target's
     for (; c < le; ++c) {
       const int j = kLeaf * s + c;
