@@ -184,10 +184,13 @@ typedef enum ss_model {
   SS_MODEL_SPLINE = 1,  /* piecewise-linear map of the target's key, knots = bucket directory */
   SS_MODEL_MLP = 2,     /* 2-16-1 fp32 MLP on the target's exponent and mantissa, trained on the GPU */
   SS_MODEL_LOGHASH = 3, /* no training: the logarithm hash of Sec. 3.4 (Eqs. 1-2), base fitted to the end points */
-  SS_MODEL_HUNT = 4     /* hunt and locate (Sec. 2.1) for coherent sequences (Sec. 5.5), 1D and 2D plans: the
+  SS_MODEL_HUNT = 4,    /* hunt and locate (Sec. 2.1) for coherent sequences (Sec. 5.5), 1D and 2D plans: the
                            first of a thread's consecutive targets (2D: pairs) takes the table's own search, the
                            others start from its answer, probe away in doubling steps and bisect the last step;
                            exact for any order.  1D hunt plans use the bucket search (algo auto or bucket) */
+  SS_MODEL_AUTO = 5     /* 1D plans: with autotune, the tuner picks per table-size bucket the fastest of the plain
+                           searches and the untrained proposals (spline, logarithm hash), timed on the bucket's
+                           own tables; every index stays exact whatever it picks.  Without autotune: as NONE */
 } ss_model;
 
 typedef struct ss_plan_opts {

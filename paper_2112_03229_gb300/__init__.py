@@ -249,8 +249,9 @@ def mlp_adam_step(params, grad, m1, m2, step, lr, beta1=0.9, beta2=0.999, eps=1e
 # ---------------------------------------------------------------------------
 # Plans: set-up once per set of tables, many batched searches
 # ---------------------------------------------------------------------------
-MODEL_NONE, MODEL_SPLINE, MODEL_MLP, MODEL_LOGHASH, MODEL_HUNT = 0, 1, 2, 3, 4
-MODELS = {"none": MODEL_NONE, "spline": MODEL_SPLINE, "mlp": MODEL_MLP, "loghash": MODEL_LOGHASH, "hunt": MODEL_HUNT}
+MODEL_NONE, MODEL_SPLINE, MODEL_MLP, MODEL_LOGHASH, MODEL_HUNT, MODEL_AUTO = 0, 1, 2, 3, 4, 5
+MODELS = {"none": MODEL_NONE, "spline": MODEL_SPLINE, "mlp": MODEL_MLP, "loghash": MODEL_LOGHASH, "hunt": MODEL_HUNT,
+          "auto": MODEL_AUTO}
 BLOB_ALGOS = ["bucket", "binary", "ballot8", "ballot16", "ballot32", "spline", "mlp", "loghash", "wide"]
 
 

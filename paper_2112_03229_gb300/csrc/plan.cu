@@ -143,7 +143,7 @@ ss_status ss::check_plan_opts(const ss_plan_opts& o, int kind) {
   if (!(o.mlp_lr >= 0.0f && o.mlp_lr < 1e30f)) return fail(SS_EINVAL, "plan: mlp_lr must be finite and >= 0");
   if (kind == 1) {
     if (o.side != SS_SIDE_LT && o.side != SS_SIDE_LE) return fail(SS_EINVAL, "plan: bad side");
-    if (o.model < SS_MODEL_NONE || o.model > SS_MODEL_HUNT) return fail(SS_EINVAL, "plan: bad model");
+    if (o.model < SS_MODEL_NONE || o.model > SS_MODEL_AUTO) return fail(SS_EINVAL, "plan: bad model");
     // the hunt reads the staged keys, which a 1D table staged for the
     // breadth-first binary search or the ballot search does not carry
     if (o.model == SS_MODEL_HUNT && o.algo != SS_ALGO_AUTO && o.algo != SS_ALGO_BUCKET)
@@ -153,6 +153,7 @@ ss_status ss::check_plan_opts(const ss_plan_opts& o, int kind) {
     return SS_OK;
   }
   if (o.side != SS_SIDE_LT) return fail(SS_EINVAL, "ss_plan_create_2d: the 2D lookup uses side SS_SIDE_LT");
+  if (o.model == SS_MODEL_AUTO) return fail(SS_EINVAL, "ss_plan_create_2d: SS_MODEL_AUTO is for 1D plans");
   if ((o.extrap != 0 && o.extrap != 1) || (o.logspace != 0 && o.logspace != 1))
     return fail(SS_EINVAL, "ss_plan_create_2d: extrap and logspace must be 0 or 1");
   if (o.model < SS_MODEL_NONE || o.model > SS_MODEL_HUNT || o.algo == SS_ALGO_BALLOT || o.algo == SS_ALGO_BRANCHY ||

@@ -179,7 +179,7 @@ ss_status plan_build_1d(ss_plan* p, const double* X, cudaStream_t stream) {
   p->dir_cap.resize(nt);
   p->algo.assign(nt, initial_algo(o));
   // without a model and an explicit algorithm, tables with a wide section use it
-  if (o.model == SS_MODEL_NONE && o.algo == SS_ALGO_AUTO)
+  if ((o.model == SS_MODEL_NONE || o.model == SS_MODEL_AUTO) && o.algo == SS_ALGO_AUTO)
     for (int k = 0; k < nt; ++k)
       if (wide_eligible(p->sizes[k] - 1)) p->algo[k] = BL_WIDE;
   p->blob_off.resize(nt);
@@ -549,13 +549,26 @@ static void write_cache(const ss_plan* p, const std::string& dev) {
 }
 
 // Apply the bucket choices to every table's algorithm (both axes for 2D).
+// Learned half-windows of the tables whose algorithm is a position
+// proposal (k_window leaves the others alone).  Plans with a fixed model get
+// them at creation; SS_MODEL_AUTO plans after each change of algorithm.
+static ss_status refresh_windows(ss_plan* p, cudaStream_t stream) {
+  if (p->opts.model != SS_MODEL_AUTO) return SS_OK;
+  WindowArgs wa{p->ntables, p->d_blobs, p->d_blob_off, p->opts.seed ^ 0xA5A5A5A5ull};
+  k_window<<<p->ntables, 256, 0, stream>>>(wa);
+  SS_CHECK_CUDA(cudaGetLastError());
+  SS_CHECK_CUDA(cudaStreamSynchronize(stream));
+  return SS_OK;
+}
+
 static ss_status apply_buckets(ss_plan* p, cudaStream_t stream) {
   for (int k = 0; k < p->ntables; ++k) {
     const int b = size_bucket(std::max(p->sizes[k], p->kind == 2 ? p->sizes_t[k] : 0));
     if (p->kind == 1) p->algo[k] = table_algo(p->bucket_algo[b], p->sizes[k]);
     else p->algo[2 * k] = p->algo[2 * k + 1] = p->bucket_algo[b];
   }
-  return plan_set_algos(p, stream);
+  if (ss_status st = plan_set_algos(p, stream)) return st;
+  return refresh_windows(p, stream);
 }
 
 ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
@@ -570,6 +583,8 @@ ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
   else if (p->opts.model == SS_MODEL_LOGHASH) cands = {BL_LOGHASH};
   else if (p->opts.model == SS_MODEL_HUNT) cands = p->kind == 1 ? std::vector<int>{BL_BUCKET}     // keys staged
                                                                   : std::vector<int>{BL_BUCKET, BL_BINARY};
+  else if (p->kind == 1 && p->opts.model == SS_MODEL_AUTO)
+    cands = {BL_BUCKET, BL_BINARY, BL_BALLOT8, BL_BALLOT16, BL_BALLOT32, BL_WIDE, BL_SPLINE, BL_LOGHASH};
   else if (p->kind == 1) cands = {BL_BUCKET, BL_BINARY, BL_BALLOT8, BL_BALLOT16, BL_BALLOT32, BL_WIDE};
   else cands = {BL_BUCKET, BL_BINARY};
   const std::vector<float> mult_cands = {0.25f, 1.0f, 4.0f};
@@ -597,6 +612,9 @@ ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
   std::vector<int> saved_algo = p->algo;
   for (int b = 0; b < kNumBuckets && st == SS_OK; ++b) {
     if (p->bucket_tables[b] == 0) continue;
+    // every bucket is timed from the initial algorithms, so an earlier
+    // bucket's last candidate does not change the kernel the others run in
+    p->algo = saved_algo;
     // representative tables of this bucket
     std::vector<int> reps;
     for (int k = 0; k < p->ntables && (int)reps.size() < kReps; ++k)
@@ -660,6 +678,7 @@ ss_status plan_tune(ss_plan* p, cudaStream_t stream) {
         else p->algo[2 * r] = p->algo[2 * r + 1] = algo;
       }
       if (ss_status s2 = plan_set_algos(p, stream)) return s2;
+      if (ss_status s2 = refresh_windows(p, stream)) return s2;
       const float saved = p->bucket_mult[b];
       p->bucket_mult[b] = mult;
       ss_status s2 = plan_bind(p, Y_off, d_Y, d_out, d_val, nullptr, stream);

@@ -90,6 +90,29 @@ def main():
                dict(algo="binary"), dict(extrap=True), dict(logspace=True)):
         check_2d(b2, **kw)
     check_2d(wl.batched_2d(ntables=4, pairs_per_table=4001, coherent=True, jump=0.02, seed=7), model="hunt")
+    # one-shot 2D: the staged-grid kernel's lean path (bucket axes) and its out-of-line paths (binary axes)
+    R, T, F, Y2 = wl.interp_2d(m=100_003, seed=8)
+    wi, wv = oracle.search_interp_2d(R.numpy(), T.numpy(), F.numpy(), Y2.numpy())
+    for algo in ("bucket", "binary"):
+        idx, val = ss.search_interp_2d(R.to(DEV), T.to(DEV), F.to(DEV), Y2.to(DEV), algo=algo)
+        np.testing.assert_array_equal(idx.cpu().numpy(), wi)
+        assert (np.abs(val.cpu().numpy() - wv) / np.abs(wv)).max() <= REL_TOL
+    # the one-call batched 2D lookup: the lean kernel, and the general one
+    # when a grid value is outside the float-float range
+    for big in (False, True):
+        b3 = wl.batched_2d(ntables=5, pairs_per_table=3001, seed=9)
+        if big:
+            F3 = b3.F.clone()
+            F3[7] = 1e250
+            b3 = wl.Batched2D(b3.R_off, b3.R, b3.T_off, b3.T, b3.F_off, F3, b3.Y_off, b3.Y2)
+        wi, wv = oracle.search_interp_2d_batched(b3.R_off.numpy(), b3.R.numpy(), b3.T_off.numpy(), b3.T.numpy(),
+                                                 b3.F_off.numpy(), b3.F.numpy(), b3.Y_off.numpy(), b3.Y2.numpy())
+        stat = ss.new_stat()
+        idx, val = ss.search_interp_2d_batched(b3.R_off, b3.R.to(DEV), b3.T_off, b3.T.to(DEV), b3.F_off,
+                                               b3.F.to(DEV), b3.Y_off, b3.Y2.to(DEV), stat=stat)
+        np.testing.assert_array_equal(idx.cpu().numpy(), wi)
+        assert (np.abs(val.cpu().numpy() - wv) / np.abs(wv)).max() <= REL_TOL
+        assert ss.read_stat(stat).flags == 0
     hits = ss.checked_hits()
     assert hits == 0, "indices out of range: %d" % hits
     print("checked build: every case exact, 0 indices out of range")

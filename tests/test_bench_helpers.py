@@ -94,3 +94,17 @@ def test_sample_parity_counts_mismatches_and_value_errors():
     r = b.sample_parity("2d_batched", (idx, np.array([1.0, np.nan])), (idx.copy(), np.array([1.0, np.nan])))
     assert r["ok"]
     assert b.sample_parity("1d", np.zeros(1, np.int32), None) is None
+
+
+def test_host_link_peak_at_the_steps_split():
+    """The end-to-end roofline: a 1D step sends 8 bytes per target and
+    returns 4, so the host-to-device direction bounds it (12 bytes per
+    8 / 210.5 GB/s); a 2D step moves 16 each way, so the rate of both
+    directions together bounds it; a one-way step gets that direction."""
+    b = load_bench()
+    link = {"h2d": 210.5, "d2h": 192.7, "both": 340.5}
+    assert abs(b.link_peak_for(8, 4, link) - 12 / (8 / 210.5)) < 1e-9
+    assert abs(b.link_peak_for(16, 16, link) - 340.5) < 1e-9
+    assert abs(b.link_peak_for(8, 0, link) - 210.5) < 1e-9
+    assert abs(b.link_peak_for(0, 4, link) - 192.7) < 1e-9
+    assert abs(b.link_peak_for(1, 100, link) - 101 / (100 / 192.7)) < 1e-9

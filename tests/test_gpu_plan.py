@@ -891,3 +891,33 @@ def test_oneshot_batched_2d_is_stream_ordered(ss):
     torch.cuda.synchronize()
     assert codes == [6] and float(x.sum()) == 4.0
 
+
+def test_plan_auto_model_picks_per_bucket(ss):
+    """SS_MODEL_AUTO: the tuner picks per table-size bucket among the plain
+    searches and the untrained proposals (spline, log hash), timed on the
+    bucket's own tables.  Indices are exact for every pick; the 64-entry
+    table, staged whole, keeps a plain search, and the 1M-entry table,
+    whose plain search finishes with dependent loads in global memory, takes
+    a proposal (the log hash measured about twice the plain search there)."""
+    tabs = [wl.log_spaced_table(64, 1e-6, 1e4, 0.1, seed=51), wl.log_spaced_table(1 << 20, 1e-6, 1e4, 0.1, seed=52)]
+    Ys = [wl.log_uniform(1_500_001, 0.5e-6, 2e4, seed=53), wl.log_uniform(2_000_003, 0.5e-6, 2e4, seed=54)]
+    X_off = torch.tensor([0, 64, 64 + (1 << 20)])
+    Y_off = torch.tensor([0, len(Ys[0]), len(Ys[0]) + len(Ys[1])])
+    X, Y = torch.cat(tabs), torch.cat(Ys)
+    want = oracle.search_1d_batched(X_off.numpy(), X.numpy(), Y_off.numpy(), Y.numpy())
+    plan = ss.Plan.create_1d(X_off, X.to(DEV), model="auto", autotune=True)
+    out = torch.full((len(Y),), -1, dtype=torch.int32, device=DEV)
+    stat = ss.new_stat()
+    plan.bind_1d(Y_off, Y.to(DEV), out, stat=stat)
+    plan.execute()
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
+    assert ss.read_stat(stat).flags == 0
+    picks = sorted(plan.choices().items())
+    assert len(picks) == 2, picks
+    assert picks[0][1][0] in ("bucket", "binary", "ballot8", "ballot16", "ballot32"), picks
+    assert picks[1][1][0] in ("spline", "loghash"), picks
+    assert 1 <= plan.info().max_window <= 8
+    # without the tuner the model is the plain search
+    plain = ss.Plan.create_1d(X_off, X.to(DEV), model="auto")
+    assert all(v[0] in ("bucket", "binary") for v in plain.choices().values())
+
