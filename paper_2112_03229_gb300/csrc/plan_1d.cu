@@ -148,7 +148,11 @@ __global__ void __launch_bounds__(256) k_prep_1d(PrepArgs a) {
       for (int j = 0; j < kLeaf; ++j) {
         const int i = s * kLeaf + j;
         const int at = j < kLeaf / 2 ? s * (kLeaf / 2) + j : (wg.L + s) * (kLeaf / 2) + (j - kLeaf / 2);
-        wl[at] = i < nk ? (uint16_t)(0x8000u | (uint32_t)((full[i] - b) >> sh)) : (uint16_t)0xFFFF;
+        // slot 15 holds the shift: its key is the leaf's sample, which the
+        // search never counts (the chosen leaf's sample is at least the target)
+        wl[at] = j == kLeaf - 1 ? (uint16_t)sh
+                 : i < nk       ? (uint16_t)(0x8000u | (uint32_t)((full[i] - b) >> sh))
+                                : (uint16_t)0xFFFF;
       }
     }
     if (tid == 0) {

@@ -17,7 +17,7 @@ using namespace ss;
 namespace {
 
 constexpr char kMagic[8] = {'S', 'S', 'P', 'L', 'A', 'N', 0, 1};
-constexpr int32_t kVersion = 10;
+constexpr int32_t kVersion = 11;
 
 struct Writer {
   FILE* f;
@@ -127,8 +127,13 @@ const char* check_layout(const ss_plan* p, const std::vector<unsigned char>& hb)
       std::vector<uint16_t> wdir((size_t)w.nb + 1);
       std::memcpy(wdir.data(), blob + g.off_wide + wg.off_dir, wdir.size() * sizeof(uint16_t));
       if (dir_occupancy(wdir.data(), w.nb, wg.L) != w.occ) return "wide directory or occupancy inconsistent";
-      for (int s2 = 0; s2 < wg.L; ++s2)
-        if (blob[g.off_wide + wg.off_shift + s2] > 63) return "wide leaf shift out of range";
+      for (int s2 = 0; s2 < wg.L; ++s2) {
+        const uint8_t sh = blob[g.off_wide + wg.off_shift + s2];
+        uint16_t last;                     // slot 15 of leaf s2: offsets 8..15 sit after all leaves' 0..7
+        std::memcpy(&last, blob + g.off_wide + wg.off_leaf + ((int64_t)(wg.L + s2) * (kLeaf / 2) + kLeaf / 2 - 1) * 2,
+                    sizeof(last));
+        if (sh > 63 || last != sh) return "wide leaf shift out of range";
+      }
     }
   }
   for (int b = 0; b < kNumBuckets; ++b)

@@ -17,9 +17,10 @@
 //
 // Wide section (a table too large for shared memory as 8-byte keys, but not
 // as 16-bit offsets): the keys form leaves of 16; per leaf, its last key (the
-// sample), a shift, and the 16 keys as offsets from the previous leaf's
-// last key, shifted right until they fit 15 bits (stored in 16, with bit 15
-// set so that the packed comparison needs no mask of its own).  A target's
+// sample), a shift, and the first 15 keys as offsets from the previous
+// leaf's last key, shifted right until they fit 15 bits (stored in 16, with
+// bit 15 set so that the packed comparison needs no mask of its own); the
+// 16th slot holds the shift (the 16th key is the sample itself).  A target's
 // leaf comes from a bucket directory over the samples; inside the leaf a
 // packed comparison of the offsets, two per 32-bit word, decides every key
 // except those whose offset equals the target's, which are compared in full
@@ -91,7 +92,8 @@ struct WideGeom {
 };
 
 // Bytes of a wide section besides its directory: header, samples (with
-// sentinels), shifts and leaves.
+// sentinels), shifts (a copy of each leaf's slot 15, which the search reads;
+// the copy is checked when a plan file is read) and leaves.
 __host__ __device__ inline int wide_rest_bytes(int L) {
   return (int)sizeof(WideHdr) + ((((L + kPad) * 8) + 15) & ~15) + ((L + 15) & ~15) + L * kLeaf * 2;
 }
@@ -283,7 +285,6 @@ struct WideView {
   WideHdr w;                    // directory parameters, in registers
   const uint16_t* dir;          // bucket directory over the samples (16-bit counts)
   const uint64_t* samples;      // last key of each leaf, then kPad sentinels
-  const uint8_t* shifts;
   const uint16_t* leaf;         // offsets 0..7 of every leaf (16 bytes each), then offsets 8..15 of every leaf
   const uint64_t* full;         // all keys, global memory (ties)
   uint64_t k0;                  // key of X[0]: the base of leaf 0
@@ -295,7 +296,6 @@ __device__ __forceinline__ WideView wide_view(const unsigned char* sec, const St
   wv.w = *reinterpret_cast<const WideHdr*>(sec);
   wv.dir = reinterpret_cast<const uint16_t*>(sec + wv.w.off_dir);
   wv.samples = reinterpret_cast<const uint64_t*>(sec + wv.w.off_samples);
-  wv.shifts = sec + wv.w.off_shift;
   wv.leaf = reinterpret_cast<const uint16_t*>(sec + wv.w.off_leaf);
   wv.full = v.full;
   wv.k0 = v.h.k0;
@@ -303,17 +303,20 @@ __device__ __forceinline__ WideView wide_view(const unsigned char* sec, const St
   return wv;
 }
 
-// Number of the eight 15-bit offsets packed two per word in a, b (uint4
-// each, every offset stored with bit 15 set) that are at least t
-// (t <= 0x8000): (0x8000 | x) - t keeps bit 15 set exactly when x >= t, and
-// never borrows into the other half of the word.  The flags of four words
-// are gathered at distinct bit positions (shifts 0..3) for one popc.
+// Number of the sixteen slots of a leaf (a, b: eight 32-bit words, two
+// 16-bit slots each) that are at least t (t <= 0x8000).  Slots 0..14 hold
+// the leaf's 15-bit key offsets with bit 15 set: (0x8000 | x) - t keeps bit
+// 15 set exactly when x >= t and never borrows into the other half of the
+// word.  Slot 15 holds the leaf's shift instead (its key is the leaf's
+// sample, at least the target by the choice of the leaf) and always counts.
+// The flags of four words are gathered at distinct bit positions (shifts
+// 0..3) for one popc; slot 15's lands on bit 28.
 __device__ __forceinline__ int count_ge15(const uint4& a, const uint4& b, uint32_t t) {
   const uint32_t t2 = t | (t << 16);
   const uint32_t m = 0x80008000u;
   const uint32_t pa = ((a.x - t2) & m) | (((a.y - t2) & m) >> 1) | (((a.z - t2) & m) >> 2) | (((a.w - t2) & m) >> 3);
   const uint32_t pb = ((b.x - t2) & m) | (((b.y - t2) & m) >> 1) | (((b.z - t2) & m) >> 2) | (((b.w - t2) & m) >> 3);
-  return __popc(pa) + __popc(pb);
+  return __popc(pa) + __popc(pb | (1u << 28));
 }
 
 // Count of keys below q on a wide section: the leaf from the sample
@@ -351,12 +354,13 @@ __device__ __forceinline__ int wide_count(const WideView& wv, uint64_t q) {
     base = s > 0 ? wv.samples[SS_IX(s - 1, nsamp)] : wv.k0;
   }
   if (q <= base) return kLeaf * s;               // only below X[0] (leaf 0)
-  const uint32_t tq = (uint32_t)((q - base) >> wv.shifts[SS_IX(s, wv.w.L)]);   // < 2^15: q <= samples[s]
   // the two halves of a leaf sit in two arrays of 16-byte entries: read at a
   // 16-byte stride, a warp's random leaves spread over all shared-memory banks
-  // (one 32-byte leaf read as two 16-byte halves used half of them)
+  // (one 32-byte leaf read as two 16-byte halves used half of them); the
+  // leaf's shift is its last slot
   const uint4* l4 = reinterpret_cast<const uint4*>(wv.leaf);
   const uint4 a = l4[SS_IX(s, wv.w.L)], b = l4[SS_IX(wv.w.L + s, 2 * wv.w.L)];
+  const uint32_t tq = (uint32_t)((q - base) >> (b.w >> 16));   // < 2^15: q <= samples[s]
   int c = kLeaf - count_ge15(a, b, tq);                          // offsets below the target's
   // a leaf's offsets never decrease, so offsets equal to the target's (whose
   // keys are compared in full) start at position c; offset c, picked from the
