@@ -411,11 +411,13 @@ __device__ __forceinline__ int plain_binary(const StagedView& v, uint64_t q) {
   return finish_full(v, search_eyt_rt(v.eyt, v.h.D, q), q);
 }
 
-// Learned search: proposal p (count units), exact check that the answer lies
-// in [p-E, p+E], then the count inside the window; plain bucket search if the
-// check fails.  Windows of at most 6 keys are scanned with independent loads
-// (one memory round trip), wider ones bisected.  KEYS reads the keys from
-// shared memory (whole table staged) or global memory (sampled table).
+// Learned search in a window: proposal p (count units), exact check that the
+// answer lies in [p-E, p+E], then the count inside the window; plain bucket
+// search if the check fails.  Windows of at most 6 keys are scanned with
+// independent loads (one memory round trip), wider ones bisected.  KEYS reads
+// the keys from shared memory (whole table staged) or global memory (sampled
+// table).  Staged tables with small windows walk from the proposal instead
+// (learned_count).
 template <class KEYS>
 __device__ __forceinline__ int window_count(KEYS key, int nk, int E, int p, uint64_t q, bool& ok) {
   const int lo = max(p - E, 0), hi = min(p + E, nk);
@@ -447,6 +449,10 @@ __device__ __forceinline__ int window_count(KEYS key, int nk, int E, int p, uint
   return c;
 }
 
+// Largest learned half-window that a staged table walks from the proposal
+// (wider windows are checked and bisected by window_count).
+constexpr int kProbeWindow = 4;
+
 __device__ __forceinline__ int learned_count(const StagedView& v, int p, uint64_t q, int& fallbacks) {
   const BlobHdr& h = v.h;
   bool ok;
@@ -454,6 +460,27 @@ __device__ __forceinline__ int learned_count(const StagedView& v, int p, uint64_
   if (h.stride == 1) {
     const uint64_t* keys = v.keys;
     const int lim = h.ns + kPad;
+    if (h.E <= kProbeWindow) {   // uniform per table
+      // the proposal's two neighbouring keys decide it in one shared-memory
+      // round trip (the answer is p when key(p-1) < q <= key(p); keys[nk] is
+      // a sentinel); otherwise they show the direction, and the answer is
+      // walked to, each step proved by the keys on both sides of it, for at
+      // most E keys before the plain search takes over.  On staged tables
+      // this reads two keys where the window check and scan read 2E + 2.
+      const int pp = min(max(p, 0), h.nk);
+      const uint64_t kb = keys[SS_IX(max(pp - 1, 0), lim)], ke = keys[SS_IX(pp, lim)];
+      const bool below = (pp > 0) & (kb >= q), above = ke < q;
+      if (!(below | above)) return pp;
+      if (above) {                               // key(pp) < q: the answer is above pp
+        for (int j = pp + 1, st = 0; st < h.E && j <= h.nk; ++st, ++j)
+          if (q <= keys[SS_IX(j, lim)]) return j;
+      } else {                                   // key(pp-1) >= q: the answer is below pp
+        for (int j = pp - 1, st = 0; st < h.E; ++st, --j)
+          if (j == 0 || keys[SS_IX(j - 1, lim)] < q) return j;
+      }
+      ++fallbacks;
+      return plain_bucket(v, q);
+    }
     c = window_count([keys, lim](int i) { return keys[SS_IX(i, lim)]; }, h.nk, h.E, p, q, ok);
   } else {
     const uint64_t* full = v.full;
