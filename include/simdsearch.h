@@ -175,10 +175,12 @@ ss_status ss_search_interp_2d_host(const double* R, int32_t nr, const double* T,
 typedef struct ss_plan ss_plan;
 
 /* Learned position model used as the proposal of every table of a plan.
- * The model only proposes: each index is checked exactly against the table
+ * The model only proposes: each index is proved exactly against the table
  * (the answer must lie in a window [p-E, p+E] whose ends are compared with
- * the target) and a failed check falls back to the plain search, so results
- * are identical with or without a model. */
+ * the target, or, on a table staged whole with E <= 4, the keys on both
+ * sides of the answer are read while walking at most E keys from p) and a
+ * failed proof falls back to the plain search, so results are identical
+ * with or without a model. */
 typedef enum ss_model {
   SS_MODEL_NONE = 0,    /* plain search only */
   SS_MODEL_SPLINE = 1,  /* piecewise-linear map of the target's key, knots = bucket directory */
