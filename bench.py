@@ -547,6 +547,8 @@ class PlanWorkload(Workload):
         res = {"model": model, "Gtargets_s": round(self.targets() / (ms / 1e3) / 1e9, 3),
                "ms_per_step": round(ms, 4), "choices": other.choices(), "max_window": inf.max_window,
                "mean_window": round(inf.mean_window, 2), "train_loss": inf.train_loss}
+        if inf.kind == 2:
+            res["lean_kernel"] = inf.lean_kernel
         self.bind(self.plan)
         del other
         return res

@@ -80,8 +80,8 @@ ss_status batch_work_2d(const char* me, int32_t ntables, const int64_t* R_off, c
   if (w.smem > max_smem_optin()) return fail(SS_EUNSUPPORTED, std::string(me) + ": axes too large for shared memory");
   // tiles as a plan without tuning takes them, capped for the corner records in flight
   int per_sm = 0;
-  if (ss_status st_ = raise_smem_limit(batched_2d_fast_kernel(), w.smem)) return st_;
-  SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_2d_fast_kernel(), kNumThreads, w.smem));
+  if (ss_status st_ = raise_smem_limit(batched_2d_fast_kernel(BL_BUCKET), w.smem)) return st_;
+  SS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_2d_fast_kernel(BL_BUCKET), kNumThreads, w.smem));
   const int resident = std::max(1, num_sms() * per_sm);
   const int64_t total = Y_off[nt] - Y_off[0];
   int dev = 0, l2 = 0;
@@ -157,7 +157,8 @@ ss_status queue_work_2d(const BatchWork2D& w, unsigned char* base, int32_t ntabl
                                        reinterpret_cast<const int64_t*>(base + w.xr),
                                        reinterpret_cast<const int64_t*>(base + w.xt),
                                        reinterpret_cast<const int64_t*>(base + w.co), cells, gate);
-  k_fast_2d_check<<<std::max(1, std::min(1024, (2 * nt + 255) / 256)), 256, 0, stream>>>(blobs, blob_off, 2 * nt, gate);
+  k_fast_2d_check<<<std::max(1, std::min(1024, (2 * nt + 255) / 256)), 256, 0, stream>>>(blobs, blob_off, 2 * nt,
+                                                                                      BL_BUCKET, gate);
   SS_CHECK_CUDA(cudaGetLastError());
   if (w.tiles.empty()) return SS_OK;
   const int ntiles = (int)w.tiles.size();
@@ -165,7 +166,7 @@ ss_status queue_work_2d(const BatchWork2D& w, unsigned char* base, int32_t ntabl
   k_pick_2d<<<1, 1, 0, stream>>>(gate, counters, ntiles);
   SS_CHECK_CUDA(cudaGetLastError());
   const int vec = (aligned(Y2, 16) && aligned(lowbounds2, 16) && aligned(values, 16)) ? (aligned(Y2, 32) ? 2 : 1) : 0;
-  const void* kerns[2] = {batched_2d_fast_kernel(), batched_2d_kernel(false, false)};
+  const void* kerns[2] = {batched_2d_fast_kernel(BL_BUCKET), batched_2d_kernel(false, false)};
   for (int j = 0; j < 2; ++j) {
     if (ss_status st_ = raise_smem_limit(kerns[j], w.smem)) return st_;
     int per_sm = 0;

@@ -100,9 +100,10 @@ __global__ void k_prep_1d(PrepArgs a);
 __global__ void k_train_mlp(TrainArgs a);
 __global__ void k_window(WindowArgs a);
 const void* batched_1d_kernel(bool le, int family);   // family: 0 plain, 1 +spline/loghash, 2 +mlp, 3 hunt
-const void* batched_2d_fast_kernel();                  // the lean 2D kernel (every axis on the common path)
+const void* batched_2d_fast_kernel(int algo);          // the lean 2D kernel for axes searched by algo
+                                                       // (bucket, spline or loghash; see k_fast_2d_check)
 __global__ void k_fast_2d_check(const unsigned char* __restrict__ blobs, const int64_t* __restrict__ blob_off,
-                                int naxes, unsigned* not_fast);
+                                int naxes, int algo, unsigned* not_fast);
 const void* batched_1d_wide_kernel(bool le);          // tables searched through their wide section
 constexpr int kWideThreads = 1024;
 const void* batched_2d_kernel(bool hunt, bool learned);   // hunt: second pair of a thread starts from the first; learned: position models compiled in

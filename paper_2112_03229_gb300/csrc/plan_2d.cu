@@ -365,11 +365,19 @@ __global__ void __launch_bounds__(kNumThreads, 3) k_batched_2d(BatchArgs2D a) {
 // interpolation option is set (checked on the device when a batch is bound,
 // k_fast_2d_check): per axis it keeps only the handful of fields that case
 // reads, as shared-memory offsets, so fewer registers stay live and more
-// warps fit on an SM than in the general kernel.
+// warps fit on an SM than in the general kernel.  Plans with the spline or
+// the logarithm-hash model run instances of it (MODEL) when, besides, every
+// axis is that model's proposal with a window of at most kProbeWindow keys:
+// the proposal is proved by the walk of the general kernel (same answers,
+// same fallbacks), the fallback is the two-key bucket scan.
 // ---------------------------------------------------------------------------
+enum FastModel { kFastPlain = 0, kFastSpline = 1, kFastLogHash = 2 };
+
 struct FastAxis {
   int keys, dir, ca, cg;     // shared-memory byte offsets: keys, directory, cell records, cell scales
   int shift, nb, n;
+  int E;                     // learned half-window (learned instances)
+  float la, lc;              // logarithm-hash coefficients (that instance)
   uint64_t base, k0;
 };
 
@@ -384,7 +392,35 @@ __device__ __forceinline__ FastAxis fast_axis(const StagedView& v, const unsigne
   f.n = v.h.n;
   f.base = v.h.base;
   f.k0 = v.h.k0;
+  f.E = v.h.E;
+  f.la = f.lc = 0.0f;
+  if (v.h.algo == BL_LOGHASH) {
+    f.la = v.mlp[kMlpParams];
+    f.lc = v.mlp[kMlpParams + 1];
+  }
   return f;
+}
+
+// Count of keys below q on a fast axis: the bucket directory's two-key scan,
+// or (learned instances) the model's proposal proved by a walk of at most E
+// keys, with the scan as fallback.  n - 1 keys are searched.
+template <int MODEL, int HI>
+__device__ __forceinline__ int fast_count(const unsigned char* smem, const FastAxis& f, double t, uint64_t q,
+                                          int& fallbacks) {
+  const uint64_t* keys = reinterpret_cast<const uint64_t*>(smem + f.keys);
+  const uint16_t* dir = reinterpret_cast<const uint16_t*>(smem + f.dir);
+  if constexpr (MODEL != kFastPlain) {
+    const int nk = f.n - 1;
+    const int p = MODEL == kFastSpline ? min((int)rintf(spline_position(dir, f.shift, f.base, f.nb, q)), nk)
+                                       : loghash_propose(f.la, f.lc, nk, t);
+    int c;
+    if (walk_count(keys, nk + kPad, nk, f.E, p, q, c)) return c;
+    ++fallbacks;
+  } else {
+    (void)t;
+    (void)fallbacks;
+  }
+  return search_bucket<2, HI>(keys, dir, f.shift, f.base, f.nb, q);
 }
 
 // Weights of coordinate bits u (key k, index i, cell c) on a fast axis.
@@ -401,19 +437,17 @@ __device__ __forceinline__ Weights fast_weights(const unsigned char* smem, const
   return cell_weights(u, t, c);
 }
 
-template <int HI>   // 1: both bucket shifts are 32 or more; -1: decided per call
+template <int MODEL, int HI>   // HI 1: both bucket shifts are 32 or more; -1: decided per call
 __device__ __forceinline__ void pair_fast(const unsigned char* smem, const FastAxis& fr, const FastAxis& ft,
                                           const float4* __restrict__ G, uint64_t keep, double rho, double tem,
-                                          int& ir, int& it, double& v, int& nans) {
+                                          int& ir, int& it, double& v, int& nans, int& fallbacks) {
   const uint64_t ur = static_cast<uint64_t>(__double_as_longlong(rho));
   const uint64_t ut = static_cast<uint64_t>(__double_as_longlong(tem));
   const uint64_t kr = order_key(rho), kt = order_key(tem);
   const bool nan = (kr < kKeyNegInf) | (kt < kKeyNegInf);
   nans += (kr < kKeyNegInf) + (kt < kKeyNegInf);
-  ir = search_bucket<2, HI>(reinterpret_cast<const uint64_t*>(smem + fr.keys),
-                            reinterpret_cast<const uint16_t*>(smem + fr.dir), fr.shift, fr.base, fr.nb, kr);
-  it = search_bucket<2, HI>(reinterpret_cast<const uint64_t*>(smem + ft.keys),
-                            reinterpret_cast<const uint16_t*>(smem + ft.dir), ft.shift, ft.base, ft.nb, kt);
+  ir = fast_count<MODEL, HI>(smem, fr, rho, kr, fallbacks);
+  it = fast_count<MODEL, HI>(smem, ft, tem, kt, fallbacks);
   const int cr = min(ir, fr.n - 2), ct = min(it, ft.n - 2);
   const int64_t cell = (int64_t)cr * (ft.n - 1) + ct;
   float q[8];
@@ -425,11 +459,12 @@ __device__ __forceinline__ void pair_fast(const unsigned char* smem, const FastA
   v = nan ? __longlong_as_double(0x7FF8000000000000ll) : ff2d(ff_add_u(ff_mul_u(wr.wbar, lo), ff_mul_u(wr.w, hi)));
 }
 
-// Four blocks of 256 threads per SM (61 registers, no spills; the general
-// kernel's 80 registers allow three).  Two pairs per thread and step, as in
+// Four blocks of 256 threads per SM (at most 64 registers, no spills, in
+// every instance; the general kernel's 80 registers allow three).  Two pairs per thread and step, as in
 // the general kernel: one pair per step measured 6 % slower.  Corner
 // gathers carry an evict-last L2 policy and the 256-bit target loads an
 // evict-first one (1-2 % measured).
+template <int MODEL>
 __global__ void __launch_bounds__(kNumThreads, 4) k_batched_2d_fast(BatchArgs2D a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const uint64_t keep = l2_policy_evict_last(), pass = l2_policy_evict_first();
@@ -441,7 +476,7 @@ __global__ void __launch_bounds__(kNumThreads, 4) k_batched_2d_fast(BatchArgs2D 
   int cur = -1;
   FastAxis fr{}, ft{};
   bool ok = true;
-  int nans = 0;
+  int nans = 0, fallbacks = 0;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(a.counter, 1);
     __syncthreads();
@@ -474,7 +509,8 @@ __global__ void __launch_bounds__(kNumThreads, 4) k_batched_2d_fast(BatchArgs2D 
     auto scalar = [&](int i) {
       int ir, it;
       double v;
-      pair_fast<-1>(smem, fr, ft, G, keep, a.Y2[2 * (b + i)], a.Y2[2 * (b + i) + 1], ir, it, v, nans);
+      pair_fast<MODEL, -1>(smem, fr, ft, G, keep, a.Y2[2 * (b + i)], a.Y2[2 * (b + i) + 1], ir, it, v, nans,
+                           fallbacks);
       a.idx[2 * (b + i)] = ir;
       a.idx[2 * (b + i) + 1] = it;
       a.val[b + i] = v;
@@ -506,8 +542,8 @@ __global__ void __launch_bounds__(kNumThreads, 4) k_batched_2d_fast(BatchArgs2D 
         }
         int i0, j0, i1, j1;
         double v0, v1;
-        pair_fast<HI>(smem, fr, ft, G, keep, p0.x, p0.y, i0, j0, v0, nans);
-        pair_fast<HI>(smem, fr, ft, G, keep, p1.x, p1.y, i1, j1, v1, nans);
+        pair_fast<MODEL, HI>(smem, fr, ft, G, keep, p0.x, p0.y, i0, j0, v0, nans, fallbacks);
+        pair_fast<MODEL, HI>(smem, fr, ft, G, keep, p1.x, p1.y, i1, j1, v1, nans, fallbacks);
         st_stream(I4 + g, make_int4(i0, j0, i1, j1));
         st_stream(V2 + g, make_double2(v0, v1));
       }
@@ -518,23 +554,34 @@ __global__ void __launch_bounds__(kNumThreads, 4) k_batched_2d_fast(BatchArgs2D 
   }
   nans = __reduce_add_sync(0xFFFFFFFFu, nans);
   if (a.stat != nullptr && (threadIdx.x & 31) == 0 && nans) atomicAdd(&a.stat->nan_targets, (unsigned long long)nans);
+  if constexpr (MODEL != kFastPlain) {
+    fallbacks = __reduce_add_sync(0xFFFFFFFFu, fallbacks);
+    if (a.stat != nullptr && (threadIdx.x & 31) == 0 && fallbacks)
+      atomicAdd(&a.stat->fallbacks, (unsigned long long)fallbacks);
+  }
   if (a.stat != nullptr && threadIdx.x == 0 && !ok) atomicOr(&a.stat->flags, SS_FLAG_STAGING_TIMEOUT);
   SS_BOUNDS_FOLD(a.stat);
 }
 
 // Eligibility of a plan for the lean kernel: *not_fast stays 0 when every
-// axis is a bucket search over a whole staged table with at most two keys
-// per bucket and float-float cell data.
+// axis is searched with algorithm `algo` over a whole staged table with at
+// most two keys per bucket and float-float cell data, and, for a position
+// model (spline, logarithm hash), with a window of at most kProbeWindow keys.
 __global__ void k_fast_2d_check(const unsigned char* __restrict__ blobs, const int64_t* __restrict__ blob_off,
-                                int naxes, unsigned* not_fast) {
+                                int naxes, int algo, unsigned* not_fast) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < naxes; j += gridDim.x * blockDim.x) {
     const BlobHdr* h = reinterpret_cast<const BlobHdr*>(blobs + blob_off[j]);
-    if (!(h->algo == BL_BUCKET && h->stride == 1 && h->occ <= 2 && h->ffok == 1 && h->off_cells >= 0))
+    if (!(h->algo == algo && h->stride == 1 && h->occ <= 2 && h->ffok == 1 && h->off_cells >= 0 &&
+          (algo == BL_BUCKET || h->E <= kProbeWindow)))
       atomicOr(not_fast, 1u);
   }
 }
 
-const void* batched_2d_fast_kernel() { return reinterpret_cast<const void*>(&k_batched_2d_fast); }
+const void* batched_2d_fast_kernel(int algo) {
+  if (algo == BL_SPLINE) return reinterpret_cast<const void*>(&k_batched_2d_fast<kFastSpline>);
+  if (algo == BL_LOGHASH) return reinterpret_cast<const void*>(&k_batched_2d_fast<kFastLogHash>);
+  return reinterpret_cast<const void*>(&k_batched_2d_fast<kFastPlain>);
+}
 
 // Kernel entry of the batched 2D lookup (template stubs stay local to this unit).
 const void* batched_2d_kernel(bool hunt, bool learned) {

@@ -329,15 +329,20 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
   // 2D plans whose every axis takes the common path (bucket search over a
   // whole staged axis, at most two keys per bucket, float-float cells) and
   // no interpolation option run the lean kernel: fewer live registers, four
-  // blocks per SM instead of three
+  // blocks per SM instead of three.  With the spline or the logarithm-hash
+  // model, so do those whose every axis has a window of at most
+  // kProbeWindow keys (that model's instance of the lean kernel).
   p->lean = 0;
-  if (p->kind == 2 && p->opts.model == SS_MODEL_NONE && !p->opts.extrap && !p->opts.logspace &&
-      p->d_grid64 == nullptr) {
+  const int lean_algo = p->opts.model == SS_MODEL_NONE      ? BL_BUCKET
+                        : p->opts.model == SS_MODEL_SPLINE  ? BL_SPLINE
+                        : p->opts.model == SS_MODEL_LOGHASH ? BL_LOGHASH
+                                                            : -1;
+  if (p->kind == 2 && lean_algo >= 0 && !p->opts.extrap && !p->opts.logspace && p->d_grid64 == nullptr) {
     if (p->d_counter == nullptr) SS_CHECK_CUDA(cudaMalloc(&p->d_counter, 2 * sizeof(int)));
     SS_CHECK_CUDA(cudaMemsetAsync(p->d_counter, 0, sizeof(int), stream));
     const int naxes = 2 * p->ntables;
     k_fast_2d_check<<<std::max(1, std::min(1024, (naxes + 255) / 256)), 256, 0, stream>>>(
-        p->d_blobs, p->d_blob_off, naxes, reinterpret_cast<unsigned*>(p->d_counter));
+        p->d_blobs, p->d_blob_off, naxes, lean_algo, reinterpret_cast<unsigned*>(p->d_counter));
     SS_CHECK_CUDA(cudaGetLastError());
     unsigned not_fast = 1;
     SS_CHECK_CUDA(cudaMemcpyAsync(&not_fast, p->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
@@ -345,7 +350,7 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
     p->lean = not_fast == 0 ? 1 : 0;
   }
   if (p->kind == 1) kern = batched_1d_kernel(p->opts.side == SS_SIDE_LE, family);
-  else if (p->lean) kern = batched_2d_fast_kernel();
+  else if (p->lean) kern = batched_2d_fast_kernel(lean_algo);
   else kern = batched_2d_kernel(p->opts.model == SS_MODEL_HUNT, family > 0);
   if (ss_status st_ = raise_smem_limit(kern, smem)) return st_;
   int per_sm = 0;

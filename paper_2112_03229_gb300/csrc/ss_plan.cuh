@@ -453,6 +453,32 @@ __device__ __forceinline__ int window_count(KEYS key, int nk, int E, int p, uint
 // (wider windows are checked and bisected by window_count).
 constexpr int kProbeWindow = 4;
 
+// Walk from proposal p on staged keys (nk searched keys, keys[nk] a
+// sentinel, E <= kProbeWindow): the proposal's two neighbouring keys decide
+// it in one shared-memory round trip (the answer is p when key(p-1) < q <=
+// key(p)); otherwise they show the direction, and the answer is walked to,
+// each step proved by the keys on both sides of it, for at most E keys.
+// Returns false when the answer lies farther (the caller searches plainly).
+// On staged tables this reads two keys where the window check and scan read
+// 2E + 2.
+__device__ __forceinline__ bool walk_count(const uint64_t* __restrict__ keys, int lim, int nk, int E, int p,
+                                           uint64_t q, int& c) {
+  (void)lim;
+  const int pp = min(max(p, 0), nk);
+  const uint64_t kb = keys[SS_IX(max(pp - 1, 0), lim)], ke = keys[SS_IX(pp, lim)];
+  const bool below = (pp > 0) & (kb >= q), above = ke < q;
+  c = pp;
+  if (!(below | above)) return true;
+  if (above) {                               // key(pp) < q: the answer is above pp
+    for (int j = pp + 1, st = 0; st < E && j <= nk; ++st, ++j)
+      if (q <= keys[SS_IX(j, lim)]) { c = j; return true; }
+  } else {                                   // key(pp-1) >= q: the answer is below pp
+    for (int j = pp - 1, st = 0; st < E; ++st, --j)
+      if (j == 0 || keys[SS_IX(j - 1, lim)] < q) { c = j; return true; }
+  }
+  return false;
+}
+
 __device__ __forceinline__ int learned_count(const StagedView& v, int p, uint64_t q, int& fallbacks) {
   const BlobHdr& h = v.h;
   bool ok;
@@ -461,23 +487,7 @@ __device__ __forceinline__ int learned_count(const StagedView& v, int p, uint64_
     const uint64_t* keys = v.keys;
     const int lim = h.ns + kPad;
     if (h.E <= kProbeWindow) {   // uniform per table
-      // the proposal's two neighbouring keys decide it in one shared-memory
-      // round trip (the answer is p when key(p-1) < q <= key(p); keys[nk] is
-      // a sentinel); otherwise they show the direction, and the answer is
-      // walked to, each step proved by the keys on both sides of it, for at
-      // most E keys before the plain search takes over.  On staged tables
-      // this reads two keys where the window check and scan read 2E + 2.
-      const int pp = min(max(p, 0), h.nk);
-      const uint64_t kb = keys[SS_IX(max(pp - 1, 0), lim)], ke = keys[SS_IX(pp, lim)];
-      const bool below = (pp > 0) & (kb >= q), above = ke < q;
-      if (!(below | above)) return pp;
-      if (above) {                               // key(pp) < q: the answer is above pp
-        for (int j = pp + 1, st = 0; st < h.E && j <= h.nk; ++st, ++j)
-          if (q <= keys[SS_IX(j, lim)]) return j;
-      } else {                                   // key(pp-1) >= q: the answer is below pp
-        for (int j = pp - 1, st = 0; st < h.E; ++st, --j)
-          if (j == 0 || keys[SS_IX(j - 1, lim)] < q) return j;
-      }
+      if (walk_count(keys, lim, h.nk, h.E, p, q, c)) return c;
       ++fallbacks;
       return plain_bucket(v, q);
     }

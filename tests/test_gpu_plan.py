@@ -617,9 +617,10 @@ def test_plan_2d_lean_kernel(ss):
     """The lean kernel runs when every axis is a bucket search over a whole
     staged axis with at most two keys per bucket and float-float cells (the
     standard batch); it gives the oracle's indices and values, on aligned
-    and misaligned arrays, with NaN pairs; plans outside its case (an
-    interpolation option, a position model, a binary-search axis) run the
-    general kernel."""
+    and misaligned arrays, with NaN pairs; so does its instance for the
+    spline and logarithm-hash models, which runs when every window is at
+    most 4 keys; plans outside its case (an interpolation option, the MLP,
+    a binary-search axis) run the general kernel."""
     b = wl.batched_2d(ntables=20, pairs_per_table=5003, seed=27)
     Y2 = b.Y2.clone()
     Y2[7, 0] = float("nan")                 # a NaN coordinate: value NaN, indices exact
@@ -651,7 +652,12 @@ def test_plan_2d_lean_kernel(ss):
         run(plan, offset)
         assert plan.info().lean_kernel == 1 and plan.info().max_occupancy <= 2
     run(ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), autotune=True), 0)
-    for kw in (dict(model="spline"), dict(algo="binary"), dict(extrap=True)):
+    for model in ("spline", "loghash"):
+        learned = ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), model=model)
+        for offset in (0, 1):
+            run(learned, offset)
+        assert learned.info().lean_kernel == (1 if learned.info().max_window <= 4 else 0), model
+    for kw in (dict(model="mlp", mlp_epochs=40), dict(algo="binary"), dict(extrap=True)):
         other = ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), **kw)
         if "extrap" not in kw:
             run(other, 0)
@@ -659,6 +665,44 @@ def test_plan_2d_lean_kernel(ss):
             other.bind_2d(b.Y_off, Y2.to(DEV), torch.empty((m, 2), dtype=torch.int32, device=DEV),
                           torch.empty(m, dtype=torch.float64, device=DEV))
         assert other.info().lean_kernel == 0, kw
+
+
+def test_plan_2d_learned_lean_forced_fallback(ss, tmp_path):
+    """The lean kernel's logarithm-hash instance with every proposal wrong:
+    a saved 2D plan whose axes' coefficients are zeroed (every proposal 0)
+    and windows set to 0 still runs the lean kernel, rejects the proposals
+    (the walk of zero keys proves only an answer of 0) and gives the
+    oracle's indices and values through the plain search, counting each
+    rejected proposal as a fallback."""
+    b = wl.batched_2d(ntables=9, pairs_per_table=4001, seed=31)
+    wi, wv = oracle.search_interp_2d_batched(b.R_off.numpy(), b.R.numpy(), b.T_off.numpy(), b.T.numpy(),
+                                             b.F_off.numpy(), b.F.numpy(), b.Y_off.numpy(), b.Y2.numpy())
+    plan = ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), model="loghash")
+    path = tmp_path / "plan2d.bin"
+    plan.save(path)
+    raw = bytearray(path.read_bytes())
+    offs, start = _blob_headers(bytes(raw))
+    assert len(offs) == 2 * 9
+    for o in offs:
+        h = start + o
+        struct.pack_into("<i", raw, h + HDR_E, 0)
+        off_mlp = struct.unpack_from("<i", raw, h + 48)[0]
+        struct.pack_into("<2f", raw, h + off_mlp + 4 * 65, 0.0, 0.0)            # a = c = 0: proposal 0
+    bad = tmp_path / "bad2d.bin"
+    bad.write_bytes(bytes(raw))
+    re = ss.Plan.load(bad)
+    m = b.Y2.shape[0]
+    idx = torch.full((m, 2), -1, dtype=torch.int32, device=DEV)
+    val = torch.empty(m, dtype=torch.float64, device=DEV)
+    stat = ss.new_stat()
+    re.bind_2d(b.Y_off, b.Y2.to(DEV), idx, val, stat=stat)
+    re.execute()
+    assert re.info().lean_kernel == 1
+    np.testing.assert_array_equal(idx.cpu().numpy(), wi)
+    assert (np.abs(val.cpu().numpy() - wv) / np.abs(wv)).max() <= REL_TOL
+    # every coordinate whose answer is not 0 is a rejected proposal
+    st = ss.read_stat(stat)
+    assert st.fallbacks == int(np.count_nonzero(wi != 0)), (st.fallbacks, int(np.count_nonzero(wi != 0)))
 
 
 @pytest.mark.parametrize("extrap,logspace", [(1, 0), (0, 1), (1, 1)])
