@@ -365,19 +365,22 @@ __global__ void __launch_bounds__(kNumThreads, 3) k_batched_2d(BatchArgs2D a) {
 // interpolation option is set (checked on the device when a batch is bound,
 // k_fast_2d_check): per axis it keeps only the handful of fields that case
 // reads, as shared-memory offsets, so fewer registers stay live and more
-// warps fit on an SM than in the general kernel.  Plans with the spline or
-// the logarithm-hash model run instances of it (MODEL) when, besides, every
-// axis is that model's proposal with a window of at most kProbeWindow keys:
-// the proposal is proved by the walk of the general kernel (same answers,
-// same fallbacks), the fallback is the two-key bucket scan.
+// warps fit on an SM than in the general kernel.  Plans with a position
+// model (spline, MLP, logarithm hash) run instances of it (MODEL) when,
+// besides, every axis is that model's proposal with a window of at most
+// kProbeWindow keys: the proposal is proved by the walk of the general
+// kernel (same answers, same fallbacks), the fallback is the two-key bucket
+// scan.
 // ---------------------------------------------------------------------------
-enum FastModel { kFastPlain = 0, kFastSpline = 1, kFastLogHash = 2 };
+enum FastModel { kFastPlain = 0, kFastSpline = 1, kFastLogHash = 2, kFastMlp = 3 };
 
 struct FastAxis {
   int keys, dir, ca, cg;     // shared-memory byte offsets: keys, directory, cell records, cell scales
   int shift, nb, n;
   int E;                     // learned half-window (learned instances)
   float la, lc;              // logarithm-hash coefficients (that instance)
+  int mlp;                   // shared-memory byte offset of the MLP parameters (that instance)
+  MlpFeatScale sc;           // MLP feature scaling (that instance)
   uint64_t base, k0;
 };
 
@@ -398,6 +401,8 @@ __device__ __forceinline__ FastAxis fast_axis(const StagedView& v, const unsigne
     f.la = v.mlp[kMlpParams];
     f.lc = v.mlp[kMlpParams + 1];
   }
+  f.mlp = (int)(reinterpret_cast<const unsigned char*>(v.mlp) - smem);
+  f.sc = MlpFeatScale{v.h.e_lo, v.h.e_scale};
   return f;
 }
 
@@ -411,8 +416,10 @@ __device__ __forceinline__ int fast_count(const unsigned char* smem, const FastA
   const uint16_t* dir = reinterpret_cast<const uint16_t*>(smem + f.dir);
   if constexpr (MODEL != kFastPlain) {
     const int nk = f.n - 1;
-    const int p = MODEL == kFastSpline ? min((int)rintf(spline_position(dir, f.shift, f.base, f.nb, q)), nk)
-                                       : loghash_propose(f.la, f.lc, nk, t);
+    int p;
+    if constexpr (MODEL == kFastSpline) p = min((int)rintf(spline_position(dir, f.shift, f.base, f.nb, q)), nk);
+    else if constexpr (MODEL == kFastLogHash) p = loghash_propose(f.la, f.lc, nk, t);
+    else p = mlp_propose(reinterpret_cast<const float*>(smem + f.mlp), f.sc, f.n, t);
     int c;
     if (walk_count(keys, nk + kPad, nk, f.E, p, q, c)) return c;
     ++fallbacks;
@@ -566,7 +573,8 @@ __global__ void __launch_bounds__(kNumThreads, 4) k_batched_2d_fast(BatchArgs2D 
 // Eligibility of a plan for the lean kernel: *not_fast stays 0 when every
 // axis is searched with algorithm `algo` over a whole staged table with at
 // most two keys per bucket and float-float cell data, and, for a position
-// model (spline, logarithm hash), with a window of at most kProbeWindow keys.
+// model (spline, MLP, logarithm hash), with a window of at most kProbeWindow
+// keys.
 __global__ void k_fast_2d_check(const unsigned char* __restrict__ blobs, const int64_t* __restrict__ blob_off,
                                 int naxes, int algo, unsigned* not_fast) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < naxes; j += gridDim.x * blockDim.x) {
@@ -580,6 +588,7 @@ __global__ void k_fast_2d_check(const unsigned char* __restrict__ blobs, const i
 const void* batched_2d_fast_kernel(int algo) {
   if (algo == BL_SPLINE) return reinterpret_cast<const void*>(&k_batched_2d_fast<kFastSpline>);
   if (algo == BL_LOGHASH) return reinterpret_cast<const void*>(&k_batched_2d_fast<kFastLogHash>);
+  if (algo == BL_MLP) return reinterpret_cast<const void*>(&k_batched_2d_fast<kFastMlp>);
   return reinterpret_cast<const void*>(&k_batched_2d_fast<kFastPlain>);
 }
 

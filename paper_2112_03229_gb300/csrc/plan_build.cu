@@ -329,13 +329,14 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
   // 2D plans whose every axis takes the common path (bucket search over a
   // whole staged axis, at most two keys per bucket, float-float cells) and
   // no interpolation option run the lean kernel: fewer live registers, four
-  // blocks per SM instead of three.  With the spline or the logarithm-hash
-  // model, so do those whose every axis has a window of at most
+  // blocks per SM instead of three.  With a position model (spline, MLP,
+  // logarithm hash), so do those whose every axis has a window of at most
   // kProbeWindow keys (that model's instance of the lean kernel).
   p->lean = 0;
   const int lean_algo = p->opts.model == SS_MODEL_NONE      ? BL_BUCKET
                         : p->opts.model == SS_MODEL_SPLINE  ? BL_SPLINE
                         : p->opts.model == SS_MODEL_LOGHASH ? BL_LOGHASH
+                        : p->opts.model == SS_MODEL_MLP     ? BL_MLP
                                                             : -1;
   if (p->kind == 2 && lean_algo >= 0 && !p->opts.extrap && !p->opts.logspace && p->d_grid64 == nullptr) {
     if (p->d_counter == nullptr) SS_CHECK_CUDA(cudaMalloc(&p->d_counter, 2 * sizeof(int)));

@@ -92,27 +92,40 @@ def test_sweep_full_size_sampled(ss):
 
 @pytest.mark.parametrize("coherent", [False, True])
 def test_batched2d_full_size_sampled(ss, coherent):
-    """1,000 2D tables, 1M pairs each (1B pairs), random or coherent order."""
+    """1,000 2D tables, 1M pairs each (1B pairs), random or coherent order:
+    the plain plan (autotuned) and each position model's plan (the spline,
+    the logarithm hash and the MLP in the lean kernel's instances when
+    their windows allow, the hunt in the general kernel), sampled against
+    the oracle."""
     b = wl.batched_2d(ntables=1000, pairs_per_table=1_000_000, coherent=coherent, seed=6, device=DEV)
-    plan = ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), autotune=True)
     m = b.Y2.shape[0]
-    idx = torch.full((m, 2), -1, dtype=torch.int32, device=DEV)
+    idx = torch.empty((m, 2), dtype=torch.int32, device=DEV)
     val = torch.empty(m, dtype=torch.float64, device=DEV)
-    plan.bind_2d(b.Y_off, b.Y2, idx, val)
-    plan.execute()
-    torch.cuda.synchronize()
-    assert int(idx.min()) >= 0
     pos = sampled_positions(m, 500_000, seed=3 + int(coherent))
     tp = torch.from_numpy(pos).to(DEV)
-    gi, gv, y = idx[tp].cpu().numpy(), val[tp].cpu().numpy(), b.Y2[tp].cpu().numpy()
+    y = b.Y2[tp].cpu().numpy()
     offs = [o.cpu().numpy() for o in (b.R_off, b.T_off, b.F_off, b.Y_off)]
     R, T, F = b.R.cpu().numpy(), b.T.cpu().numpy(), b.F.cpu().numpy()
     tab = np.searchsorted(offs[3], pos, side="right") - 1
+    want_i = np.empty((len(pos), 2), dtype=np.int32)
+    want_v = np.empty(len(pos))
     for t in np.unique(tab):
         sel = tab == t
-        wi, wv = oracle.search_interp_2d(R[offs[0][t]:offs[0][t + 1]], T[offs[1][t]:offs[1][t + 1]],
-                                         F[offs[2][t]:offs[2][t + 1]], y[sel])
-        np.testing.assert_array_equal(gi[sel], wi)
-        assert (np.abs(gv[sel] - wv) <= REL_TOL * np.abs(wv)).all()
-    del idx, val, b, plan
+        want_i[sel], want_v[sel] = oracle.search_interp_2d(R[offs[0][t]:offs[0][t + 1]], T[offs[1][t]:offs[1][t + 1]],
+                                                           F[offs[2][t]:offs[2][t + 1]], y[sel])
+    for model in ("none", "spline", "loghash", "mlp", "hunt"):
+        plan = ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), model=model,
+                                 autotune=model == "none")
+        idx.fill_(-1)
+        plan.bind_2d(b.Y_off, b.Y2, idx, val)
+        plan.execute()
+        torch.cuda.synchronize()
+        assert int(idx.min()) >= 0, model                 # every pair written
+        if model in ("spline", "loghash", "mlp"):
+            assert plan.info().lean_kernel == (1 if plan.info().max_window <= 4 else 0), model
+        np.testing.assert_array_equal(idx[tp].cpu().numpy(), want_i, err_msg=model)
+        gv = val[tp].cpu().numpy()
+        assert (np.abs(gv - want_v) <= REL_TOL * np.abs(want_v)).all(), model
+        del plan
+    del idx, val, b
     torch.cuda.empty_cache()

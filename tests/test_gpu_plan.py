@@ -617,10 +617,10 @@ def test_plan_2d_lean_kernel(ss):
     """The lean kernel runs when every axis is a bucket search over a whole
     staged axis with at most two keys per bucket and float-float cells (the
     standard batch); it gives the oracle's indices and values, on aligned
-    and misaligned arrays, with NaN pairs; so does its instance for the
-    spline and logarithm-hash models, which runs when every window is at
-    most 4 keys; plans outside its case (an interpolation option, the MLP,
-    a binary-search axis) run the general kernel."""
+    and misaligned arrays, with NaN pairs; so do its instances for the
+    spline, MLP and logarithm-hash models, which run when every window is
+    at most 4 keys; plans outside its case (an interpolation option, the
+    hunt, a binary-search axis) run the general kernel."""
     b = wl.batched_2d(ntables=20, pairs_per_table=5003, seed=27)
     Y2 = b.Y2.clone()
     Y2[7, 0] = float("nan")                 # a NaN coordinate: value NaN, indices exact
@@ -652,12 +652,12 @@ def test_plan_2d_lean_kernel(ss):
         run(plan, offset)
         assert plan.info().lean_kernel == 1 and plan.info().max_occupancy <= 2
     run(ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), autotune=True), 0)
-    for model in ("spline", "loghash"):
+    for model in ("spline", "loghash", "mlp"):
         learned = ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), model=model)
         for offset in (0, 1):
             run(learned, offset)
         assert learned.info().lean_kernel == (1 if learned.info().max_window <= 4 else 0), model
-    for kw in (dict(model="mlp", mlp_epochs=40), dict(algo="binary"), dict(extrap=True)):
+    for kw in (dict(model="hunt"), dict(algo="binary"), dict(extrap=True)):
         other = ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), **kw)
         if "extrap" not in kw:
             run(other, 0)
@@ -667,17 +667,20 @@ def test_plan_2d_lean_kernel(ss):
         assert other.info().lean_kernel == 0, kw
 
 
-def test_plan_2d_learned_lean_forced_fallback(ss, tmp_path):
-    """The lean kernel's logarithm-hash instance with every proposal wrong:
-    a saved 2D plan whose axes' coefficients are zeroed (every proposal 0)
-    and windows set to 0 still runs the lean kernel, rejects the proposals
+@pytest.mark.parametrize("model", ["loghash", "mlp"])
+def test_plan_2d_learned_lean_forced_fallback(ss, tmp_path, model):
+    """The lean kernel's logarithm-hash and MLP instances with every
+    proposal wrong: a saved 2D plan whose axes' coefficients (log hash) or
+    parameters (MLP) are zeroed, so that every proposal is 0, and whose
+    windows are set to 0 still runs the lean kernel, rejects the proposals
     (the walk of zero keys proves only an answer of 0) and gives the
     oracle's indices and values through the plain search, counting each
     rejected proposal as a fallback."""
     b = wl.batched_2d(ntables=9, pairs_per_table=4001, seed=31)
     wi, wv = oracle.search_interp_2d_batched(b.R_off.numpy(), b.R.numpy(), b.T_off.numpy(), b.T.numpy(),
                                              b.F_off.numpy(), b.F.numpy(), b.Y_off.numpy(), b.Y2.numpy())
-    plan = ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), model="loghash")
+    plan = ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), model=model,
+                             mlp_epochs=40 if model == "mlp" else None)
     path = tmp_path / "plan2d.bin"
     plan.save(path)
     raw = bytearray(path.read_bytes())
@@ -687,7 +690,10 @@ def test_plan_2d_learned_lean_forced_fallback(ss, tmp_path):
         h = start + o
         struct.pack_into("<i", raw, h + HDR_E, 0)
         off_mlp = struct.unpack_from("<i", raw, h + 48)[0]
-        struct.pack_into("<2f", raw, h + off_mlp + 4 * 65, 0.0, 0.0)            # a = c = 0: proposal 0
+        if model == "loghash":
+            struct.pack_into("<2f", raw, h + off_mlp + 4 * 65, 0.0, 0.0)        # a = c = 0: proposal 0
+        else:
+            struct.pack_into("<65f", raw, h + off_mlp, *([0.0] * 65))           # network output 0: proposal 0
     bad = tmp_path / "bad2d.bin"
     bad.write_bytes(bytes(raw))
     re = ss.Plan.load(bad)
