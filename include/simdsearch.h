@@ -233,8 +233,8 @@ typedef struct ss_plan_info {
   int32_t max_occupancy;    /* most keys in one directory bucket over the tables staged whole */
   int32_t lean_kernel;      /* 2D: 1 if the bound batch runs the lean kernel (every axis searched over a whole
                                staged axis with at most two keys per directory bucket, float-float cells, no
-                               interpolation option; no position model, or the spline, MLP or logarithm-hash
-                               model with every learned half-window at most 4 keys) */
+                               interpolation option; no position model, the hunt, or the spline, MLP or
+                               logarithm-hash model with every learned half-window at most 4 keys) */
 } ss_plan_info;
 
 /* Fill *opts with the defaults. */

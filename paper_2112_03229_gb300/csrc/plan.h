@@ -100,8 +100,9 @@ __global__ void k_prep_1d(PrepArgs a);
 __global__ void k_train_mlp(TrainArgs a);
 __global__ void k_window(WindowArgs a);
 const void* batched_1d_kernel(bool le, int family);   // family: 0 plain, 1 +spline/loghash, 2 +mlp, 3 hunt
-const void* batched_2d_fast_kernel(int algo);          // the lean 2D kernel for axes searched by algo
-                                                       // (bucket, spline or loghash; see k_fast_2d_check)
+const void* batched_2d_fast_kernel(int algo, bool hunt = false);   // the lean 2D kernel for axes searched by
+                                                       // algo (bucket, spline, mlp or loghash; see k_fast_2d_check),
+                                                       // or its hunt instance (bucket axes)
 __global__ void k_fast_2d_check(const unsigned char* __restrict__ blobs, const int64_t* __restrict__ blob_off,
                                 int naxes, int algo, unsigned* not_fast);
 const void* batched_1d_wide_kernel(bool le);          // tables searched through their wide section

@@ -370,9 +370,11 @@ __global__ void __launch_bounds__(kNumThreads, 3) k_batched_2d(BatchArgs2D a) {
 // besides, every axis is that model's proposal with a window of at most
 // kProbeWindow keys: the proposal is proved by the walk of the general
 // kernel (same answers, same fallbacks), the fallback is the two-key bucket
-// scan.
+// scan.  Hunt plans (Sec. 2.1) run the instance in which a thread's second
+// pair of a step hunts from the first pair's answers, as in the general
+// kernel.
 // ---------------------------------------------------------------------------
-enum FastModel { kFastPlain = 0, kFastSpline = 1, kFastLogHash = 2, kFastMlp = 3 };
+enum FastModel { kFastPlain = 0, kFastSpline = 1, kFastLogHash = 2, kFastMlp = 3, kFastHunt = 4 };
 
 struct FastAxis {
   int keys, dir, ca, cg;     // shared-memory byte offsets: keys, directory, cell records, cell scales
@@ -408,13 +410,23 @@ __device__ __forceinline__ FastAxis fast_axis(const StagedView& v, const unsigne
 
 // Count of keys below q on a fast axis: the bucket directory's two-key scan,
 // or (learned instances) the model's proposal proved by a walk of at most E
-// keys, with the scan as fallback.  n - 1 keys are searched.
+// keys, with the scan as fallback, or (hunt instance, guess >= 0) a hunt
+// from the guess with the scan beyond its probes.  n - 1 keys are searched.
 template <int MODEL, int HI>
 __device__ __forceinline__ int fast_count(const unsigned char* smem, const FastAxis& f, double t, uint64_t q,
-                                          int& fallbacks) {
+                                          int& fallbacks, int guess) {
   const uint64_t* keys = reinterpret_cast<const uint64_t*>(smem + f.keys);
   const uint16_t* dir = reinterpret_cast<const uint16_t*>(smem + f.dir);
-  if constexpr (MODEL != kFastPlain) {
+  if constexpr (MODEL == kFastHunt) {
+    (void)t;
+    (void)fallbacks;
+    if (guess >= 0) {
+      const int lim = f.n - 1 + kPad;
+      return hunt_from([keys, lim](int i) { return keys[SS_IX(i, lim)]; }, f.n - 1, guess, q,
+                       [&](uint64_t qq) { return search_bucket<2, HI>(keys, dir, f.shift, f.base, f.nb, qq); });
+    }
+  } else if constexpr (MODEL != kFastPlain) {
+    (void)guess;
     const int nk = f.n - 1;
     int p;
     if constexpr (MODEL == kFastSpline) p = min((int)rintf(spline_position(dir, f.shift, f.base, f.nb, q)), nk);
@@ -426,6 +438,7 @@ __device__ __forceinline__ int fast_count(const unsigned char* smem, const FastA
   } else {
     (void)t;
     (void)fallbacks;
+    (void)guess;
   }
   return search_bucket<2, HI>(keys, dir, f.shift, f.base, f.nb, q);
 }
@@ -444,17 +457,19 @@ __device__ __forceinline__ Weights fast_weights(const unsigned char* smem, const
   return cell_weights(u, t, c);
 }
 
+// gr, gt: the hunt instance's guesses (below zero: none)
 template <int MODEL, int HI>   // HI 1: both bucket shifts are 32 or more; -1: decided per call
 __device__ __forceinline__ void pair_fast(const unsigned char* smem, const FastAxis& fr, const FastAxis& ft,
                                           const float4* __restrict__ G, uint64_t keep, double rho, double tem,
-                                          int& ir, int& it, double& v, int& nans, int& fallbacks) {
+                                          int& ir, int& it, double& v, int& nans, int& fallbacks, int gr = -1,
+                                          int gt = -1) {
   const uint64_t ur = static_cast<uint64_t>(__double_as_longlong(rho));
   const uint64_t ut = static_cast<uint64_t>(__double_as_longlong(tem));
   const uint64_t kr = order_key(rho), kt = order_key(tem);
   const bool nan = (kr < kKeyNegInf) | (kt < kKeyNegInf);
   nans += (kr < kKeyNegInf) + (kt < kKeyNegInf);
-  ir = fast_count<MODEL, HI>(smem, fr, rho, kr, fallbacks);
-  it = fast_count<MODEL, HI>(smem, ft, tem, kt, fallbacks);
+  ir = fast_count<MODEL, HI>(smem, fr, rho, kr, fallbacks, gr);
+  it = fast_count<MODEL, HI>(smem, ft, tem, kt, fallbacks, gt);
   const int cr = min(ir, fr.n - 2), ct = min(it, ft.n - 2);
   const int64_t cell = (int64_t)cr * (ft.n - 1) + ct;
   float q[8];
@@ -550,7 +565,7 @@ __global__ void __launch_bounds__(kNumThreads, 4) k_batched_2d_fast(BatchArgs2D 
         int i0, j0, i1, j1;
         double v0, v1;
         pair_fast<MODEL, HI>(smem, fr, ft, G, keep, p0.x, p0.y, i0, j0, v0, nans, fallbacks);
-        pair_fast<MODEL, HI>(smem, fr, ft, G, keep, p1.x, p1.y, i1, j1, v1, nans, fallbacks);
+        pair_fast<MODEL, HI>(smem, fr, ft, G, keep, p1.x, p1.y, i1, j1, v1, nans, fallbacks, i0, j0);
         st_stream(I4 + g, make_int4(i0, j0, i1, j1));
         st_stream(V2 + g, make_double2(v0, v1));
       }
@@ -585,7 +600,8 @@ __global__ void k_fast_2d_check(const unsigned char* __restrict__ blobs, const i
   }
 }
 
-const void* batched_2d_fast_kernel(int algo) {
+const void* batched_2d_fast_kernel(int algo, bool hunt) {
+  if (hunt) return reinterpret_cast<const void*>(&k_batched_2d_fast<kFastHunt>);
   if (algo == BL_SPLINE) return reinterpret_cast<const void*>(&k_batched_2d_fast<kFastSpline>);
   if (algo == BL_LOGHASH) return reinterpret_cast<const void*>(&k_batched_2d_fast<kFastLogHash>);
   if (algo == BL_MLP) return reinterpret_cast<const void*>(&k_batched_2d_fast<kFastMlp>);

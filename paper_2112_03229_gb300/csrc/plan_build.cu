@@ -331,9 +331,11 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
   // no interpolation option run the lean kernel: fewer live registers, four
   // blocks per SM instead of three.  With a position model (spline, MLP,
   // logarithm hash), so do those whose every axis has a window of at most
-  // kProbeWindow keys (that model's instance of the lean kernel).
+  // kProbeWindow keys (that model's instance of the lean kernel), and hunt
+  // plans on such axes (the hunt's instance).
   p->lean = 0;
-  const int lean_algo = p->opts.model == SS_MODEL_NONE      ? BL_BUCKET
+  const bool hunt = p->opts.model == SS_MODEL_HUNT;
+  const int lean_algo = p->opts.model == SS_MODEL_NONE || hunt ? BL_BUCKET
                         : p->opts.model == SS_MODEL_SPLINE  ? BL_SPLINE
                         : p->opts.model == SS_MODEL_LOGHASH ? BL_LOGHASH
                         : p->opts.model == SS_MODEL_MLP     ? BL_MLP
@@ -351,7 +353,7 @@ ss_status plan_bind(ss_plan* p, const std::vector<int64_t>& Y_off, const double*
     p->lean = not_fast == 0 ? 1 : 0;
   }
   if (p->kind == 1) kern = batched_1d_kernel(p->opts.side == SS_SIDE_LE, family);
-  else if (p->lean) kern = batched_2d_fast_kernel(lean_algo);
+  else if (p->lean) kern = batched_2d_fast_kernel(lean_algo, hunt);
   else kern = batched_2d_kernel(p->opts.model == SS_MODEL_HUNT, family > 0);
   if (ss_status st_ = raise_smem_limit(kern, smem)) return st_;
   int per_sm = 0;

@@ -619,8 +619,8 @@ def test_plan_2d_lean_kernel(ss):
     standard batch); it gives the oracle's indices and values, on aligned
     and misaligned arrays, with NaN pairs; so do its instances for the
     spline, MLP and logarithm-hash models, which run when every window is
-    at most 4 keys; plans outside its case (an interpolation option, the
-    hunt, a binary-search axis) run the general kernel."""
+    at most 4 keys, and for the hunt; plans outside its case (an
+    interpolation option, a binary-search axis) run the general kernel."""
     b = wl.batched_2d(ntables=20, pairs_per_table=5003, seed=27)
     Y2 = b.Y2.clone()
     Y2[7, 0] = float("nan")                 # a NaN coordinate: value NaN, indices exact
@@ -657,7 +657,11 @@ def test_plan_2d_lean_kernel(ss):
         for offset in (0, 1):
             run(learned, offset)
         assert learned.info().lean_kernel == (1 if learned.info().max_window <= 4 else 0), model
-    for kw in (dict(model="hunt"), dict(algo="binary"), dict(extrap=True)):
+    hunt = ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), model="hunt")
+    for offset in (0, 1):
+        run(hunt, offset)
+        assert hunt.info().lean_kernel == 1
+    for kw in (dict(algo="binary"), dict(extrap=True)):
         other = ss.Plan.create_2d(b.R_off, b.R.to(DEV), b.T_off, b.T.to(DEV), b.F_off, b.F.to(DEV), **kw)
         if "extrap" not in kw:
             run(other, 0)
