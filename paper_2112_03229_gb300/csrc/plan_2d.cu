@@ -408,6 +408,35 @@ __device__ __forceinline__ FastAxis fast_axis(const StagedView& v, const unsigne
   return f;
 }
 
+// The MLP's proposal (mlp_propose, same arithmetic in the same order) with
+// its parameters read four at a time.  The staged part of an MLP axis
+// begins with its parameters, right after the 128-byte header, and each
+// axis is staged at a 128-byte boundary of shared memory, so p is 16-byte
+// aligned (the bounds-checked build takes mlp_propose for any p that is
+// not, which nothing staged produces).
+__device__ __forceinline__ int fast_mlp_propose(const float* __restrict__ p, const MlpFeatScale& s, int n,
+                                                double t) {
+#ifdef SS_CHECKED
+  if ((reinterpret_cast<uintptr_t>(p) & 15) != 0) return mlp_propose(p, s, n, t);
+#endif
+  float x0, x1;
+  mlp_features(t, s, x0, x1);
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+  float y = p[4 * kHidden];
+#pragma unroll
+  for (int k4 = 0; k4 < kHidden / 4; ++k4) {
+    // units 4 k4 .. 4 k4 + 3: input weights (interleaved pairs), biases, output weights
+    const float4 wa = p4[2 * k4], wb = p4[2 * k4 + 1];
+    const float4 bk = p4[kHidden / 2 + k4], vk = p4[3 * kHidden / 4 + k4];
+    y = fmaf(vk.x, fmaxf(fmaf(wa.x, x0, fmaf(wa.y, x1, bk.x)), 0.0f), y);
+    y = fmaf(vk.y, fmaxf(fmaf(wa.z, x0, fmaf(wa.w, x1, bk.y)), 0.0f), y);
+    y = fmaf(vk.z, fmaxf(fmaf(wb.x, x0, fmaf(wb.y, x1, bk.z)), 0.0f), y);
+    y = fmaf(vk.w, fmaxf(fmaf(wb.z, x0, fmaf(wb.w, x1, bk.w)), 0.0f), y);
+  }
+  const float pos = rintf(y * (float)(n - 1));
+  return (int)fminf(fmaxf(pos, 0.0f), (float)(n - 1));     // NaN -> 0 through fmaxf
+}
+
 // Count of keys below q on a fast axis: the bucket directory's two-key scan,
 // or (learned instances) the model's proposal proved by a walk of at most E
 // keys, with the scan as fallback, or (hunt instance, guess >= 0) a hunt
@@ -431,7 +460,7 @@ __device__ __forceinline__ int fast_count(const unsigned char* smem, const FastA
     int p;
     if constexpr (MODEL == kFastSpline) p = min((int)rintf(spline_position(dir, f.shift, f.base, f.nb, q)), nk);
     else if constexpr (MODEL == kFastLogHash) p = loghash_propose(f.la, f.lc, nk, t);
-    else p = mlp_propose(reinterpret_cast<const float*>(smem + f.mlp), f.sc, f.n, t);
+    else p = fast_mlp_propose(reinterpret_cast<const float*>(smem + f.mlp), f.sc, f.n, t);
     int c;
     if (walk_count(keys, nk + kPad, nk, f.E, p, q, c)) return c;
     ++fallbacks;
